@@ -1,0 +1,593 @@
+/*
+ * CPU oracle for fixed-precision multiprecision Gaussian elimination.
+ *
+ * TEST INFRASTRUCTURE ONLY. This file is the plain, slow, obviously correct
+ * statement of what the GPU library computes. Only the test suite, the smoke
+ * check and the benchmark's CPU-baseline leg may load it. It shares no code,
+ * header, table or helper with the CUDA library.
+ *
+ * Number format (the method fixes a p-bit working precision, Sec. 4.3):
+ *   x = (-1)^s * m * 2^(e - p),  m an integer in [2^(p-1), 2^p) held as
+ *   n = p/32 little-endian uint32 limbs, e an int64.  Zero is +0:
+ *   s = 0, m = 0, e = INT64_MIN.  No infinities, no NaN.
+ * Every operation returns the exact result rounded to nearest, ties to even,
+ * at p bits: RN(a*b), RN(a+b), RN(a-b), RN(1/a).  The one rounding routine
+ * `rnd` below is used by all of them.
+ *
+ * Elimination (Sec. 3, "Gauss elimination without pivoting"; Alg. 1 read as
+ * in the text that surrounds it, the augmented matrix [A I]):
+ *   for k = 1..N:
+ *     D_k = RN(D_{k-1} * a_kk), D_0 = 1             (Alg. 1 step 2.1)
+ *     stop if a_kk == 0 and k < N
+ *     r_k = RN(1 / a_kk)
+ *     z_ik = RN(a_ik * r_k),  i > k                  (Alg. 1 step 2.2.1)
+ *     a_ij = RN(a_ij - RN(z_ik * a_kj)),  i > k, j > k   (step 2.2.2)
+ *   In "lastcol" mode the same row operation is applied to the identity
+ *   block of [A I], whose non-zero part is stored in A's strict lower
+ *   triangle (Sec. 3, storage in N^2 + O(N)):
+ *     l_ij = RN(l_ij - RN(z_ik * l_kj)),  i > k, j < k
+ *     l_ik = -z_ik   (exact)
+ *   The signed minors of the last column (eq. minorsdef) are then
+ *     C_jN = RN(D_{N-1} * l_Nj) (j < N),  C_NN = D_{N-1}.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <pthread.h>
+
+#define ZEXP INT64_MIN
+
+enum { OR_OK = 0, OR_EINVAL = 1, OR_ENOMEM = 2, OR_EZEROPIVOT = 4, OR_EZERODIV = 7 };
+
+/* ------------------------------------------------------------------------- */
+/* Plain big-integer helpers on little-endian uint32 limb arrays.            */
+/* ------------------------------------------------------------------------- */
+
+/* Number of significant bits of x (0 for x == 0). */
+static int64_t bitlen(const uint32_t *x, int L) {
+  for (int i = L - 1; i >= 0; --i)
+    if (x[i]) return (int64_t)i * 32 + (32 - __builtin_clz(x[i]));
+  return 0;
+}
+
+static int getbit(const uint32_t *x, int L, int64_t i) {
+  if (i < 0 || i >= (int64_t)L * 32) return 0;
+  return (x[i >> 5] >> (i & 31)) & 1u;
+}
+
+/* 1 if any bit of x with index < i is set. */
+static int anybelow(const uint32_t *x, int L, int64_t i) {
+  if (i <= 0) return 0;
+  if (i > (int64_t)L * 32) i = (int64_t)L * 32;
+  int64_t full = i >> 5;
+  for (int64_t w = 0; w < full; ++w)
+    if (x[w]) return 1;
+  int rem = (int)(i & 31);
+  if (rem && (x[full] & ((1u << rem) - 1u))) return 1;
+  return 0;
+}
+
+/* out[0..Lo) = floor(x / 2^sh) truncated to Lo limbs (sh >= 0). */
+static void shr(const uint32_t *x, int L, int64_t sh, uint32_t *out, int Lo) {
+  int64_t q = sh >> 5;
+  int r = (int)(sh & 31);
+  for (int i = 0; i < Lo; ++i) {
+    int64_t s = i + q;
+    uint64_t lo = (s < L) ? x[s] : 0;
+    uint64_t hi = (s + 1 < L) ? x[s + 1] : 0;
+    out[i] = (uint32_t)(((hi << 32) | lo) >> r);
+  }
+}
+
+/* out[0..Lo) = (x * 2^sh) truncated to Lo limbs (sh >= 0). */
+static void shl(const uint32_t *x, int L, int64_t sh, uint32_t *out, int Lo) {
+  int64_t q = sh >> 5;
+  int r = (int)(sh & 31);
+  for (int i = 0; i < Lo; ++i) {
+    int64_t s = i - q;
+    uint64_t cur = (s >= 0 && s < L) ? x[s] : 0;
+    uint64_t low = (s - 1 >= 0 && s - 1 < L) ? x[s - 1] : 0;
+    uint64_t v = (cur << r) | (r ? (low >> (32 - r)) : 0);
+    out[i] = (uint32_t)v;
+  }
+}
+
+/* -1, 0, +1 comparing two L-limb integers. */
+static int cmpn(const uint32_t *a, const uint32_t *b, int L) {
+  for (int i = L - 1; i >= 0; --i) {
+    if (a[i] != b[i]) return a[i] > b[i] ? 1 : -1;
+  }
+  return 0;
+}
+
+/* a += b (L limbs), returns carry. */
+static uint32_t addn(uint32_t *a, const uint32_t *b, int L) {
+  uint64_t c = 0;
+  for (int i = 0; i < L; ++i) {
+    c += (uint64_t)a[i] + b[i];
+    a[i] = (uint32_t)c;
+    c >>= 32;
+  }
+  return (uint32_t)c;
+}
+
+/* a -= b (L limbs), returns borrow. */
+static uint32_t subn(uint32_t *a, const uint32_t *b, int L) {
+  int64_t br = 0;
+  for (int i = 0; i < L; ++i) {
+    int64_t d = (int64_t)a[i] - (int64_t)b[i] - br;
+    br = d < 0;
+    a[i] = (uint32_t)(d + (br ? ((int64_t)1 << 32) : 0));
+  }
+  return (uint32_t)br;
+}
+
+/* r[0..2n) = a * b, schoolbook. */
+static void muln(const uint32_t *a, const uint32_t *b, int n, uint32_t *r) {
+  memset(r, 0, sizeof(uint32_t) * 2 * (size_t)n);
+  for (int i = 0; i < n; ++i) {
+    uint64_t c = 0;
+    for (int j = 0; j < n; ++j) {
+      uint64_t t = (uint64_t)a[i] * b[j] + r[i + j] + c;
+      r[i + j] = (uint32_t)t;
+      c = t >> 32;
+    }
+    r[i + n] = (uint32_t)c;
+  }
+}
+
+/* ------------------------------------------------------------------------- */
+/* The one rounding routine.                                                 */
+/* Rounds the non-negative exact value (X + f) * 2^E to p bits, where X is an */
+/* L-limb integer and f is a fraction in (0,1) when sticky_in is set, else 0. */
+/* sticky_in requires bitlen(X) > p, so that the round bit lies inside X.     */
+/* Writes mantissa (n limbs), exponent and sign s.  X == 0 gives +0.          */
+/* ------------------------------------------------------------------------- */
+static void rnd(const uint32_t *X, int L, int64_t E, int sticky_in, int p, int n, int s, int8_t *os,
+                int64_t *oe, uint32_t *om) {
+  int64_t t = bitlen(X, L);
+  if (t == 0) {
+    *os = 0;
+    *oe = ZEXP;
+    memset(om, 0, sizeof(uint32_t) * n);
+    return;
+  }
+  if (t <= p) { /* exact: X fits in p bits (sticky_in must be 0 here) */
+    shl(X, L, p - t, om, n);
+    *os = (int8_t)s;
+    *oe = t + E;
+    return;
+  }
+  int64_t sh = t - p;
+  shr(X, L, sh, om, n);
+  int rbit = getbit(X, L, sh - 1);
+  int st = anybelow(X, L, sh - 1) || sticky_in;
+  if (rbit && (st || (om[0] & 1u))) {
+    uint64_t c = 1;
+    for (int i = 0; i < n && c; ++i) {
+      c += om[i];
+      om[i] = (uint32_t)c;
+      c >>= 32;
+    }
+    if (c) { /* mantissa overflowed to 2^p: renormalise to 2^(p-1) */
+      memset(om, 0, sizeof(uint32_t) * n);
+      om[n - 1] = 0x80000000u;
+      t += 1;
+    }
+  }
+  *os = (int8_t)s;
+  *oe = t + E;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Operations on numbers.                                                    */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+  int p, n;
+  uint32_t *buf; /* scratch, 6n+8 limbs */
+} ctx_t;
+
+static int iszero(int64_t e) { return e == ZEXP; }
+
+static void setzero(int8_t *s, int64_t *e, uint32_t *m, int n) {
+  *s = 0;
+  *e = ZEXP;
+  memset(m, 0, sizeof(uint32_t) * n);
+}
+
+static void copynum(int8_t s, int64_t e, const uint32_t *m, int n, int8_t *os, int64_t *oe, uint32_t *om) {
+  *os = s;
+  *oe = e;
+  if (om != m) memmove(om, m, sizeof(uint32_t) * n);
+}
+
+/* RN(a * b) */
+static void op_mul(ctx_t *c, int8_t sa, int64_t ea, const uint32_t *ma, int8_t sb, int64_t eb, const uint32_t *mb,
+                   int8_t *os, int64_t *oe, uint32_t *om) {
+  int n = c->n, p = c->p;
+  if (iszero(ea) || iszero(eb)) {
+    setzero(os, oe, om, n);
+    return;
+  }
+  uint32_t *X = c->buf; /* 2n limbs */
+  muln(ma, mb, n, X);
+  /* a*b = ma*mb * 2^(ea+eb-2p) */
+  rnd(X, 2 * n, ea + eb - 2 * (int64_t)p, 0, p, n, (sa ^ sb) & 1, os, oe, om);
+}
+
+/* RN(a + (-1)^negb * b) */
+static void op_add(ctx_t *c, int8_t sa, int64_t ea, const uint32_t *ma, int8_t sb0, int64_t eb, const uint32_t *mb,
+                   int negb, int8_t *os, int64_t *oe, uint32_t *om) {
+  int n = c->n, p = c->p;
+  int sb = (sb0 ^ negb) & 1;
+  if (iszero(eb)) {
+    if (iszero(ea)) setzero(os, oe, om, n);
+    else copynum(sa, ea, ma, n, os, oe, om);
+    return;
+  }
+  if (iszero(ea)) {
+    copynum((int8_t)sb, eb, mb, n, os, oe, om);
+    return;
+  }
+  /* Order by magnitude: |A| >= |B|. */
+  int swap = (eb > ea) || (eb == ea && cmpn(mb, ma, n) > 0);
+  int8_t sA = swap ? (int8_t)sb : sa, sB = swap ? sa : (int8_t)sb;
+  int64_t eA = swap ? eb : ea, eB = swap ? ea : eb;
+  const uint32_t *mA = swap ? mb : ma, *mB = swap ? ma : mb;
+  int64_t d = eA - eB; /* >= 0 */
+  if (d >= (int64_t)p + 2) {
+    /* |B| < 2^eB <= 2^(eA-p-2) = ulp(A)/4.  A +- B lies strictly within a
+       quarter ulp of A (within half an ulp of the finer binade below A when
+       A is a power of two), so RN returns A. */
+    copynum(sA, eA, mA, n, os, oe, om);
+    return;
+  }
+  /* Exact: X = mA*2^d +- mB, value = X * 2^(eB-p); X < 2^(p+d+1) <= 2^(2p+2). */
+  int L = 2 * n + 2;
+  uint32_t *X = c->buf, *Y = c->buf + L;
+  shl(mA, n, d, X, L);
+  memset(Y, 0, sizeof(uint32_t) * L);
+  memcpy(Y, mB, sizeof(uint32_t) * n);
+  if (sA == sB) addn(X, Y, L);
+  else subn(X, Y, L); /* X >= Y since |A| >= |B| */
+  rnd(X, L, eB - p, 0, p, n, sA, os, oe, om);
+}
+
+/* RN(1 / a); returns OR_EZERODIV for a == 0. */
+static int op_recip(ctx_t *c, int8_t sa, int64_t ea, const uint32_t *ma, int8_t *os, int64_t *oe, uint32_t *om) {
+  int n = c->n, p = c->p;
+  if (iszero(ea)) return OR_EZERODIV;
+  /* 2^(2p) = q*m + r by restoring binary long division, q < 2^(p+2). */
+  int L = n + 2;
+  uint32_t *q = c->buf, *r = c->buf + L, *m = c->buf + 2 * L;
+  memset(q, 0, sizeof(uint32_t) * L);
+  memset(r, 0, sizeof(uint32_t) * L);
+  memset(m, 0, sizeof(uint32_t) * L);
+  memcpy(m, ma, sizeof(uint32_t) * n);
+  for (int64_t i = 2 * (int64_t)p; i >= 0; --i) {
+    /* r = 2r + (bit i of 2^(2p)) */
+    uint32_t carry = (i == 2 * (int64_t)p) ? 1u : 0u;
+    for (int w = 0; w < L; ++w) {
+      uint32_t nc = r[w] >> 31;
+      r[w] = (r[w] << 1) | carry;
+      carry = nc;
+    }
+    if (cmpn(r, m, L) >= 0) {
+      subn(r, m, L);
+      if (i < (int64_t)L * 32) q[i >> 5] |= 1u << (i & 31);
+    }
+  }
+  int rem_nz = bitlen(r, L) != 0;
+  /* 1/a = 2^(p-ea)/ma = (q + r/ma) * 2^(-p-ea); q > 2^p has > p bits. */
+  rnd(q, L, -(int64_t)p - ea, rem_nz, p, n, sa & 1, os, oe, om);
+  return OR_OK;
+}
+
+/* Exact lift of a double (finite) to p bits, p >= 64. */
+static void op_from_f64(ctx_t *c, double v, int8_t *os, int64_t *oe, uint32_t *om) {
+  int n = c->n, p = c->p;
+  if (v == 0.0) {
+    setzero(os, oe, om, n);
+    return;
+  }
+  uint64_t bits;
+  memcpy(&bits, &v, 8);
+  int s = (int)(bits >> 63);
+  int bexp = (int)((bits >> 52) & 0x7ff);
+  uint64_t frac = bits & ((1ull << 52) - 1);
+  uint64_t M;
+  int64_t E;
+  if (bexp == 0) { /* subnormal */
+    M = frac;
+    E = -1074;
+  } else {
+    M = frac | (1ull << 52);
+    E = bexp - 1075;
+  }
+  uint32_t X[2] = {(uint32_t)M, (uint32_t)(M >> 32)};
+  rnd(X, 2, E, 0, p, n, s, os, oe, om);
+}
+
+static void op_from_i64(ctx_t *c, int64_t v, int8_t *os, int64_t *oe, uint32_t *om) {
+  int n = c->n, p = c->p;
+  if (v == 0) {
+    setzero(os, oe, om, n);
+    return;
+  }
+  int s = v < 0;
+  uint64_t M = s ? (uint64_t)0 - (uint64_t)v : (uint64_t)v;
+  uint32_t X[2] = {(uint32_t)M, (uint32_t)(M >> 32)};
+  rnd(X, 2, 0, 0, p, n, s, os, oe, om);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Exported element-wise operations on SoA arrays (count elements each).      */
+/* ------------------------------------------------------------------------- */
+static int ctx_init(ctx_t *c, int p) {
+  if (p < 64 || p % 32) return OR_EINVAL;
+  c->p = p;
+  c->n = p / 32;
+  c->buf = (uint32_t *)calloc((size_t)6 * c->n + 16, sizeof(uint32_t));
+  return c->buf ? OR_OK : OR_ENOMEM;
+}
+
+int or_mul_v(int64_t cnt, int p, const int8_t *sa, const int64_t *ea, const uint32_t *ma, const int8_t *sb,
+             const int64_t *eb, const uint32_t *mb, int8_t *so, int64_t *eo, uint32_t *mo) {
+  ctx_t c;
+  int st = ctx_init(&c, p);
+  if (st) return st;
+  int n = c.n;
+  for (int64_t i = 0; i < cnt; ++i)
+    op_mul(&c, sa[i], ea[i], ma + i * n, sb[i], eb[i], mb + i * n, so + i, eo + i, mo + i * n);
+  free(c.buf);
+  return OR_OK;
+}
+
+int or_add_v(int64_t cnt, int p, int negb, const int8_t *sa, const int64_t *ea, const uint32_t *ma, const int8_t *sb,
+             const int64_t *eb, const uint32_t *mb, int8_t *so, int64_t *eo, uint32_t *mo) {
+  ctx_t c;
+  int st = ctx_init(&c, p);
+  if (st) return st;
+  int n = c.n;
+  for (int64_t i = 0; i < cnt; ++i)
+    op_add(&c, sa[i], ea[i], ma + i * n, sb[i], eb[i], mb + i * n, negb, so + i, eo + i, mo + i * n);
+  free(c.buf);
+  return OR_OK;
+}
+
+int or_recip_v(int64_t cnt, int p, const int8_t *sa, const int64_t *ea, const uint32_t *ma, int8_t *so, int64_t *eo,
+               uint32_t *mo) {
+  ctx_t c;
+  int st = ctx_init(&c, p);
+  if (st) return st;
+  int n = c.n;
+  for (int64_t i = 0; i < cnt && st == OR_OK; ++i) st = op_recip(&c, sa[i], ea[i], ma + i * n, so + i, eo + i, mo + i * n);
+  free(c.buf);
+  return st;
+}
+
+int or_from_f64_v(int64_t cnt, int p, const double *v, int8_t *so, int64_t *eo, uint32_t *mo) {
+  ctx_t c;
+  int st = ctx_init(&c, p);
+  if (st) return st;
+  for (int64_t i = 0; i < cnt; ++i) op_from_f64(&c, v[i], so + i, eo + i, mo + i * c.n);
+  free(c.buf);
+  return OR_OK;
+}
+
+int or_from_i64_v(int64_t cnt, int p, const int64_t *v, int8_t *so, int64_t *eo, uint32_t *mo) {
+  ctx_t c;
+  int st = ctx_init(&c, p);
+  if (st) return st;
+  for (int64_t i = 0; i < cnt; ++i) op_from_i64(&c, v[i], so + i, eo + i, mo + i * c.n);
+  free(c.buf);
+  return OR_OK;
+}
+
+/* Cauchy matrix A_ij = RN(1 / RN(x_i + y_j)), x_i and y_j lifted exactly. */
+int or_cauchy(int64_t N, int p, const double *x, const double *y, int8_t *so, int64_t *eo, uint32_t *mo) {
+  ctx_t c;
+  int st = ctx_init(&c, p);
+  if (st) return st;
+  int n = c.n;
+  uint32_t *tm = (uint32_t *)calloc((size_t)3 * n, sizeof(uint32_t));
+  uint32_t *xm = tm + n, *ym = tm + 2 * n;
+  for (int64_t i = 0; i < N && st == OR_OK; ++i) {
+    for (int64_t j = 0; j < N; ++j) {
+      int8_t xs, ys, ts;
+      int64_t xe, ye, te;
+      op_from_f64(&c, x[i], &xs, &xe, xm);
+      op_from_f64(&c, y[j], &ys, &ye, ym);
+      op_add(&c, xs, xe, xm, ys, ye, ym, 0, &ts, &te, tm);
+      int64_t idx = i * N + j;
+      st = op_recip(&c, ts, te, tm, so + idx, eo + idx, mo + idx * n);
+      if (st) break;
+    }
+  }
+  free(tm);
+  free(c.buf);
+  return st;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Gaussian elimination without pivoting, in place, with a row-parallel      */
+/* thread pool (the rows of one step are independent; splitting them among   */
+/* threads does not change any result, as in the paper's pthread scheme).     */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+  int64_t N;
+  int p, n, lastcol;
+  int8_t *S;
+  int64_t *E;
+  uint32_t *M;
+  /* current step data */
+  int64_t k;
+  int8_t *zs;
+  int64_t *ze;
+  uint32_t *zm;
+} ge_t;
+
+typedef struct {
+  ge_t *g;
+  int64_t i0, i1;
+  int err;
+} work_t;
+
+static void *update_rows(void *arg) {
+  work_t *w = (work_t *)arg;
+  ge_t *g = w->g;
+  ctx_t c;
+  if (ctx_init(&c, g->p)) {
+    w->err = OR_ENOMEM;
+    return NULL;
+  }
+  int n = g->n;
+  int64_t N = g->N, k = g->k;
+  uint32_t *t = (uint32_t *)calloc(n, sizeof(uint32_t));
+  for (int64_t i = w->i0; i < w->i1; ++i) {
+    int64_t zi = i - (k + 1);
+    int8_t zs = g->zs[zi];
+    int64_t ze = g->ze[zi];
+    const uint32_t *zm = g->zm + zi * n;
+    for (int64_t j = g->lastcol ? 0 : k + 1; j < N; ++j) {
+      if (j == k) continue;
+      int64_t ij = i * N + j, kj = k * N + j;
+      int8_t ts;
+      int64_t te;
+      op_mul(&c, zs, ze, zm, g->S[kj], g->E[kj], g->M + kj * n, &ts, &te, t);
+      op_add(&c, g->S[ij], g->E[ij], g->M + ij * n, ts, te, t, 1, g->S + ij, g->E + ij, g->M + ij * n);
+    }
+    if (g->lastcol) { /* l_ik = -z_ik, exact; +0 stays +0 */
+      int64_t ik = i * N + k;
+      int8_t s = iszero(ze) ? 0 : (int8_t)(zs ^ 1);
+      copynum(s, ze, zm, n, g->S + ik, g->E + ik, g->M + ik * n);
+    }
+  }
+  free(t);
+  free(c.buf);
+  return NULL;
+}
+
+/*
+ * In-place elimination of the N x N row-major matrix (S, E, M) at p bits.
+ * D (N numbers) receives the leading minors D_1..D_N.  *zero_k receives the
+ * 1-based index of the first exactly zero pivot (0 if none).  Returns
+ * OR_EZEROPIVOT when that pivot is at k < N (elimination stopped, D_k..D_N
+ * are +0), else OR_OK.  k_end limits the steps run (k_end = N for all):
+ * steps k0+1..k_end are run, with D holding D_1..D_k0 on entry.
+ */
+int or_ge_range(int64_t N, int p, int lastcol, int nthreads, int64_t k0, int64_t k_end, int8_t *S, int64_t *E,
+                uint32_t *M, int8_t *Ds, int64_t *De, uint32_t *Dm, int64_t *zero_k) {
+  ctx_t c;
+  int st = ctx_init(&c, p);
+  if (st) return st;
+  if (N < 1 || k0 < 0 || k_end > N || k0 > k_end) {
+    free(c.buf);
+    return OR_EINVAL;
+  }
+  if (nthreads < 1) nthreads = 1;
+  int n = c.n;
+  ge_t g = {N, p, n, lastcol, S, E, M, 0, NULL, NULL, NULL};
+  g.zs = (int8_t *)calloc(N, 1);
+  g.ze = (int64_t *)calloc(N, sizeof(int64_t));
+  g.zm = (uint32_t *)calloc((size_t)N * n, sizeof(uint32_t));
+  uint32_t *r = (uint32_t *)calloc(n, sizeof(uint32_t));
+  uint32_t *one = (uint32_t *)calloc(n, sizeof(uint32_t));
+  one[n - 1] = 0x80000000u; /* 1 = 2^(p-1) * 2^(1-p) */
+  pthread_t *th = (pthread_t *)calloc(nthreads, sizeof(pthread_t));
+  work_t *wk = (work_t *)calloc(nthreads, sizeof(work_t));
+  if (zero_k) *zero_k = 0;
+  for (int64_t k = k0; k < k_end; ++k) { /* 0-based step k = paper's k+1 */
+    int64_t kk = k * N + k;
+    /* D_k = RN(D_{k-1} * a_kk), D_0 = 1 */
+    if (k == 0) op_mul(&c, 0, 1, one, S[kk], E[kk], M + kk * n, Ds, De, Dm);
+    else op_mul(&c, Ds[k - 1], De[k - 1], Dm + (k - 1) * n, S[kk], E[kk], M + kk * n, Ds + k, De + k, Dm + k * n);
+    if (iszero(E[kk])) {
+      if (zero_k) *zero_k = k + 1;
+      for (int64_t q = k; q < N; ++q) setzero(Ds + q, De + q, Dm + q * n, n);
+      if (k < N - 1) st = OR_EZEROPIVOT;
+      break;
+    }
+    if (k == N - 1) break;
+    int8_t rs;
+    int64_t re;
+    op_recip(&c, S[kk], E[kk], M + kk * n, &rs, &re, r);
+    /* multipliers z_ik = RN(a_ik * r_k) */
+    for (int64_t i = k + 1; i < N; ++i) {
+      int64_t ik = i * N + k, zi = i - (k + 1);
+      op_mul(&c, S[ik], E[ik], M + ik * n, rs, re, r, g.zs + zi, g.ze + zi, g.zm + zi * n);
+    }
+    g.k = k;
+    int64_t rows = N - (k + 1);
+    int T = nthreads;
+    if (T > rows) T = (int)rows;
+    for (int t = 0; t < T; ++t) {
+      wk[t].g = &g;
+      wk[t].i0 = k + 1 + rows * t / T;
+      wk[t].i1 = k + 1 + rows * (t + 1) / T;
+      wk[t].err = 0;
+    }
+    if (T == 1) update_rows(&wk[0]);
+    else {
+      for (int t = 0; t < T; ++t) pthread_create(&th[t], NULL, update_rows, &wk[t]);
+      for (int t = 0; t < T; ++t) pthread_join(th[t], NULL);
+    }
+    for (int t = 0; t < T; ++t)
+      if (wk[t].err) st = wk[t].err;
+    if (st) break;
+  }
+  free(wk);
+  free(th);
+  free(one);
+  free(r);
+  free(g.zm);
+  free(g.ze);
+  free(g.zs);
+  free(c.buf);
+  return st;
+}
+
+/*
+ * Last-column signed minors from an eliminated matrix in lastcol mode:
+ *   C_jN = RN(D_{N-1} * l_Nj), j < N;  C_NN = D_{N-1}   (eq. minorsdef)
+ * normalised != 0 returns delta_{N,j} = C_jN / C_1N instead (eq. minors),
+ * formed as RN(l_Nj * RN(1 / l_N1)) with delta_{N,1} = 1, delta_{N,N} =
+ * RN(1 / l_N1).  Dnm1 is D_{N-1} (D_0 = 1 when N == 1).
+ */
+int or_lastcol(int64_t N, int p, int normalised, const int8_t *S, const int64_t *E, const uint32_t *M, int8_t dsg,
+               int64_t dex, const uint32_t *dm, int8_t *os, int64_t *oe, uint32_t *om) {
+  ctx_t c;
+  int st = ctx_init(&c, p);
+  if (st) return st;
+  int n = c.n;
+  const int64_t row = (N - 1) * N;
+  if (!normalised) {
+    for (int64_t j = 0; j + 1 < N; ++j)
+      op_mul(&c, dsg, dex, dm, S[row + j], E[row + j], M + (row + j) * n, os + j, oe + j, om + j * n);
+    copynum(dsg, dex, dm, n, os + N - 1, oe + N - 1, om + (N - 1) * n);
+  } else {
+    uint32_t *r = (uint32_t *)calloc(n, sizeof(uint32_t));
+    int8_t rs;
+    int64_t re;
+    if (N == 1) { /* delta_{1,1} = 1 */
+      memset(om, 0, sizeof(uint32_t) * n);
+      om[n - 1] = 0x80000000u;
+      os[0] = 0;
+      oe[0] = 1;
+    } else {
+      st = op_recip(&c, S[row], E[row], M + row * n, &rs, &re, r);
+      if (st == OR_OK) {
+        memset(om, 0, sizeof(uint32_t) * n);
+        om[n - 1] = 0x80000000u;
+        os[0] = 0;
+        oe[0] = 1;
+        for (int64_t j = 1; j + 1 < N; ++j)
+          op_mul(&c, S[row + j], E[row + j], M + (row + j) * n, rs, re, r, os + j, oe + j, om + j * n);
+        copynum(rs, re, r, n, os + N - 1, oe + N - 1, om + (N - 1) * n);
+      }
+    }
+    free(r);
+  }
+  free(c.buf);
+  return st;
+}
