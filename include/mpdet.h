@@ -1,0 +1,164 @@
+/*
+ * mpdet — fixed-precision multiprecision Gaussian elimination on one GPU.
+ *
+ * Computes, for a real N x N matrix A held at p bits, the determinant, all N
+ * top-left leading minors and the signed minors of the last column, by
+ * Gaussian elimination without pivoting (Beliakov & Matiyasevich, Sec. 3 and
+ * Algorithm 1, with the augmented matrix [A I] of Sec. 3 for the minors).
+ *
+ * Number format (every call): a number is
+ *     x = (-1)^s * m * 2^(e - p),   2^(p-1) <= m < 2^p,
+ * with m stored as n = p/32 little-endian uint32 limbs and e an int64; zero is
+ * s = 0, m = 0, e = INT64_MIN (no -0, no infinities, no NaN).  Every operation
+ * of the method is the exact result rounded to nearest, ties to even, at p
+ * bits, in a fixed order:
+ *     D_k  = RN(D_{k-1} * a_kk)          (D_0 = 1)     Alg. 1 step 2.1
+ *     r_k  = RN(1 / a_kk)
+ *     z_ik = RN(a_ik * r_k),        i > k              Alg. 1 step 2.2.1
+ *     a_ij = RN(a_ij - RN(z_ik * a_kj)),  i, j > k     Alg. 1 step 2.2.2
+ * and in MPDET_LASTCOL mode the same row operation on the identity block of
+ * [A I], stored in A's strict lower triangle (Sec. 3, memory N^2 + O(N)):
+ *     l_ij = RN(l_ij - RN(z_ik * l_kj)),  i > k, j < k;   l_ik = -z_ik.
+ * Results are therefore bit-for-bit reproducible and independent of the
+ * kernels' tiling.
+ *
+ * Arrays of numbers cross the ABI as mpdet_numv (structure of arrays):
+ * count numbers, sign[count] int8, exp[count] int64, limbs[count * n] uint32
+ * (number i's limbs at limbs[i*n .. i*n + n)).  Row-major for matrices.
+ *
+ * Pointers: with device_ptr = 0 an argument is host memory and the call is
+ * synchronous (it returns after the results are in host memory).  With
+ * device_ptr = 1 it is device memory of the handle's GPU (for instance a torch
+ * CUDA tensor) and the call is asynchronous on the handle's stream: results
+ * are valid after that stream synchronises, and errors found on the device
+ * (zero pivots) are reported by mpdet_status.  Device buffers of numbers must
+ * be 16-byte aligned.
+ *
+ * Ownership: the handle owns all of its device memory; caller buffers are
+ * only read or written during the call (or, for device_ptr = 1, during the
+ * stream work the call enqueues).
+ *
+ * Errors: every call returns a status code; nothing is thrown across the ABI.
+ * mpdet_last_error gives a message for the last failing call on a handle.
+ * After MPDET_EZEROPIVOT the handle stays usable (a new matrix may be set);
+ * after MPDET_ECUDA it should be freed.
+ */
+#ifndef MPDET_H
+#define MPDET_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+  int8_t* sign;
+  int64_t* exp;
+  uint32_t* limbs;
+} mpdet_numv;
+
+typedef struct mpdet_ctx* mpdet_t;
+
+enum {
+  MPDET_OK = 0,
+  MPDET_EINVAL = 1,      /* bad argument (size, precision, null pointer, state order) */
+  MPDET_ENOMEM = 2,      /* device or host allocation failed */
+  MPDET_ECUDA = 3,       /* a CUDA call failed; see mpdet_last_error */
+  MPDET_EZEROPIVOT = 4,  /* exact zero pivot a_kk at k < N: elimination stopped */
+  MPDET_ETIMEOUT = 5,    /* a bounded device wait gave up */
+  MPDET_ESTATE = 6,      /* call out of order (e.g. minors before the factorisation) */
+  MPDET_EZERODIV = 7     /* normalised minors requested but l_N1 (hence C_1N) is zero */
+};
+
+enum { MPDET_LASTCOL = 1 };
+
+/* Create a handle for N x N matrices at p bits on the current CUDA device.
+ * p must be a power of two with 128 <= p <= 32768 (n = p/32 limbs; the kernel
+ * families cover these sizes).  flags: 0 or MPDET_LASTCOL (keep L for the
+ * last-column minors, 1.5x the work: Sec. 3 counts it as twice the row
+ * operations).  cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ * Allocates (4n + 9) * N^2 bytes of device memory plus O(N n).
+ * Errors: MPDET_EINVAL (N < 1, unsupported p, out == NULL), MPDET_ENOMEM,
+ * MPDET_ECUDA. */
+int mpdet_create(int64_t N, int32_t p_bits, uint32_t flags, void* cuda_stream, mpdet_t* out);
+
+/* Set A from an N x N row-major double matrix with leading dimension ld >= N
+ * (exact lift: every finite double is representable at p >= 64).  Resets the
+ * factorisation.  Step a1 of the method (input lift). */
+int mpdet_set_f64(mpdet_t h, const double* A, int64_t ld, int device_ptr);
+
+/* Same for int32 entries (exact). */
+int mpdet_set_i32(mpdet_t h, const int32_t* A, int64_t ld, int device_ptr);
+
+/* Set A from N*N numbers already at p bits (copied; must be canonical). */
+int mpdet_set_mp(mpdet_t h, mpdet_numv A, int device_ptr);
+
+/* Set the Cauchy matrix A_ij = RN(1 / RN(x_i + y_j)) generated on the device
+ * (x, y: N doubles each).  The seeded stand-in for the paper's interpolating
+ * matrices of eq. (det) and eq. (betaNew), which are nearly singular. */
+int mpdet_set_cauchy(mpdet_t h, const double* x, const double* y, int device_ptr);
+
+/* Run elimination steps k0+1 .. k1 (1-based; 0 <= k0 <= k1 <= N), asynchronous
+ * on the handle's stream.  k0 must equal the number of steps already done
+ * (windows run in order; a factorisation can be split to time it or to
+ * checkpoint it with mpdet_get_mp / mpdet_get_minors).  Errors: MPDET_ESTATE
+ * (no matrix, or k0 out of order), MPDET_EINVAL, MPDET_ECUDA. */
+int mpdet_factor_range(mpdet_t h, int64_t k0, int64_t k1);
+
+/* Finish the factorisation (all remaining steps) and return det = D_N (one
+ * number) and the leading minors D_1..D_N (N numbers); either output may have
+ * NULL pointers to skip it.  zero_pivot_k (may be NULL, host) receives the
+ * 1-based index of the first exactly zero pivot or 0.
+ * Returns MPDET_EZEROPIVOT when that pivot is at k < N (D_1..D_{k-1} are
+ * valid, D_k..D_N are +0); a zero pivot at k = N only makes det = +0 and
+ * returns MPDET_OK.  With device_ptr = 1 the outputs are device buffers, the
+ * call does not synchronise and zero pivots are read with mpdet_status. */
+int mpdet_factor(mpdet_t h, mpdet_numv det, mpdet_numv minors, int64_t* zero_pivot_k, int device_ptr);
+
+/* Synchronise the handle's stream and read the status of the last
+ * factorisation: MPDET_OK or MPDET_EZEROPIVOT, zero_pivot_k as above. */
+int mpdet_status(mpdet_t h, int64_t* zero_pivot_k);
+
+/* Signed minors of the last column (eq. minorsdef):
+ *     C_jN = (-1)^(j+N) det(A without row j and column N) = RN(D_{N-1} * l_Nj),
+ *     C_NN = D_{N-1},
+ * N numbers.  normalised != 0 returns delta_{N,j} = C_jN / C_1N (eq. minors),
+ * formed as RN(l_Nj * RN(1/l_N1)) with delta_{N,1} = 1 exactly.
+ * Needs MPDET_LASTCOL and a completed factorisation without a zero pivot
+ * before step N.  Errors: MPDET_ESTATE, MPDET_EZERODIV (normalised with
+ * l_N1 = 0). */
+int mpdet_lastcol_minors(mpdet_t h, mpdet_numv out, int normalised, int device_ptr);
+
+/* Copy out the leading minors computed so far (D_1..D_N; entries of steps not
+ * yet run are +0). */
+int mpdet_get_minors(mpdet_t h, mpdet_numv out, int device_ptr);
+
+/* Copy out the in-place N x N array (U in the upper triangle including the
+ * diagonal; in MPDET_LASTCOL mode L's strict lower part below it; otherwise
+ * the strict lower part is unspecified), e.g. to checkpoint a window. */
+int mpdet_get_mp(mpdet_t h, mpdet_numv out, int device_ptr);
+
+/* Restore a checkpoint: the in-place array after k_done steps and the
+ * leading minors D_1..D_{k_done} (N numbers, later entries ignored).  The
+ * next mpdet_factor_range must start at k0 = k_done. */
+int mpdet_resume(mpdet_t h, mpdet_numv A, mpdet_numv minors, int64_t k_done, int device_ptr);
+
+/* Steps completed so far (0..N). */
+int64_t mpdet_steps_done(mpdet_t h);
+
+/* Release the handle and its device memory (NULL is accepted). */
+int mpdet_free(mpdet_t h);
+
+/* Message for the last failing call on h (static string when h == NULL). */
+const char* mpdet_last_error(mpdet_t h);
+
+/* Limb count and slice geometry chosen for p: n = p/32, W limbs per lane,
+ * G lanes per number; returns MPDET_EINVAL for an unsupported p. */
+int mpdet_geometry(int32_t p_bits, int32_t* n, int32_t* W, int32_t* G);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPDET_H */

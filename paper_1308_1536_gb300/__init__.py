@@ -1,0 +1,244 @@
+"""mpdet: multiprecision Gaussian elimination without pivoting on a GB300.
+
+Thin Python binding over the C ABI of ``libmpdet.so`` (include/mpdet.h):
+argument marshalling only.  Every step of the computation runs in the CUDA
+kernels of the library; there is no CPU fallback, and ``load()`` raises when
+the compiled library is missing or cannot be loaded.
+
+Numbers cross the boundary as structure-of-arrays triples
+``(sign int8[c], exp int64[c], limbs uint32[c, n])`` with
+x = (-1)^sign * limbs * 2^(exp - p); zero is (0, INT64_MIN, 0).
+Host inputs are numpy arrays; device inputs are torch CUDA tensors (passed
+by pointer with ``device_ptr = 1``, asynchronous on the handle's stream).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+ZEXP = np.iinfo(np.int64).min
+OK, EINVAL, ENOMEM, ECUDA, EZEROPIVOT, ETIMEOUT, ESTATE, EZERODIV = range(8)
+LASTCOL = 1
+_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EZEROPIVOT", 5: "ETIMEOUT", 6: "ESTATE",
+          7: "EZERODIV"}
+
+_lib = None
+
+
+class MpdetError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"mpdet {_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class NumV(ctypes.Structure):
+    _fields_ = [("sign", ctypes.c_void_p), ("exp", ctypes.c_void_p), ("limbs", ctypes.c_void_p)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libmpdet.so (building it in-tree if missing and nvcc is present)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path) or not _build.up_to_date():
+        if not build_if_missing:
+            raise RuntimeError(f"libmpdet not built at {path}")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    P, i64, i32, u32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32
+    sig = {
+        "mpdet_create": ([i64, i32, u32, P, ctypes.POINTER(P)], ctypes.c_int),
+        "mpdet_set_f64": ([P, P, i64, ctypes.c_int], ctypes.c_int),
+        "mpdet_set_i32": ([P, P, i64, ctypes.c_int], ctypes.c_int),
+        "mpdet_set_mp": ([P, NumV, ctypes.c_int], ctypes.c_int),
+        "mpdet_set_cauchy": ([P, P, P, ctypes.c_int], ctypes.c_int),
+        "mpdet_factor_range": ([P, i64, i64], ctypes.c_int),
+        "mpdet_factor": ([P, NumV, NumV, ctypes.POINTER(i64), ctypes.c_int], ctypes.c_int),
+        "mpdet_status": ([P, ctypes.POINTER(i64)], ctypes.c_int),
+        "mpdet_lastcol_minors": ([P, NumV, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+        "mpdet_get_minors": ([P, NumV, ctypes.c_int], ctypes.c_int),
+        "mpdet_get_mp": ([P, NumV, ctypes.c_int], ctypes.c_int),
+        "mpdet_resume": ([P, NumV, NumV, i64, ctypes.c_int], ctypes.c_int),
+        "mpdet_steps_done": ([P], i64),
+        "mpdet_free": ([P], ctypes.c_int),
+        "mpdet_last_error": ([P], ctypes.c_char_p),
+        "mpdet_geometry": ([i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def geometry(p: int):
+    """(n, W, G): limbs per number, limbs per lane, lanes per number."""
+    lib = load()
+    n, W, G = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    rc = lib.mpdet_geometry(p, ctypes.byref(n), ctypes.byref(W), ctypes.byref(G))
+    if rc:
+        raise MpdetError(rc, f"unsupported precision p = {p}")
+    return n.value, W.value, G.value
+
+
+def empty(count: int, p: int):
+    n = p // 32
+    return (np.zeros(count, np.int8), np.full(count, ZEXP, np.int64), np.zeros((count, n), np.uint32))
+
+
+def _is_dev(a) -> bool:
+    return hasattr(a, "is_cuda") and bool(a.is_cuda)
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if _is_dev(a):
+        return ctypes.c_void_p(a.data_ptr())
+    assert isinstance(a, np.ndarray) and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _numv(t) -> NumV:
+    if t is None:
+        return NumV(None, None, None)
+    s, e, m = t
+    return NumV(_ptr(s), _ptr(e), _ptr(m))
+
+
+class Mpdet:
+    """One N x N matrix at p bits on the current CUDA device.
+
+    ``lastcol=True`` keeps L in A's strict lower triangle so that the signed
+    minors of the last column are available after the factorisation.
+    """
+
+    def __init__(self, N: int, p: int, lastcol: bool = False, stream=None):
+        self.lib = load()
+        self.N, self.p, self.n = int(N), int(p), int(p) // 32
+        self.lastcol = bool(lastcol)
+        if stream is None:
+            try:
+                import torch
+
+                stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else None
+            except Exception:  # torch without CUDA: legacy default stream
+                stream = None
+        self.stream = stream
+        h = ctypes.c_void_p()
+        rc = self.lib.mpdet_create(self.N, self.p, LASTCOL if lastcol else 0, ctypes.c_void_p(stream or 0),
+                                   ctypes.byref(h))
+        if rc:
+            raise MpdetError(rc, f"create(N={N}, p={p})")
+        self.h = h
+
+    # -- lifetime -----------------------------------------------------------
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mpdet_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _check(self, rc, what, ok=(OK,)):
+        if rc not in ok:
+            raise MpdetError(rc, f"{what}: {self.lib.mpdet_last_error(self.h).decode(errors='replace')}")
+        return rc
+
+    # -- inputs -------------------------------------------------------------
+    def set_f64(self, A, ld=None):
+        dev = _is_dev(A)
+        if not dev:
+            A = np.ascontiguousarray(A, np.float64)
+        ld = self.N if ld is None else ld
+        self._check(self.lib.mpdet_set_f64(self.h, _ptr(A), ld, int(dev)), "set_f64")
+
+    def set_i32(self, A, ld=None):
+        dev = _is_dev(A)
+        if not dev:
+            A = np.ascontiguousarray(A, np.int32)
+        ld = self.N if ld is None else ld
+        self._check(self.lib.mpdet_set_i32(self.h, _ptr(A), ld, int(dev)), "set_i32")
+
+    def set_cauchy(self, x, y):
+        dev = _is_dev(x)
+        if not dev:
+            x = np.ascontiguousarray(x, np.float64)
+            y = np.ascontiguousarray(y, np.float64)
+        self._check(self.lib.mpdet_set_cauchy(self.h, _ptr(x), _ptr(y), int(dev)), "set_cauchy")
+
+    def set_mp(self, A):
+        dev = _is_dev(A[0])
+        if not dev:
+            A = tuple(np.ascontiguousarray(t) for t in A)
+        self._check(self.lib.mpdet_set_mp(self.h, _numv(A), int(dev)), "set_mp")
+
+    # -- elimination --------------------------------------------------------
+    def factor_range(self, k0: int, k1: int):
+        self._check(self.lib.mpdet_factor_range(self.h, k0, k1), "factor_range")
+
+    def factor(self, out=None):
+        """Run the remaining steps.  Host mode (out=None): returns
+        (status, zero_k, minors) with minors = D_1..D_N (det = minors[-1]).
+        Device mode: ``out`` is a triple of CUDA tensors for D_1..D_N; the
+        call is asynchronous and returns None."""
+        zk = ctypes.c_int64(0)
+        if out is not None:
+            self._check(self.lib.mpdet_factor(self.h, NumV(None, None, None), _numv(out), ctypes.byref(zk), 1),
+                        "factor")
+            return None
+        D = empty(self.N, self.p)
+        rc = self._check(self.lib.mpdet_factor(self.h, NumV(None, None, None), _numv(D), ctypes.byref(zk), 0),
+                         "factor", ok=(OK, EZEROPIVOT))
+        return rc, int(zk.value), D
+
+    def status(self):
+        zk = ctypes.c_int64(0)
+        rc = self._check(self.lib.mpdet_status(self.h, ctypes.byref(zk)), "status", ok=(OK, EZEROPIVOT))
+        return rc, int(zk.value)
+
+    def lastcol_minors(self, normalised: bool = False, out=None):
+        if out is not None:
+            self._check(self.lib.mpdet_lastcol_minors(self.h, _numv(out), int(normalised), 1), "lastcol_minors")
+            return None
+        C = empty(self.N, self.p)
+        self._check(self.lib.mpdet_lastcol_minors(self.h, _numv(C), int(normalised), 0), "lastcol_minors")
+        return C
+
+    def get_minors(self):
+        D = empty(self.N, self.p)
+        self._check(self.lib.mpdet_get_minors(self.h, _numv(D), 0), "get_minors")
+        return D
+
+    def get_mp(self):
+        X = empty(self.N * self.N, self.p)
+        self._check(self.lib.mpdet_get_mp(self.h, _numv(X), 0), "get_mp")
+        return X
+
+    def resume(self, X, D, k_done: int):
+        X = tuple(np.ascontiguousarray(t) for t in X)
+        D = tuple(np.ascontiguousarray(t) for t in D)
+        self._check(self.lib.mpdet_resume(self.h, _numv(X), _numv(D), int(k_done), 0), "resume")
+
+    def steps_done(self) -> int:
+        return int(self.lib.mpdet_steps_done(self.h))

@@ -1,0 +1,541 @@
+// Elimination kernels, templated on the slice width W and group size G
+// (n = W*G limbs per number).  Each translation unit inst_*.cu instantiates
+// one family of (W, G) and exports its launchers through a KernelSet.
+//
+// Matrix layout in HBM (one N x N array of numbers, row-major):
+//   sign  int8   [N*N]
+//   exp   int64  [N*N]
+//   limbs uint32 [N*N][n]   (each number's n limbs contiguous, 16-byte aligned)
+// A group of G lanes moves one number with uint4 loads of its slices.
+#pragma once
+#include "mpdev.cuh"
+#include "kernelset.h"
+
+namespace mpd {
+
+// Per-group shared scratch for sub_round / recip_round (words).
+template <int W, int G>
+struct Scratch {
+  static constexpr int n = W * G;
+  static constexpr int words = ((n + 8 + 3) / 4) * 4 + 4;  // 16-byte multiple, odd-ish stride via +4
+};
+
+__device__ __forceinline__ int status_set(const int* status) { return *(volatile const int*)status; }
+
+__host__ __device__ constexpr int upd_pad4(int w) { return (w + 3) / 4 * 4; }
+
+// ---------------------------------------------------------------------------
+// a1: exact lift of f64 / int32 entries.  value = (-1)^s * mant * 2^E with a
+// mant of t significant bits becomes m = mant << (p - t), e = E + t; only the
+// top two limbs of m can be non-zero (t <= 53).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void lift_u64(uint64_t mant, int64_t E, int& t_out, uint32_t& top1, uint32_t& top0) {
+  int t = 64 - __clzll((long long)mant);
+  uint64_t al = mant << (64 - t);  // top bit at bit 63
+  top1 = (uint32_t)(al >> 32);
+  top0 = (uint32_t)al;
+  t_out = t;
+  (void)E;
+}
+
+template <int W, int G>
+__global__ void k_lift(const void* __restrict__ src, int kind, int64_t ld, int64_t N, MpArr X, int p) {
+  constexpr int n = W * G;
+  Grp<G> gp;
+  const int64_t ngroups_total = (int64_t)gridDim.x * (blockDim.x / G);
+  const int64_t grp0 = (int64_t)blockIdx.x * (blockDim.x / G) + threadIdx.x / G;
+  for (int64_t idx = grp0; idx < N * N; idx += ngroups_total) {
+    const int64_t i = idx / N, j = idx % N;
+    uint64_t mant = 0;
+    int64_t E = 0;
+    int s = 0;
+    if (kind == 0) {  // f64
+      double v = reinterpret_cast<const double*>(src)[i * ld + j];
+      uint64_t bits = (uint64_t)__double_as_longlong(v);
+      s = (int)(bits >> 63);
+      int be = (int)((bits >> 52) & 0x7ff);
+      uint64_t fr = bits & ((1ull << 52) - 1);
+      if (be == 0) {
+        mant = fr;
+        E = -1074;
+      } else {
+        mant = fr | (1ull << 52);
+        E = be - 1075;
+      }
+    } else {  // int32
+      int32_t v = reinterpret_cast<const int32_t*>(src)[i * ld + j];
+      s = v < 0;
+      mant = (uint64_t)(s ? -(int64_t)v : (int64_t)v);
+      E = 0;
+    }
+    uint32_t L[W];
+#pragma unroll
+    for (int q = 0; q < W; ++q) L[q] = 0u;
+    int8_t so = 0;
+    int64_t eo = ZEXP;
+    if (mant != 0) {
+      int t;
+      uint32_t t1, t0;
+      lift_u64(mant, E, t, t1, t0);
+      if (gp.g == G - 1) {
+        L[W - 1] = t1;
+        L[W - 2] = t0;
+      }
+      so = (int8_t)s;
+      eo = E + t;
+    }
+    store_slice<W>(X.m + idx * n + gp.g * W, L);
+    if (gp.g == 0) {
+      X.s[idx] = so;
+      X.e[idx] = eo;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a1: Cauchy matrix A_ij = RN(1 / RN(x_i + y_j)), generated on the device.
+// ---------------------------------------------------------------------------
+template <int W, int G>
+__device__ __forceinline__ void lift_f64_slice(const Grp<G>& gp, double v, int8_t& s, int64_t& e, uint32_t (&L)[W]) {
+  uint64_t bits = (uint64_t)__double_as_longlong(v);
+  int sg = (int)(bits >> 63);
+  int be = (int)((bits >> 52) & 0x7ff);
+  uint64_t fr = bits & ((1ull << 52) - 1);
+  uint64_t mant = be ? (fr | (1ull << 52)) : fr;
+  int64_t E = be ? (int64_t)be - 1075 : -1074;
+#pragma unroll
+  for (int q = 0; q < W; ++q) L[q] = 0u;
+  if (mant == 0) {
+    s = 0;
+    e = ZEXP;
+    return;
+  }
+  int t;
+  uint32_t t1, t0;
+  lift_u64(mant, E, t, t1, t0);
+  if (gp.g == G - 1) {
+    L[W - 1] = t1;
+    L[W - 2] = t0;
+  }
+  s = (int8_t)sg;
+  e = E + t;
+}
+
+template <int W, int G>
+__global__ void k_cauchy(const double* __restrict__ x, const double* __restrict__ y, int64_t N, MpArr X, int p) {
+  constexpr int n = W * G;
+  constexpr int SW = Scratch<W, G>::words;
+  extern __shared__ __align__(16) uint32_t smem[];
+  Grp<G> gp;
+  const int gib = threadIdx.x / G;
+  uint32_t* buf = smem + gib * SW;
+  // groups of one warp advance together so that the trip count is warp-uniform
+  constexpr int GPW = 32 / G;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  const int64_t nwarps = (int64_t)gridDim.x * blockDim.x / 32;
+  const int64_t total = N * N;
+  for (int64_t base = warp * GPW; base < total; base += nwarps * GPW) {
+    int64_t idx = base + gp.lane / G;
+    const bool active = idx < total;
+    if (!active) idx = total - 1;
+    const int64_t i = idx / N, j = idx % N;
+    int8_t xs, ys;
+    int64_t xe, ye;
+    uint32_t XL[W], YL[W];
+    lift_f64_slice<W, G>(gp, x[i], xs, xe, XL);
+    lift_f64_slice<W, G>(gp, y[j], ys, ye, YL);
+    // s = RN(x + y) = RN(x - (-y))
+    sub_round<W, G>(gp, p, xs, xe, XL, (int8_t)(ys ^ (ye != ZEXP ? 1 : 0)), ye, YL, buf);
+    uint32_t Mr[W];
+    if (xe == ZEXP) {  // x_i + y_j == 0 has no reciprocal: divide a dummy, store +0
+#pragma unroll
+      for (int q = 0; q < W; ++q) XL[q] = 0u;
+      if (gp.g == G - 1) XL[W - 1] = 0x80000000u;
+    }
+    const int adj = recip_round<W, G>(gp, XL, buf, Mr);
+    if (active && xe != ZEXP) {
+      store_slice<W>(X.m + idx * n + gp.g * W, Mr);
+      if (gp.g == 0) {
+        X.s[idx] = xs;
+        X.e[idx] = (int64_t)adj - xe;
+      }
+    } else if (active) {  // x_i + y_j == 0: no reciprocal; mark by +0
+      uint32_t Z[W];
+#pragma unroll
+      for (int q = 0; q < W; ++q) Z[q] = 0u;
+      store_slice<W>(X.m + idx * n + gp.g * W, Z);
+      if (gp.g == 0) {
+        X.s[idx] = 0;
+        X.e[idx] = ZEXP;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a2: pivot of step k (0-based): D_k = RN(D_{k-1} * a_kk) (D_{-1} = 1),
+// zero-pivot check, r_k = RN(1 / a_kk).  One warp; group 0 does the work.
+// status[0]: 0 ok, MPDET_EZEROPIVOT once a zero pivot was met before the last
+// step; *zero_k: 1-based index of the first zero pivot.
+// ---------------------------------------------------------------------------
+template <int W, int G>
+__global__ void k_pivot(MpArr X, int64_t N, int64_t k, MpArr D, MpArr R, int* status, int64_t* zero_k, int p) {
+  constexpr int n = W * G;
+  constexpr int SW = Scratch<W, G>::words;
+  __shared__ __align__(16) uint32_t sbuf[(32 / G) * SW];
+  __shared__ __align__(16) uint32_t dprev[n];
+  Grp<G> gp;
+  const bool mine = threadIdx.x < G;  // group 0 of warp 0
+  uint32_t* buf = sbuf + (threadIdx.x / G) * SW;
+  const int64_t kk = k * N + k;
+  uint32_t A[W];
+  load_slice<W>(X.m + kk * n + gp.g * W, A);
+  const int8_t as = X.s[kk];
+  const int64_t ae = X.e[kk];
+  // D_k
+  uint32_t Dm[W];
+  int8_t ds;
+  int64_t de;
+  if (k == 0) {
+#pragma unroll
+    for (int q = 0; q < W; ++q) Dm[q] = A[q];
+    ds = as;
+    de = ae;
+  } else {
+    for (int q = threadIdx.x; q < n; q += blockDim.x) dprev[q] = D.m[(k - 1) * n + q];
+    __syncwarp();
+    const int8_t ps = D.s[k - 1];
+    const int64_t pe = D.e[k - 1];
+    int adj = mul_round<W, G>(gp, A, dprev, Dm);
+    if (pe == ZEXP || ae == ZEXP) {
+      ds = 0;
+      de = ZEXP;
+#pragma unroll
+      for (int q = 0; q < W; ++q) Dm[q] = 0u;
+    } else {
+      ds = (int8_t)(ps ^ as);
+      de = pe + ae + adj;
+    }
+  }
+  if (mine) {
+    store_slice<W>(D.m + k * n + gp.g * W, Dm);
+    if (gp.g == 0) {
+      D.s[k] = ds;
+      D.e[k] = de;
+    }
+  }
+  const bool already = status_set(status) != 0;
+  if (ae == ZEXP && !already) {
+    if (mine && gp.g == 0) {
+      if (*zero_k == 0) *zero_k = k + 1;
+      if (k < N - 1) *status = 4;  // MPDET_EZEROPIVOT
+    }
+    return;
+  }
+  if (already || k == N - 1) return;
+  uint32_t Mr[W];
+  int adj = recip_round<W, G>(gp, A, buf, Mr);
+  if (mine) {
+    store_slice<W>(R.m + gp.g * W, Mr);
+    if (gp.g == 0) {
+      R.s[0] = as;
+      R.e[0] = (int64_t)adj - ae;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a3: multipliers z_i = RN(a_ik * r_k), i > k.  In lastcol mode the
+// eliminated entry becomes l_ik = -z_ik (exact).
+// ---------------------------------------------------------------------------
+template <int W, int G>
+__global__ void k_mult(MpArr X, int64_t N, int64_t k, MpArr R, MpArr Z, const int* status, int p, int lastcol) {
+  constexpr int n = W * G;
+  __shared__ __align__(16) uint32_t rm[n];
+  if (status_set(status)) return;
+  Grp<G> gp;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) rm[q] = R.m[q];
+  __syncthreads();
+  const int8_t rs = R.s[0];
+  const int64_t re = R.e[0];
+  const int gpb = blockDim.x / G;
+  int64_t i = k + 1 + (int64_t)blockIdx.x * gpb + threadIdx.x / G;
+  const bool active = i < N;
+  if (!active) i = N - 1;
+  const int64_t ik = i * N + k;
+  uint32_t A[W], M[W];
+  load_slice<W>(X.m + ik * n + gp.g * W, A);
+  const int8_t as = X.s[ik];
+  const int64_t ae = X.e[ik];
+  int adj = mul_round<W, G>(gp, A, rm, M);
+  const bool zero = (ae == ZEXP);
+  if (zero) {
+#pragma unroll
+    for (int q = 0; q < W; ++q) M[q] = 0u;
+  }
+  if (active) {
+    store_slice<W>(Z.m + i * n + gp.g * W, M);
+    if (lastcol) store_slice<W>(X.m + ik * n + gp.g * W, M);
+    if (gp.g == 0) {
+      const int8_t zs = zero ? 0 : (int8_t)(as ^ rs);
+      const int64_t ze = zero ? ZEXP : ae + re + adj;
+      Z.s[i] = zs;
+      Z.e[i] = ze;
+      if (lastcol) {
+        X.s[ik] = zero ? 0 : (int8_t)(zs ^ 1);
+        X.e[ik] = ze;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a4/a5: Schur update of step k:
+//   x_ij = RN(x_ij - RN(z_i * x_kj))  for i > k and j > k
+//   (lastcol mode: every j != k, which updates L's row segment j < k too).
+// Block: GPB groups, each owning one column j and holding the pivot-row
+// element x_kj's slice in registers; the block walks rows [i0, i1) with the
+// multipliers z_i staged in shared memory (a broadcast read for the groups).
+// ---------------------------------------------------------------------------
+template <int W, int G>
+__global__ void __launch_bounds__(128) k_update(MpArr X, int64_t N, int64_t k, MpArr Z, const int* status, int p,
+                                               int lastcol, int rows_per_cta) {
+  constexpr int n = W * G;
+  constexpr int SW = Scratch<W, G>::words;
+  extern __shared__ __align__(16) uint32_t smem[];
+  if (status_set(status)) return;
+  Grp<G> gp;
+  const int gpb = blockDim.x / G;
+  const int gib = threadIdx.x / G;
+  // shared layout (words, every region a multiple of 4 words = 16 bytes):
+  //   z mantissas rows*n | z exponents 2*rows (+pad) | z signs rows bytes (+pad) | per-group scratch
+  uint32_t* zbuf = smem;
+  int64_t* ze_s = reinterpret_cast<int64_t*>(smem + rows_per_cta * n);
+  int8_t* zs_s = reinterpret_cast<int8_t*>(smem + rows_per_cta * n + upd_pad4(2 * rows_per_cta));
+  uint32_t* buf = smem + rows_per_cta * n + upd_pad4(2 * rows_per_cta) + upd_pad4((rows_per_cta + 3) / 4) + gib * SW;
+  const int64_t ncols = lastcol ? N - 1 : N - k - 1;
+  const int64_t i0 = k + 1 + (int64_t)blockIdx.y * rows_per_cta;
+  const int64_t i1 = (i0 + rows_per_cta < N) ? i0 + rows_per_cta : N;
+  const int nr = (int)(i1 - i0);
+  // stage multipliers
+  for (int q = threadIdx.x; q < nr * n / 4; q += blockDim.x)
+    reinterpret_cast<uint4*>(zbuf)[q] = reinterpret_cast<const uint4*>(Z.m + i0 * n)[q];
+  for (int q = threadIdx.x; q < nr; q += blockDim.x) {
+    ze_s[q] = Z.e[i0 + q];
+    zs_s[q] = Z.s[i0 + q];
+  }
+  __syncthreads();
+  int64_t c = (int64_t)blockIdx.x * gpb + gib;
+  const bool active = c < ncols;
+  if (!active) c = ncols - 1;
+  const int64_t j = lastcol ? (c < k ? c : c + 1) : k + 1 + c;
+  // pivot-row element x_kj
+  const int64_t kj = k * N + j;
+  uint32_t Bk[W];
+  load_slice<W>(X.m + kj * n + gp.g * W, Bk);
+  const int8_t bs = X.s[kj];
+  const int64_t be = X.e[kj];
+#pragma unroll 1
+  for (int r = 0; r < nr; ++r) {
+    const int64_t ij = (i0 + r) * N + j;
+    uint32_t Xv[W], T[W];
+    load_slice<W>(X.m + ij * n + gp.g * W, Xv);
+    int8_t xs = X.s[ij];
+    int64_t xe = X.e[ij];
+    const int64_t zer = ze_s[r];
+    int adj = mul_round<W, G>(gp, Bk, zbuf + r * n, T);
+    const bool tz = (zer == ZEXP) || (be == ZEXP);
+    const int8_t ts = tz ? 0 : (int8_t)(zs_s[r] ^ bs);
+    const int64_t te = tz ? ZEXP : zer + be + adj;
+    if (tz) {
+#pragma unroll
+      for (int q = 0; q < W; ++q) T[q] = 0u;
+    }
+    sub_round<W, G>(gp, p, xs, xe, Xv, ts, te, T, buf);
+    if (active) {
+      store_slice<W>(X.m + ij * n + gp.g * W, Xv);
+      if (gp.g == 0) {
+        X.s[ij] = xs;
+        X.e[ij] = xe;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a6: last-column minors.  out_j = RN(f * l_Nj) for j < N-1 (0-based), where
+// f = D_{N-1} (signed minors C_jN) or f = RN(1/l_N1) (normalised minors,
+// then out_0 = 1 exactly); out_{N-1} = D_{N-1} or RN(1/l_N1) respectively.
+// F holds f (one number).  Threads: groups over j.
+// ---------------------------------------------------------------------------
+template <int W, int G>
+__global__ void k_lastcol(MpArr X, int64_t N, MpArr F, MpArr out, int normalised) {
+  constexpr int n = W * G;
+  __shared__ __align__(16) uint32_t fm[n];
+  Grp<G> gp;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) fm[q] = F.m[q];
+  __syncthreads();
+  const int8_t fs = F.s[0];
+  const int64_t fe = F.e[0];
+  const int gpb = blockDim.x / G;
+  int64_t j = (int64_t)blockIdx.x * gpb + threadIdx.x / G;
+  const bool active = j < N;
+  if (!active) j = N - 1;
+  const int64_t Nj = (N - 1) * N + j;
+  uint32_t L[W], M[W];
+  load_slice<W>(X.m + Nj * n + gp.g * W, L);
+  const int8_t ls = X.s[Nj];
+  const int64_t le = X.e[Nj];
+  int adj = mul_round<W, G>(gp, L, fm, M);
+  int8_t os;
+  int64_t oe;
+  if (le == ZEXP || fe == ZEXP) {
+    os = 0;
+    oe = ZEXP;
+#pragma unroll
+    for (int q = 0; q < W; ++q) M[q] = 0u;
+  } else {
+    os = (int8_t)(ls ^ fs);
+    oe = le + fe + adj;
+  }
+  if (j == N - 1) {  // C_NN = D_{N-1}; delta_{N,N} = RN(1/l_N1): both are f itself
+#pragma unroll
+    for (int q = 0; q < W; ++q) M[q] = fm[gp.g * W + q];
+    os = fs;
+    oe = fe;
+  }
+  if (normalised && j == 0) {  // delta_{N,1} = 1
+#pragma unroll
+    for (int q = 0; q < W; ++q) M[q] = 0u;
+    if (gp.g == G - 1) M[W - 1] = 0x80000000u;
+    os = 0;
+    oe = 1;
+  }
+  if (active) {
+    store_slice<W>(out.m + j * n + gp.g * W, M);
+    if (gp.g == 0) {
+      out.s[j] = os;
+      out.e[j] = oe;
+    }
+  }
+}
+
+// RN(1/src[idx]) into dst[0]; one warp, group 0.  Sets *status = code when
+// src[idx] is zero.
+template <int W, int G>
+__global__ void k_recip1(MpArr src, int64_t idx, MpArr dst, int* status, int code) {
+  constexpr int n = W * G;
+  constexpr int SW = Scratch<W, G>::words;
+  __shared__ __align__(16) uint32_t sbuf[(32 / G) * SW];
+  Grp<G> gp;
+  uint32_t A[W], M[W];
+  load_slice<W>(src.m + idx * n + gp.g * W, A);
+  const int8_t as = src.s[idx];
+  const int64_t ae = src.e[idx];
+  if (ae == ZEXP) {
+    if (threadIdx.x == 0) *status = code;
+    return;
+  }
+  int adj = recip_round<W, G>(gp, A, sbuf + (threadIdx.x / G) * SW, M);
+  if (threadIdx.x < G) {
+    store_slice<W>(dst.m + gp.g * W, M);
+    if (gp.g == 0) {
+      dst.s[0] = as;
+      dst.e[0] = (int64_t)adj - ae;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------
+template <int W, int G>
+struct Launch {
+  static constexpr int n = W * G;
+  static constexpr int SW = Scratch<W, G>::words;
+  static constexpr int NT = 128;  // threads per block (4 warps)
+
+  static cudaError_t lift(const void* src, int kind, int64_t ld, int64_t N, MpArr X, int p, int nsm, cudaStream_t st) {
+    int64_t groups = N * N;
+    int64_t blocks = (groups + NT / G - 1) / (NT / G);
+    int64_t cap = (int64_t)nsm * 16;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    k_lift<W, G><<<(unsigned)blocks, NT, 0, st>>>(src, kind, ld, N, X, p);
+    return cudaGetLastError();
+  }
+  static cudaError_t cauchy(const double* x, const double* y, int64_t N, MpArr X, int p, int nsm, cudaStream_t st) {
+    int64_t groups = N * N;
+    int64_t blocks = (groups + NT / G - 1) / (NT / G);
+    int64_t cap = (int64_t)nsm * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    size_t sm = (size_t)(NT / G) * SW * 4;
+    cudaFuncSetAttribute(k_cauchy<W, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_cauchy<W, G><<<(unsigned)blocks, NT, sm, st>>>(x, y, N, X, p);
+    return cudaGetLastError();
+  }
+  static cudaError_t pivot(MpArr X, int64_t N, int64_t k, MpArr D, MpArr R, int* status, int64_t* zk, int p,
+                           cudaStream_t st) {
+    k_pivot<W, G><<<1, 32, 0, st>>>(X, N, k, D, R, status, zk, p);
+    return cudaGetLastError();
+  }
+  static cudaError_t mult(MpArr X, int64_t N, int64_t k, MpArr R, MpArr Z, const int* status, int p, int lastcol,
+                          cudaStream_t st) {
+    int64_t rows = N - k - 1;
+    if (rows <= 0) return cudaSuccess;
+    int64_t blocks = (rows + NT / G - 1) / (NT / G);
+    k_mult<W, G><<<(unsigned)blocks, NT, 0, st>>>(X, N, k, R, Z, status, p, lastcol);
+    return cudaGetLastError();
+  }
+  static size_t update_smem(int rows_per_cta) {
+    return (size_t)(rows_per_cta * n + upd_pad4(2 * rows_per_cta) + upd_pad4((rows_per_cta + 3) / 4) + (NT / G) * SW) * 4;
+  }
+  static cudaError_t update(MpArr X, int64_t N, int64_t k, MpArr Z, const int* status, int p, int lastcol, int nsm,
+                            cudaStream_t st) {
+    int64_t rows = N - k - 1;
+    int64_t ncols = lastcol ? N - 1 : N - k - 1;
+    if (rows <= 0 || ncols <= 0) return cudaSuccess;
+    const int gpb = NT / G;
+    int64_t bx = (ncols + gpb - 1) / gpb;
+    // rows per block: enough blocks for ~4 waves of 4 blocks per SM
+    int64_t target = (int64_t)nsm * 16;
+    int64_t by_needed = (target + bx - 1) / bx;
+    int64_t rpc = (rows + by_needed - 1) / by_needed;
+    int64_t rmax = 32;
+    while (rmax > 1 && update_smem((int)rmax) > 96 * 1024) rmax /= 2;
+    if (rpc > rmax) rpc = rmax;
+    if (rpc < 1) rpc = 1;
+    int64_t by = (rows + rpc - 1) / rpc;
+    size_t sm = update_smem((int)rpc);
+    cudaFuncSetAttribute(k_update<W, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    dim3 grid((unsigned)bx, (unsigned)by);
+    k_update<W, G><<<grid, NT, sm, st>>>(X, N, k, Z, status, p, lastcol, (int)rpc);
+    return cudaGetLastError();
+  }
+  static cudaError_t lastcol(MpArr X, int64_t N, MpArr F, MpArr out, int normalised, cudaStream_t st) {
+    int64_t blocks = (N + NT / G - 1) / (NT / G);
+    k_lastcol<W, G><<<(unsigned)blocks, NT, 0, st>>>(X, N, F, out, normalised);
+    return cudaGetLastError();
+  }
+  static cudaError_t recip1(MpArr src, int64_t idx, MpArr dst, int* status, int code, cudaStream_t st) {
+    k_recip1<W, G><<<1, 32, 0, st>>>(src, idx, dst, status, code);
+    return cudaGetLastError();
+  }
+  static KernelSet make() {
+    KernelSet s;
+    s.W = W;
+    s.G = G;
+    s.lift = &lift;
+    s.cauchy = &cauchy;
+    s.pivot = &pivot;
+    s.mult = &mult;
+    s.update = &update;
+    s.lastcol = &lastcol;
+    s.recip1 = &recip1;
+    return s;
+  }
+};
+
+}  // namespace mpd

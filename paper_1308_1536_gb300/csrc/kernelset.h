@@ -1,0 +1,40 @@
+// Internal interface between the C-ABI layer and the per-(W, G) kernel
+// instantiations.  Not part of the public ABI.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mpd {
+
+// Structure-of-arrays view of numbers in device memory (n limbs each).
+struct MpArr {
+  int8_t* s;
+  int64_t* e;
+  uint32_t* m;
+};
+
+struct KernelSet {
+  int W, G;
+  // kind 0: double entries, 1: int32 entries
+  cudaError_t (*lift)(const void* src, int kind, int64_t ld, int64_t N, MpArr X, int p, int nsm, cudaStream_t st);
+  cudaError_t (*cauchy)(const double* x, const double* y, int64_t N, MpArr X, int p, int nsm, cudaStream_t st);
+  cudaError_t (*pivot)(MpArr X, int64_t N, int64_t k, MpArr D, MpArr R, int* status, int64_t* zk, int p,
+                       cudaStream_t st);
+  cudaError_t (*mult)(MpArr X, int64_t N, int64_t k, MpArr R, MpArr Z, const int* status, int p, int lastcol,
+                      cudaStream_t st);
+  cudaError_t (*update)(MpArr X, int64_t N, int64_t k, MpArr Z, const int* status, int p, int lastcol, int nsm,
+                        cudaStream_t st);
+  cudaError_t (*lastcol)(MpArr X, int64_t N, MpArr F, MpArr out, int normalised, cudaStream_t st);
+  cudaError_t (*recip1)(MpArr src, int64_t idx, MpArr dst, int* status, int code, cudaStream_t st);
+};
+
+// Kernel set for n = p/32 limbs, or nullptr if this n is not instantiated.
+const KernelSet* kernel_set_for(int n);
+
+// per-translation-unit registries
+const KernelSet* kernel_set_w4(int G);
+const KernelSet* kernel_set_w8(int G);
+const KernelSet* kernel_set_w16(int G);
+const KernelSet* kernel_set_w32(int G);
+
+}  // namespace mpd

@@ -1,0 +1,384 @@
+// C-ABI layer of libmpdet: handle life cycle, argument checks, device buffers
+// and the step loop of the elimination (Sec. 3 / Algorithm 1).  Every
+// arithmetic step runs in the kernels of kernels.cuh; this file only moves
+// data and enqueues launches.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "../../include/mpdet.h"
+#include "kernelset.h"
+
+using mpd::KernelSet;
+using mpd::MpArr;
+
+namespace mpd {
+const KernelSet* kernel_set_for(int n) {
+  if (n == 4) return kernel_set_w4(1);
+  if (n == 8) return kernel_set_w8(1);
+  if (n >= 16 && n <= 512 && (n & (n - 1)) == 0) return kernel_set_w16(n / 16);
+  if (n == 1024) return kernel_set_w32(32);
+  return nullptr;
+}
+}  // namespace mpd
+
+struct mpdet_ctx {
+  int64_t N = 0;
+  int p = 0, n = 0;
+  uint32_t flags = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0, nsm = 0;
+  const KernelSet* ks = nullptr;
+  MpArr X{}, D{}, Z{}, R{}, T{};  // matrix, minors, multipliers, reciprocal, temp (N numbers)
+  int* status = nullptr;          // [0] code
+  int64_t* zero_k = nullptr;
+  void* stage = nullptr;  // device staging for host inputs
+  size_t stage_bytes = 0;
+  int64_t k_done = 0;
+  bool have_matrix = false;
+  char err[512] = {0};
+};
+
+static const char* g_static_err = "no handle";
+
+static int fail(mpdet_t h, int code, const char* fmt, ...) {
+  if (h) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(h->err, sizeof h->err, fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
+#define CU(h, call)                                                                          \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess) return fail(h, MPDET_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+static int alloc_arr(mpdet_t h, MpArr* a, int64_t count) {
+  int n = h->n;
+  if (cudaMalloc(&a->m, (size_t)count * n * 4) != cudaSuccess) return fail(h, MPDET_ENOMEM, "cudaMalloc limbs");
+  if (cudaMalloc(&a->e, (size_t)count * 8) != cudaSuccess) return fail(h, MPDET_ENOMEM, "cudaMalloc exp");
+  if (cudaMalloc(&a->s, (size_t)count) != cudaSuccess) return fail(h, MPDET_ENOMEM, "cudaMalloc sign");
+  return MPDET_OK;
+}
+
+static void free_arr(MpArr* a) {
+  if (a->m) cudaFree(a->m);
+  if (a->e) cudaFree(a->e);
+  if (a->s) cudaFree(a->s);
+  *a = MpArr{};
+}
+
+// zero (+0) numbers: sign 0, exp INT64_MIN, limbs 0
+static cudaError_t zero_arr(MpArr a, int64_t count, int n, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(a.m, 0, (size_t)count * n * 4, st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(a.s, 0, (size_t)count, st);
+  if (e != cudaSuccess) return e;
+  // INT64_MIN = 0x8000000000000000: bytes 00 .. 00 80 (little endian); fill by a 2D memset of the top byte
+  e = cudaMemsetAsync(a.e, 0, (size_t)count * 8, st);
+  if (e != cudaSuccess) return e;
+  return cudaMemset2DAsync(reinterpret_cast<char*>(a.e) + 7, 8, 0x80, 1, (size_t)count, st);
+}
+
+extern "C" int mpdet_geometry(int32_t p_bits, int32_t* n, int32_t* W, int32_t* G) {
+  if (p_bits < 128 || p_bits > 32768 || (p_bits & (p_bits - 1))) return MPDET_EINVAL;
+  const KernelSet* ks = mpd::kernel_set_for(p_bits / 32);
+  if (!ks) return MPDET_EINVAL;
+  if (n) *n = p_bits / 32;
+  if (W) *W = ks->W;
+  if (G) *G = ks->G;
+  return MPDET_OK;
+}
+
+extern "C" int mpdet_create(int64_t N, int32_t p_bits, uint32_t flags, void* cuda_stream, mpdet_t* out) {
+  if (!out) return MPDET_EINVAL;
+  *out = nullptr;
+  if (N < 1 || N > (int64_t)1 << 20) return MPDET_EINVAL;
+  if (flags & ~(uint32_t)MPDET_LASTCOL) return MPDET_EINVAL;
+  if (mpdet_geometry(p_bits, nullptr, nullptr, nullptr) != MPDET_OK) return MPDET_EINVAL;
+  mpdet_t h = new (std::nothrow) mpdet_ctx();
+  if (!h) return MPDET_ENOMEM;
+  h->N = N;
+  h->p = p_bits;
+  h->n = p_bits / 32;
+  h->flags = flags;
+  h->stream = (cudaStream_t)cuda_stream;
+  h->ks = mpd::kernel_set_for(h->n);
+  int rc = MPDET_OK;
+  if (cudaGetDevice(&h->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
+    rc = MPDET_ECUDA;
+  }
+  if (rc == MPDET_OK) rc = alloc_arr(h, &h->X, N * N);
+  if (rc == MPDET_OK) rc = alloc_arr(h, &h->D, N);
+  if (rc == MPDET_OK) rc = alloc_arr(h, &h->Z, N);
+  if (rc == MPDET_OK) rc = alloc_arr(h, &h->T, N);
+  if (rc == MPDET_OK) rc = alloc_arr(h, &h->R, 1);
+  if (rc == MPDET_OK && cudaMalloc(&h->status, 16) != cudaSuccess) rc = MPDET_ENOMEM;
+  if (rc == MPDET_OK && cudaMalloc(&h->zero_k, 16) != cudaSuccess) rc = MPDET_ENOMEM;
+  if (rc == MPDET_OK && (cudaMemsetAsync(h->status, 0, 16, h->stream) != cudaSuccess ||
+                         cudaMemsetAsync(h->zero_k, 0, 16, h->stream) != cudaSuccess ||
+                         zero_arr(h->D, N, h->n, h->stream) != cudaSuccess ||
+                         cudaStreamSynchronize(h->stream) != cudaSuccess))
+    rc = MPDET_ECUDA;
+  if (rc != MPDET_OK) {
+    cudaGetLastError();
+    mpdet_free(h);
+    return rc;
+  }
+  *out = h;
+  return MPDET_OK;
+}
+
+extern "C" int mpdet_free(mpdet_t h) {
+  if (!h) return MPDET_OK;
+  free_arr(&h->X);
+  free_arr(&h->D);
+  free_arr(&h->Z);
+  free_arr(&h->T);
+  free_arr(&h->R);
+  if (h->status) cudaFree(h->status);
+  if (h->zero_k) cudaFree(h->zero_k);
+  if (h->stage) cudaFree(h->stage);
+  delete h;
+  return MPDET_OK;
+}
+
+extern "C" const char* mpdet_last_error(mpdet_t h) { return h ? h->err : g_static_err; }
+
+extern "C" int64_t mpdet_steps_done(mpdet_t h) { return h ? h->k_done : -1; }
+
+static int stage_in(mpdet_t h, const void* src, size_t bytes, const void** dev) {
+  if (h->stage_bytes < bytes) {
+    if (h->stage) cudaFree(h->stage);
+    h->stage = nullptr;
+    h->stage_bytes = 0;
+    if (cudaMalloc(&h->stage, bytes) != cudaSuccess) return fail(h, MPDET_ENOMEM, "staging buffer of %zu bytes", bytes);
+    h->stage_bytes = bytes;
+  }
+  CU(h, cudaMemcpyAsync(h->stage, src, bytes, cudaMemcpyHostToDevice, h->stream));
+  *dev = h->stage;
+  return MPDET_OK;
+}
+
+// reset factorisation state after a new matrix
+static int reset_state(mpdet_t h) {
+  CU(h, cudaMemsetAsync(h->status, 0, 16, h->stream));
+  CU(h, cudaMemsetAsync(h->zero_k, 0, 16, h->stream));
+  CU(h, zero_arr(h->D, h->N, h->n, h->stream));
+  h->k_done = 0;
+  h->have_matrix = true;
+  return MPDET_OK;
+}
+
+static int finish_call(mpdet_t h, int device_ptr) {
+  CU(h, cudaGetLastError());
+  if (!device_ptr) CU(h, cudaStreamSynchronize(h->stream));
+  return MPDET_OK;
+}
+
+static int set_dense(mpdet_t h, const void* A, int64_t ld, int device_ptr, int kind) {
+  if (!h || !A || ld < h->N) return fail(h, MPDET_EINVAL, "set: bad argument");
+  const void* src = A;
+  if (!device_ptr) {
+    size_t es = kind == 0 ? 8 : 4;
+    // pack rows (ld may exceed N): stage the whole ld-strided block
+    size_t bytes = (size_t)((h->N - 1) * ld + h->N) * es;
+    int rc = stage_in(h, A, bytes, &src);
+    if (rc) return rc;
+  }
+  int rc = reset_state(h);
+  if (rc) return rc;
+  CU(h, h->ks->lift(src, kind, ld, h->N, h->X, h->p, h->nsm, h->stream));
+  return finish_call(h, device_ptr);
+}
+
+extern "C" int mpdet_set_f64(mpdet_t h, const double* A, int64_t ld, int device_ptr) {
+  return set_dense(h, A, ld, device_ptr, 0);
+}
+
+extern "C" int mpdet_set_i32(mpdet_t h, const int32_t* A, int64_t ld, int device_ptr) {
+  return set_dense(h, A, ld, device_ptr, 1);
+}
+
+static int copy_arr(mpdet_t h, MpArr dst_dev, const mpdet_numv& src, int64_t count, int device_ptr, bool to_dev) {
+  cudaMemcpyKind kind = device_ptr ? cudaMemcpyDeviceToDevice : (to_dev ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost);
+  size_t nb = (size_t)count * h->n * 4;
+  if (to_dev) {
+    if (src.limbs) CU(h, cudaMemcpyAsync(dst_dev.m, src.limbs, nb, kind, h->stream));
+    if (src.exp) CU(h, cudaMemcpyAsync(dst_dev.e, src.exp, (size_t)count * 8, kind, h->stream));
+    if (src.sign) CU(h, cudaMemcpyAsync(dst_dev.s, src.sign, (size_t)count, kind, h->stream));
+  } else {
+    if (src.limbs) CU(h, cudaMemcpyAsync(src.limbs, dst_dev.m, nb, kind, h->stream));
+    if (src.exp) CU(h, cudaMemcpyAsync(src.exp, dst_dev.e, (size_t)count * 8, kind, h->stream));
+    if (src.sign) CU(h, cudaMemcpyAsync(src.sign, dst_dev.s, (size_t)count, kind, h->stream));
+  }
+  return MPDET_OK;
+}
+
+extern "C" int mpdet_set_mp(mpdet_t h, mpdet_numv A, int device_ptr) {
+  if (!h || !A.sign || !A.exp || !A.limbs) return fail(h, MPDET_EINVAL, "set_mp: null pointer");
+  int rc = reset_state(h);
+  if (rc) return rc;
+  rc = copy_arr(h, h->X, A, h->N * h->N, device_ptr, true);
+  if (rc) return rc;
+  return finish_call(h, device_ptr);
+}
+
+extern "C" int mpdet_set_cauchy(mpdet_t h, const double* x, const double* y, int device_ptr) {
+  if (!h || !x || !y) return fail(h, MPDET_EINVAL, "set_cauchy: null pointer");
+  const double *dx = x, *dy = y;
+  if (!device_ptr) {
+    size_t nb = (size_t)h->N * 8;
+    if (h->stage_bytes < 2 * nb) {
+      if (h->stage) cudaFree(h->stage);
+      h->stage = nullptr;
+      h->stage_bytes = 0;
+      if (cudaMalloc(&h->stage, 2 * nb) != cudaSuccess) return fail(h, MPDET_ENOMEM, "staging");
+      h->stage_bytes = 2 * nb;
+    }
+    CU(h, cudaMemcpyAsync(h->stage, x, nb, cudaMemcpyHostToDevice, h->stream));
+    CU(h, cudaMemcpyAsync((char*)h->stage + nb, y, nb, cudaMemcpyHostToDevice, h->stream));
+    dx = (const double*)h->stage;
+    dy = (const double*)((char*)h->stage + nb);
+  }
+  int rc = reset_state(h);
+  if (rc) return rc;
+  CU(h, h->ks->cauchy(dx, dy, h->N, h->X, h->p, h->nsm, h->stream));
+  return finish_call(h, device_ptr);
+}
+
+// enqueue steps k (0-based) in [k0, k1)
+static int run_steps(mpdet_t h, int64_t k0, int64_t k1) {
+  const int lastcol = (h->flags & MPDET_LASTCOL) ? 1 : 0;
+  for (int64_t k = k0; k < k1; ++k) {
+    CU(h, h->ks->pivot(h->X, h->N, k, h->D, h->R, h->status, h->zero_k, h->p, h->stream));
+    if (k < h->N - 1) {
+      CU(h, h->ks->mult(h->X, h->N, k, h->R, h->Z, h->status, h->p, lastcol, h->stream));
+      CU(h, h->ks->update(h->X, h->N, k, h->Z, h->status, h->p, lastcol, h->nsm, h->stream));
+    }
+  }
+  h->k_done = k1;
+  return MPDET_OK;
+}
+
+extern "C" int mpdet_factor_range(mpdet_t h, int64_t k0, int64_t k1) {
+  if (!h) return MPDET_EINVAL;
+  if (!h->have_matrix) return fail(h, MPDET_ESTATE, "factor_range: no matrix set");
+  if (k0 != h->k_done || k1 < k0 || k1 > h->N)
+    return fail(h, MPDET_ESTATE, "factor_range: window [%lld, %lld) but %lld steps done", (long long)k0, (long long)k1,
+                (long long)h->k_done);
+  int rc = run_steps(h, k0, k1);
+  if (rc) return rc;
+  CU(h, cudaGetLastError());
+  return MPDET_OK;
+}
+
+extern "C" int mpdet_status(mpdet_t h, int64_t* zero_pivot_k) {
+  if (!h) return MPDET_EINVAL;
+  int st[4] = {0};
+  int64_t zk[2] = {0};
+  CU(h, cudaMemcpyAsync(st, h->status, 16, cudaMemcpyDeviceToHost, h->stream));
+  CU(h, cudaMemcpyAsync(zk, h->zero_k, 16, cudaMemcpyDeviceToHost, h->stream));
+  CU(h, cudaStreamSynchronize(h->stream));
+  if (zero_pivot_k) *zero_pivot_k = zk[0];
+  if (st[0] == MPDET_EZEROPIVOT) return fail(h, MPDET_EZEROPIVOT, "zero pivot at k = %lld", (long long)zk[0]);
+  return st[0];
+}
+
+extern "C" int mpdet_get_minors(mpdet_t h, mpdet_numv out, int device_ptr) {
+  if (!h) return MPDET_EINVAL;
+  int rc = copy_arr(h, h->D, out, h->N, device_ptr, false);
+  if (rc) return rc;
+  return finish_call(h, device_ptr);
+}
+
+extern "C" int mpdet_factor(mpdet_t h, mpdet_numv det, mpdet_numv minors, int64_t* zero_pivot_k, int device_ptr) {
+  if (!h) return MPDET_EINVAL;
+  if (!h->have_matrix) return fail(h, MPDET_ESTATE, "factor: no matrix set");
+  int rc = run_steps(h, h->k_done, h->N);
+  if (rc) return rc;
+  MpArr last{h->D.s + (h->N - 1), h->D.e + (h->N - 1), h->D.m + (size_t)(h->N - 1) * h->n};
+  rc = copy_arr(h, last, det, 1, device_ptr, false);
+  if (rc) return rc;
+  rc = copy_arr(h, h->D, minors, h->N, device_ptr, false);
+  if (rc) return rc;
+  rc = finish_call(h, device_ptr);
+  if (rc) return rc;
+  if (device_ptr) {
+    if (zero_pivot_k) *zero_pivot_k = -1;  // unknown until mpdet_status
+    return MPDET_OK;
+  }
+  return mpdet_status(h, zero_pivot_k);
+}
+
+extern "C" int mpdet_lastcol_minors(mpdet_t h, mpdet_numv out, int normalised, int device_ptr) {
+  if (!h) return MPDET_EINVAL;
+  if (!(h->flags & MPDET_LASTCOL)) return fail(h, MPDET_ESTATE, "lastcol_minors: handle created without MPDET_LASTCOL");
+  if (!h->have_matrix || h->k_done != h->N) return fail(h, MPDET_ESTATE, "lastcol_minors: factorisation not complete");
+  int64_t zk = 0;
+  int st = mpdet_status(h, &zk);
+  if (st == MPDET_EZEROPIVOT) return fail(h, MPDET_EZEROPIVOT, "lastcol_minors: zero pivot at k = %lld", (long long)zk);
+  if (st) return st;
+  const int64_t N = h->N;
+  if (N == 1) {  // C_11 = D_0 = 1, delta_{1,1} = 1
+    uint32_t* one = new uint32_t[h->n]();
+    one[h->n - 1] = 0x80000000u;
+    int8_t s = 0;
+    int64_t e = 1;
+    cudaMemcpyKind k = device_ptr ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
+    cudaError_t ce = cudaMemcpy(out.limbs, one, h->n * 4, k);
+    if (ce == cudaSuccess) ce = cudaMemcpy(out.exp, &e, 8, k);
+    if (ce == cudaSuccess) ce = cudaMemcpy(out.sign, &s, 1, k);
+    delete[] one;
+    if (ce != cudaSuccess) return fail(h, MPDET_ECUDA, "lastcol N=1 copy: %s", cudaGetErrorString(ce));
+    return MPDET_OK;
+  }
+  MpArr F;
+  if (normalised) {
+    // F = RN(1 / l_N1) into R; status 7 if l_N1 == 0
+    CU(h, h->ks->recip1(h->X, (N - 1) * N, h->R, h->status, MPDET_EZERODIV, h->stream));
+    F = h->R;
+  } else {
+    F = MpArr{h->D.s + (N - 2), h->D.e + (N - 2), h->D.m + (size_t)(N - 2) * h->n};
+  }
+  CU(h, h->ks->lastcol(h->X, N, F, h->T, normalised, h->stream));
+  if (normalised) {
+    int sts[4] = {0};
+    CU(h, cudaMemcpyAsync(sts, h->status, 16, cudaMemcpyDeviceToHost, h->stream));
+    CU(h, cudaStreamSynchronize(h->stream));
+    if (sts[0] == MPDET_EZERODIV) {
+      CU(h, cudaMemsetAsync(h->status, 0, 16, h->stream));
+      return fail(h, MPDET_EZERODIV, "normalised minors: l_N1 is zero");
+    }
+  }
+  int rc = copy_arr(h, h->T, out, N, device_ptr, false);
+  if (rc) return rc;
+  return finish_call(h, device_ptr);
+}
+
+extern "C" int mpdet_get_mp(mpdet_t h, mpdet_numv out, int device_ptr) {
+  if (!h) return MPDET_EINVAL;
+  int rc = copy_arr(h, h->X, out, h->N * h->N, device_ptr, false);
+  if (rc) return rc;
+  return finish_call(h, device_ptr);
+}
+
+extern "C" int mpdet_resume(mpdet_t h, mpdet_numv A, mpdet_numv minors, int64_t k_done, int device_ptr) {
+  if (!h || k_done < 0 || k_done > h->N) return fail(h, MPDET_EINVAL, "resume: bad argument");
+  int rc = reset_state(h);
+  if (rc) return rc;
+  rc = copy_arr(h, h->X, A, h->N * h->N, device_ptr, true);
+  if (rc) return rc;
+  if (k_done > 0) {
+    rc = copy_arr(h, h->D, minors, k_done, device_ptr, true);
+    if (rc) return rc;
+  }
+  h->k_done = k_done;
+  return finish_call(h, device_ptr);
+}

@@ -1,0 +1,60 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds and
+loads, exports every function declared in include/*.h, and rejects bad
+arguments before touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(mpdet_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_1308_1536_gb300 as m
+
+    return m.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("mpdet_create", "mpdet_factor", "mpdet_lastcol_minors", "mpdet_free", "mpdet_set_cauchy",
+                     "mpdet_factor_range"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_geometry_and_invalid_precisions(lib):
+    import paper_1308_1536_gb300 as m
+
+    assert m.geometry(512) == (16, 16, 1)
+    assert m.geometry(2048) == (64, 16, 4)
+    assert m.geometry(32768) == (1024, 32, 32)
+    for p in (0, 64, 96, 1000, 3072, 65536):
+        with pytest.raises(m.MpdetError):
+            m.geometry(p)
+
+
+def test_create_rejects_bad_arguments_without_a_device(lib):
+    h = ctypes.c_void_p()
+    assert lib.mpdet_create(0, 512, 0, None, ctypes.byref(h)) == 1  # N < 1
+    assert lib.mpdet_create(8, 100, 0, None, ctypes.byref(h)) == 1  # p not supported
+    assert lib.mpdet_create(8, 512, 0x10, None, ctypes.byref(h)) == 1  # unknown flag
+    assert lib.mpdet_create(8, 512, 0, None, None) == 1  # no output
+    assert lib.mpdet_free(None) == 0
+    assert lib.mpdet_last_error(None) == b"no handle"
