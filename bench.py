@@ -1,0 +1,364 @@
+#!/usr/bin/env python
+"""Benchmark of multiprecision Gaussian elimination (det, leading minors and
+last-column minors) on one or more GB300s.
+
+One step = the whole hot path on the N = 1024, p = 2048 workload: for a seeded
+Cauchy matrix (generated on the device, A_ij = RN(1/RN(x_i+y_j))) and a seeded
+integer matrix with entries in [-1000, 1000] (lifted on the device): the
+elimination without pivoting in last-column mode (pivots, reciprocals,
+multipliers, Schur updates of U and L) and the last-column signed minors.
+
+value   = algorithmic limb multiply-accumulates of the step (every p x p-bit
+          product of the elimination counted as n^2 = (p/32)^2 limb MACs)
+          / device time of the step, inputs resident in HBM.
+e2e     = the same through the C ABI with host buffers: pinned host inputs
+          copied in and minors copied out inside the timed region.
+roofline: the Schur-update kernel (the dominant one), timed live with CUDA
+          events around each of its launches, against the integer-multiply
+          peak SMs x 32 limb-MAC/clk (64 IMAD lanes per SM, two IMAD-pipe slots
+          per 32x32->64-bit product) x max SM clock.
+--impl reference: the CPU oracle on this host's cores, on a bounded sample of
+          the same workload (leading K x K blocks of both matrices).
+With --gpus N > 1 (torchrun) every rank runs its own replica of the step on
+its GPU (independent problems, no collective); value sums over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1308_1536_gb300 import workloads as W  # noqa: E402
+
+METRIC = "mp elimination limb-MAC/s"
+UNIT = "limb-MAC/s"
+ORACLE_SAMPLE_K = 160
+
+
+def elim_products(N: int, lastcol: bool) -> int:
+    """p x p-bit products of one elimination: multipliers, Schur updates (full
+    rows in lastcol mode), D_k and the last-column finalisation."""
+    upd = sum((N - k - 1) * ((N - 1) if lastcol else (N - k - 1)) for k in range(N - 1))
+    mult = N * (N - 1) // 2
+    dk = N - 1
+    fin = (N - 1) if lastcol else 0
+    return upd + mult + dk + fin
+
+
+def step_limb_macs(N: int, p: int, matrices: int = 2) -> float:
+    n = p // 32
+    return float(matrices) * elim_products(N, True) * n * n
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1308_1536_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, fn), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"bench_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def recorded_traffic():
+    """dram bytes per Schur-update launch from the committed ncu summary, valid
+    only for the kernel sources it was measured on."""
+    try:
+        t = json.load(open(os.path.join(ROOT, "profiles", "k_update_traffic.json")))
+    except Exception:
+        return None
+    if t.get("source_sha") != kernel_source_sha():
+        return None
+    return t.get("bytes_per_launch")
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded sample (cpu_baseline and --impl reference)
+# ---------------------------------------------------------------------------
+def oracle_sample(K: int = ORACLE_SAMPLE_K):
+    import oracle
+
+    oracle.build()
+    cfg = W.C2
+    N, p = cfg["N"], cfg["p"]
+    x, y = W.cauchy_xy(N, cfg["seed"])
+    A = W.int_matrix(N, cfg["seed"] + 100)
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    for kind in ("cauchy", "int"):
+        M = oracle.cauchy(x[:K], y[:K], p) if kind == "cauchy" else oracle.from_int(A[:K, :K].reshape(-1), p)
+        st, zk, D, X = oracle.ge(M, K, p, lastcol=True, nthreads=threads)
+        oracle.lastcol_minors(X, D, K, p)
+    dt = time.perf_counter() - t0
+    macs = step_limb_macs(K, p, 2)
+    return {"value": macs / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"leading {K}x{K} blocks of both workload matrices (Cauchy and integer), p={p}, lastcol mode, "
+                      f"{threads} threads; {dt:.2f} s", "seconds": dt}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        oracle_sample(max(32, ORACLE_SAMPLE_K // 4))
+    vals, secs = [], []
+    for _ in range(args.steps):
+        r = oracle_sample()
+        vals.append(r["value"])
+        secs.append(r["seconds"])
+    v = statistics.median(vals)
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(secs),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+           "config": {"workload": "cauchy+int N=1024 p=2048 lastcol (oracle sample: leading "
+                                  f"{ORACLE_SAMPLE_K}x{ORACLE_SAMPLE_K} blocks)", "N": W.C2["N"], "p": W.C2["p"]},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": r["cores"], "kind": "oracle", "sample": r["sample"]},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_gpu(args):
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_1308_1536_gb300 as m
+
+    m.load()
+    cfg = W.C2
+    N, p = args.N or cfg["N"], args.p or cfg["p"]
+    n = p // 32
+    x, y = W.cauchy_xy(N, cfg["seed"])
+    A = W.int_matrix(N, cfg["seed"] + 100).astype(np.int32)
+    xd, yd = torch.tensor(x, device=dev), torch.tensor(y, device=dev)
+    Ad = torch.tensor(A, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    hc = m.Mpdet(N, p, lastcol=True, stream=stream.cuda_stream)
+    hi = m.Mpdet(N, p, lastcol=True, stream=stream.cuda_stream)
+
+    def dev_out():
+        return (torch.empty(N, dtype=torch.int8, device=dev), torch.empty(N, dtype=torch.int64, device=dev),
+                torch.empty((N, n), dtype=torch.int32, device=dev))
+
+    Dc, Cc, Di, Ci = dev_out(), dev_out(), dev_out(), dev_out()
+
+    def step():
+        hc.set_cauchy(xd, yd)
+        hc.factor(out=Dc)
+        hc.lastcol_minors(out=Cc)
+        hi.set_i32(Ad)
+        hi.factor(out=Di)
+        hi.lastcol_minors(out=Ci)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    l0 = hc.profile_read()["launches"] + hi.profile_read()["launches"]
+    hc.profile(True)
+    hi.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    pc, pi = hc.profile_read(), hi.profile_read()
+    hc.profile(False)
+    hi.profile(False)
+    launches = (pc["launches"] + pi["launches"] - l0) // args.steps
+    assert hc.status()[0] == 0 and hi.status()[0] == 0
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    macs = step_limb_macs(N, p, 2)
+    value = macs * world / (ms / 1e3)
+
+    # end-to-end through the C ABI with host buffers (pinned inputs)
+    xh = torch.from_numpy(x).pin_memory()
+    yh = torch.from_numpy(y).pin_memory()
+    Ah = torch.from_numpy(A).pin_memory()
+
+    def step_e2e():
+        hc.set_cauchy(xh, yh)
+        rc1, _, D1 = hc.factor()
+        C1 = hc.lastcol_minors()
+        hi.set_i32(Ah)
+        rc2, _, D2 = hi.factor()
+        C2 = hi.lastcol_minors()
+        return D1, C1, D2, C2
+
+    step_e2e()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        outs = step_e2e()
+    barrier()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    h2d = x.nbytes + y.nbytes + A.nbytes
+    d2h = sum(a.nbytes for o in outs for a in o)
+
+    if rank == 0:
+        props = torch.cuda.get_device_properties(dev)
+        nsm = props.multi_processor_count
+        clocks = clk.summary()
+        peaks = measured_peaks()
+        fmax = float(clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0)
+        peak = nsm * 32 * fmax * 1e6
+        upd_ms = pc["update_ms"] + pi["update_ms"]
+        upd_macs = pc["update_limb_macs"] + pi["update_limb_macs"]
+        upd_launches = pc["update_launches"] + pi["update_launches"]
+        achieved = upd_macs / (upd_ms / 1e3)
+        tr = recorded_traffic()
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"cauchy+int N={N} p={p} lastcol: det, {N} leading minors and {N} "
+                                   "last-column minors of two matrices per step",
+                       "N": N, "p": p, "matrices": 2, "parallelism": f"replica x{world}",
+                       "l2": "inputs larger than L2 (each matrix %.0f MB in HBM)" % (N * N * (4 * n + 9) / 1e6)},
+            "e2e": {"value": macs * world / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms},
+            "gpu_launches": int(launches * args.steps),
+            "roofline": {"bound": "alu", "kernel": "k_update (Schur update)", "achieved": achieved / 1e12,
+                         "peak": peak / 1e12, "unit": "Tlimb-MAC/s", "frac": achieved / peak,
+                         "traffic": tr, "update_share": upd_ms / (ms * args.steps),
+                         "launches": int(upd_launches),
+                         "peak_basis": f"{nsm} SMs x 32 limb-MAC/clk x {fmax:.0f} MHz"},
+            "clocks": clocks,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            cb = oracle_sample()
+            cb.pop("seconds", None)
+            out["cpu_baseline"] = cb
+        print(json.dumps(out))
+    hc.close()
+    hi.close()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mpdet", choices=["mpdet", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--N", type=int, default=0, help="profiling aid: override N (default: the workload's 1024)")
+    ap.add_argument("--p", type=int, default=0, help="profiling aid: override p (default: the workload's 2048)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -147,6 +147,18 @@ int mpdet_resume(mpdet_t h, mpdet_numv A, mpdet_numv minors, int64_t k_done, int
 /* Steps completed so far (0..N). */
 int64_t mpdet_steps_done(mpdet_t h);
 
+/* Instrumentation (not part of the computation).  mpdet_profile(h, 1)
+ * brackets every later Schur-update launch (step 2.2.2, the dominant kernel)
+ * with a CUDA event pair on the handle's stream and resets the counters;
+ * mpdet_profile(h, 0) stops.  mpdet_profile_read synchronises the stream and
+ * returns the summed device time of those launches (ms), their number, their
+ * algorithmic work in limb multiply-accumulates (products * n^2) and the
+ * total number of kernels this handle has enqueued since creation.  Any
+ * output pointer may be NULL. */
+int mpdet_profile(mpdet_t h, int enable);
+int mpdet_profile_read(mpdet_t h, double* update_ms, int64_t* update_launches, double* update_limb_macs,
+                       int64_t* launches);
+
 /* Release the handle and its device memory (NULL is accepted). */
 int mpdet_free(mpdet_t h);
 

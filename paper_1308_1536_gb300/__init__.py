@@ -72,6 +72,9 @@ def load(build_if_missing: bool = True):
         "mpdet_free": ([P], ctypes.c_int),
         "mpdet_last_error": ([P], ctypes.c_char_p),
         "mpdet_geometry": ([i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)], ctypes.c_int),
+        "mpdet_profile": ([P, ctypes.c_int], ctypes.c_int),
+        "mpdet_profile_read": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
+                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -100,10 +103,15 @@ def _is_dev(a) -> bool:
     return hasattr(a, "is_cuda") and bool(a.is_cuda)
 
 
+def _is_torch(a) -> bool:
+    return hasattr(a, "data_ptr") and hasattr(a, "is_cuda")
+
+
 def _ptr(a):
     if a is None:
         return None
-    if _is_dev(a):
+    if _is_torch(a):  # CUDA tensor (device pointer) or pinned / CPU tensor (host pointer)
+        assert a.is_contiguous()
         return ctypes.c_void_p(a.data_ptr())
     assert isinstance(a, np.ndarray) and a.flags.c_contiguous
     return a.ctypes.data_as(ctypes.c_void_p)
@@ -168,21 +176,21 @@ class Mpdet:
     # -- inputs -------------------------------------------------------------
     def set_f64(self, A, ld=None):
         dev = _is_dev(A)
-        if not dev:
+        if not dev and not _is_torch(A):
             A = np.ascontiguousarray(A, np.float64)
         ld = self.N if ld is None else ld
         self._check(self.lib.mpdet_set_f64(self.h, _ptr(A), ld, int(dev)), "set_f64")
 
     def set_i32(self, A, ld=None):
         dev = _is_dev(A)
-        if not dev:
+        if not dev and not _is_torch(A):
             A = np.ascontiguousarray(A, np.int32)
         ld = self.N if ld is None else ld
         self._check(self.lib.mpdet_set_i32(self.h, _ptr(A), ld, int(dev)), "set_i32")
 
     def set_cauchy(self, x, y):
         dev = _is_dev(x)
-        if not dev:
+        if not dev and not _is_torch(x):
             x = np.ascontiguousarray(x, np.float64)
             y = np.ascontiguousarray(y, np.float64)
         self._check(self.lib.mpdet_set_cauchy(self.h, _ptr(x), _ptr(y), int(dev)), "set_cauchy")
@@ -242,3 +250,14 @@ class Mpdet:
 
     def steps_done(self) -> int:
         return int(self.lib.mpdet_steps_done(self.h))
+
+    # -- instrumentation ----------------------------------------------------
+    def profile(self, enable: bool = True):
+        self._check(self.lib.mpdet_profile(self.h, int(enable)), "profile")
+
+    def profile_read(self):
+        """dict(update_ms, update_launches, update_limb_macs, launches)."""
+        ms, nl, macs, total = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_int64()
+        self._check(self.lib.mpdet_profile_read(self.h, ctypes.byref(ms), ctypes.byref(nl), ctypes.byref(macs),
+                                                ctypes.byref(total)), "profile_read")
+        return dict(update_ms=ms.value, update_launches=nl.value, update_limb_macs=macs.value, launches=total.value)

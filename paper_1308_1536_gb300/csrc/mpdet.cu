@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "../../include/mpdet.h"
 #include "kernelset.h"
@@ -38,6 +39,15 @@ struct mpdet_ctx {
   int64_t k_done = 0;
   bool have_matrix = false;
   char err[512] = {0};
+  // instrumentation: kernel launches enqueued, and optional event pairs
+  // around every Schur-update launch
+  int64_t launches = 0;
+  bool profile = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  double upd_ms = 0.0;
+  int64_t upd_launches = 0;
+  double upd_products = 0.0;
 };
 
 static const char* g_static_err = "no handle";
@@ -145,6 +155,7 @@ extern "C" int mpdet_free(mpdet_t h) {
   if (h->status) cudaFree(h->status);
   if (h->zero_k) cudaFree(h->zero_k);
   if (h->stage) cudaFree(h->stage);
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   delete h;
   return MPDET_OK;
 }
@@ -195,6 +206,7 @@ static int set_dense(mpdet_t h, const void* A, int64_t ld, int device_ptr, int k
   int rc = reset_state(h);
   if (rc) return rc;
   CU(h, h->ks->lift(src, kind, ld, h->N, h->X, h->p, h->nsm, h->stream));
+  h->launches += 1;
   return finish_call(h, device_ptr);
 }
 
@@ -250,20 +262,73 @@ extern "C" int mpdet_set_cauchy(mpdet_t h, const double* x, const double* y, int
   int rc = reset_state(h);
   if (rc) return rc;
   CU(h, h->ks->cauchy(dx, dy, h->N, h->X, h->p, h->nsm, h->stream));
+  h->launches += 1;
   return finish_call(h, device_ptr);
+}
+
+static int next_event(mpdet_t h, cudaEvent_t* ev) {
+  if (h->ev_used == h->ev_pool.size()) {
+    cudaEvent_t e;
+    CU(h, cudaEventCreate(&e));
+    h->ev_pool.push_back(e);
+  }
+  *ev = h->ev_pool[h->ev_used++];
+  return MPDET_OK;
 }
 
 // enqueue steps k (0-based) in [k0, k1)
 static int run_steps(mpdet_t h, int64_t k0, int64_t k1) {
   const int lastcol = (h->flags & MPDET_LASTCOL) ? 1 : 0;
+  const int64_t N = h->N;
   for (int64_t k = k0; k < k1; ++k) {
-    CU(h, h->ks->pivot(h->X, h->N, k, h->D, h->R, h->status, h->zero_k, h->p, h->stream));
-    if (k < h->N - 1) {
-      CU(h, h->ks->mult(h->X, h->N, k, h->R, h->Z, h->status, h->p, lastcol, h->stream));
-      CU(h, h->ks->update(h->X, h->N, k, h->Z, h->status, h->p, lastcol, h->nsm, h->stream));
+    CU(h, h->ks->pivot(h->X, N, k, h->D, h->R, h->status, h->zero_k, h->p, h->stream));
+    h->launches += 1;
+    if (k < N - 1) {
+      CU(h, h->ks->mult(h->X, N, k, h->R, h->Z, h->status, h->p, lastcol, h->stream));
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      if (h->profile) {
+        int rc = next_event(h, &e0);
+        if (!rc) rc = next_event(h, &e1);
+        if (rc) return rc;
+        CU(h, cudaEventRecord(e0, h->stream));
+      }
+      CU(h, h->ks->update(h->X, N, k, h->Z, h->status, h->p, lastcol, h->nsm, h->stream));
+      if (h->profile) {
+        CU(h, cudaEventRecord(e1, h->stream));
+        h->upd_launches += 1;
+        h->upd_products += (double)(N - k - 1) * (double)(lastcol ? N - 1 : N - k - 1);
+      }
+      h->launches += 2;
     }
   }
   h->k_done = k1;
+  return MPDET_OK;
+}
+
+extern "C" int mpdet_profile(mpdet_t h, int enable) {
+  if (!h) return MPDET_EINVAL;
+  h->profile = enable != 0;
+  h->ev_used = 0;
+  h->upd_ms = 0.0;
+  h->upd_launches = 0;
+  h->upd_products = 0.0;
+  return MPDET_OK;
+}
+
+extern "C" int mpdet_profile_read(mpdet_t h, double* update_ms, int64_t* update_launches, double* update_limb_macs,
+                                  int64_t* launches) {
+  if (!h) return MPDET_EINVAL;
+  CU(h, cudaStreamSynchronize(h->stream));
+  for (size_t i = 0; i + 1 < h->ev_used; i += 2) {
+    float ms = 0.f;
+    CU(h, cudaEventElapsedTime(&ms, h->ev_pool[i], h->ev_pool[i + 1]));
+    h->upd_ms += ms;
+  }
+  h->ev_used = 0;
+  if (update_ms) *update_ms = h->upd_ms;
+  if (update_launches) *update_launches = h->upd_launches;
+  if (update_limb_macs) *update_limb_macs = h->upd_products * (double)h->n * (double)h->n;
+  if (launches) *launches = h->launches;
   return MPDET_OK;
 }
 
@@ -343,11 +408,13 @@ extern "C" int mpdet_lastcol_minors(mpdet_t h, mpdet_numv out, int normalised, i
   if (normalised) {
     // F = RN(1 / l_N1) into R; status 7 if l_N1 == 0
     CU(h, h->ks->recip1(h->X, (N - 1) * N, h->R, h->status, MPDET_EZERODIV, h->stream));
+    h->launches += 1;
     F = h->R;
   } else {
     F = MpArr{h->D.s + (N - 2), h->D.e + (N - 2), h->D.m + (size_t)(N - 2) * h->n};
   }
   CU(h, h->ks->lastcol(h->X, N, F, h->T, normalised, h->stream));
+  h->launches += 1;
   if (normalised) {
     int sts[4] = {0};
     CU(h, cudaMemcpyAsync(sts, h->status, 16, cudaMemcpyDeviceToHost, h->stream));
