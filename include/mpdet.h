@@ -117,7 +117,8 @@ int mpdet_factor_range(mpdet_t h, int64_t k0, int64_t k1);
 int mpdet_factor(mpdet_t h, mpdet_numv det, mpdet_numv minors, int64_t* zero_pivot_k, int device_ptr);
 
 /* Synchronise the handle's stream and read the status of the last
- * factorisation: MPDET_OK or MPDET_EZEROPIVOT, zero_pivot_k as above. */
+ * factorisation: MPDET_OK, MPDET_EZEROPIVOT (zero_pivot_k as above) or
+ * MPDET_EZERODIV (normalised minors with l_N1 = 0, device mode). */
 int mpdet_status(mpdet_t h, int64_t* zero_pivot_k);
 
 /* Signed minors of the last column (eq. minorsdef):
@@ -127,7 +128,9 @@ int mpdet_status(mpdet_t h, int64_t* zero_pivot_k);
  * formed as RN(l_Nj * RN(1/l_N1)) with delta_{N,1} = 1 exactly.
  * Needs MPDET_LASTCOL and a completed factorisation without a zero pivot
  * before step N.  Errors: MPDET_ESTATE, MPDET_EZERODIV (normalised with
- * l_N1 = 0). */
+ * l_N1 = 0).  With device_ptr = 1 nothing is synchronised: a zero pivot or
+ * l_N1 = 0 leaves the outputs undefined and is reported by mpdet_status
+ * (MPDET_EZEROPIVOT or MPDET_EZERODIV). */
 int mpdet_lastcol_minors(mpdet_t h, mpdet_numv out, int normalised, int device_ptr);
 
 /* Copy out the leading minors computed so far (D_1..D_N; entries of steps not
@@ -146,6 +149,13 @@ int mpdet_resume(mpdet_t h, mpdet_numv A, mpdet_numv minors, int64_t k_done, int
 
 /* Steps completed so far (0..N). */
 int64_t mpdet_steps_done(mpdet_t h);
+
+/* Tuning knobs (results are identical for every setting; only speed
+ * changes).  MPDET_TUNE_UPDATE_VARIANT selects the register budget of the
+ * Schur-update kernel: value v in 0..3 compiles it for at least 3 + v
+ * resident 128-thread blocks per SM.  Errors: MPDET_EINVAL. */
+enum { MPDET_TUNE_UPDATE_VARIANT = 1 };
+int mpdet_tune(mpdet_t h, int param, int value);
 
 /* Instrumentation (not part of the computation).  mpdet_profile(h, 1)
  * brackets every later Schur-update launch (step 2.2.2, the dominant kernel)

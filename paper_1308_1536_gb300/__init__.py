@@ -73,6 +73,7 @@ def load(build_if_missing: bool = True):
         "mpdet_last_error": ([P], ctypes.c_char_p),
         "mpdet_geometry": ([i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)], ctypes.c_int),
         "mpdet_profile": ([P, ctypes.c_int], ctypes.c_int),
+        "mpdet_tune": ([P, ctypes.c_int, ctypes.c_int], ctypes.c_int),
         "mpdet_profile_read": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)], ctypes.c_int),
     }
@@ -250,6 +251,10 @@ class Mpdet:
 
     def steps_done(self) -> int:
         return int(self.lib.mpdet_steps_done(self.h))
+
+    # -- tuning (bit-identical results for every setting) -------------------
+    def tune(self, update_variant: int):
+        self._check(self.lib.mpdet_tune(self.h, 1, int(update_variant)), "tune")
 
     # -- instrumentation ----------------------------------------------------
     def profile(self, enable: bool = True):

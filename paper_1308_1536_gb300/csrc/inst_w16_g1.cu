@@ -1,0 +1,9 @@
+// Kernel instantiation: 16 limbs per lane, 1 lanes per number (n = 16).
+#include "kernels.cuh"
+
+namespace mpd {
+const KernelSet* kernel_set_w16_g1() {
+  static const KernelSet s = Launch<16, 1>::make();
+  return &s;
+}
+}  // namespace mpd

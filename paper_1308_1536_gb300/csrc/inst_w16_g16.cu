@@ -1,0 +1,9 @@
+// Kernel instantiation: 16 limbs per lane, 16 lanes per number (n = 256).
+#include "kernels.cuh"
+
+namespace mpd {
+const KernelSet* kernel_set_w16_g16() {
+  static const KernelSet s = Launch<16, 16>::make();
+  return &s;
+}
+}  // namespace mpd

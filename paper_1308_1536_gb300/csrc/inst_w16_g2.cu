@@ -1,0 +1,9 @@
+// Kernel instantiation: 16 limbs per lane, 2 lanes per number (n = 32).
+#include "kernels.cuh"
+
+namespace mpd {
+const KernelSet* kernel_set_w16_g2() {
+  static const KernelSet s = Launch<16, 2>::make();
+  return &s;
+}
+}  // namespace mpd

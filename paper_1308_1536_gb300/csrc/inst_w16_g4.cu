@@ -1,0 +1,9 @@
+// Kernel instantiation: 16 limbs per lane, 4 lanes per number (n = 64).
+#include "kernels.cuh"
+
+namespace mpd {
+const KernelSet* kernel_set_w16_g4() {
+  static const KernelSet s = Launch<16, 4>::make();
+  return &s;
+}
+}  // namespace mpd

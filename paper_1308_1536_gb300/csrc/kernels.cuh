@@ -298,9 +298,9 @@ __global__ void k_mult(MpArr X, int64_t N, int64_t k, MpArr R, MpArr Z, const in
 // element x_kj's slice in registers; the block walks rows [i0, i1) with the
 // multipliers z_i staged in shared memory (a broadcast read for the groups).
 // ---------------------------------------------------------------------------
-template <int W, int G>
-__global__ void __launch_bounds__(128) k_update(MpArr X, int64_t N, int64_t k, MpArr Z, const int* status, int p,
-                                               int lastcol, int rows_per_cta) {
+template <int W, int G, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_update(MpArr X, int64_t N, int64_t k, MpArr Z, const int* status,
+                                                     int p, int lastcol, int rows_per_cta) {
   constexpr int n = W * G;
   constexpr int SW = Scratch<W, G>::words;
   extern __shared__ __align__(16) uint32_t smem[];
@@ -340,11 +340,11 @@ __global__ void __launch_bounds__(128) k_update(MpArr X, int64_t N, int64_t k, M
   for (int r = 0; r < nr; ++r) {
     const int64_t ij = (i0 + r) * N + j;
     uint32_t Xv[W], T[W];
-    load_slice<W>(X.m + ij * n + gp.g * W, Xv);
     int8_t xs = X.s[ij];
     int64_t xe = X.e[ij];
     const int64_t zer = ze_s[r];
     int adj = mul_round<W, G>(gp, Bk, zbuf + r * n, T);
+    load_slice<W>(X.m + ij * n + gp.g * W, Xv);
     const bool tz = (zer == ZEXP) || (be == ZEXP);
     const int8_t ts = tz ? 0 : (int8_t)(zs_s[r] ^ bs);
     const int64_t te = tz ? ZEXP : zer + be + adj;
@@ -370,9 +370,10 @@ __global__ void __launch_bounds__(128) k_update(MpArr X, int64_t N, int64_t k, M
 // F holds f (one number).  Threads: groups over j.
 // ---------------------------------------------------------------------------
 template <int W, int G>
-__global__ void k_lastcol(MpArr X, int64_t N, MpArr F, MpArr out, int normalised) {
+__global__ void k_lastcol(MpArr X, int64_t N, MpArr F, MpArr out, int normalised, const int* status) {
   constexpr int n = W * G;
   __shared__ __align__(16) uint32_t fm[n];
+  if (status_set(status)) return;  // zero pivot or zero l_N1: outputs are not defined
   Grp<G> gp;
   for (int q = threadIdx.x; q < n; q += blockDim.x) fm[q] = F.m[q];
   __syncthreads();
@@ -492,6 +493,7 @@ struct Launch {
   static size_t update_smem(int rows_per_cta) {
     return (size_t)(rows_per_cta * n + upd_pad4(2 * rows_per_cta) + upd_pad4((rows_per_cta + 3) / 4) + (NT / G) * SW) * 4;
   }
+  template <int MINB>
   static cudaError_t update(MpArr X, int64_t N, int64_t k, MpArr Z, const int* status, int p, int lastcol, int nsm,
                             cudaStream_t st) {
     int64_t rows = N - k - 1;
@@ -509,14 +511,15 @@ struct Launch {
     if (rpc < 1) rpc = 1;
     int64_t by = (rows + rpc - 1) / rpc;
     size_t sm = update_smem((int)rpc);
-    cudaFuncSetAttribute(k_update<W, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(k_update<W, G, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     dim3 grid((unsigned)bx, (unsigned)by);
-    k_update<W, G><<<grid, NT, sm, st>>>(X, N, k, Z, status, p, lastcol, (int)rpc);
+    k_update<W, G, MINB><<<grid, NT, sm, st>>>(X, N, k, Z, status, p, lastcol, (int)rpc);
     return cudaGetLastError();
   }
-  static cudaError_t lastcol(MpArr X, int64_t N, MpArr F, MpArr out, int normalised, cudaStream_t st) {
+  static cudaError_t lastcol(MpArr X, int64_t N, MpArr F, MpArr out, int normalised, const int* status,
+                             cudaStream_t st) {
     int64_t blocks = (N + NT / G - 1) / (NT / G);
-    k_lastcol<W, G><<<(unsigned)blocks, NT, 0, st>>>(X, N, F, out, normalised);
+    k_lastcol<W, G><<<(unsigned)blocks, NT, 0, st>>>(X, N, F, out, normalised, status);
     return cudaGetLastError();
   }
   static cudaError_t recip1(MpArr src, int64_t idx, MpArr dst, int* status, int code, cudaStream_t st) {
@@ -531,7 +534,10 @@ struct Launch {
     s.cauchy = &cauchy;
     s.pivot = &pivot;
     s.mult = &mult;
-    s.update = &update;
+    s.update[0] = &update<3>;
+    s.update[1] = &update<4>;
+    s.update[2] = &update<5>;
+    s.update[3] = &update<6>;
     s.lastcol = &lastcol;
     s.recip1 = &recip1;
     return s;

@@ -22,19 +22,30 @@ struct KernelSet {
                        cudaStream_t st);
   cudaError_t (*mult)(MpArr X, int64_t N, int64_t k, MpArr R, MpArr Z, const int* status, int p, int lastcol,
                       cudaStream_t st);
-  cudaError_t (*update)(MpArr X, int64_t N, int64_t k, MpArr Z, const int* status, int p, int lastcol, int nsm,
-                        cudaStream_t st);
-  cudaError_t (*lastcol)(MpArr X, int64_t N, MpArr F, MpArr out, int normalised, cudaStream_t st);
+  // Schur update, one entry per register budget: variant v is compiled for
+  // at least 3 + v resident 128-thread blocks per SM
+  static constexpr int kUpdateVariants = 4;
+  cudaError_t (*update[kUpdateVariants])(MpArr X, int64_t N, int64_t k, MpArr Z, const int* status, int p,
+                                         int lastcol, int nsm, cudaStream_t st);
+  cudaError_t (*lastcol)(MpArr X, int64_t N, MpArr F, MpArr out, int normalised, const int* status,
+                         cudaStream_t st);
   cudaError_t (*recip1)(MpArr src, int64_t idx, MpArr dst, int* status, int code, cudaStream_t st);
 };
 
 // Kernel set for n = p/32 limbs, or nullptr if this n is not instantiated.
 const KernelSet* kernel_set_for(int n);
 
-// per-translation-unit registries
-const KernelSet* kernel_set_w4(int G);
-const KernelSet* kernel_set_w8(int G);
-const KernelSet* kernel_set_w16(int G);
-const KernelSet* kernel_set_w32(int G);
+// one translation unit per (W, G): inst_w<W>_g<G>.cu
+#define MPD_DECLARE_SET(W, G) const KernelSet* kernel_set_w##W##_g##G();
+MPD_DECLARE_SET(4, 1)
+MPD_DECLARE_SET(8, 1)
+MPD_DECLARE_SET(16, 1)
+MPD_DECLARE_SET(16, 2)
+MPD_DECLARE_SET(16, 4)
+MPD_DECLARE_SET(16, 8)
+MPD_DECLARE_SET(16, 16)
+MPD_DECLARE_SET(16, 32)
+MPD_DECLARE_SET(32, 32)
+#undef MPD_DECLARE_SET
 
 }  // namespace mpd

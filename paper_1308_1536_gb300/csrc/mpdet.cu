@@ -16,11 +16,24 @@ using mpd::MpArr;
 
 namespace mpd {
 const KernelSet* kernel_set_for(int n) {
-  if (n == 4) return kernel_set_w4(1);
-  if (n == 8) return kernel_set_w8(1);
-  if (n >= 16 && n <= 512 && (n & (n - 1)) == 0) return kernel_set_w16(n / 16);
-  if (n == 1024) return kernel_set_w32(32);
-  return nullptr;
+  switch (n) {
+    case 4: return kernel_set_w4_g1();
+    case 8: return kernel_set_w8_g1();
+    case 16: return kernel_set_w16_g1();
+    case 32: return kernel_set_w16_g2();
+    case 64: return kernel_set_w16_g4();
+    case 128: return kernel_set_w16_g8();
+    case 256: return kernel_set_w16_g16();
+    case 512: return kernel_set_w16_g32();
+    case 1024: return kernel_set_w32_g32();
+    default: return nullptr;
+  }
+}
+
+// Default register-budget variant of the Schur update per limb count.
+int default_update_variant(int n) {
+  (void)n;
+  return 1;
 }
 }  // namespace mpd
 
@@ -37,6 +50,7 @@ struct mpdet_ctx {
   void* stage = nullptr;  // device staging for host inputs
   size_t stage_bytes = 0;
   int64_t k_done = 0;
+  int upd_variant = 1;
   bool have_matrix = false;
   char err[512] = {0};
   // instrumentation: kernel launches enqueued, and optional event pairs
@@ -119,6 +133,7 @@ extern "C" int mpdet_create(int64_t N, int32_t p_bits, uint32_t flags, void* cud
   h->flags = flags;
   h->stream = (cudaStream_t)cuda_stream;
   h->ks = mpd::kernel_set_for(h->n);
+  h->upd_variant = mpd::default_update_variant(h->n);
   int rc = MPDET_OK;
   if (cudaGetDevice(&h->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
@@ -292,7 +307,7 @@ static int run_steps(mpdet_t h, int64_t k0, int64_t k1) {
         if (rc) return rc;
         CU(h, cudaEventRecord(e0, h->stream));
       }
-      CU(h, h->ks->update(h->X, N, k, h->Z, h->status, h->p, lastcol, h->nsm, h->stream));
+      CU(h, h->ks->update[h->upd_variant](h->X, N, k, h->Z, h->status, h->p, lastcol, h->nsm, h->stream));
       if (h->profile) {
         CU(h, cudaEventRecord(e1, h->stream));
         h->upd_launches += 1;
@@ -303,6 +318,18 @@ static int run_steps(mpdet_t h, int64_t k0, int64_t k1) {
   }
   h->k_done = k1;
   return MPDET_OK;
+}
+
+extern "C" int mpdet_tune(mpdet_t h, int param, int value) {
+  if (!h) return MPDET_EINVAL;
+  switch (param) {
+    case MPDET_TUNE_UPDATE_VARIANT:
+      if (value < 0 || value >= KernelSet::kUpdateVariants) return fail(h, MPDET_EINVAL, "tune: variant %d", value);
+      h->upd_variant = value;
+      return MPDET_OK;
+    default:
+      return fail(h, MPDET_EINVAL, "tune: unknown parameter %d", param);
+  }
 }
 
 extern "C" int mpdet_profile(mpdet_t h, int enable) {
@@ -353,6 +380,7 @@ extern "C" int mpdet_status(mpdet_t h, int64_t* zero_pivot_k) {
   CU(h, cudaStreamSynchronize(h->stream));
   if (zero_pivot_k) *zero_pivot_k = zk[0];
   if (st[0] == MPDET_EZEROPIVOT) return fail(h, MPDET_EZEROPIVOT, "zero pivot at k = %lld", (long long)zk[0]);
+  if (st[0] == MPDET_EZERODIV) return fail(h, MPDET_EZERODIV, "normalised minors: l_N1 is zero");
   return st[0];
 }
 
@@ -386,10 +414,12 @@ extern "C" int mpdet_lastcol_minors(mpdet_t h, mpdet_numv out, int normalised, i
   if (!h) return MPDET_EINVAL;
   if (!(h->flags & MPDET_LASTCOL)) return fail(h, MPDET_ESTATE, "lastcol_minors: handle created without MPDET_LASTCOL");
   if (!h->have_matrix || h->k_done != h->N) return fail(h, MPDET_ESTATE, "lastcol_minors: factorisation not complete");
-  int64_t zk = 0;
-  int st = mpdet_status(h, &zk);
-  if (st == MPDET_EZEROPIVOT) return fail(h, MPDET_EZEROPIVOT, "lastcol_minors: zero pivot at k = %lld", (long long)zk);
-  if (st) return st;
+  if (!device_ptr) {  // device mode: the kernels skip on a bad status, read later by mpdet_status
+    int64_t zk = 0;
+    int st = mpdet_status(h, &zk);
+    if (st == MPDET_EZEROPIVOT) return fail(h, MPDET_EZEROPIVOT, "lastcol_minors: zero pivot at k = %lld", (long long)zk);
+    if (st) return st;
+  }
   const int64_t N = h->N;
   if (N == 1) {  // C_11 = D_0 = 1, delta_{1,1} = 1
     uint32_t* one = new uint32_t[h->n]();
@@ -413,9 +443,9 @@ extern "C" int mpdet_lastcol_minors(mpdet_t h, mpdet_numv out, int normalised, i
   } else {
     F = MpArr{h->D.s + (N - 2), h->D.e + (N - 2), h->D.m + (size_t)(N - 2) * h->n};
   }
-  CU(h, h->ks->lastcol(h->X, N, F, h->T, normalised, h->stream));
+  CU(h, h->ks->lastcol(h->X, N, F, h->T, normalised, h->status, h->stream));
   h->launches += 1;
-  if (normalised) {
+  if (normalised && !device_ptr) {
     int sts[4] = {0};
     CU(h, cudaMemcpyAsync(sts, h->status, 16, cudaMemcpyDeviceToHost, h->stream));
     CU(h, cudaStreamSynchronize(h->stream));
