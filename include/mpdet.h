@@ -68,7 +68,8 @@ enum {
   MPDET_EZEROPIVOT = 4,  /* exact zero pivot a_kk at k < N: elimination stopped */
   MPDET_ETIMEOUT = 5,    /* a bounded device wait gave up */
   MPDET_ESTATE = 6,      /* call out of order (e.g. minors before the factorisation) */
-  MPDET_EZERODIV = 7     /* normalised minors requested but l_N1 (hence C_1N) is zero */
+  MPDET_EZERODIV = 7,    /* normalised minors requested but l_N1 (hence C_1N) is zero */
+  MPDET_ENOSCRATCH = 8   /* problem larger than mpdet_factor_noalloc's static working memory */
 };
 
 enum { MPDET_LASTCOL = 1 };
@@ -168,6 +169,41 @@ int mpdet_tune(mpdet_t h, int param, int value);
 int mpdet_profile(mpdet_t h, int enable);
 int mpdet_profile_read(mpdet_t h, double* update_ms, int64_t* update_launches, double* update_limb_macs,
                        int64_t* launches);
+
+/* Factorisation that allocates no memory.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory, such as
+ * code running while a stream is captured into a CUDA graph, host frameworks
+ * that give a plugin its buffers and forbid it its own allocations, and
+ * latency-bound loops that cannot take an allocation mid-step.
+ *
+ * It runs the same kernels and the same rounded operations as mpdet_factor
+ * (results are bit-identical), with all working memory (the in-place matrix,
+ * the multipliers, the reciprocal, the status words) in one static device
+ * array of MPDET_NOALLOC_SCRATCH_BYTES bytes inside the library, which every
+ * GPU that loads the library holds until the process exits.  That bounds the
+ * problem size: N^2 (4n + 9) + N (4n + 9) + 4n + ~2.5 KB of padding <= 16 MiB
+ * with n = p/32 (about N <= 478 at p = 512, N <= 251 at p = 2048); larger
+ * problems return MPDET_ENOSCRATCH and should use mpdet_create.
+ *
+ * Arguments (all device memory of the current device, 16-byte aligned):
+ *   A       N*N numbers, row-major, read only (copied into the scratch);
+ *   minors  N numbers, receives D_1..D_N (D_N = det);
+ *   lastcol N numbers, receives C_1N..C_NN when flags has MPDET_LASTCOL
+ *           (may be NULL pointers otherwise).
+ * zero_pivot_k (host, may be NULL) and the return value are as for
+ * mpdet_factor.  The call is enqueued on cuda_stream and synchronises that
+ * stream before it returns.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture.  Every call uses the same array and the array keeps the
+ * previous call's contents; the call clears what has to start at zero.
+ * Calls that overlap on the GPU (other threads or streams, another device's
+ * calls excepted) race on the array and give undefined results.
+ * Errors: MPDET_EINVAL, MPDET_ENOSCRATCH, MPDET_ECUDA, MPDET_EZEROPIVOT. */
+#define MPDET_NOALLOC_SCRATCH_BYTES (16u << 20)
+int mpdet_factor_noalloc(int64_t N, int32_t p_bits, uint32_t flags, mpdet_numv A, mpdet_numv minors,
+                         mpdet_numv lastcol, int64_t* zero_pivot_k, void* cuda_stream);
 
 /* Release the handle and its device memory (NULL is accepted). */
 int mpdet_free(mpdet_t h);

@@ -21,10 +21,10 @@ import numpy as np
 from . import build as _build
 
 ZEXP = np.iinfo(np.int64).min
-OK, EINVAL, ENOMEM, ECUDA, EZEROPIVOT, ETIMEOUT, ESTATE, EZERODIV = range(8)
+OK, EINVAL, ENOMEM, ECUDA, EZEROPIVOT, ETIMEOUT, ESTATE, EZERODIV, ENOSCRATCH = range(9)
 LASTCOL = 1
 _NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EZEROPIVOT", 5: "ETIMEOUT", 6: "ESTATE",
-          7: "EZERODIV"}
+          7: "EZERODIV", 8: "ENOSCRATCH"}
 
 _lib = None
 
@@ -74,6 +74,7 @@ def load(build_if_missing: bool = True):
         "mpdet_geometry": ([i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)], ctypes.c_int),
         "mpdet_profile": ([P, ctypes.c_int], ctypes.c_int),
         "mpdet_tune": ([P, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+        "mpdet_factor_noalloc": ([i64, i32, u32, NumV, NumV, NumV, ctypes.POINTER(i64), P], ctypes.c_int),
         "mpdet_profile_read": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)], ctypes.c_int),
     }
@@ -93,6 +94,23 @@ def geometry(p: int):
     if rc:
         raise MpdetError(rc, f"unsupported precision p = {p}")
     return n.value, W.value, G.value
+
+
+def factor_noalloc(A, N: int, p: int, minors, lastcol=None, stream=None):
+    """Elimination with no allocation (mpdet_factor_noalloc): A, minors and
+    lastcol are triples of CUDA tensors (device memory); the library keeps its
+    working memory in a static device array.  Returns (status, zero_k)."""
+    lib = load()
+    if stream is None:
+        import torch
+
+        stream = torch.cuda.current_stream().cuda_stream
+    zk = ctypes.c_int64(0)
+    rc = lib.mpdet_factor_noalloc(int(N), int(p), LASTCOL if lastcol is not None else 0, _numv(A), _numv(minors),
+                                  _numv(lastcol), ctypes.byref(zk), ctypes.c_void_p(stream or 0))
+    if rc not in (OK, EZEROPIVOT):
+        raise MpdetError(rc, f"factor_noalloc(N={N}, p={p})")
+    return rc, int(zk.value)
 
 
 def empty(count: int, p: int):
