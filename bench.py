@@ -60,6 +60,11 @@ def step_limb_macs(N: int, p: int, matrices: int = 2) -> float:
     return float(matrices) * elim_products(N, True) * n * n
 
 
+def batch_products(Ns) -> int:
+    """p x p-bit products of a batch (no L): multipliers, updates, D_k."""
+    return int(sum(elim_products(int(N), False) for N in Ns))
+
+
 def kernel_source_sha() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1308_1536_gb300", "csrc")
@@ -192,6 +197,77 @@ def run_reference(args):
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
     return 0
+
+
+def bench_batch(args, dev, m):
+    """Workload C3: 4096 matrices, N ~ U[8, 256], half Cauchy half integer,
+    p = 1024, det and leading minors of each, one persistent launch per step
+    (inputs resident in HBM as p-bit numbers; the timed step copies them to
+    the working array and factors).  The single-matrix path is timed on a
+    sample of the same matrices at the same p for comparison."""
+    import torch
+
+    cfg = W.C3
+    p = cfg["p"]
+    n = p // 32
+    Ns, kinds, seeds = W.batch_sizes(cfg["count"], cfg["Nmin"], cfg["Nmax"], cfg["seed"])
+    b = m.Batch(Ns, p, stream=torch.cuda.current_stream(dev).cuda_stream)
+    inputs = []
+    for i in range(len(Ns)):
+        N = int(Ns[i])
+        if kinds[i] == "cauchy":
+            d = W.cauchy_xy(N, int(seeds[i]))
+            b.set_cauchy(i, *d)
+        else:
+            d = W.int_matrix(N, int(seeds[i]))
+            b.set_i32(i, d)
+        inputs.append(d)
+    tot = int(np.sum(Ns))
+    out = (torch.empty(tot, dtype=torch.int8, device=dev), torch.empty(tot, dtype=torch.int64, device=dev),
+           torch.empty((tot, n), dtype=torch.int32, device=dev))
+    zk = torch.empty(len(Ns), dtype=torch.int64, device=dev)
+    for _ in range(args.warmup):
+        b.factor(out=out, zero_k=zk)
+    torch.cuda.synchronize(dev)
+    l0 = b.launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        b.factor(out=out, zero_k=zk)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / args.steps
+    launches = (b.launches() - l0) // args.steps
+    b.close()
+    macs = batch_products(Ns) * n * n
+    # single-matrix path on a sample (every 16th matrix), same p, same GPU
+    sample = list(range(0, len(Ns), 16))
+    handles = {}
+    t_single = 0.0
+    for rep in range(2):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for i in sample:
+            N = int(Ns[i])
+            h = handles.get(N)
+            if h is None:
+                h = handles[N] = m.Mpdet(N, p, stream=torch.cuda.current_stream(dev).cuda_stream)
+            if kinds[i] == "cauchy":
+                h.set_cauchy(*inputs[i])
+            else:
+                h.set_i32(inputs[i])
+            h.factor_range(0, N)
+        torch.cuda.synchronize(dev)
+        t_single = time.perf_counter() - t0  # second repetition counts (handles warm)
+    for h in handles.values():
+        h.close()
+    single_dets = len(sample) / t_single
+    return {"workload": "4096 matrices N~U[8,256], half Cauchy half integer, p=1024: det + leading minors",
+            "dets_per_s": len(Ns) / (ms / 1e3), "ms_per_step": ms, "limb_macs_per_s": macs / (ms / 1e3),
+            "gpu_launches_per_step": int(launches),
+            "single_path_dets_per_s": single_dets,
+            "vs_single_path": (len(Ns) / (ms / 1e3)) / single_dets,
+            "single_path_sample": f"every 16th matrix ({len(sample)}), set + factor per matrix, includes input lift"}
 
 
 # ---------------------------------------------------------------------------
@@ -359,6 +435,8 @@ def run_gpu(args):
                          "peak_basis": f"{nsm} SMs x 32 limb-MAC/clk x {fmax:.0f} MHz"},
             "clocks": clocks,
         }
+        if not args.no_extras:
+            out["batch"] = bench_batch(args, dev, m)
         if world == 1 and not args.no_cpu_baseline:
             cb = oracle_sample()
             cb.pop("seconds", None)
@@ -380,6 +458,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mpdet", choices=["mpdet", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batch and adjoint workloads")
     ap.add_argument("--N", type=int, default=0, help="profiling aid: override N (default: the workload's 1024)")
     ap.add_argument("--p", type=int, default=0, help="profiling aid: override p (default: the workload's 2048)")
     ap.add_argument("--update-variant", type=int, default=-1, help="tuning aid: Schur-update register budget 0..3")

@@ -205,6 +205,35 @@ int mpdet_profile_read(mpdet_t h, double* update_ms, int64_t* update_launches, d
 int mpdet_factor_noalloc(int64_t N, int32_t p_bits, uint32_t flags, mpdet_numv A, mpdet_numv minors,
                          mpdet_numv lastcol, int64_t* zero_pivot_k, void* cuda_stream);
 
+/* ---- Batches (step a7): many independent matrices of uneven N ------------
+ * The paper needs the minors for a whole series of sizes N = 2, 3, ... and for
+ * parameter sweeps (Sec. 1, Sec. 3); a batch factors many such matrices in
+ * one persistent launch: 128-thread blocks take matrices from an atomic queue
+ * ordered by decreasing N and run all of each matrix's steps (det and leading
+ * minors; no L).  Every matrix's results equal mpdet_factor's bit for bit.
+ *
+ * mpdet_batch_create: count matrices of sizes Ns[0..count) (host) at p bits;
+ *   allocates 2 sum(N_i^2) + sum(N_i) numbers plus per-block scratch.
+ * mpdet_batch_set_*: input of matrix m (as mpdet_set_*); kept by the handle.
+ *   Every matrix must be set before the first mpdet_batch_factor.
+ * mpdet_batch_factor: eliminates a working copy of the stored inputs (one
+ *   device-to-device copy and one persistent launch); minors receives
+ *   sum(N_i) numbers, matrix m's D_1..D_{N_m} first at offset
+ *   N_0 + .. + N_{m-1}; zero_k (count int64, may be NULL) the 1-based first
+ *   zero pivot of each matrix or 0 (a zero pivot before N_m stops that
+ *   matrix: its later minors are +0).  device_ptr as for mpdet_factor.
+ * mpdet_batch_launches: kernels enqueued by the handle so far.
+ * Errors: MPDET_EINVAL, MPDET_ENOMEM, MPDET_ECUDA. */
+typedef struct mpdet_batch_ctx* mpdet_batch_t;
+int mpdet_batch_create(int64_t count, const int64_t* Ns, int32_t p_bits, void* cuda_stream, mpdet_batch_t* out);
+int mpdet_batch_set_f64(mpdet_batch_t b, int64_t m, const double* A, int64_t ld, int device_ptr);
+int mpdet_batch_set_i32(mpdet_batch_t b, int64_t m, const int32_t* A, int64_t ld, int device_ptr);
+int mpdet_batch_set_cauchy(mpdet_batch_t b, int64_t m, const double* x, const double* y, int device_ptr);
+int mpdet_batch_set_mp(mpdet_batch_t b, int64_t m, mpdet_numv A, int device_ptr);
+int mpdet_batch_factor(mpdet_batch_t b, mpdet_numv minors, int64_t* zero_k, int device_ptr);
+int64_t mpdet_batch_launches(mpdet_batch_t b);
+int mpdet_batch_free(mpdet_batch_t b);
+
 /* Release the handle and its device memory (NULL is accepted). */
 int mpdet_free(mpdet_t h);
 

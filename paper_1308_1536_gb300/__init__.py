@@ -74,6 +74,14 @@ def load(build_if_missing: bool = True):
         "mpdet_geometry": ([i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)], ctypes.c_int),
         "mpdet_profile": ([P, ctypes.c_int], ctypes.c_int),
         "mpdet_tune": ([P, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+        "mpdet_batch_create": ([i64, P, i32, P, ctypes.POINTER(P)], ctypes.c_int),
+        "mpdet_batch_set_f64": ([P, i64, P, i64, ctypes.c_int], ctypes.c_int),
+        "mpdet_batch_set_i32": ([P, i64, P, i64, ctypes.c_int], ctypes.c_int),
+        "mpdet_batch_set_cauchy": ([P, i64, P, P, ctypes.c_int], ctypes.c_int),
+        "mpdet_batch_set_mp": ([P, i64, NumV, ctypes.c_int], ctypes.c_int),
+        "mpdet_batch_factor": ([P, NumV, P, ctypes.c_int], ctypes.c_int),
+        "mpdet_batch_launches": ([P], i64),
+        "mpdet_batch_free": ([P], ctypes.c_int),
         "mpdet_factor_noalloc": ([i64, i32, u32, NumV, NumV, NumV, ctypes.POINTER(i64), P], ctypes.c_int),
         "mpdet_profile_read": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)], ctypes.c_int),
@@ -284,3 +292,83 @@ class Mpdet:
         self._check(self.lib.mpdet_profile_read(self.h, ctypes.byref(ms), ctypes.byref(nl), ctypes.byref(macs),
                                                 ctypes.byref(total)), "profile_read")
         return dict(update_ms=ms.value, update_launches=nl.value, update_limb_macs=macs.value, launches=total.value)
+
+
+class Batch:
+    """Many independent matrices of sizes Ns at p bits, factored in one
+    persistent launch (det and leading minors of each)."""
+
+    def __init__(self, Ns, p: int, stream=None):
+        self.lib = load()
+        self.Ns = np.ascontiguousarray(np.asarray(Ns, dtype=np.int64))
+        self.p, self.n = int(p), int(p) // 32
+        self.offsets = np.concatenate([[0], np.cumsum(self.Ns)]).astype(np.int64)
+        if stream is None:
+            try:
+                import torch
+
+                stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else None
+            except Exception:
+                stream = None
+        h = ctypes.c_void_p()
+        rc = self.lib.mpdet_batch_create(len(self.Ns), self.Ns.ctypes.data_as(ctypes.c_void_p), self.p,
+                                         ctypes.c_void_p(stream or 0), ctypes.byref(h))
+        if rc:
+            raise MpdetError(rc, f"batch_create(count={len(self.Ns)}, p={p})")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mpdet_batch_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, what):
+        if rc:
+            raise MpdetError(rc, what)
+
+    def set_cauchy(self, m, x, y):
+        dev = _is_dev(x)
+        if not dev and not _is_torch(x):
+            x = np.ascontiguousarray(x, np.float64)
+            y = np.ascontiguousarray(y, np.float64)
+        self._check(self.lib.mpdet_batch_set_cauchy(self.h, int(m), _ptr(x), _ptr(y), int(dev)), "batch_set_cauchy")
+
+    def set_i32(self, m, A):
+        dev = _is_dev(A)
+        if not dev and not _is_torch(A):
+            A = np.ascontiguousarray(A, np.int32)
+        self._check(self.lib.mpdet_batch_set_i32(self.h, int(m), _ptr(A), int(self.Ns[m]), int(dev)),
+                    "batch_set_i32")
+
+    def set_f64(self, m, A):
+        dev = _is_dev(A)
+        if not dev and not _is_torch(A):
+            A = np.ascontiguousarray(A, np.float64)
+        self._check(self.lib.mpdet_batch_set_f64(self.h, int(m), _ptr(A), int(self.Ns[m]), int(dev)),
+                    "batch_set_f64")
+
+    def factor(self, out=None, zero_k=None):
+        """Host mode: returns (zero_k[count], minors triple of sum(N) numbers);
+        matrix m's minors are rows offsets[m]:offsets[m+1].  Device mode:
+        ``out`` (and optionally ``zero_k``) are CUDA tensors; asynchronous."""
+        if out is not None:
+            self._check(self.lib.mpdet_batch_factor(self.h, _numv(out), _ptr(zero_k), 1), "batch_factor")
+            return None
+        D = empty(int(self.offsets[-1]), self.p)
+        zk = np.zeros(len(self.Ns), np.int64)
+        self._check(self.lib.mpdet_batch_factor(self.h, _numv(D), zk.ctypes.data_as(ctypes.c_void_p), 0),
+                    "batch_factor")
+        return zk, D
+
+    def minors_of(self, D, m):
+        a, b = int(self.offsets[m]), int(self.offsets[m + 1])
+        return tuple(t[a:b] for t in D)
+
+    def launches(self) -> int:
+        return int(self.lib.mpdet_batch_launches(self.h))

@@ -448,6 +448,174 @@ __global__ void k_recip1(MpArr src, int64_t idx, MpArr dst, int* status, int cod
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// a7: batch.  One persistent launch factors many independent matrices of
+// uneven N (det and leading minors; no pivoting, no L).  Each 128-thread
+// block takes the next matrix from an atomic queue (the host orders it by
+// decreasing N, so the longest jobs start first) and runs every step of its
+// elimination with block barriers between the phases: pivot (warp 0),
+// multipliers and the Schur update (all groups, flattened over the items).
+// Z: per-block multiplier scratch of max_n numbers.
+// ---------------------------------------------------------------------------
+struct BatchDesc {
+  const int64_t* N;      // size of matrix m
+  const int64_t* xoff;   // first number of matrix m in X
+  const int64_t* doff;   // first number of D_1 of matrix m in D
+  const int32_t* order;  // processing order
+  int64_t* zero_k;       // first zero pivot of matrix m (1-based), 0 if none
+  int* queue;            // next position in order (zeroed before the launch)
+  int64_t count;
+  int64_t max_n;
+};
+
+template <int W, int G>
+__global__ void __launch_bounds__(128, 4) k_batch(MpArr Xall, MpArr Dall, MpArr Zall, BatchDesc bd, int p) {
+  constexpr int n = W * G;
+  constexpr int SW = Scratch<W, G>::words;
+  constexpr int NG = 128 / G;  // groups per block
+  __shared__ __align__(16) uint32_t sbuf[NG * SW];
+  __shared__ __align__(16) uint32_t r_m[n];
+  __shared__ int64_t r_e;
+  __shared__ int8_t r_s;
+  __shared__ int s_job, s_zero;
+  Grp<G> gp;
+  const int gid = threadIdx.x / G;
+  uint32_t* buf = sbuf + gid * SW;
+  MpArr Z{Zall.s + blockIdx.x * bd.max_n, Zall.e + blockIdx.x * bd.max_n, Zall.m + (size_t)blockIdx.x * bd.max_n * n};
+  for (;;) {
+    if (threadIdx.x == 0) s_job = atomicAdd(bd.queue, 1);
+    __syncthreads();
+    const int job = s_job;
+    __syncthreads();
+    if (job >= bd.count) break;
+    const int m = bd.order[job];
+    const int64_t N = bd.N[m];
+    MpArr X{Xall.s + bd.xoff[m], Xall.e + bd.xoff[m], Xall.m + (size_t)bd.xoff[m] * n};
+    MpArr D{Dall.s + bd.doff[m], Dall.e + bd.doff[m], Dall.m + (size_t)bd.doff[m] * n};
+    for (int64_t k = 0; k < N; ++k) {
+      const int64_t kk = k * N + k;
+      if (threadIdx.x < 32) {  // warp 0: pivot
+        uint32_t A[W], Dm[W];
+        load_slice<W>(X.m + kk * n + gp.g * W, A);
+        const int8_t as = X.s[kk];
+        const int64_t ae = X.e[kk];
+        int8_t ds = as;
+        int64_t de = ae;
+        if (k == 0) {
+#pragma unroll
+          for (int q = 0; q < W; ++q) Dm[q] = A[q];
+        } else {
+          const int adj = mul_round<W, G>(gp, A, D.m + (k - 1) * n, Dm);
+          const int8_t ps = D.s[k - 1];
+          const int64_t pe = D.e[k - 1];
+          if (pe == ZEXP || ae == ZEXP) {
+            ds = 0;
+            de = ZEXP;
+#pragma unroll
+            for (int q = 0; q < W; ++q) Dm[q] = 0u;
+          } else {
+            ds = (int8_t)(ps ^ as);
+            de = pe + ae + adj;
+          }
+        }
+        if (threadIdx.x < G) {
+          store_slice<W>(D.m + k * n + gp.g * W, Dm);
+          if (gp.g == 0) {
+            D.s[k] = ds;
+            D.e[k] = de;
+          }
+        }
+        if (threadIdx.x == 0) s_zero = (ae == ZEXP);
+        if (ae != ZEXP && k < N - 1) {  // warp-uniform: every lane read the same pivot
+          uint32_t Mr[W];
+          const int adj = recip_round<W, G>(gp, A, buf, Mr);
+          if (threadIdx.x < G) {
+            store_slice<W>(r_m + gp.g * W, Mr);
+            if (gp.g == 0) {
+              r_s = as;
+              r_e = (int64_t)adj - ae;
+            }
+          }
+        }
+      }
+      __syncthreads();
+      if (s_zero) {
+        if (threadIdx.x == 0) bd.zero_k[m] = k + 1;
+        // D_k is +0 already; D_{k+1}..D_N are +0 too
+        for (int64_t q = k + 1 + threadIdx.x; q < N; q += blockDim.x) {
+          D.s[q] = 0;
+          D.e[q] = ZEXP;
+          for (int l = 0; l < n; ++l) D.m[q * n + l] = 0u;
+        }
+        __syncthreads();
+        break;
+      }
+      if (k == N - 1) break;
+      if (threadIdx.x == 0) bd.zero_k[m] = 0;
+      const int64_t R = N - k - 1;
+      // multipliers z_i = RN(a_ik * r_k)
+      for (int64_t t0 = 0; t0 < R; t0 += NG) {
+        int64_t t = t0 + gid;
+        const bool active = t < R;
+        if (!active) t = R - 1;
+        const int64_t i = k + 1 + t, ik = i * N + k;
+        uint32_t A[W], M[W];
+        load_slice<W>(X.m + ik * n + gp.g * W, A);
+        const int adj = mul_round<W, G>(gp, A, r_m, M);
+        const int64_t ae = X.e[ik];
+        if (active) {
+          const bool zero = (ae == ZEXP);
+          if (zero) {
+#pragma unroll
+            for (int q = 0; q < W; ++q) M[q] = 0u;
+          }
+          store_slice<W>(Z.m + i * n + gp.g * W, M);
+          if (gp.g == 0) {
+            Z.s[i] = zero ? 0 : (int8_t)(X.s[ik] ^ r_s);
+            Z.e[i] = zero ? ZEXP : ae + r_e + adj;
+          }
+        }
+      }
+      __syncthreads();
+      // Schur update of the trailing R x R block, items (i, j) flattened
+      const int64_t items = R * R;
+      for (int64_t t0 = 0; t0 < items; t0 += NG) {
+        int64_t t = t0 + gid;
+        const bool active = t < items;
+        if (!active) t = items - 1;
+        const int64_t i = k + 1 + t / R, j = k + 1 + t % R;
+        const int64_t kj = k * N + j, ij = i * N + j;
+        uint32_t Bk[W], T[W], Xv[W];
+        load_slice<W>(X.m + kj * n + gp.g * W, Bk);
+        const int8_t bs = X.s[kj];
+        const int64_t be = X.e[kj];
+        const int64_t zer = Z.e[i];
+        const int adj = mul_round<W, G>(gp, Bk, Z.m + i * n, T);
+        const bool tz = (zer == ZEXP) || (be == ZEXP);
+        const int8_t ts = tz ? 0 : (int8_t)(Z.s[i] ^ bs);
+        const int64_t te = tz ? ZEXP : zer + be + adj;
+        if (tz) {
+#pragma unroll
+          for (int q = 0; q < W; ++q) T[q] = 0u;
+        }
+        load_slice<W>(X.m + ij * n + gp.g * W, Xv);
+        int8_t xs = X.s[ij];
+        int64_t xe = X.e[ij];
+        sub_round<W, G>(gp, p, xs, xe, Xv, ts, te, T, buf);
+        if (active) {
+          store_slice<W>(X.m + ij * n + gp.g * W, Xv);
+          if (gp.g == 0) {
+            X.s[ij] = xs;
+            X.e[ij] = xe;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------
@@ -526,6 +694,17 @@ struct Launch {
     k_recip1<W, G><<<1, 32, 0, st>>>(src, idx, dst, status, code);
     return cudaGetLastError();
   }
+  static cudaError_t batch(MpArr X, MpArr D, MpArr Z, const BatchDescHost& h, int p, int blocks,
+                           cudaStream_t st) {
+    BatchDesc bd{h.N, h.xoff, h.doff, h.order, h.zero_k, h.queue, h.count, h.max_n};
+    k_batch<W, G><<<blocks, 128, 0, st>>>(X, D, Z, bd, p);
+    return cudaGetLastError();
+  }
+  static int batch_blocks_per_sm() {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<W, G>, 128, 0) != cudaSuccess) return 1;
+    return nb > 0 ? nb : 1;
+  }
   static KernelSet make() {
     KernelSet s;
     s.W = W;
@@ -540,6 +719,8 @@ struct Launch {
     s.update[3] = &update<6>;
     s.lastcol = &lastcol;
     s.recip1 = &recip1;
+    s.batch = &batch;
+    s.batch_blocks_per_sm = &batch_blocks_per_sm;
     return s;
   }
 };

@@ -13,6 +13,18 @@ struct MpArr {
   uint32_t* m;
 };
 
+// Device pointers describing a batch of independent matrices.
+struct BatchDescHost {
+  const int64_t* N;
+  const int64_t* xoff;
+  const int64_t* doff;
+  const int32_t* order;
+  int64_t* zero_k;
+  int* queue;
+  int64_t count;
+  int64_t max_n;
+};
+
 struct KernelSet {
   int W, G;
   // kind 0: double entries, 1: int32 entries
@@ -30,6 +42,9 @@ struct KernelSet {
   cudaError_t (*lastcol)(MpArr X, int64_t N, MpArr F, MpArr out, int normalised, const int* status,
                          cudaStream_t st);
   cudaError_t (*recip1)(MpArr src, int64_t idx, MpArr dst, int* status, int code, cudaStream_t st);
+  // persistent batch kernel (blocks = resident blocks to launch)
+  cudaError_t (*batch)(MpArr X, MpArr D, MpArr Z, const BatchDescHost& bd, int p, int blocks, cudaStream_t st);
+  int (*batch_blocks_per_sm)();
 };
 
 // Kernel set for n = p/32 limbs, or nullptr if this n is not instantiated.
