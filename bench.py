@@ -270,6 +270,51 @@ def bench_batch(args, dev, m):
             "single_path_sample": f"every 16th matrix ({len(sample)}), set + factor per matrix, includes input lift"}
 
 
+def bench_adjoint(args, dev, m):
+    """Workload C4: N = 512, p = 4096, the nearly singular Gaussian matrix:
+    one gradient call = exact lift, elimination in lastcol mode, log|det|,
+    back substitution X = U^-1 L and the binary64 gradient A^-T (device
+    input and output).  Compared with the plain single-matrix path (lift and
+    elimination for det only) at the same N and p."""
+    import torch
+
+    cfg = W.C4
+    N, p = cfg["N"], cfg["p"]
+    n = p // 32
+    A = torch.tensor(W.nearly_singular_f64(N, cfg["seed"]), dtype=torch.float64, device=dev)
+    G = torch.empty((N, N), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    h = m.Mpdet(N, p, lastcol=True, stream=stream)
+    hp = m.Mpdet(N, p, lastcol=False, stream=stream)
+    D = (torch.empty(N, dtype=torch.int8, device=dev), torch.empty(N, dtype=torch.int64, device=dev),
+         torch.empty((N, n), dtype=torch.int32, device=dev))
+    for _ in range(max(1, args.warmup // 2)):
+        h.logabsdet_grad(A, grad=True, out=G)
+        hp.set_f64(A)
+        hp.factor(out=D)
+    steps = max(1, args.steps)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        h.logabsdet_grad(A, grad=True, out=G)
+    torch.cuda.synchronize(dev)
+    t_grad = (time.perf_counter() - t0) / steps
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        hp.set_f64(A)
+        hp.factor(out=D)
+    torch.cuda.synchronize(dev)
+    t_plain = (time.perf_counter() - t0) / steps
+    h.close()
+    hp.close()
+    # products: lastcol elimination + back substitution (N rows of N, then k*N updates)
+    prods = elim_products(N, True) + N * N + N * (N - 1) // 2 * N
+    return {"workload": "N=512 p=4096 nearly singular N(0,1) matrix: log|det| and d log|det|/dA in binary64",
+            "grad_calls_per_s": 1.0 / t_grad, "ms_per_call": t_grad * 1e3,
+            "limb_macs_per_s": prods * n * n / t_grad,
+            "plain_det_calls_per_s": 1.0 / t_plain, "grad_cost_vs_plain_det": t_grad / t_plain}
+
+
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
@@ -437,6 +482,7 @@ def run_gpu(args):
         }
         if not args.no_extras:
             out["batch"] = bench_batch(args, dev, m)
+            out["adjoint"] = bench_adjoint(args, dev, m)
         if world == 1 and not args.no_cpu_baseline:
             cb = oracle_sample()
             cb.pop("seconds", None)

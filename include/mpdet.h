@@ -205,6 +205,31 @@ int mpdet_profile_read(mpdet_t h, double* update_ms, int64_t* update_launches, d
 int mpdet_factor_noalloc(int64_t N, int32_t p_bits, uint32_t flags, mpdet_numv A, mpdet_numv minors,
                          mpdet_numv lastcol, int64_t* zero_pivot_k, void* cuda_stream);
 
+/* ---- Adjoint (step a8) ----------------------------------------------------
+ * All (N-1) x (N-1) minors are partial derivatives of the determinant (Sec.
+ * 3, the Strassen argument), so d log|det| / dA = A^-T = C / det (cofactor
+ * matrix over the determinant).  mpdet_logabsdet_grad lifts the binary64
+ * matrix A (N x N, row-major, leading dimension ld) exactly to p bits, runs
+ * the elimination in MPDET_LASTCOL mode (L A = U), returns log|det| and the
+ * sign (host scalars; log|det| = ln(m/2^p) + e ln 2 in binary64; a zero
+ * determinant gives -inf and sign 0) and, when grad != NULL, solves
+ * X = U^-1 L = A^-1 at p bits by back substitution from the bottom row up:
+ *     X_kc = RN(S_kc * RN(1/u_kk)), all c;  S_ic = RN(S_ic - RN(u_ik X_kc)), i < k
+ * (S = L initially), and writes grad[i*N + j] = grad_scale * RN64(X_ji)
+ * (binary64, nearest even, subnormals included).  Nothing is kept between
+ * calls but the buffers: the factor is recomputed, not stored.
+ * The handle must be created with MPDET_LASTCOL when grad != NULL.
+ * device_ptr applies to A and grad; the call synchronises.
+ * Errors: MPDET_EZEROPIVOT (zero pivot before N: no elimination without
+ * pivoting), MPDET_EZERODIV (det = 0 and a gradient was asked for),
+ * MPDET_ESTATE, MPDET_EINVAL, MPDET_ENOMEM, MPDET_ECUDA. */
+int mpdet_logabsdet_grad(mpdet_t h, const double* A, int64_t ld, double* logabs, int* sign, double* grad,
+                         double grad_scale, int device_ptr);
+
+/* A^-1 (N*N numbers) from the last mpdet_logabsdet_grad call with a
+ * gradient (before the binary64 rounding).  Errors: MPDET_ESTATE. */
+int mpdet_get_inverse(mpdet_t h, mpdet_numv out, int device_ptr);
+
 /* ---- Batches (step a7): many independent matrices of uneven N ------------
  * The paper needs the minors for a whole series of sizes N = 2, 3, ... and for
  * parameter sweeps (Sec. 1, Sec. 3); a batch factors many such matrices in

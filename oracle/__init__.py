@@ -27,6 +27,10 @@ Functions and the passages they follow:
   identity block of [A I] stored in A's strict lower triangle.
 * ``lastcol_minors``: C_jN = D_{N-1} * l_Nj (eq. minorsdef) and the
   normalised minors of eq. (minors).
+* ``usolve``: X = A^-1 = U^-1 L from a lastcol elimination, the adjoint of
+  log|det| (d log|det| / dA = A^-T; all minors are partial derivatives of
+  the determinant, Sec. 3), by right-looking back substitution.
+* ``to_f64``: round numbers to binary64 (nearest even, subnormals).
 """
 from __future__ import annotations
 
@@ -54,7 +58,7 @@ def build(force: bool = False) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread", "-o", tmp, _SRC])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -74,8 +78,10 @@ def _load():
             lib.or_cauchy.argtypes = [i64, i32, P, P, P, P, P]
             lib.or_ge_range.argtypes = [i64, i32, i32, i32, i64, i64, P, P, P, P, P, P, P]
             lib.or_lastcol.argtypes = [i64, i32, i32, P, P, P, ctypes.c_int8, i64, P, P, P, P]
+            lib.or_usolve.argtypes = [i64, i32, i32, P, P, P, P, P, P]
+            lib.or_to_f64_v.argtypes = [i64, i32, P, P, P, P]
             for f in ("or_mul_v", "or_add_v", "or_recip_v", "or_from_f64_v", "or_from_i64_v", "or_cauchy",
-                      "or_ge_range", "or_lastcol"):
+                      "or_ge_range", "or_lastcol", "or_usolve", "or_to_f64_v"):
                 getattr(lib, f).restype = i32
             _lib = lib
     return _lib
@@ -196,3 +202,30 @@ def lastcol_minors(X, D, N: int, p: int, normalised: bool = False):
                             *map(_ptr, o))
     _check(st, "lastcol")
     return o
+
+
+def usolve(X, N: int, p: int, nthreads: int = 1):
+    """A^-1 (N*N numbers, row-major) from a lastcol-mode elimination X."""
+    S, E, M = _norm(X, p)
+    o = empty(N * N, p)
+    _check(_load().or_usolve(N, p, int(nthreads), _ptr(S), _ptr(E), _ptr(M), *map(_ptr, o)), "usolve")
+    return o
+
+
+def to_f64(x, p: int):
+    S, E, M = _norm(x, p)
+    out = np.zeros(S.shape[0], np.float64)
+    _check(_load().or_to_f64_v(S.shape[0], p, _ptr(S), _ptr(E), _ptr(M), _ptr(out)), "to_f64")
+    return out
+
+
+def logabsdet(D, N: int, p: int):
+    """(sign, log|det|) from the leading minors D (det = D_N): the mantissa
+    as a double times 2^(e-p), logarithm taken in binary64."""
+    import math
+
+    s, e, m = (t[N - 1] for t in _norm(D, p))
+    if int(e) == ZEXP:
+        return 0.0, float("-inf")
+    top = int(m[-1]) * 2.0 ** -32 + int(m[-2]) * 2.0 ** -64  # m / 2^p in [1/2, 1)
+    return (-1.0 if int(s) else 1.0), math.log(top) + float(int(e)) * math.log(2.0)

@@ -29,11 +29,21 @@
  *     l_ik = -z_ik   (exact)
  *   The signed minors of the last column (eq. minorsdef) are then
  *     C_jN = RN(D_{N-1} * l_Nj) (j < N),  C_NN = D_{N-1}.
+ *
+ * Adjoint.  All (N-1) x (N-1) minors are partial derivatives of the
+ * determinant (Sec. 3, the Strassen argument), so d log|det| / dA = A^-T.
+ * With L A = U from the lastcol elimination, A^-1 = U^-1 L, solved by back
+ * substitution in right-looking order (rows from the bottom up):
+ *     S = L (unit diagonal, zeros above it)
+ *     for k = N..1:  X_kc = RN(S_kc * RN(1/u_kk)),  all c
+ *                    S_ic = RN(S_ic - RN(u_ik * X_kc)),  i < k, all c
+ * and each X_ji is rounded to binary64 (nearest even, subnormals included).
  */
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 #include <pthread.h>
+#include <math.h>
 
 #define ZEXP INT64_MIN
 
@@ -590,4 +600,127 @@ int or_lastcol(int64_t N, int p, int normalised, const int8_t *S, const int64_t 
   }
   free(c.buf);
   return st;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Adjoint: X = U^-1 L from a lastcol elimination (right-looking back        */
+/* substitution in the order stated at the top of this file).                */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+  int64_t N;
+  int p, n;
+  const int8_t *US;
+  const int64_t *UE;
+  const uint32_t *UM; /* eliminated array (U above, L below) */
+  int8_t *S;
+  int64_t *E;
+  uint32_t *M; /* S / X */
+  int64_t k;
+  int64_t i0, i1;
+} us_t;
+
+static void *usolve_rows(void *arg) {
+  us_t *u = (us_t *)arg;
+  ctx_t c;
+  if (ctx_init(&c, u->p)) return NULL;
+  int n = u->n;
+  int64_t N = u->N, k = u->k;
+  uint32_t *t = (uint32_t *)calloc(n, sizeof(uint32_t));
+  for (int64_t i = u->i0; i < u->i1; ++i) {
+    int64_t ik = i * N + k;
+    for (int64_t col = 0; col < N; ++col) {
+      int64_t ic = i * N + col, kc = k * N + col;
+      int8_t ts;
+      int64_t te;
+      op_mul(&c, u->US[ik], u->UE[ik], u->UM + ik * n, u->S[kc], u->E[kc], u->M + kc * n, &ts, &te, t);
+      op_add(&c, u->S[ic], u->E[ic], u->M + ic * n, ts, te, t, 1, u->S + ic, u->E + ic, u->M + ic * n);
+    }
+  }
+  free(t);
+  free(c.buf);
+  return NULL;
+}
+
+/* X (N*N numbers, row-major) = A^-1 from the lastcol-mode array (S,E,M) of
+ * or_ge_range.  Returns OR_EZERODIV if a pivot is zero. */
+int or_usolve(int64_t N, int p, int nthreads, const int8_t *S, const int64_t *E, const uint32_t *M, int8_t *XS,
+              int64_t *XE, uint32_t *XM) {
+  ctx_t c;
+  int st = ctx_init(&c, p);
+  if (st) return st;
+  int n = c.n;
+  if (nthreads < 1) nthreads = 1;
+  /* S = L: l_ij below the diagonal, 1 on it, +0 above */
+  for (int64_t i = 0; i < N; ++i)
+    for (int64_t j = 0; j < N; ++j) {
+      int64_t ij = i * N + j;
+      if (j < i) copynum(S[ij], E[ij], M + ij * n, n, XS + ij, XE + ij, XM + ij * n);
+      else if (j == i) {
+        setzero(XS + ij, XE + ij, XM + ij * n, n);
+        XM[ij * n + n - 1] = 0x80000000u;
+        XE[ij] = 1;
+      } else setzero(XS + ij, XE + ij, XM + ij * n, n);
+    }
+  uint32_t *r = (uint32_t *)calloc(n, sizeof(uint32_t));
+  pthread_t *th = (pthread_t *)calloc(nthreads, sizeof(pthread_t));
+  us_t *wk = (us_t *)calloc(nthreads, sizeof(us_t));
+  for (int64_t k = N - 1; k >= 0 && st == OR_OK; --k) {
+    int64_t kk = k * N + k;
+    int8_t rs;
+    int64_t re;
+    st = op_recip(&c, S[kk], E[kk], M + kk * n, &rs, &re, r);
+    if (st) break;
+    for (int64_t col = 0; col < N; ++col) { /* X_kc = RN(S_kc * r_k) */
+      int64_t kc = k * N + col;
+      op_mul(&c, XS[kc], XE[kc], XM + kc * n, rs, re, r, XS + kc, XE + kc, XM + kc * n);
+    }
+    int T = nthreads;
+    if (T > k) T = (int)k;
+    for (int t = 0; t < T; ++t) {
+      us_t w = {N, p, n, S, E, M, XS, XE, XM, k, k * t / T, k * (t + 1) / T};
+      wk[t] = w;
+    }
+    if (T <= 1) {
+      if (k > 0) {
+        us_t w = {N, p, n, S, E, M, XS, XE, XM, k, 0, k};
+        usolve_rows(&w);
+      }
+    } else {
+      for (int t = 0; t < T; ++t) pthread_create(&th[t], NULL, usolve_rows, &wk[t]);
+      for (int t = 0; t < T; ++t) pthread_join(th[t], NULL);
+    }
+  }
+  free(wk);
+  free(th);
+  free(r);
+  free(c.buf);
+  return st;
+}
+
+/* RN to binary64, nearest even, with subnormals and overflow to +-inf.
+ * value = m * 2^(e-p) lies in [2^(e-1), 2^e); binary64 keeps multiples of the
+ * quantum 2^q, q = max(e - 53, -1074).  K = m * 2^(e-p-q) rounded to an
+ * integer (a right shift by p + q - e >= p - 53 bits, the shifted-out bits
+ * round); the result is K * 2^q, exact in binary64 (K <= 2^53). */
+static double to_f64_one(int p, int n, int8_t s, int64_t e, const uint32_t *m) {
+  if (e == ZEXP) return 0.0;
+  if (e > 1100) return s ? -HUGE_VAL : HUGE_VAL;
+  if (e < -1100) return s ? -0.0 : 0.0;
+  int64_t q = (e - 53 < -1074) ? -1074 : e - 53;
+  int64_t rs = (int64_t)p + q - e;
+  uint32_t buf[2];
+  shr(m, n, rs, buf, 2);
+  uint64_t K = ((uint64_t)buf[1] << 32) | buf[0];
+  int rbit = getbit(m, n, rs - 1);
+  int st = anybelow(m, n, rs - 1);
+  if (rbit && (st || (K & 1))) K += 1;
+  double v = ldexp((double)K, (int)q);
+  return s ? -v : v;
+}
+
+int or_to_f64_v(int64_t cnt, int p, const int8_t *S, const int64_t *E, const uint32_t *M, double *out) {
+  if (p < 64 || p % 32) return OR_EINVAL;
+  int n = p / 32;
+  for (int64_t i = 0; i < cnt; ++i) out[i] = to_f64_one(p, n, S[i], E[i], M + i * n);
+  return OR_OK;
 }

@@ -82,6 +82,9 @@ def load(build_if_missing: bool = True):
         "mpdet_batch_factor": ([P, NumV, P, ctypes.c_int], ctypes.c_int),
         "mpdet_batch_launches": ([P], i64),
         "mpdet_batch_free": ([P], ctypes.c_int),
+        "mpdet_logabsdet_grad": ([P, P, i64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), P,
+                                  ctypes.c_double, ctypes.c_int], ctypes.c_int),
+        "mpdet_get_inverse": ([P, NumV, ctypes.c_int], ctypes.c_int),
         "mpdet_factor_noalloc": ([i64, i32, u32, NumV, NumV, NumV, ctypes.POINTER(i64), P], ctypes.c_int),
         "mpdet_profile_read": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)], ctypes.c_int),
@@ -278,6 +281,34 @@ class Mpdet:
     def steps_done(self) -> int:
         return int(self.lib.mpdet_steps_done(self.h))
 
+    # -- adjoint --------------------------------------------------------------
+    def logabsdet_grad(self, A, grad: bool = True, scale: float = 1.0, out=None):
+        """(sign, log|det|, G) for the binary64 matrix A (numpy or CUDA
+        tensor): G = scale * A^-T rounded to binary64 (None if grad=False).
+        With a CUDA tensor A the gradient is written to ``out`` (a CUDA
+        float64 tensor, allocated if None) and returned."""
+        dev = _is_dev(A)
+        if not dev and not _is_torch(A):
+            A = np.ascontiguousarray(A, np.float64)
+        la, sg = ctypes.c_double(), ctypes.c_int()
+        G = None
+        if grad:
+            if dev:
+                import torch
+
+                G = out if out is not None else torch.empty((self.N, self.N), dtype=torch.float64, device=A.device)
+            else:
+                G = np.empty((self.N, self.N), np.float64)
+        rc = self.lib.mpdet_logabsdet_grad(self.h, _ptr(A), self.N, ctypes.byref(la), ctypes.byref(sg), _ptr(G),
+                                           float(scale), int(dev))
+        self._check(rc, "logabsdet_grad")
+        return sg.value, la.value, G
+
+    def get_inverse(self):
+        Xi = empty(self.N * self.N, self.p)
+        self._check(self.lib.mpdet_get_inverse(self.h, _numv(Xi), 0), "get_inverse")
+        return Xi
+
     # -- tuning (bit-identical results for every setting) -------------------
     def tune(self, update_variant: int):
         self._check(self.lib.mpdet_tune(self.h, 1, int(update_variant)), "tune")
@@ -372,3 +403,43 @@ class Batch:
 
     def launches(self) -> int:
         return int(self.lib.mpdet_batch_launches(self.h))
+
+
+_grad_handles = {}
+
+
+def _handle_for(N: int, p: int, device):
+    import torch
+
+    key = (N, p, device)
+    h = _grad_handles.get(key)
+    if h is None:
+        with torch.cuda.device(device):
+            h = _grad_handles[key] = Mpdet(N, p, lastcol=True)
+    return h
+
+
+def mp_logabsdet(A, p: int = 4096):
+    """log|det(A)| of a float64 CUDA matrix, computed at p bits, as a
+    differentiable torch op: backward returns grad * A^-T from the adjoint
+    kernels (the factor is recomputed in the backward pass, not stored)."""
+    import torch
+
+    class _MpLogDet(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, A_):
+            h = _handle_for(A_.shape[0], p, A_.device)
+            Ac = A_.detach().contiguous()
+            s, la, _ = h.logabsdet_grad(Ac, grad=False)
+            ctx.save_for_backward(Ac)
+            ctx.sign = s
+            return torch.tensor(la, dtype=torch.float64, device=A_.device)
+
+        @staticmethod
+        def backward(ctx, g):
+            (Ac,) = ctx.saved_tensors
+            h = _handle_for(Ac.shape[0], p, Ac.device)
+            _, _, G = h.logabsdet_grad(Ac, grad=True, scale=float(g.item()))
+            return G
+
+    return _MpLogDet.apply(A)

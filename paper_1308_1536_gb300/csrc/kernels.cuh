@@ -8,6 +8,8 @@
 //   limbs uint32 [N*N][n]   (each number's n limbs contiguous, 16-byte aligned)
 // A group of G lanes moves one number with uint4 loads of its slices.
 #pragma once
+#include <math_constants.h>
+
 #include "mpdev.cuh"
 #include "kernelset.h"
 
@@ -291,21 +293,30 @@ __global__ void k_mult(MpArr X, int64_t N, int64_t k, MpArr R, MpArr Z, const in
 }
 
 // ---------------------------------------------------------------------------
-// a4/a5: Schur update of step k:
-//   x_ij = RN(x_ij - RN(z_i * x_kj))  for i > k and j > k
-//   (lastcol mode: every j != k, which updates L's row segment j < k too).
-// Block: GPB groups, each owning one column j and holding the pivot-row
-// element x_kj's slice in registers; the block walks rows [i0, i1) with the
-// multipliers z_i staged in shared memory (a broadcast read for the groups).
+// a4/a5 (and the adjoint's back substitution): rank-1 update
+//   x_ij = RN(x_ij - RN(z_i * x_{brow,j}))
+// for rows i in [row0, row0 + nrows) and the columns j selected by cmode:
+//   0: j > kcol (Schur update of step kcol)
+//   1: j != kcol (lastcol mode: also L's row segment j < kcol)
+//   2: every j (back substitution)
+// z_i is Z[i].  Block: GPB groups, each owning one column j and holding the
+// pivot-row element x_{brow,j}'s slice in registers; the block walks rows
+// [i0, i1) with the multipliers staged in shared memory (broadcast reads).
 // ---------------------------------------------------------------------------
+struct UpdArgs {
+  int64_t N, brow, row0, nrows, kcol;
+  int cmode;
+};
+
 template <int W, int G, int MINB>
-__global__ void __launch_bounds__(128, MINB) k_update(MpArr X, int64_t N, int64_t k, MpArr Z, const int* status,
-                                                     int p, int lastcol, int rows_per_cta) {
+__global__ void __launch_bounds__(128, MINB) k_update(MpArr X, UpdArgs a, MpArr Z, const int* status, int p,
+                                                     int rows_per_cta) {
   constexpr int n = W * G;
   constexpr int SW = Scratch<W, G>::words;
   extern __shared__ __align__(16) uint32_t smem[];
   if (status_set(status)) return;
   Grp<G> gp;
+  const int64_t N = a.N;
   const int gpb = blockDim.x / G;
   const int gib = threadIdx.x / G;
   // shared layout (words, every region a multiple of 4 words = 16 bytes):
@@ -314,9 +325,10 @@ __global__ void __launch_bounds__(128, MINB) k_update(MpArr X, int64_t N, int64_
   int64_t* ze_s = reinterpret_cast<int64_t*>(smem + rows_per_cta * n);
   int8_t* zs_s = reinterpret_cast<int8_t*>(smem + rows_per_cta * n + upd_pad4(2 * rows_per_cta));
   uint32_t* buf = smem + rows_per_cta * n + upd_pad4(2 * rows_per_cta) + upd_pad4((rows_per_cta + 3) / 4) + gib * SW;
-  const int64_t ncols = lastcol ? N - 1 : N - k - 1;
-  const int64_t i0 = k + 1 + (int64_t)blockIdx.y * rows_per_cta;
-  const int64_t i1 = (i0 + rows_per_cta < N) ? i0 + rows_per_cta : N;
+  const int64_t ncols = a.cmode == 0 ? N - a.kcol - 1 : (a.cmode == 1 ? N - 1 : N);
+  const int64_t i0 = a.row0 + (int64_t)blockIdx.y * rows_per_cta;
+  const int64_t rend = a.row0 + a.nrows;
+  const int64_t i1 = (i0 + rows_per_cta < rend) ? i0 + rows_per_cta : rend;
   const int nr = (int)(i1 - i0);
   // stage multipliers
   for (int q = threadIdx.x; q < nr * n / 4; q += blockDim.x)
@@ -329,9 +341,9 @@ __global__ void __launch_bounds__(128, MINB) k_update(MpArr X, int64_t N, int64_
   int64_t c = (int64_t)blockIdx.x * gpb + gib;
   const bool active = c < ncols;
   if (!active) c = ncols - 1;
-  const int64_t j = lastcol ? (c < k ? c : c + 1) : k + 1 + c;
-  // pivot-row element x_kj
-  const int64_t kj = k * N + j;
+  const int64_t j = a.cmode == 0 ? a.kcol + 1 + c : (a.cmode == 1 ? (c < a.kcol ? c : c + 1) : c);
+  // pivot-row element x_{brow,j}
+  const int64_t kj = a.brow * N + j;
   uint32_t Bk[W];
   load_slice<W>(X.m + kj * n + gp.g * W, Bk);
   const int8_t bs = X.s[kj];
@@ -360,6 +372,120 @@ __global__ void __launch_bounds__(128, MINB) k_update(MpArr X, int64_t N, int64_
         X.e[ij] = xe;
       }
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint helpers.
+// k_init_s: S = L from a lastcol elimination X (l_ij below the diagonal, 1 on
+// it, +0 above).  k_rowscale: row k of S times the reciprocal R[0]:
+// X_kc = RN(S_kc * r_k).  k_to_f64: G_ij = scale * RN64(X_ji), binary64 round
+// to nearest even with subnormals (quantum 2^max(e-53, -1074)).
+// ---------------------------------------------------------------------------
+template <int W, int G>
+__global__ void k_init_s(MpArr X, int64_t N, MpArr S) {
+  constexpr int n = W * G;
+  Grp<G> gp;
+  const int64_t ngroups_total = (int64_t)gridDim.x * (blockDim.x / G);
+  for (int64_t idx = (int64_t)blockIdx.x * (blockDim.x / G) + threadIdx.x / G; idx < N * N; idx += ngroups_total) {
+    const int64_t i = idx / N, j = idx % N;
+    uint32_t L[W];
+    int8_t s = 0;
+    int64_t e = ZEXP;
+    if (j < i) {
+      load_slice<W>(X.m + idx * n + gp.g * W, L);
+      s = X.s[idx];
+      e = X.e[idx];
+    } else {
+#pragma unroll
+      for (int q = 0; q < W; ++q) L[q] = 0u;
+      if (j == i) {
+        if (gp.g == G - 1) L[W - 1] = 0x80000000u;
+        e = 1;
+      }
+    }
+    store_slice<W>(S.m + idx * n + gp.g * W, L);
+    if (gp.g == 0) {
+      S.s[idx] = s;
+      S.e[idx] = e;
+    }
+  }
+}
+
+template <int W, int G>
+__global__ void k_rowscale(MpArr S, int64_t N, int64_t k, MpArr R) {
+  constexpr int n = W * G;
+  __shared__ __align__(16) uint32_t rm[n];
+  Grp<G> gp;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) rm[q] = R.m[q];
+  __syncthreads();
+  const int8_t rs = R.s[0];
+  const int64_t re = R.e[0];
+  int64_t c = (int64_t)blockIdx.x * (blockDim.x / G) + threadIdx.x / G;
+  const bool active = c < N;
+  if (!active) c = N - 1;
+  const int64_t kc = k * N + c;
+  uint32_t A[W], M[W];
+  load_slice<W>(S.m + kc * n + gp.g * W, A);
+  const int8_t as = S.s[kc];
+  const int64_t ae = S.e[kc];
+  const int adj = mul_round<W, G>(gp, A, rm, M);
+  if (active) {
+    const bool zero = (ae == ZEXP) || (re == ZEXP);
+    if (zero) {
+#pragma unroll
+      for (int q = 0; q < W; ++q) M[q] = 0u;
+    }
+    store_slice<W>(S.m + kc * n + gp.g * W, M);
+    if (gp.g == 0) {
+      S.s[kc] = zero ? 0 : (int8_t)(as ^ rs);
+      S.e[kc] = zero ? ZEXP : ae + re + adj;
+    }
+  }
+}
+
+template <int W, int G>
+__global__ void k_to_f64(MpArr Xs, int64_t N, double* __restrict__ out, double scale, int p, int transpose) {
+  constexpr int n = W * G;
+  static_assert(W >= 2, "the top two limbs live in one lane");
+  Grp<G> gp;
+  const int64_t ngroups_total = (int64_t)gridDim.x * (blockDim.x / G);
+  constexpr int GPW = 32 / G;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  const int64_t nwarps = (int64_t)gridDim.x * blockDim.x / 32;
+  (void)ngroups_total;
+  for (int64_t base = warp * GPW; base < N * N; base += nwarps * GPW) {
+    int64_t idx = base + gp.lane / G;
+    const bool active = idx < N * N;
+    if (!active) idx = N * N - 1;
+    const int64_t i = idx / N, j = idx % N;
+    const int64_t src = transpose ? j * N + i : idx;
+    uint32_t M[W];
+    load_slice<W>(Xs.m + src * n + gp.g * W, M);
+    const int8_t s = Xs.s[src];
+    const int64_t e = Xs.e[src];
+    // lower limbs (all but the top two) for the sticky bit
+    bool low = false;
+#pragma unroll
+    for (int q = 0; q < W; ++q)
+      if (!(gp.g == G - 1 && q >= W - 2)) low |= (M[q] != 0u);
+    const bool lowany = gp.ballot(low) != 0u;
+    const uint64_t hi64 = ((uint64_t)gp.from(M[W - 1], G - 1) << 32) | gp.from(M[W - 2], G - 1);
+    double v;
+    if (e == ZEXP) v = 0.0;
+    else if (e > 1100) v = s ? -CUDART_INF : CUDART_INF;
+    else if (e < -1100) v = s ? -0.0 : 0.0;
+    else {
+      const int64_t q = (e - 53 < -1074) ? -1074 : e - 53;
+      const int64_t t = (int64_t)p + q - e - (p - 64);  // right shift of hi64 (>= 11)
+      const uint64_t K0 = t < 64 ? (hi64 >> t) : 0ull;
+      const uint32_t rbit = (t - 1 < 64) ? (uint32_t)((hi64 >> (t - 1)) & 1ull) : 0u;
+      const bool st = lowany || ((t - 1 < 64) ? (hi64 & ((1ull << (t - 1)) - 1ull)) != 0ull : hi64 != 0ull);
+      const uint64_t K = K0 + ((rbit && (st || (K0 & 1ull))) ? 1ull : 0ull);
+      v = ldexp((double)K, (int)q);
+      if (s) v = -v;
+    }
+    if (active && gp.g == 0) out[idx] = v * scale;
   }
 }
 
@@ -662,10 +788,9 @@ struct Launch {
     return (size_t)(rows_per_cta * n + upd_pad4(2 * rows_per_cta) + upd_pad4((rows_per_cta + 3) / 4) + (NT / G) * SW) * 4;
   }
   template <int MINB>
-  static cudaError_t update(MpArr X, int64_t N, int64_t k, MpArr Z, const int* status, int p, int lastcol, int nsm,
-                            cudaStream_t st) {
-    int64_t rows = N - k - 1;
-    int64_t ncols = lastcol ? N - 1 : N - k - 1;
+  static cudaError_t update_any(MpArr X, UpdArgs a, MpArr Z, const int* status, int p, int nsm, cudaStream_t st) {
+    const int64_t ncols = a.cmode == 0 ? a.N - a.kcol - 1 : (a.cmode == 1 ? a.N - 1 : a.N);
+    const int64_t rows = a.nrows;
     if (rows <= 0 || ncols <= 0) return cudaSuccess;
     const int gpb = NT / G;
     int64_t bx = (ncols + gpb - 1) / gpb;
@@ -681,7 +806,36 @@ struct Launch {
     size_t sm = update_smem((int)rpc);
     cudaFuncSetAttribute(k_update<W, G, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     dim3 grid((unsigned)bx, (unsigned)by);
-    k_update<W, G, MINB><<<grid, NT, sm, st>>>(X, N, k, Z, status, p, lastcol, (int)rpc);
+    k_update<W, G, MINB><<<grid, NT, sm, st>>>(X, a, Z, status, p, (int)rpc);
+    return cudaGetLastError();
+  }
+  template <int MINB>
+  static cudaError_t update(MpArr X, int64_t N, int64_t k, MpArr Z, const int* status, int p, int lastcol, int nsm,
+                            cudaStream_t st) {
+    UpdArgs a{N, k, k + 1, N - k - 1, k, lastcol ? 1 : 0};
+    return update_any<MINB>(X, a, Z, status, p, nsm, st);
+  }
+  static cudaError_t usolve_update(MpArr S, int64_t N, int64_t k, MpArr Z, const int* status, int p, int nsm,
+                                   cudaStream_t st) {
+    UpdArgs a{N, k, 0, k, 0, 2};
+    return update_any<4>(S, a, Z, status, p, nsm, st);
+  }
+  static cudaError_t init_s(MpArr X, int64_t N, MpArr S, int nsm, cudaStream_t st) {
+    int64_t blocks = (N * N + NT / G - 1) / (NT / G);
+    if (blocks > (int64_t)nsm * 16) blocks = (int64_t)nsm * 16;
+    k_init_s<W, G><<<(unsigned)blocks, NT, 0, st>>>(X, N, S);
+    return cudaGetLastError();
+  }
+  static cudaError_t rowscale(MpArr S, int64_t N, int64_t k, MpArr R, cudaStream_t st) {
+    int64_t blocks = (N + NT / G - 1) / (NT / G);
+    k_rowscale<W, G><<<(unsigned)blocks, NT, 0, st>>>(S, N, k, R);
+    return cudaGetLastError();
+  }
+  static cudaError_t to_f64(MpArr X, int64_t N, double* out, double scale, int p, int transpose, int nsm,
+                            cudaStream_t st) {
+    int64_t blocks = (N * N + NT / G - 1) / (NT / G);
+    if (blocks > (int64_t)nsm * 16) blocks = (int64_t)nsm * 16;
+    k_to_f64<W, G><<<(unsigned)blocks, NT, 0, st>>>(X, N, out, scale, p, transpose);
     return cudaGetLastError();
   }
   static cudaError_t lastcol(MpArr X, int64_t N, MpArr F, MpArr out, int normalised, const int* status,
@@ -720,6 +874,10 @@ struct Launch {
     s.lastcol = &lastcol;
     s.recip1 = &recip1;
     s.batch = &batch;
+    s.usolve_update = &usolve_update;
+    s.init_s = &init_s;
+    s.rowscale = &rowscale;
+    s.to_f64 = &to_f64;
     s.batch_blocks_per_sm = &batch_blocks_per_sm;
     return s;
   }

@@ -45,6 +45,13 @@ struct KernelSet {
   // persistent batch kernel (blocks = resident blocks to launch)
   cudaError_t (*batch)(MpArr X, MpArr D, MpArr Z, const BatchDescHost& bd, int p, int blocks, cudaStream_t st);
   int (*batch_blocks_per_sm)();
+  // adjoint (back substitution X = U^-1 L and the binary64 gradient)
+  cudaError_t (*usolve_update)(MpArr S, int64_t N, int64_t k, MpArr Z, const int* status, int p, int nsm,
+                               cudaStream_t st);
+  cudaError_t (*init_s)(MpArr X, int64_t N, MpArr S, int nsm, cudaStream_t st);
+  cudaError_t (*rowscale)(MpArr S, int64_t N, int64_t k, MpArr R, cudaStream_t st);
+  cudaError_t (*to_f64)(MpArr X, int64_t N, double* out, double scale, int p, int transpose, int nsm,
+                        cudaStream_t st);
 };
 
 // Kernel set for n = p/32 limbs, or nullptr if this n is not instantiated.

@@ -4,6 +4,7 @@
 // data and enqueues launches.
 #include <cstdarg>
 #include <cstdio>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -45,6 +46,7 @@ struct mpdet_ctx {
   int device = 0, nsm = 0;
   const KernelSet* ks = nullptr;
   MpArr X{}, D{}, Z{}, R{}, T{};  // matrix, minors, multipliers, reciprocal, temp (N numbers)
+  MpArr S{};                      // adjoint: S = L, then X = A^-1 (N*N numbers, allocated on first use)
   int* status = nullptr;          // [0] code
   int64_t* zero_k = nullptr;
   void* stage = nullptr;  // device staging for host inputs
@@ -167,6 +169,7 @@ extern "C" int mpdet_free(mpdet_t h) {
   free_arr(&h->Z);
   free_arr(&h->T);
   free_arr(&h->R);
+  free_arr(&h->S);
   if (h->status) cudaFree(h->status);
   if (h->zero_k) cudaFree(h->zero_k);
   if (h->stage) cudaFree(h->stage);
@@ -477,5 +480,82 @@ extern "C" int mpdet_resume(mpdet_t h, mpdet_numv A, mpdet_numv minors, int64_t 
     if (rc) return rc;
   }
   h->k_done = k_done;
+  return finish_call(h, device_ptr);
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint (step a8): log|det| and d log|det| / dA = A^-T.
+// ---------------------------------------------------------------------------
+extern "C" int mpdet_logabsdet_grad(mpdet_t h, const double* A, int64_t ld, double* logabs, int* sign, double* grad,
+                                    double grad_scale, int device_ptr) {
+  if (!h || !A || !logabs || !sign) return fail(h, MPDET_EINVAL, "logabsdet_grad: null argument");
+  if (grad && !(h->flags & MPDET_LASTCOL)) return fail(h, MPDET_ESTATE, "logabsdet_grad: gradient needs MPDET_LASTCOL");
+  int rc = set_dense(h, A, ld, device_ptr, 0);
+  if (rc) return rc;
+  rc = run_steps(h, 0, h->N);
+  if (rc) return rc;
+  int64_t zk = 0;
+  int st = mpdet_status(h, &zk);
+  const int64_t N = h->N, n = h->n;
+  // det = D_N on the host: log|det| = ln(m / 2^p) + e ln 2 in binary64
+  int8_t ds = 0;
+  int64_t de = 0;
+  uint32_t top[2] = {0, 0};
+  CU(h, cudaMemcpyAsync(&ds, h->D.s + (N - 1), 1, cudaMemcpyDeviceToHost, h->stream));
+  CU(h, cudaMemcpyAsync(&de, h->D.e + (N - 1), 8, cudaMemcpyDeviceToHost, h->stream));
+  CU(h, cudaMemcpyAsync(top, h->D.m + (size_t)(N - 1) * n + (n - 2), 8, cudaMemcpyDeviceToHost, h->stream));
+  CU(h, cudaStreamSynchronize(h->stream));
+  if (de == INT64_MIN) {
+    *logabs = -HUGE_VAL;
+    *sign = 0;
+    if (st) return st;
+    return grad ? fail(h, MPDET_EZERODIV, "logabsdet_grad: singular matrix (det = 0), no gradient") : MPDET_OK;
+  }
+  *sign = ds ? -1 : 1;
+  *logabs = log((double)top[1] * 0x1p-32 + (double)top[0] * 0x1p-64) + (double)de * 0.69314718055994530942;
+  if (st) return st;
+  if (!grad) return MPDET_OK;
+  if (!h->S.m && alloc_arr(h, &h->S, N * N)) return MPDET_ENOMEM;
+  CU(h, h->ks->init_s(h->X, N, h->S, h->nsm, h->stream));
+  h->launches += 1;
+  for (int64_t k = N - 1; k >= 0; --k) {
+    CU(h, h->ks->recip1(h->X, k * N + k, h->R, h->status, MPDET_EZERODIV, h->stream));
+    CU(h, h->ks->rowscale(h->S, N, k, h->R, h->stream));
+    h->launches += 2;
+    if (k > 0) {  // Z[0..k) = U column k, rows above the diagonal
+      CU(h, cudaMemcpy2DAsync(h->Z.m, (size_t)n * 4, h->X.m + (size_t)k * n, (size_t)N * n * 4, (size_t)n * 4, (size_t)k,
+                              cudaMemcpyDeviceToDevice, h->stream));
+      CU(h, cudaMemcpy2DAsync(h->Z.e, 8, h->X.e + k, (size_t)N * 8, 8, (size_t)k, cudaMemcpyDeviceToDevice, h->stream));
+      CU(h, cudaMemcpy2DAsync(h->Z.s, 1, h->X.s + k, (size_t)N, 1, (size_t)k, cudaMemcpyDeviceToDevice, h->stream));
+      CU(h, h->ks->usolve_update(h->S, N, k, h->Z, h->status, h->p, h->nsm, h->stream));
+      h->launches += 1;
+    }
+  }
+  double* g = grad;
+  if (!device_ptr) {
+    size_t bytes = (size_t)N * N * 8;
+    if (h->stage_bytes < bytes) {
+      if (h->stage) cudaFree(h->stage);
+      h->stage = nullptr;
+      h->stage_bytes = 0;
+      if (cudaMalloc(&h->stage, bytes) != cudaSuccess) return fail(h, MPDET_ENOMEM, "gradient staging");
+      h->stage_bytes = bytes;
+    }
+    g = (double*)h->stage;
+  }
+  CU(h, h->ks->to_f64(h->S, N, g, grad_scale, h->p, 1, h->nsm, h->stream));
+  h->launches += 1;
+  if (!device_ptr) CU(h, cudaMemcpyAsync(grad, g, (size_t)N * N * 8, cudaMemcpyDeviceToHost, h->stream));
+  CU(h, cudaStreamSynchronize(h->stream));
+  return mpdet_status(h, nullptr);
+}
+
+// Copy out A^-1 (N*N numbers, row-major) computed by the last
+// mpdet_logabsdet_grad call with a gradient.
+extern "C" int mpdet_get_inverse(mpdet_t h, mpdet_numv out, int device_ptr) {
+  if (!h) return MPDET_EINVAL;
+  if (!h->S.m) return fail(h, MPDET_ESTATE, "get_inverse: no gradient computed yet");
+  int rc = copy_arr(h, h->S, out, h->N * h->N, device_ptr, false);
+  if (rc) return rc;
   return finish_call(h, device_ptr);
 }
