@@ -259,6 +259,13 @@ int mpdet_batch_factor(mpdet_batch_t b, mpdet_numv minors, int64_t* zero_k, int 
 int64_t mpdet_batch_launches(mpdet_batch_t b);
 int mpdet_batch_free(mpdet_batch_t b);
 
+/* Element-wise arithmetic of the kernels on device arrays of count numbers
+ * (diagnostics and tests of the arithmetic core; the method's rounding rules):
+ * op 0: out = RN(a*b), 1: RN(a-b), 2: RN(a+b), 3: RN(1/a) (b ignored; 1/0
+ * gives +0).  All pointers are device memory; synchronises cuda_stream.
+ * Errors: MPDET_EINVAL, MPDET_ECUDA. */
+int mpdet_ops(int op, int64_t count, int32_t p_bits, mpdet_numv a, mpdet_numv b, mpdet_numv out, void* cuda_stream);
+
 /* Release the handle and its device memory (NULL is accepted). */
 int mpdet_free(mpdet_t h);
 

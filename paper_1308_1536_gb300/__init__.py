@@ -85,6 +85,7 @@ def load(build_if_missing: bool = True):
         "mpdet_logabsdet_grad": ([P, P, i64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), P,
                                   ctypes.c_double, ctypes.c_int], ctypes.c_int),
         "mpdet_get_inverse": ([P, NumV, ctypes.c_int], ctypes.c_int),
+        "mpdet_ops": ([ctypes.c_int, i64, i32, NumV, NumV, NumV, P], ctypes.c_int),
         "mpdet_factor_noalloc": ([i64, i32, u32, NumV, NumV, NumV, ctypes.POINTER(i64), P], ctypes.c_int),
         "mpdet_profile_read": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)], ctypes.c_int),
@@ -122,6 +123,24 @@ def factor_noalloc(A, N: int, p: int, minors, lastcol=None, stream=None):
     if rc not in (OK, EZEROPIVOT):
         raise MpdetError(rc, f"factor_noalloc(N={N}, p={p})")
     return rc, int(zk.value)
+
+
+def ops(op: str, a, b, p: int):
+    """Element-wise RN(a*b) ('mul'), RN(a-b) ('sub'), RN(a+b) ('add') or
+    RN(1/a) ('recip') on the GPU; a, b host triples; returns a host triple."""
+    import torch
+
+    code = {"mul": 0, "sub": 1, "add": 2, "recip": 3}[op]
+    lib = load()
+    count = len(a[0])
+    dev = lambda t: (torch.from_numpy(np.ascontiguousarray(t[0])).cuda(), torch.from_numpy(np.ascontiguousarray(t[1])).cuda(),
+                     torch.from_numpy(np.ascontiguousarray(t[2]).view(np.int32)).cuda())
+    A, B = dev(a), dev(b if b is not None else a)
+    O = dev(empty(count, p))
+    rc = lib.mpdet_ops(code, count, p, _numv(A), _numv(B), _numv(O), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if rc:
+        raise MpdetError(rc, f"ops({op})")
+    return (O[0].cpu().numpy(), O[1].cpu().numpy(), O[2].cpu().numpy().view(np.uint32))
 
 
 def empty(count: int, p: int):

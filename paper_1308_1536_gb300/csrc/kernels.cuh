@@ -742,6 +742,76 @@ __global__ void __launch_bounds__(128, 4) k_batch(MpArr Xall, MpArr Dall, MpArr 
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Element-wise operations on arrays of numbers (diagnostics and tests of the
+// arithmetic core): op 0: RN(a*b), 1: RN(a-b), 2: RN(a+b), 3: RN(1/a).
+// ---------------------------------------------------------------------------
+template <int W, int G>
+__global__ void k_ops(int op, int64_t count, MpArr A, MpArr B, MpArr O, int p) {
+  constexpr int n = W * G;
+  constexpr int SW = Scratch<W, G>::words;
+  constexpr int GPW = 32 / G;
+  extern __shared__ __align__(16) uint32_t smem[];
+  Grp<G> gp;
+  uint32_t* buf = smem + (threadIdx.x / G) * SW;
+  uint32_t* zb = smem + (blockDim.x / G) * SW + (threadIdx.x / G) * n;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  const int64_t nwarps = (int64_t)gridDim.x * blockDim.x / 32;
+  for (int64_t base = warp * GPW; base < count; base += nwarps * GPW) {
+    int64_t idx = base + gp.lane / G;
+    const bool active = idx < count;
+    if (!active) idx = count - 1;
+    uint32_t a[W], b[W], o[W];
+    load_slice<W>(A.m + idx * n + gp.g * W, a);
+    load_slice<W>(B.m + idx * n + gp.g * W, b);
+    int8_t as = A.s[idx], bs = B.s[idx], os = 0;
+    int64_t ae = A.e[idx], be = B.e[idx], oe = ZEXP;
+    if (op == 0) {
+      store_slice<W>(zb + gp.g * W, b);
+      __syncwarp();
+      const int adj = mul_round<W, G>(gp, a, zb, o);
+      __syncwarp();
+      if (ae == ZEXP || be == ZEXP) {
+#pragma unroll
+        for (int q = 0; q < W; ++q) o[q] = 0u;
+      } else {
+        os = (int8_t)(as ^ bs);
+        oe = ae + be + adj;
+      }
+    } else if (op == 1 || op == 2) {
+      const int8_t bsx = (op == 2 && be != ZEXP) ? (int8_t)(bs ^ 1) : bs;  // a + b = a - (-b)
+      sub_round<W, G>(gp, p, as, ae, a, bsx, be, b, buf);
+#pragma unroll
+      for (int q = 0; q < W; ++q) o[q] = a[q];
+      os = as;
+      oe = ae;
+    } else {
+      const bool z = (ae == ZEXP);
+      if (z) {  // no reciprocal of zero: divide a dummy, report +0
+#pragma unroll
+        for (int q = 0; q < W; ++q) a[q] = 0u;
+        if (gp.g == G - 1) a[W - 1] = 0x80000000u;
+      }
+      const int adj = recip_round<W, G>(gp, a, buf, o);
+      if (z) {
+#pragma unroll
+        for (int q = 0; q < W; ++q) o[q] = 0u;
+      } else {
+        os = as;
+        oe = (int64_t)adj - ae;
+      }
+    }
+    if (active) {
+      store_slice<W>(O.m + idx * n + gp.g * W, o);
+      if (gp.g == 0) {
+        O.s[idx] = os;
+        O.e[idx] = oe;
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------
@@ -859,6 +929,15 @@ struct Launch {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<W, G>, 128, 0) != cudaSuccess) return 1;
     return nb > 0 ? nb : 1;
   }
+  static cudaError_t ops(int op, int64_t count, MpArr A, MpArr B, MpArr O, int p, int nsm, cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    int64_t blocks = (count + NT / G - 1) / (NT / G);
+    if (blocks > (int64_t)nsm * 8) blocks = (int64_t)nsm * 8;
+    size_t sm = (size_t)(NT / G) * (SW + n) * 4;
+    cudaFuncSetAttribute(k_ops<W, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_ops<W, G><<<(unsigned)blocks, NT, sm, st>>>(op, count, A, B, O, p);
+    return cudaGetLastError();
+  }
   static KernelSet make() {
     KernelSet s;
     s.W = W;
@@ -875,6 +954,7 @@ struct Launch {
     s.recip1 = &recip1;
     s.batch = &batch;
     s.usolve_update = &usolve_update;
+    s.ops = &ops;
     s.init_s = &init_s;
     s.rowscale = &rowscale;
     s.to_f64 = &to_f64;

@@ -45,6 +45,8 @@ struct KernelSet {
   // persistent batch kernel (blocks = resident blocks to launch)
   cudaError_t (*batch)(MpArr X, MpArr D, MpArr Z, const BatchDescHost& bd, int p, int blocks, cudaStream_t st);
   int (*batch_blocks_per_sm)();
+  // element-wise arithmetic (diagnostics)
+  cudaError_t (*ops)(int op, int64_t count, MpArr A, MpArr B, MpArr O, int p, int nsm, cudaStream_t st);
   // adjoint (back substitution X = U^-1 L and the binary64 gradient)
   cudaError_t (*usolve_update)(MpArr S, int64_t N, int64_t k, MpArr Z, const int* status, int p, int nsm,
                                cudaStream_t st);

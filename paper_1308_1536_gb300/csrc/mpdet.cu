@@ -559,3 +559,24 @@ extern "C" int mpdet_get_inverse(mpdet_t h, mpdet_numv out, int device_ptr) {
   if (rc) return rc;
   return finish_call(h, device_ptr);
 }
+
+// Element-wise arithmetic on device arrays (diagnostics and tests).
+extern "C" int mpdet_ops(int op, int64_t count, int32_t p_bits, mpdet_numv a, mpdet_numv b, mpdet_numv out,
+                         void* cuda_stream) {
+  int32_t n = 0;
+  if (op < 0 || op > 3 || count < 0 || mpdet_geometry(p_bits, &n, nullptr, nullptr) != MPDET_OK) return MPDET_EINVAL;
+  if (!a.sign || !a.exp || !a.limbs || !b.sign || !b.exp || !b.limbs || !out.sign || !out.exp || !out.limbs)
+    return MPDET_EINVAL;
+  const KernelSet* ks = mpd::kernel_set_for(n);
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return MPDET_ECUDA;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (ks->ops(op, count, MpArr{a.sign, a.exp, a.limbs}, MpArr{b.sign, b.exp, b.limbs},
+              MpArr{out.sign, out.exp, out.limbs}, p_bits, nsm, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    return MPDET_ECUDA;
+  }
+  return MPDET_OK;
+}

@@ -346,22 +346,46 @@ __device__ __forceinline__ void sub_round(const Grp<G>& gp, int p, int8_t& xs, i
     int64_t d64 = eA - eB;
     d = (int)(d64 > (int64_t)(p + 72) ? (int64_t)(p + 72) : d64);
   }
-  // B's slice to shared memory, zero tail
-  store_slice<W>(buf + g * W, Bv);
-  if (g == G - 1) {
+  // Aligned B: frame limb f holds bits [32f + d - 64, ..) of B.  Fast path
+  // (every group of the warp has d < 64, or B == 0): the shift stays within
+  // two limbs and is done in registers with the next lane's first limbs.
+  // Otherwise B goes through shared memory and the bits below the frame are
+  // jammed into the sticky bit.
+  uint32_t Y[W], y0, y1;
+  const bool fastA = (eB == ZEXP) || (eA != ZEXP && eA - eB <= 63);
+  if (__all_sync(FULL, fastA)) {
+    const int da = (eB == ZEXP) ? 0 : d;
+    const int q = da >> 5, r = da & 31;
+    uint32_t n0 = __shfl_down_sync(FULL, Bv[0], 1), n1 = __shfl_down_sync(FULL, Bv[1], 1);
+    if (g == G - 1) n0 = n1 = 0u;
+    uint32_t Bx[W + 2];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) buf[n + i] = 0u;
+    for (int i = 0; i < W; ++i) Bx[i] = Bv[i];
+    Bx[W] = n0;
+    Bx[W + 1] = n1;
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+      const uint32_t lo = q ? Bx[i + 1] : Bx[i];
+      const uint32_t hi = q ? Bx[i + 2] : Bx[i + 1];
+      Y[i] = __funnelshift_r(lo, hi, r);
+    }
+    y0 = q ? __funnelshift_r(0u, Bv[0], r) : 0u;
+    y1 = q ? __funnelshift_r(Bv[0], Bv[1], r) : __funnelshift_r(0u, Bv[0], r);
+  } else {
+    store_slice<W>(buf + g * W, Bv);
+    if (g == G - 1) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) buf[n + i] = 0u;
+    }
+    __syncwarp();
+    // sticky of B's bits below the frame (bit index d - 64 of B)
+    const bool lost = gp.ballot(any_below<W>(Bv, g * W, d - 64)) != 0u;
+#pragma unroll
+    for (int i = 0; i < W; ++i) Y[i] = funnel(buf, 32 * (2 + g * W + i) + d - 64, n);
+    y0 = funnel(buf, d - 64, n) | (lost ? 1u : 0u);
+    y1 = funnel(buf, 32 + d - 64, n);
+    __syncwarp();
   }
-  __syncwarp();
-  // sticky of B's bits below the frame (bit index d - 64 of B)
-  const bool lost = gp.ballot(any_below<W>(Bv, g * W, d - 64)) != 0u;
-  // aligned B: frame limb f holds bits [32f + d - 64, ..) of B
-  uint32_t Y[W];
-#pragma unroll
-  for (int i = 0; i < W; ++i) Y[i] = funnel(buf, 32 * (2 + g * W + i) + d - 64, n);
-  uint32_t y0 = funnel(buf, d - 64, n) | (lost ? 1u : 0u);
-  uint32_t y1 = funnel(buf, 32 + d - 64, n);
-  __syncwarp();
   // S = A*2^64 +- Ybar  (two's complement for subtraction)
   const uint32_t inv = eff_sub ? 0xffffffffu : 0u;
 #pragma unroll
@@ -408,33 +432,58 @@ __device__ __forceinline__ void sub_round(const Grp<G>& gp, int p, int8_t& xs, i
   } else {
     topbit = 32 * tf + 31 - __clz(tl);
   }
-  // frame to shared memory
-#pragma unroll
-  for (int i = 0; i < W; ++i) buf[2 + g * W + i] = S[i];  // frame limbs 2..n+1 (8-byte offset: scalar stores)
-  if (g == 0) {
-    buf[0] = s0;
-    buf[1] = s1;
-  }
-  if (g == G - 1) buf[n + 2] = sx;
-  __syncwarp();
-  // mantissa: output limb l takes frame bits [32l + sh, ..), sh = topbit-(p-1)
+  // mantissa: output limb l takes frame bits [32l + sh, ..), sh = topbit-(p-1).
+  // Fast path (every group of the warp has sh in [32, 65] or a zero result):
+  // at most 32 bits of cancellation, the shift uses the neighbouring lanes'
+  // edge limbs and the round and sticky bits lie in lane 0's guard limbs.
   const int sh = topbit - (p - 1);
   uint32_t Mo[W];
-#pragma unroll
-  for (int i = 0; i < W; ++i) Mo[i] = funnel(buf, 32 * (g * W + i) + sh, n + 3);
   uint32_t rbit = 0u;
   bool st = false;
-  if (sh >= 1) {
-    rbit = (funnel(buf, sh - 1, n + 3)) & 1u;
+  const bool fastN = zero || (sh >= 32 && sh <= 65);
+  if (__all_sync(FULL, fastN)) {
+    uint32_t prev = __shfl_up_sync(FULL, S[W - 1], 1);
+    uint32_t next = __shfl_down_sync(FULL, S[0], 1);
+    if (g == 0) prev = s1;
+    if (g == G - 1) next = sx;
+    const int q = sh >> 5, r = sh & 31;  // q in {1, 2}
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+      const uint32_t lo = (q == 1) ? (i == 0 ? prev : S[i - 1]) : S[i];
+      const uint32_t hi = (q == 1) ? S[i] : (i == W - 1 ? next : S[i + 1]);
+      Mo[i] = __funnelshift_r(lo, hi, r);
+    }
+    const uint64_t g64 = ((uint64_t)s1 << 32) | s0;
+    const int rb = zero ? 40 : sh - 1;  // 31..64 (any in-range value for a zero result)
+    uint32_t r0 = (rb < 64) ? (uint32_t)((g64 >> rb) & 1ull) : (S[0] & 1u);
+    uint32_t t0 = (rb < 64) ? (uint32_t)((g64 & ((1ull << rb) - 1ull)) != 0ull) : (uint32_t)(g64 != 0ull);
+    rbit = gp.from(r0, 0);
+    st = gp.from(t0, 0) != 0u;
+    if (zero) rbit = 0u;
+  } else {
+    // frame to shared memory
+#pragma unroll
+    for (int i = 0; i < W; ++i) buf[2 + g * W + i] = S[i];  // frame limbs 2..n+1 (8-byte offset: scalar stores)
+    if (g == 0) {
+      buf[0] = s0;
+      buf[1] = s1;
+    }
+    if (g == G - 1) buf[n + 2] = sx;
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < W; ++i) Mo[i] = funnel(buf, 32 * (g * W + i) + sh, n + 3);
+    if (sh >= 1) {
+      rbit = (funnel(buf, sh - 1, n + 3)) & 1u;
+    }
+    // sticky: frame bits below sh-1 (this lane's frame limbs, lane 0's guards)
+    bool stl = any_below<W>(S, 2 + g * W, sh - 1);
+    if (g == 0) {
+      uint32_t gv[2] = {s0, s1};
+      stl = stl || any_below<2>(gv, 0, sh - 1);
+    }
+    st = gp.ballot(stl && sh >= 2) != 0u;
+    __syncwarp();
   }
-  // sticky: frame bits below sh-1 (this lane's frame limbs, lane 0's guards)
-  bool stl = any_below<W>(S, 2 + g * W, sh - 1);
-  if (g == 0) {
-    uint32_t gv[2] = {s0, s1};
-    stl = stl || any_below<2>(gv, 0, sh - 1);
-  }
-  st = gp.ballot(stl && sh >= 2) != 0u;
-  __syncwarp();
   uint32_t lsb = gp.from(Mo[0], 0) & 1u;
   uint32_t inc = rbit & ((st ? 1u : 0u) | lsb);
   uint32_t ones = gp.ballot(all_ones<W>(Mo));
