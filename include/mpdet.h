@@ -153,9 +153,12 @@ int64_t mpdet_steps_done(mpdet_t h);
 
 /* Tuning knobs (results are identical for every setting; only speed
  * changes).  MPDET_TUNE_UPDATE_VARIANT selects the register budget of the
- * Schur-update kernel: value v in 0..3 compiles it for at least 3 + v
- * resident 128-thread blocks per SM.  Errors: MPDET_EINVAL. */
-enum { MPDET_TUNE_UPDATE_VARIANT = 1 };
+ * IMAD Schur-update kernel: value v in 0..3 compiles it for at least 3 + v
+ * resident 128-thread blocks per SM.  MPDET_TUNE_ENGINE selects how the
+ * update forms its products: 1 (default) on the tensor cores as an exact
+ * digit convolution where that engine exists (p = 2048), 0 with IMAD limb
+ * products everywhere.  Errors: MPDET_EINVAL. */
+enum { MPDET_TUNE_UPDATE_VARIANT = 1, MPDET_TUNE_ENGINE = 2 };
 int mpdet_tune(mpdet_t h, int param, int value);
 
 /* Instrumentation (not part of the computation).  mpdet_profile(h, 1)

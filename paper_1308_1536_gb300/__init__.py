@@ -329,8 +329,13 @@ class Mpdet:
         return Xi
 
     # -- tuning (bit-identical results for every setting) -------------------
-    def tune(self, update_variant: int):
-        self._check(self.lib.mpdet_tune(self.h, 1, int(update_variant)), "tune")
+    def tune(self, update_variant: int | None = None, engine: int | None = None):
+        """update_variant: IMAD update register budget 0..3; engine: 1 tensor
+        cores (p = 2048), 0 IMAD.  Results are bit-identical for every setting."""
+        if update_variant is not None:
+            self._check(self.lib.mpdet_tune(self.h, 1, int(update_variant)), "tune")
+        if engine is not None:
+            self._check(self.lib.mpdet_tune(self.h, 2, int(engine)), "tune")
 
     # -- instrumentation ----------------------------------------------------
     def profile(self, enable: bool = True):

@@ -308,6 +308,9 @@ struct UpdArgs {
   int cmode;
 };
 
+// tensor-core engine for p = 2048 (tc_update.cu)
+cudaError_t update_tc_p2048(MpArr X, UpdArgs a, MpArr Z, int* status, int p, int nsm, cudaStream_t st);
+
 template <int W, int G, int MINB>
 __global__ void __launch_bounds__(128, MINB) k_update(MpArr X, UpdArgs a, MpArr Z, const int* status, int p,
                                                      int rows_per_cta) {

@@ -1,0 +1,340 @@
+// Tensor-core engine for the rank-1 update at p = 2048 (n = 64 limbs).
+//
+// The exact 2p-bit product of two mantissas is a convolution of their 8-bit
+// digits: c_r = sum_s z[s] * b[r - s], P = sum_r c_r 2^(8r).  Every c_r is a
+// sum of at most 256 products of digits <= 255, so it is below 2^24 and exact
+// in fp32; bf16 holds every digit exactly.  For a block of 128 rows i and one
+// column j the c_r of all 128 products are one GEMM on the 5th-generation
+// tensor cores: D[i][r] = sum_k A[i][k] * B[k][r] with A[i][k'] = z_i[255-k']
+// (digits reversed along K) and B[k'][r] = b_j[r - 255 + k'], a Hankel matrix:
+// its 8x8 core matrices depend only on (n-core + k-core), so 95 distinct cores
+// (12 KB of shared memory) serve the whole 256 x 512 operand through one
+// descriptor with equal leading and stride byte offsets.  D lives in tensor
+// memory (4 tiles of 128 columns); each thread then owns one row, turns its
+// 512 exact column sums into the 128-limb product with a running carry,
+// rounds it to p bits (round to nearest even) and leaves it in shared memory,
+// where the lane groups of the IMAD engine subtract it from x_ij with the same
+// sub_round.  Results are bit-identical to the IMAD engine.
+//
+// tcgen05 use: one thread issues the MMAs (kind::f16, bf16 inputs, fp32
+// accumulate, M = 128, N = 128, K = 16), tcgen05.commit signals an mbarrier
+// per tile; every wait is bounded and reports MPDET_ETIMEOUT through the
+// status word; the block always frees its tensor memory.
+#include <cuda_bf16.h>
+
+#include "kernels.cuh"
+
+namespace mpd {
+namespace tc {
+
+constexpr int n = 64;      // limbs per number
+constexpr int KD = 256;    // 8-bit digits per mantissa
+constexpr int M = 128;     // rows per block (MMA M)
+constexpr int NT = 128;    // output positions per tile (MMA N)
+constexpr int TILES = 4;   // 512 output positions
+constexpr int NCORE = 95;  // Hankel cores
+constexpr int W = 16, G = 4;
+constexpr int SW = Scratch<W, G>::words;
+constexpr int RSTR = 68;   // words per staged row (16-byte aligned; 8 rows hit distinct bank quads)
+
+// shared memory layout (bytes)
+constexpr int OFF_A = 0;                        // 128 x 256 bf16 = 64 KB
+constexpr int OFF_H = OFF_A + M * KD * 2;       // Hankel cores, 95 x 128 B
+constexpr int OFF_T = OFF_H + 12288;            // rounded products, 128 x 68 words
+constexpr int OFF_X = OFF_T + M * RSTR * 4;     // x_ij rows of the column, 128 x 68 words
+constexpr int OFF_B = OFF_X + M * RSTR * 4;     // b_j limbs, 64 words
+constexpr int OFF_TE = OFF_B + 256;             // 128 int64 exponents of t
+constexpr int OFF_XE = OFF_TE + M * 8;          // 128 int64 exponents of x
+constexpr int OFF_TS = OFF_XE + M * 8;          // 128 int8 signs of t, 128 multiplier flags
+constexpr int OFF_XS = OFF_TS + 256;            // 128 int8 signs of x
+constexpr int OFF_SCR = OFF_XS + 128;           // 32 groups x SW words
+constexpr int OFF_BAR = OFF_SCR + 32 * SW * 4;  // mbarriers + tmem slot
+constexpr int SMEM = OFF_BAR + 128;
+
+__device__ __forceinline__ void cp16(uint32_t saddr, const void* g) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr), "l"(g));
+}
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  // no swizzle, K-major: LBO steps between core matrices along K, SBO along M/N
+  return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)((lbo & 0x3FFFF) >> 4) << 16) |
+         ((uint64_t)((sbo & 0x3FFFF) >> 4) << 32) | ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ bool bar_wait(uint32_t addr, uint32_t phase) {
+  uint32_t done = 0;
+  for (int it = 0; it < (1 << 24) && !done; ++it)
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(done)
+                 : "r"(addr), "r"(phase));
+  return done != 0;
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+        "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;");
+}
+
+// bf16 of a digit 0..255 (exact): the bit pattern of (float)d >> 16
+__device__ __forceinline__ uint16_t dbf(uint32_t d) { return (uint16_t)(__float_as_uint((float)d) >> 16); }
+
+__global__ void __launch_bounds__(128, 1) k_update_tc(MpArr X, UpdArgs a, MpArr Z, int* status, int p, int col_chunk) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  if (status_set(status)) return;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  unsigned char* sA = sm + OFF_A;
+  unsigned char* sH = sm + OFF_H;
+  uint32_t* sT = reinterpret_cast<uint32_t*>(sm + OFF_T);
+  uint32_t* sX = reinterpret_cast<uint32_t*>(sm + OFF_X);
+  uint32_t* sB = reinterpret_cast<uint32_t*>(sm + OFF_B);
+  int64_t* sTe = reinterpret_cast<int64_t*>(sm + OFF_TE);
+  int64_t* sXe = reinterpret_cast<int64_t*>(sm + OFF_XE);
+  int8_t* sTs = reinterpret_cast<int8_t*>(sm + OFF_TS);
+  int8_t* sXs = reinterpret_cast<int8_t*>(sm + OFF_XS);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + OFF_BAR);  // 4 tile barriers
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + OFF_BAR + 64);
+  const int64_t N = a.N;
+  const int64_t ncols = a.cmode == 0 ? N - a.kcol - 1 : (a.cmode == 1 ? N - 1 : N);
+  const int64_t i0 = a.row0 + (int64_t)blockIdx.y * M;
+  const int64_t rend = a.row0 + a.nrows;
+  const int64_t c0 = (int64_t)blockIdx.x * col_chunk;
+  const int64_t c1 = (c0 + col_chunk < ncols) ? c0 + col_chunk : ncols;
+
+  // ---- A: digits of the 128 multipliers, K reversed (k' = 255 - s) --------
+  // core (k-core c, row-group g) at c*128 + g*4096, row r of the core at +16r
+  {
+    const int64_t i = i0 + tid;  // one row per thread
+    const bool have = i < rend && Z.e[i < rend ? i : i0] != ZEXP;
+    const uint32_t* zm = Z.m + (i < rend ? i : i0) * n;
+    unsigned char* rowbase = sA + (tid >> 3) * 4096 + (tid & 7) * 16;
+    for (int c = 0; c < 32; ++c) {
+      // digits s = 255-8c .. 248-8c are bytes of limbs 63-2c (high 4) and 62-2c (low 4), reversed
+      uint32_t hi = have ? zm[63 - 2 * c] : 0u, lo = have ? zm[62 - 2 * c] : 0u;
+      uint32_t w0 = dbf(hi >> 24) | ((uint32_t)dbf((hi >> 16) & 255) << 16);
+      uint32_t w1 = dbf((hi >> 8) & 255) | ((uint32_t)dbf(hi & 255) << 16);
+      uint32_t w2 = dbf(lo >> 24) | ((uint32_t)dbf((lo >> 16) & 255) << 16);
+      uint32_t w3 = dbf((lo >> 8) & 255) | ((uint32_t)dbf(lo & 255) << 16);
+      *reinterpret_cast<uint4*>(rowbase + c * 128) = make_uint4(w0, w1, w2, w3);
+    }
+    sTs[M + tid] = have ? 1 : 0;  // multiplier present (non-zero, row in range)
+  }
+  if (tid == 0)
+    for (int t = 0; t < TILES; ++t) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bars[t])));
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)), "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tslot;
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+  Grp<G> gp;
+  const int gid = tid / G;  // 32 groups
+  uint32_t* scr = reinterpret_cast<uint32_t*>(sm + OFF_SCR) + gid * SW;
+  const int8_t zsign = (i0 + tid < rend) ? Z.s[i0 + tid] : 0;
+  const int64_t zexp = (i0 + tid < rend) ? Z.e[i0 + tid] : ZEXP;
+  uint32_t phase = 0;
+  bool ok = true;
+
+  for (int64_t c = c0; c < c1 && ok; ++c) {
+    const int64_t j = a.cmode == 0 ? a.kcol + 1 + c : (a.cmode == 1 ? (c < a.kcol ? c : c + 1) : c);
+    const int64_t kj = a.brow * N + j;
+    const int64_t be = X.e[kj];
+    const int8_t bs = X.s[kj];
+    // ---- stage b_j and the 128 x_ij of this column (cp.async) ---------------
+    if (tid < 16) cp16(su32(sB) + 16 * tid, X.m + kj * n + 4 * tid);
+    asm volatile("cp.async.commit_group;");
+    {
+      const int64_t i = i0 + tid;
+      const int64_t ij = (i < rend ? i : i0) * N + j;
+      sXs[tid] = X.s[ij];
+      sXe[tid] = X.e[ij];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) cp16(su32(sX + tid * RSTR) + 16 * q, X.m + ij * n + 4 * q);
+    }
+    asm volatile("cp.async.commit_group;");
+    asm volatile("cp.async.wait_group 1;");  // b_j has landed (x_ij may still be in flight)
+    __syncthreads();
+    // ---- Hankel cores of b_j: H_d[nn][kk] = b[8d + nn + kk - 255] ----------
+    {
+      const unsigned char* bb = reinterpret_cast<const unsigned char*>(sB);  // little-endian digits
+      for (int q = tid; q < NCORE * 8; q += 128) {  // one core row (8 bf16) per item
+        const int d = q >> 3, nn = q & 7;
+        const int base = 8 * d + nn - 255;  // digit index of kk = 0
+        uint32_t w[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          uint32_t h2[2];
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int idx = base + 2 * e + u;
+            const uint32_t dg = (idx >= 0 && idx < KD && be != ZEXP) ? bb[idx] : 0u;
+            h2[u] = dbf(dg);
+          }
+          w[e] = h2[0] | (h2[1] << 16);
+        }
+        *reinterpret_cast<uint4*>(sH + d * 128 + nn * 16) = make_uint4(w[0], w[1], w[2], w[3]);
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    // ---- MMAs: 4 tiles x 16 K-steps ----------------------------------------
+    if (tid == 0) {
+      for (int t = 0; t < TILES; ++t) {
+        for (int ks = 0; ks < KD / 16; ++ks) {
+          const uint64_t ad = desc(su32(sA) + ks * 256, 128, 4096);
+          const uint64_t bd = desc(su32(sH) + (16 * t + 2 * ks) * 128, 128, 128);
+          const uint32_t acc = ks > 0 ? 1u : 0u;
+          asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+                           tmem + (uint32_t)(t * NT)),
+                       "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(&bars[t])));
+      }
+    }
+    // ---- epilogue: thread = row; column sums -> 128 limbs -> RN to p bits --
+    uint32_t up[64];  // limbs 64..127
+    uint32_t l63 = 0, sticky = 0;
+    uint64_t acc = 0;
+    bool okc = true;
+#pragma unroll
+    for (int t = 0; t < TILES; ++t) {
+      if (okc && !bar_wait(su32(&bars[t]), phase)) okc = false;
+      okc = __all_sync(0xffffffffu, okc);  // warp-uniform: tcgen05.ld is warp-collective
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      if (okc) {
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch) {  // 32 columns = 8 limbs per chunk
+          uint32_t v[32];
+          tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * NT + ch * 32), v);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const uint64_t c0v = __float2uint_rz(__uint_as_float(v[4 * q]));
+            const uint64_t c1v = __float2uint_rz(__uint_as_float(v[4 * q + 1]));
+            const uint64_t c2v = __float2uint_rz(__uint_as_float(v[4 * q + 2]));
+            const uint64_t c3v = __float2uint_rz(__uint_as_float(v[4 * q + 3]));
+            acc += c0v + (c1v << 8) + (c2v << 16) + (c3v << 24);
+            const uint32_t limb = (uint32_t)acc;
+            acc >>= 32;
+            const int L = t * 32 + ch * 8 + q;
+            if (L >= 64) up[L >= 64 ? L - 64 : 0] = limb;
+            else if (L == 63) l63 = limb;
+            else sticky |= limb;
+          }
+        }
+      }
+    }
+    ok = __syncthreads_and(okc) != 0;
+    if (!ok) break;
+    // round (same rule as mul_round): product has 2p or 2p-1 bits
+    {
+      const uint32_t top = up[63] >> 31;
+      uint32_t rbit, st;
+      if (top) {
+        rbit = l63 >> 31;
+        st = (l63 & 0x7fffffffu) | sticky;
+      } else {
+#pragma unroll
+        for (int q = 63; q > 0; --q) up[q] = (up[q] << 1) | (up[q - 1] >> 31);
+        up[0] = (up[0] << 1) | (l63 >> 31);
+        rbit = (l63 >> 30) & 1u;
+        st = (l63 & 0x3fffffffu) | sticky;
+      }
+      uint32_t inc = rbit & ((st != 0u) | (up[0] & 1u));
+      uint32_t carry = inc;
+#pragma unroll
+      for (int q = 0; q < 64; ++q) {
+        const uint64_t s = (uint64_t)up[q] + carry;
+        up[q] = (uint32_t)s;
+        carry = (uint32_t)(s >> 32);
+      }
+      int adj = top ? 0 : -1;
+      if (carry) {
+        up[63] = 0x80000000u;
+        adj += 1;
+      }
+      const bool tz = !sTs[M + tid] || be == ZEXP;
+#pragma unroll
+      for (int q = 0; q < 64; q += 4)
+        *reinterpret_cast<uint4*>(sT + tid * RSTR + q) =
+            tz ? make_uint4(0u, 0u, 0u, 0u) : make_uint4(up[q], up[q + 1], up[q + 2], up[q + 3]);
+      sTe[tid] = tz ? ZEXP : zexp + be + adj;
+      sTs[tid] = tz ? (int8_t)0 : (int8_t)(zsign ^ bs);
+    }
+    asm volatile("cp.async.wait_group 0;");  // x_ij rows have landed
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    // ---- x_ij = RN(x_ij - t_i) by lane groups (4 rows per group) ------------
+#pragma unroll 1
+    for (int rr = 0; rr < 4; ++rr) {
+      const int r = gid + 32 * rr;
+      const int64_t i = i0 + r;
+      const bool active = i < rend;
+      const int64_t ij = (active ? i : i0) * N + j;
+      uint32_t Xv[W], T[W];
+      load_slice<W>(sX + r * RSTR + gp.g * W, Xv);
+      load_slice<W>(sT + r * RSTR + gp.g * W, T);
+      int8_t xs = sXs[r];
+      int64_t xe = sXe[r];
+      sub_round<W, G>(gp, p, xs, xe, Xv, sTs[r], sTe[r], T, scr);
+      if (active) {
+        store_slice<W>(X.m + ij * n + gp.g * W, Xv);
+        if (gp.g == 0) {
+          X.s[ij] = xs;
+          X.e[ij] = xe;
+        }
+      }
+    }
+    phase ^= 1u;
+    __syncthreads();  // sT and sH are rewritten by the next column
+  }
+  if (!ok && tid == 0) atomicExch(status, 5);  // MPDET_ETIMEOUT
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
+}  // namespace tc
+
+// Launch: 128-row blocks x column chunks sized to fill the SMs once.
+cudaError_t update_tc_p2048(MpArr X, UpdArgs a, MpArr Z, int* status, int p, int nsm, cudaStream_t st) {
+  const int64_t ncols = a.cmode == 0 ? a.N - a.kcol - 1 : (a.cmode == 1 ? a.N - 1 : a.N);
+  if (a.nrows <= 0 || ncols <= 0) return cudaSuccess;
+  const int64_t by = (a.nrows + tc::M - 1) / tc::M;
+  int64_t bx = nsm / by;  // one wave: at most one block per SM
+  if (bx > ncols) bx = ncols;
+  if (bx < 1) bx = 1;
+  const int64_t chunk = (ncols + bx - 1) / bx;
+  bx = (ncols + chunk - 1) / chunk;
+  cudaFuncSetAttribute(tc::k_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM);
+  dim3 grid((unsigned)bx, (unsigned)by);
+  tc::k_update_tc<<<grid, 128, tc::SMEM, st>>>(X, a, Z, status, p, (int)chunk);
+  return cudaGetLastError();
+}
+
+// Schur update of step k (lastcol: every column but k) on the tensor cores.
+cudaError_t update_tc_p2048_step(MpArr X, int64_t N, int64_t k, MpArr Z, int* status, int p, int lastcol, int nsm,
+                                 cudaStream_t st) {
+  UpdArgs a{N, k, k + 1, N - k - 1, k, lastcol ? 1 : 0};
+  return update_tc_p2048(X, a, Z, status, p, nsm, st);
+}
+
+// Back-substitution update of the adjoint (rows [0, k), every column).
+cudaError_t usolve_tc_p2048(MpArr S, int64_t N, int64_t k, MpArr Z, int* status, int p, int nsm, cudaStream_t st) {
+  UpdArgs a{N, k, 0, k, 0, 2};
+  return update_tc_p2048(S, a, Z, status, p, nsm, st);
+}
+
+}  // namespace mpd
