@@ -156,8 +156,10 @@ int64_t mpdet_steps_done(mpdet_t h);
  * IMAD Schur-update kernel: value v in 0..3 compiles it for at least 3 + v
  * resident 128-thread blocks per SM.  MPDET_TUNE_ENGINE selects how the
  * update forms its products: 1 (default) on the tensor cores as an exact
- * digit convolution where that engine exists (p = 2048), 0 with IMAD limb
- * products everywhere.  Errors: MPDET_EINVAL. */
+ * digit convolution where that engine exists (p = 2048), warp-specialised so
+ * that the tensor core, the rounding and the subtraction overlap; 2 the same
+ * one phase at a time; 0 with IMAD limb products everywhere.
+ * Errors: MPDET_EINVAL. */
 enum { MPDET_TUNE_UPDATE_VARIANT = 1, MPDET_TUNE_ENGINE = 2 };
 int mpdet_tune(mpdet_t h, int param, int value);
 

@@ -59,9 +59,11 @@ struct KernelSet {
 struct UpdArgs;  // kernels.cuh
 
 // Tensor-core engine of the rank-1 update, p = 2048 only (tc_update.cu).
+// pipelined = 1: warp-specialised kernel (tensor core, epilogue and subtraction overlap); 0: one role at a time
 cudaError_t update_tc_p2048_step(MpArr X, int64_t N, int64_t k, MpArr Z, int* status, int p, int lastcol, int nsm,
-                                 cudaStream_t st);
-cudaError_t usolve_tc_p2048(MpArr S, int64_t N, int64_t k, MpArr Z, int* status, int p, int nsm, cudaStream_t st);
+                                 cudaStream_t st, int pipelined);
+cudaError_t usolve_tc_p2048(MpArr S, int64_t N, int64_t k, MpArr Z, int* status, int p, int nsm, cudaStream_t st,
+                            int pipelined);
 
 // Kernel set for n = p/32 limbs, or nullptr if this n is not instantiated.
 const KernelSet* kernel_set_for(int n);

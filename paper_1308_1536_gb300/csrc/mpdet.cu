@@ -53,7 +53,7 @@ struct mpdet_ctx {
   size_t stage_bytes = 0;
   int64_t k_done = 0;
   int upd_variant = 1;
-  int engine = 1;  // 1: tensor cores where the kernel family has them (p = 2048), 0: IMAD
+  int engine = 1;  // 1: tensor cores, pipelined (p = 2048); 2: tensor cores, one role at a time; 0: IMAD
   bool have_matrix = false;
   char err[512] = {0};
   // instrumentation: kernel launches enqueued, and optional event pairs
@@ -311,8 +311,9 @@ static int run_steps(mpdet_t h, int64_t k0, int64_t k1) {
         if (rc) return rc;
         CU(h, cudaEventRecord(e0, h->stream));
       }
-      if (h->engine == 1 && h->p == 2048)
-        CU(h, mpd::update_tc_p2048_step(h->X, N, k, h->Z, h->status, h->p, lastcol, h->nsm, h->stream));
+      if (h->engine >= 1 && h->p == 2048)
+        CU(h, mpd::update_tc_p2048_step(h->X, N, k, h->Z, h->status, h->p, lastcol, h->nsm, h->stream,
+                                        h->engine == 1 ? 1 : 0));
       else
         CU(h, h->ks->update[h->upd_variant](h->X, N, k, h->Z, h->status, h->p, lastcol, h->nsm, h->stream));
       if (h->profile) {
@@ -335,7 +336,7 @@ extern "C" int mpdet_tune(mpdet_t h, int param, int value) {
       h->upd_variant = value;
       return MPDET_OK;
     case MPDET_TUNE_ENGINE:
-      if (value < 0 || value > 1) return fail(h, MPDET_EINVAL, "tune: engine %d", value);
+      if (value < 0 || value > 2) return fail(h, MPDET_EINVAL, "tune: engine %d", value);
       h->engine = value;
       return MPDET_OK;
     default:
@@ -535,8 +536,8 @@ extern "C" int mpdet_logabsdet_grad(mpdet_t h, const double* A, int64_t ld, doub
                               cudaMemcpyDeviceToDevice, h->stream));
       CU(h, cudaMemcpy2DAsync(h->Z.e, 8, h->X.e + k, (size_t)N * 8, 8, (size_t)k, cudaMemcpyDeviceToDevice, h->stream));
       CU(h, cudaMemcpy2DAsync(h->Z.s, 1, h->X.s + k, (size_t)N, 1, (size_t)k, cudaMemcpyDeviceToDevice, h->stream));
-      if (h->engine == 1 && h->p == 2048)
-        CU(h, mpd::usolve_tc_p2048(h->S, N, k, h->Z, h->status, h->p, h->nsm, h->stream));
+      if (h->engine >= 1 && h->p == 2048)
+        CU(h, mpd::usolve_tc_p2048(h->S, N, k, h->Z, h->status, h->p, h->nsm, h->stream, h->engine == 1 ? 1 : 0));
       else
         CU(h, h->ks->usolve_update(h->S, N, k, h->Z, h->status, h->p, h->nsm, h->stream));
       h->launches += 1;

@@ -306,10 +306,342 @@ __global__ void __launch_bounds__(128, 1) k_update_tc(MpArr X, UpdArgs a, MpArr 
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
+
+// ---------------------------------------------------------------------------
+// Pipelined version: 12 warps in three roles so that the tensor core, the
+// epilogue and the subtraction of consecutive columns overlap.
+//   warps 0-3  (E): one thread per row; drain the four tensor-memory tiles of
+//                   a column, form and round the product, stage it (2 buffers)
+//   warps 4-7  (S): lane groups subtract the staged products from x_ij
+//   warps 8-11 (P): build the Hankel cores of the next column (2 buffers);
+//                   thread 256 issues the MMAs of each tile as soon as the
+//                   epilogue has released that tile
+// mbarriers: full[t] (MMA -> E), empty[t] (E -> MMA), hfree[b] (MMA -> P),
+// tfull[b] (E -> S), tfree[b] (S -> E).  For a barrier that completes once
+// per use, the parity awaited at its u-th completion is u & 1.  Every wait
+// is bounded; a timeout sets MPDET_ETIMEOUT and all roles drain.
+// ---------------------------------------------------------------------------
+namespace pipe {
+constexpr int NTH = 384;
+constexpr int OFF_A = 0;                               // 64 KB
+constexpr int OFF_H = OFF_A + M * KD * 2;              // 2 x 12 KB Hankel buffers
+constexpr int OFF_B = OFF_H + 2 * 12288;               // 2 x 256 B b_j limbs
+constexpr int OFF_T = OFF_B + 512;                     // 2 x 128 x 68 words staged products
+constexpr int OFF_TE = OFF_T + 2 * M * RSTR * 4;       // 2 x 128 int64
+constexpr int OFF_TS = OFF_TE + 2 * M * 8;             // 2 x 128 int8
+constexpr int OFF_FL = OFF_TS + 2 * M;                 // 128 multiplier flags
+constexpr int OFF_SCR = OFF_FL + M;                    // 32 groups x SW words
+constexpr int OFF_BAR = OFF_SCR + 32 * SW * 4;         // barriers
+constexpr int SMEM = OFF_BAR + 256;
+constexpr int LIMIT = 1 << 22;
+
+__device__ __forceinline__ void arrive(uint32_t bar) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(bar));
+}
+// barrier 1 over the 128 producer threads, returning the OR of q over them
+__device__ __forceinline__ bool pbar_or(bool q) {
+  uint32_t r;
+  __syncwarp();
+  asm volatile("{\n .reg .pred a, b;\n setp.ne.u32 a, %1, 0;\n bar.red.or.pred b, 1, 128, a;\n selp.u32 %0, 1, 0, b;\n}"
+               : "=r"(r)
+               : "r"((uint32_t)q));
+  return r != 0;
+}
+__device__ __forceinline__ void pbar() {
+  __syncwarp();
+  asm volatile("bar.sync 1, 128;");
+}
+__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity) {
+  uint32_t done = 0;
+  for (int it = 0; it < LIMIT && !done; ++it)
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(done)
+                 : "r"(bar), "r"(parity));
+  return done != 0;
+}
+}  // namespace pipe
+
+__global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a, MpArr Z, int* status, int p,
+                                                            int col_chunk) {
+  using pipe::arrive;
+  using pipe::wait_bar;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  if (status_set(status)) return;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  unsigned char* sA = sm + pipe::OFF_A;
+  uint32_t* sBl = reinterpret_cast<uint32_t*>(sm + pipe::OFF_B);
+  uint32_t* sT = reinterpret_cast<uint32_t*>(sm + pipe::OFF_T);
+  int64_t* sTe = reinterpret_cast<int64_t*>(sm + pipe::OFF_TE);
+  int8_t* sTs = reinterpret_cast<int8_t*>(sm + pipe::OFF_TS);
+  int8_t* sFl = reinterpret_cast<int8_t*>(sm + pipe::OFF_FL);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + pipe::OFF_BAR);
+  // bars: 0-3 full, 4-7 empty, 8-9 hfree, 10-11 tfull, 12-13 tfree; slot 14: tmem address; 15: error flag
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(&bars[14]);
+  volatile int* eflag = reinterpret_cast<volatile int*>(&bars[15]);
+  const uint32_t b_full = su32(&bars[0]), b_empty = su32(&bars[4]), b_hfree = su32(&bars[8]);
+  const uint32_t b_tfull = su32(&bars[10]), b_tfree = su32(&bars[12]);
+  const int64_t N = a.N;
+  const int64_t ncols = a.cmode == 0 ? N - a.kcol - 1 : (a.cmode == 1 ? N - 1 : N);
+  const int64_t i0 = a.row0 + (int64_t)blockIdx.y * M;
+  const int64_t rend = a.row0 + a.nrows;
+  const int64_t c0 = (int64_t)blockIdx.x * col_chunk;
+  const int64_t c1 = (c0 + col_chunk < ncols) ? c0 + col_chunk : ncols;
+  const int nc = (int)(c1 > c0 ? c1 - c0 : 0);
+  auto colj = [&](int c) -> int64_t {
+    const int64_t cc = c0 + c;
+    return a.cmode == 0 ? a.kcol + 1 + cc : (a.cmode == 1 ? (cc < a.kcol ? cc : cc + 1) : cc);
+  };
+
+  // ---- set-up: A (rows by warps 0-3), barriers, tensor memory ------------
+  if (tid < M) {
+    const int64_t i = i0 + tid;
+    const bool have = i < rend && Z.e[i < rend ? i : i0] != ZEXP;
+    const uint32_t* zm = Z.m + (i < rend ? i : i0) * n;
+    unsigned char* rowbase = sA + (tid >> 3) * 4096 + (tid & 7) * 16;
+    for (int c = 0; c < 32; ++c) {
+      uint32_t hi = have ? zm[63 - 2 * c] : 0u, lo = have ? zm[62 - 2 * c] : 0u;
+      uint32_t w0 = dbf(hi >> 24) | ((uint32_t)dbf((hi >> 16) & 255) << 16);
+      uint32_t w1 = dbf((hi >> 8) & 255) | ((uint32_t)dbf(hi & 255) << 16);
+      uint32_t w2 = dbf(lo >> 24) | ((uint32_t)dbf((lo >> 16) & 255) << 16);
+      uint32_t w3 = dbf((lo >> 8) & 255) | ((uint32_t)dbf(lo & 255) << 16);
+      *reinterpret_cast<uint4*>(rowbase + c * 128) = make_uint4(w0, w1, w2, w3);
+    }
+    sFl[tid] = have ? 1 : 0;
+  }
+  if (tid == 0) {
+    for (int t = 0; t < 4; ++t) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b_full + 8 * t));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(b_empty + 8 * t), "r"(M));
+    }
+    for (int b = 0; b < 2; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b_hfree + 8 * b));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(b_tfull + 8 * b), "r"(M));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(b_tfree + 8 * b), "r"(M));
+    }
+    *eflag = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)), "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.proxy.async.shared::cta;");
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tslot;
+
+  if (warp >= 8) {
+    // ================= P: Hankel producer and MMA issuer =================
+    const int pt = tid - 256;
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+    for (int c = 0; c < nc; ++c) {
+      const int hb = c & 1;
+      unsigned char* sH = sm + pipe::OFF_H + hb * 12288;
+      uint32_t* sB = sBl + hb * 64;
+      bool bad = false;
+      if (pt == 0 && c >= 2 && !wait_bar(b_hfree + 8 * hb, ((c - 2) >> 1) & 1)) bad = true;
+      if (pipe::pbar_or(bad || *eflag != 0)) {
+        *eflag = 1;
+        break;
+      }
+      const int64_t kj = a.brow * N + colj(c);
+      const bool bz = X.e[kj] == ZEXP;
+      if (pt < 64) sB[pt] = X.m[kj * n + pt];
+      pipe::pbar();
+      const unsigned char* bb = reinterpret_cast<const unsigned char*>(sB);
+      for (int q = pt; q < NCORE * 8; q += 128) {
+        const int d = q >> 3, nn = q & 7;
+        const int base = 8 * d + nn - 255;
+        uint32_t w[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          uint32_t h2[2];
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int idx = base + 2 * e + u;
+            h2[u] = dbf((idx >= 0 && idx < KD && !bz) ? bb[idx] : 0u);
+          }
+          w[e] = h2[0] | (h2[1] << 16);
+        }
+        *reinterpret_cast<uint4*>(sH + d * 128 + nn * 16) = make_uint4(w[0], w[1], w[2], w[3]);
+      }
+      asm volatile("fence.proxy.async.shared::cta;");
+      pipe::pbar();
+      if (pt == 0) {
+        for (int t = 0; t < 4; ++t) {
+          if (c >= 1 && !wait_bar(b_empty + 8 * t, (c - 1) & 1)) {
+            *eflag = 1;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          for (int ks = 0; ks < KD / 16; ++ks) {
+            const uint64_t ad = desc(su32(sA) + ks * 256, 128, 4096);
+            const uint64_t bd = desc(su32(sH) + (16 * t + 2 * ks) * 128, 128, 128);
+            const uint32_t acc = ks > 0 ? 1u : 0u;
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+                    tmem + (uint32_t)(t * NT)),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(b_full + 8 * t));
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(b_hfree + 8 * hb));
+      }
+    }
+  } else if (warp < 4) {
+    // ================= E: epilogue, one thread per row ====================
+    const int r = tid;
+    const int8_t zsign = (i0 + r < rend) ? Z.s[i0 + r] : 0;
+    const int64_t zexp = (i0 + r < rend) ? Z.e[i0 + r] : ZEXP;
+    const bool have = sFl[r] != 0;
+    for (int c = 0; c < nc; ++c) {
+      const int tb = c & 1;
+      const int64_t kj = a.brow * N + colj(c);
+      const int64_t be = X.e[kj];
+      const int8_t bs = X.s[kj];
+      uint32_t up[64];
+      uint32_t l63 = 0, sticky = 0;
+      uint64_t acc = 0;
+      bool okc = true;
+#pragma unroll
+      for (int t = 0; t < TILES; ++t) {
+        if (okc && !wait_bar(b_full + 8 * t, c & 1)) okc = false;
+        okc = __all_sync(0xffffffffu, okc) && !*eflag;
+        okc = __all_sync(0xffffffffu, okc);
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (okc) {
+#pragma unroll
+          for (int ch = 0; ch < 4; ++ch) {
+            uint32_t v[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * NT + ch * 32), v);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const uint64_t c0v = __float2uint_rz(__uint_as_float(v[4 * q]));
+              const uint64_t c1v = __float2uint_rz(__uint_as_float(v[4 * q + 1]));
+              const uint64_t c2v = __float2uint_rz(__uint_as_float(v[4 * q + 2]));
+              const uint64_t c3v = __float2uint_rz(__uint_as_float(v[4 * q + 3]));
+              acc += c0v + (c1v << 8) + (c2v << 16) + (c3v << 24);
+              const uint32_t limb = (uint32_t)acc;
+              acc >>= 32;
+              const int L = t * 32 + ch * 8 + q;
+              if (L >= 64) up[L >= 64 ? L - 64 : 0] = limb;
+              else if (L == 63) l63 = limb;
+              else sticky |= limb;
+            }
+          }
+          asm volatile("tcgen05.fence::before_thread_sync;");
+          arrive(b_empty + 8 * t);
+        }
+      }
+      if (!okc) {  // warp-uniform
+        *eflag = 1;
+        break;
+      }
+      const uint32_t top = up[63] >> 31;
+      uint32_t rbit, st;
+      if (top) {
+        rbit = l63 >> 31;
+        st = (l63 & 0x7fffffffu) | sticky;
+      } else {
+#pragma unroll
+        for (int q = 63; q > 0; --q) up[q] = (up[q] << 1) | (up[q - 1] >> 31);
+        up[0] = (up[0] << 1) | (l63 >> 31);
+        rbit = (l63 >> 30) & 1u;
+        st = (l63 & 0x3fffffffu) | sticky;
+      }
+      uint32_t carry = rbit & ((st != 0u) | (up[0] & 1u));
+#pragma unroll
+      for (int q = 0; q < 64; ++q) {
+        const uint64_t s2 = (uint64_t)up[q] + carry;
+        up[q] = (uint32_t)s2;
+        carry = (uint32_t)(s2 >> 32);
+      }
+      int adj = top ? 0 : -1;
+      if (carry) {
+        up[63] = 0x80000000u;
+        adj += 1;
+      }
+      const bool tz = !have || be == ZEXP;
+      bool okw = (c < 2) || wait_bar(b_tfree + 8 * tb, ((c - 2) >> 1) & 1);
+      okw = __all_sync(0xffffffffu, okw);
+      if (!okw) {
+        *eflag = 1;
+        break;
+      }
+      uint32_t* T = sT + tb * (M * RSTR);
+#pragma unroll
+      for (int q = 0; q < 64; q += 4)
+        *reinterpret_cast<uint4*>(T + r * RSTR + q) =
+            tz ? make_uint4(0u, 0u, 0u, 0u) : make_uint4(up[q], up[q + 1], up[q + 2], up[q + 3]);
+      sTe[tb * M + r] = tz ? ZEXP : zexp + be + adj;
+      sTs[tb * M + r] = tz ? (int8_t)0 : (int8_t)(zsign ^ bs);
+      arrive(b_tfull + 8 * tb);
+    }
+  } else {
+    // ================= S: subtraction by lane groups ======================
+    Grp<G> gp;
+    const int st_ = tid - 128;
+    const int gid = st_ / G;  // 32 groups
+    uint32_t* scr = reinterpret_cast<uint32_t*>(sm + pipe::OFF_SCR) + gid * SW;
+    for (int c = 0; c < nc; ++c) {
+      const int tb = c & 1;
+      const int64_t j = colj(c);
+      bool okc = wait_bar(b_tfull + 8 * tb, (c >> 1) & 1);
+      okc = __all_sync(0xffffffffu, okc) && !*eflag;
+      okc = __all_sync(0xffffffffu, okc);
+      if (!okc) {
+        *eflag = 1;
+        break;
+      }
+      const uint32_t* Tb = sT + tb * (M * RSTR);
+      // software-pipelined loads of x_ij for the group's four rows
+      uint32_t Xn[W];
+      int64_t ijn = ((i0 + gid < rend) ? i0 + gid : i0) * N + j;
+      load_slice<W>(X.m + ijn * n + gp.g * W, Xn);
+      int8_t xsn = X.s[ijn];
+      int64_t xen = X.e[ijn];
+#pragma unroll 1
+      for (int rr = 0; rr < 4; ++rr) {
+        const int rrow = gid + 32 * rr;
+        const int64_t i = i0 + rrow;
+        const bool active = i < rend;
+        const int64_t ij = ijn;
+        uint32_t Xv[W], T[W];
+#pragma unroll
+        for (int q = 0; q < W; ++q) Xv[q] = Xn[q];
+        int8_t xs = xsn;
+        int64_t xe = xen;
+        if (rr < 3) {
+          const int64_t in2 = i0 + gid + 32 * (rr + 1);
+          ijn = (in2 < rend ? in2 : i0) * N + j;
+          load_slice<W>(X.m + ijn * n + gp.g * W, Xn);
+          xsn = X.s[ijn];
+          xen = X.e[ijn];
+        }
+        load_slice<W>(Tb + rrow * RSTR + gp.g * W, T);
+        sub_round<W, G>(gp, p, xs, xe, Xv, sTs[tb * M + rrow], sTe[tb * M + rrow], T, scr);
+        if (active) {
+          store_slice<W>(X.m + ij * n + gp.g * W, Xv);
+          if (gp.g == 0) {
+            X.s[ij] = xs;
+            X.e[ij] = xe;
+          }
+        }
+      }
+      arrive(b_tfree + 8 * tb);
+    }
+  }
+  if (tid == 0 && *eflag) atomicExch(status, 5);  // MPDET_ETIMEOUT
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
 }  // namespace tc
 
 // Launch: 128-row blocks x column chunks sized to fill the SMs once.
-cudaError_t update_tc_p2048(MpArr X, UpdArgs a, MpArr Z, int* status, int p, int nsm, cudaStream_t st) {
+cudaError_t update_tc_p2048(MpArr X, UpdArgs a, MpArr Z, int* status, int p, int nsm, cudaStream_t st,
+                            int pipelined) {
   const int64_t ncols = a.cmode == 0 ? a.N - a.kcol - 1 : (a.cmode == 1 ? a.N - 1 : a.N);
   if (a.nrows <= 0 || ncols <= 0) return cudaSuccess;
   const int64_t by = (a.nrows + tc::M - 1) / tc::M;
@@ -318,23 +650,29 @@ cudaError_t update_tc_p2048(MpArr X, UpdArgs a, MpArr Z, int* status, int p, int
   if (bx < 1) bx = 1;
   const int64_t chunk = (ncols + bx - 1) / bx;
   bx = (ncols + chunk - 1) / chunk;
-  cudaFuncSetAttribute(tc::k_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM);
   dim3 grid((unsigned)bx, (unsigned)by);
-  tc::k_update_tc<<<grid, 128, tc::SMEM, st>>>(X, a, Z, status, p, (int)chunk);
+  if (pipelined) {
+    cudaFuncSetAttribute(tc::k_update_tcp, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::pipe::SMEM);
+    tc::k_update_tcp<<<grid, tc::pipe::NTH, tc::pipe::SMEM, st>>>(X, a, Z, status, p, (int)chunk);
+  } else {
+    cudaFuncSetAttribute(tc::k_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM);
+    tc::k_update_tc<<<grid, 128, tc::SMEM, st>>>(X, a, Z, status, p, (int)chunk);
+  }
   return cudaGetLastError();
 }
 
 // Schur update of step k (lastcol: every column but k) on the tensor cores.
 cudaError_t update_tc_p2048_step(MpArr X, int64_t N, int64_t k, MpArr Z, int* status, int p, int lastcol, int nsm,
-                                 cudaStream_t st) {
+                                 cudaStream_t st, int pipelined) {
   UpdArgs a{N, k, k + 1, N - k - 1, k, lastcol ? 1 : 0};
-  return update_tc_p2048(X, a, Z, status, p, nsm, st);
+  return update_tc_p2048(X, a, Z, status, p, nsm, st, pipelined);
 }
 
 // Back-substitution update of the adjoint (rows [0, k), every column).
-cudaError_t usolve_tc_p2048(MpArr S, int64_t N, int64_t k, MpArr Z, int* status, int p, int nsm, cudaStream_t st) {
+cudaError_t usolve_tc_p2048(MpArr S, int64_t N, int64_t k, MpArr Z, int* status, int p, int nsm, cudaStream_t st,
+                            int pipelined) {
   UpdArgs a{N, k, 0, k, 0, 2};
-  return update_tc_p2048(S, a, Z, status, p, nsm, st);
+  return update_tc_p2048(S, a, Z, status, p, nsm, st, pipelined);
 }
 
 }  // namespace mpd

@@ -32,11 +32,12 @@ def test_tensor_engine_equals_imad_engine(mpdet, N, kind):
     g = W.rng(N * 7 + len(kind))
     data = W.cauchy_xy(N, N) if kind == "cauchy" else (W.int_matrix(N, N) if kind == "int" else g.standard_normal((N, N)))
     for lastcol in (False, True):
-        a = run(mpdet, N, p, kind, data, 1, lastcol)
         b = run(mpdet, N, p, kind, data, 0, lastcol)
-        assert a[:2] == b[:2]
-        assert X.same(a[2], b[2]), "leading minors differ between engines"
-        assert X.same(a[3], b[3]), "in-place arrays differ between engines"
+        for engine in (1, 2):
+            a = run(mpdet, N, p, kind, data, engine, lastcol)
+            assert a[:2] == b[:2]
+            assert X.same(a[2], b[2]), f"leading minors differ between engines {engine} and 0"
+            assert X.same(a[3], b[3]), f"in-place arrays differ between engines {engine} and 0"
 
 
 def test_tensor_engine_vs_oracle(mpdet, oracle_lib):
