@@ -345,8 +345,11 @@ def run_gpu(args):
     hc = m.Mpdet(N, p, lastcol=True, stream=sa.cuda_stream)
     hi = m.Mpdet(N, p, lastcol=True, stream=sb.cuda_stream)
     if args.update_variant >= 0:
-        hc.tune(args.update_variant)
-        hi.tune(args.update_variant)
+        hc.tune(update_variant=args.update_variant)
+        hi.tune(update_variant=args.update_variant)
+    if args.engine >= 0:
+        hc.tune(engine=args.engine)
+        hi.tune(engine=args.engine)
 
     def dev_out():
         return (torch.empty(N, dtype=torch.int8, device=dev), torch.empty(N, dtype=torch.int64, device=dev),
@@ -462,6 +465,24 @@ def run_gpu(args):
         upd_launches = pc["update_launches"] + pi["update_launches"]
         achieved = upd_macs / (upd_ms / 1e3)
         tr = recorded_traffic()
+        tensor = (p == 2048 and args.engine != 0)
+        if tensor:
+            # exact digit convolution on the tensor cores: one limb-MAC is 16 products of 8-bit digits,
+            # 32 flops; peak = measured bf16 dense throughput (sustained: the kernel runs inside a long step)
+            tpeak = float(peaks.get("bf16_tflops_sustained") or 1700.0)
+            roof = {"bound": "tensor", "kernel": "k_update_tcp (Schur update, tcgen05 digit convolution)",
+                    "achieved": achieved * 32 / 1e12, "peak": tpeak, "unit": "TFLOP/s",
+                    "frac": achieved * 32 / 1e12 / tpeak, "traffic": tr,
+                    "peak_basis": "MEASURED_PEAKS bf16_tflops_sustained (of measured)",
+                    "imad_equivalent": {"achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tlimb-MAC/s",
+                                        "frac": achieved / peak,
+                                        "peak_basis": f"{nsm} SMs x 32 limb-MAC/clk x {fmax:.0f} MHz"}}
+        else:
+            roof = {"bound": "alu", "kernel": "k_update (Schur update, IMAD)", "achieved": achieved / 1e12,
+                    "peak": peak / 1e12, "unit": "Tlimb-MAC/s", "frac": achieved / peak, "traffic": tr,
+                    "peak_basis": f"{nsm} SMs x 32 limb-MAC/clk x {fmax:.0f} MHz"}
+        roof["update_share"] = upd_ms / serial_ms
+        roof["launches"] = int(upd_launches)
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -469,15 +490,12 @@ def run_gpu(args):
             "config": {"workload": f"cauchy+int N={N} p={p} lastcol: det, {N} leading minors and {N} "
                                    "last-column minors of two matrices per step",
                        "N": N, "p": p, "matrices": 2, "parallelism": f"replica x{world}",
+                       "engine": "tensor" if tensor else "imad",
                        "l2": "inputs larger than L2 (each matrix %.0f MB in HBM)" % (N * N * (4 * n + 9) / 1e6)},
             "e2e": {"value": macs * world / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms},
             "gpu_launches": int(launches * args.steps),
-            "roofline": {"bound": "alu", "kernel": "k_update (Schur update)", "achieved": achieved / 1e12,
-                         "peak": peak / 1e12, "unit": "Tlimb-MAC/s", "frac": achieved / peak,
-                         "traffic": tr, "update_share": upd_ms / serial_ms,
-                         "launches": int(upd_launches),
-                         "peak_basis": f"{nsm} SMs x 32 limb-MAC/clk x {fmax:.0f} MHz"},
+            "roofline": roof,
             "clocks": clocks,
         }
         if not args.no_extras:
@@ -508,6 +526,7 @@ def main():
     ap.add_argument("--N", type=int, default=0, help="profiling aid: override N (default: the workload's 1024)")
     ap.add_argument("--p", type=int, default=0, help="profiling aid: override p (default: the workload's 2048)")
     ap.add_argument("--update-variant", type=int, default=-1, help="tuning aid: Schur-update register budget 0..3")
+    ap.add_argument("--engine", type=int, default=-1, help="tuning aid: 0 IMAD, 1 tensor pipelined, 2 tensor serial")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
