@@ -59,6 +59,7 @@ struct KernelSet {
 struct UpdArgs;  // kernels.cuh
 
 // Tensor-core engine of the rank-1 update, p = 2048 only (tc_update.cu).
+bool tc_supports(int p, int pipelined);
 // pipelined = 1: warp-specialised kernel (tensor core, epilogue and subtraction overlap); 0: one role at a time
 cudaError_t update_tc_p2048_step(MpArr X, int64_t N, int64_t k, MpArr Z, int* status, int p, int lastcol, int nsm,
                                  cudaStream_t st, int pipelined);

@@ -311,7 +311,7 @@ static int run_steps(mpdet_t h, int64_t k0, int64_t k1) {
         if (rc) return rc;
         CU(h, cudaEventRecord(e0, h->stream));
       }
-      if (h->engine >= 1 && h->p == 2048)
+      if (h->engine >= 1 && mpd::tc_supports(h->p, h->engine == 1))
         CU(h, mpd::update_tc_p2048_step(h->X, N, k, h->Z, h->status, h->p, lastcol, h->nsm, h->stream,
                                         h->engine == 1 ? 1 : 0));
       else
@@ -536,7 +536,7 @@ extern "C" int mpdet_logabsdet_grad(mpdet_t h, const double* A, int64_t ld, doub
                               cudaMemcpyDeviceToDevice, h->stream));
       CU(h, cudaMemcpy2DAsync(h->Z.e, 8, h->X.e + k, (size_t)N * 8, 8, (size_t)k, cudaMemcpyDeviceToDevice, h->stream));
       CU(h, cudaMemcpy2DAsync(h->Z.s, 1, h->X.s + k, (size_t)N, 1, (size_t)k, cudaMemcpyDeviceToDevice, h->stream));
-      if (h->engine >= 1 && h->p == 2048)
+      if (h->engine >= 1 && mpd::tc_supports(h->p, h->engine == 1))
         CU(h, mpd::usolve_tc_p2048(h->S, N, k, h->Z, h->status, h->p, h->nsm, h->stream, h->engine == 1 ? 1 : 0));
       else
         CU(h, h->ks->usolve_update(h->S, N, k, h->Z, h->status, h->p, h->nsm, h->stream));

@@ -1,4 +1,4 @@
-// Tensor-core engine for the rank-1 update at p = 2048 (n = 64 limbs).
+// Tensor-core engine for the rank-1 update at p = 512, 1024, 2048 (n = 16, 32, 64 limbs).
 //
 // The exact 2p-bit product of two mantissas is a convolution of their 8-bit
 // digits: c_r = sum_s z[s] * b[r - s], P = sum_r c_r 2^(8r).  Every c_r is a
@@ -323,17 +323,35 @@ __global__ void __launch_bounds__(128, 1) k_update_tc(MpArr X, UpdArgs a, MpArr 
 // ---------------------------------------------------------------------------
 namespace pipe {
 constexpr int NTH = 384;
-constexpr int OFF_A = 0;                               // 64 KB
-constexpr int OFF_H = OFF_A + M * KD * 2;              // 2 x 12 KB Hankel buffers
-constexpr int OFF_B = OFF_H + 2 * 12288;               // 2 x 256 B b_j limbs
-constexpr int OFF_T = OFF_B + 512;                     // 2 x 128 x 68 words staged products
-constexpr int OFF_TE = OFF_T + 2 * M * RSTR * 4;       // 2 x 128 int64
-constexpr int OFF_TS = OFF_TE + 2 * M * 8;             // 2 x 128 int8
-constexpr int OFF_FL = OFF_TS + 2 * M;                 // 128 multiplier flags
-constexpr int OFF_SCR = OFF_FL + M;                    // 32 groups x SW words
-constexpr int OFF_BAR = OFF_SCR + 32 * SW * 4;         // barriers
-constexpr int SMEM = OFF_BAR + 256;
 constexpr int LIMIT = 1 << 22;
+
+// Geometry for mantissas of KD 8-bit digits (NL = KD/4 limbs; p = 8 KD).
+template <int KD_>
+struct Cfg {
+  static constexpr int KD = KD_;
+  static constexpr int NL = KD / 4;                 // limbs
+  static constexpr int TILES = 2 * KD / 128;        // 128-column tensor-memory tiles (2 KD positions)
+  static constexpr int TCOLS = TILES * 128;         // allocated columns (a power of two >= 32)
+  static constexpr int NCORE = 16 * TILES + KD / 8 - 1;  // Hankel cores
+  static constexpr int HBYTES = (NCORE * 128 + 1023) / 1024 * 1024;
+  static constexpr int G = NL / 16;                 // lanes per number in the subtraction (W = 16)
+  static constexpr int NGRP = 128 / G;              // subtraction groups
+  static constexpr int RPG = M / NGRP;              // rows per group
+  static constexpr int RSTR = NL + 4;               // words per staged row
+  static constexpr int SW = Scratch<16, G>::words;
+  static constexpr int OFF_A = 0;                           // M x KD bf16
+  static constexpr int OFF_H = OFF_A + M * KD * 2;          // 2 Hankel buffers
+  static constexpr int OFF_B = OFF_H + 2 * HBYTES;          // 2 x NL limbs of b_j
+  static constexpr int OFF_T = OFF_B + 2 * NL * 4;          // 2 x M x RSTR words staged products
+  static constexpr int OFF_TE = OFF_T + 2 * M * RSTR * 4;   // 2 x M int64
+  static constexpr int OFF_TS = OFF_TE + 2 * M * 8;         // 2 x M int8
+  static constexpr int OFF_FL = OFF_TS + 2 * M;             // M multiplier flags
+  static constexpr int OFF_SCR = OFF_FL + M;                // NGRP groups x SW words
+  static constexpr int OFF_BAR = OFF_SCR + NGRP * SW * 4;   // barriers
+  static constexpr int SMEM = OFF_BAR + 256;
+  static_assert(NL % 16 == 0 && G >= 1 && G <= 4, "tensor engine covers p = 512, 1024, 2048");
+  static_assert(OFF_SCR % 16 == 0 && OFF_BAR % 8 == 0 && OFF_T % 16 == 0, "alignment");
+};
 
 __device__ __forceinline__ void arrive(uint32_t bar) {
   asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(bar));
@@ -361,20 +379,23 @@ __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity) {
 }
 }  // namespace pipe
 
+template <int KD>
 __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a, MpArr Z, int* status, int p,
                                                             int col_chunk) {
   using pipe::arrive;
   using pipe::wait_bar;
+  using C = pipe::Cfg<KD>;
+  constexpr int NL = C::NL, TILES = C::TILES, NCORE = C::NCORE, RSTR = C::RSTR, GS = C::G, SWS = C::SW;
   extern __shared__ __align__(1024) unsigned char sm[];
   if (status_set(status)) return;
   const int tid = threadIdx.x, warp = tid >> 5;
-  unsigned char* sA = sm + pipe::OFF_A;
-  uint32_t* sBl = reinterpret_cast<uint32_t*>(sm + pipe::OFF_B);
-  uint32_t* sT = reinterpret_cast<uint32_t*>(sm + pipe::OFF_T);
-  int64_t* sTe = reinterpret_cast<int64_t*>(sm + pipe::OFF_TE);
-  int8_t* sTs = reinterpret_cast<int8_t*>(sm + pipe::OFF_TS);
-  int8_t* sFl = reinterpret_cast<int8_t*>(sm + pipe::OFF_FL);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + pipe::OFF_BAR);
+  unsigned char* sA = sm + C::OFF_A;
+  uint32_t* sBl = reinterpret_cast<uint32_t*>(sm + C::OFF_B);
+  uint32_t* sT = reinterpret_cast<uint32_t*>(sm + C::OFF_T);
+  int64_t* sTe = reinterpret_cast<int64_t*>(sm + C::OFF_TE);
+  int8_t* sTs = reinterpret_cast<int8_t*>(sm + C::OFF_TS);
+  int8_t* sFl = reinterpret_cast<int8_t*>(sm + C::OFF_FL);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + C::OFF_BAR);
   // bars: 0-3 full, 4-7 empty, 8-9 hfree, 10-11 tfull, 12-13 tfree; slot 14: tmem address; 15: error flag
   uint32_t* tslot = reinterpret_cast<uint32_t*>(&bars[14]);
   volatile int* eflag = reinterpret_cast<volatile int*>(&bars[15]);
@@ -396,10 +417,10 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
   if (tid < M) {
     const int64_t i = i0 + tid;
     const bool have = i < rend && Z.e[i < rend ? i : i0] != ZEXP;
-    const uint32_t* zm = Z.m + (i < rend ? i : i0) * n;
-    unsigned char* rowbase = sA + (tid >> 3) * 4096 + (tid & 7) * 16;
-    for (int c = 0; c < 32; ++c) {
-      uint32_t hi = have ? zm[63 - 2 * c] : 0u, lo = have ? zm[62 - 2 * c] : 0u;
+    const uint32_t* zm = Z.m + (i < rend ? i : i0) * NL;
+    unsigned char* rowbase = sA + (tid >> 3) * (KD * 16) + (tid & 7) * 16;
+    for (int c = 0; c < KD / 8; ++c) {
+      uint32_t hi = have ? zm[NL - 1 - 2 * c] : 0u, lo = have ? zm[NL - 2 - 2 * c] : 0u;
       uint32_t w0 = dbf(hi >> 24) | ((uint32_t)dbf((hi >> 16) & 255) << 16);
       uint32_t w1 = dbf((hi >> 8) & 255) | ((uint32_t)dbf(hi & 255) << 16);
       uint32_t w2 = dbf(lo >> 24) | ((uint32_t)dbf((lo >> 16) & 255) << 16);
@@ -421,7 +442,7 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
     *eflag = 0;
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)), "r"(512));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)), "r"(C::TCOLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("fence.proxy.async.shared::cta;");
@@ -436,8 +457,8 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
     for (int c = 0; c < nc; ++c) {
       const int hb = c & 1;
-      unsigned char* sH = sm + pipe::OFF_H + hb * 12288;
-      uint32_t* sB = sBl + hb * 64;
+      unsigned char* sH = sm + C::OFF_H + hb * C::HBYTES;
+      uint32_t* sB = sBl + hb * NL;
       bool bad = false;
       if (pt == 0 && c >= 2 && !wait_bar(b_hfree + 8 * hb, ((c - 2) >> 1) & 1)) bad = true;
       if (pipe::pbar_or(bad || *eflag != 0)) {
@@ -446,12 +467,12 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
       }
       const int64_t kj = a.brow * N + colj(c);
       const bool bz = X.e[kj] == ZEXP;
-      if (pt < 64) sB[pt] = X.m[kj * n + pt];
+      if (pt < NL) sB[pt] = X.m[kj * NL + pt];
       pipe::pbar();
       const unsigned char* bb = reinterpret_cast<const unsigned char*>(sB);
       for (int q = pt; q < NCORE * 8; q += 128) {
         const int d = q >> 3, nn = q & 7;
-        const int base = 8 * d + nn - 255;
+        const int base = 8 * d + nn - (KD - 1);
         uint32_t w[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -468,14 +489,14 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
       asm volatile("fence.proxy.async.shared::cta;");
       pipe::pbar();
       if (pt == 0) {
-        for (int t = 0; t < 4; ++t) {
+        for (int t = 0; t < TILES; ++t) {
           if (c >= 1 && !wait_bar(b_empty + 8 * t, (c - 1) & 1)) {
             *eflag = 1;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;");
           for (int ks = 0; ks < KD / 16; ++ks) {
-            const uint64_t ad = desc(su32(sA) + ks * 256, 128, 4096);
+            const uint64_t ad = desc(su32(sA) + ks * 256, 128, KD * 16);
             const uint64_t bd = desc(su32(sH) + (16 * t + 2 * ks) * 128, 128, 128);
             const uint32_t acc = ks > 0 ? 1u : 0u;
             asm volatile(
@@ -499,8 +520,8 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
       const int64_t kj = a.brow * N + colj(c);
       const int64_t be = X.e[kj];
       const int8_t bs = X.s[kj];
-      uint32_t up[64];
-      uint32_t l63 = 0, sticky = 0;
+      uint32_t up[NL];
+      uint32_t l63 = 0, sticky = 0;  // limb NL-1 and the OR of limbs 0..NL-2
       uint64_t acc = 0;
       bool okc = true;
 #pragma unroll
@@ -524,8 +545,8 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
               const uint32_t limb = (uint32_t)acc;
               acc >>= 32;
               const int L = t * 32 + ch * 8 + q;
-              if (L >= 64) up[L >= 64 ? L - 64 : 0] = limb;
-              else if (L == 63) l63 = limb;
+              if (L >= NL) up[L >= NL ? L - NL : 0] = limb;
+              else if (L == NL - 1) l63 = limb;
               else sticky |= limb;
             }
           }
@@ -537,28 +558,28 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
         *eflag = 1;
         break;
       }
-      const uint32_t top = up[63] >> 31;
+      const uint32_t top = up[NL - 1] >> 31;
       uint32_t rbit, st;
       if (top) {
         rbit = l63 >> 31;
         st = (l63 & 0x7fffffffu) | sticky;
       } else {
 #pragma unroll
-        for (int q = 63; q > 0; --q) up[q] = (up[q] << 1) | (up[q - 1] >> 31);
+        for (int q = NL - 1; q > 0; --q) up[q] = (up[q] << 1) | (up[q - 1] >> 31);
         up[0] = (up[0] << 1) | (l63 >> 31);
         rbit = (l63 >> 30) & 1u;
         st = (l63 & 0x3fffffffu) | sticky;
       }
       uint32_t carry = rbit & ((st != 0u) | (up[0] & 1u));
 #pragma unroll
-      for (int q = 0; q < 64; ++q) {
+      for (int q = 0; q < NL; ++q) {
         const uint64_t s2 = (uint64_t)up[q] + carry;
         up[q] = (uint32_t)s2;
         carry = (uint32_t)(s2 >> 32);
       }
       int adj = top ? 0 : -1;
       if (carry) {
-        up[63] = 0x80000000u;
+        up[NL - 1] = 0x80000000u;
         adj += 1;
       }
       const bool tz = !have || be == ZEXP;
@@ -570,7 +591,7 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
       }
       uint32_t* T = sT + tb * (M * RSTR);
 #pragma unroll
-      for (int q = 0; q < 64; q += 4)
+      for (int q = 0; q < NL; q += 4)
         *reinterpret_cast<uint4*>(T + r * RSTR + q) =
             tz ? make_uint4(0u, 0u, 0u, 0u) : make_uint4(up[q], up[q + 1], up[q + 2], up[q + 3]);
       sTe[tb * M + r] = tz ? ZEXP : zexp + be + adj;
@@ -579,10 +600,10 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
     }
   } else {
     // ================= S: subtraction by lane groups ======================
-    Grp<G> gp;
+    Grp<GS> gp;
     const int st_ = tid - 128;
-    const int gid = st_ / G;  // 32 groups
-    uint32_t* scr = reinterpret_cast<uint32_t*>(sm + pipe::OFF_SCR) + gid * SW;
+    const int gid = st_ / GS;  // C::NGRP groups
+    uint32_t* scr = reinterpret_cast<uint32_t*>(sm + C::OFF_SCR) + gid * SWS;
     for (int c = 0; c < nc; ++c) {
       const int tb = c & 1;
       const int64_t j = colj(c);
@@ -597,12 +618,12 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
       // software-pipelined loads of x_ij for the group's four rows
       uint32_t Xn[W];
       int64_t ijn = ((i0 + gid < rend) ? i0 + gid : i0) * N + j;
-      load_slice<W>(X.m + ijn * n + gp.g * W, Xn);
+      load_slice<W>(X.m + ijn * NL + gp.g * W, Xn);
       int8_t xsn = X.s[ijn];
       int64_t xen = X.e[ijn];
 #pragma unroll 1
-      for (int rr = 0; rr < 4; ++rr) {
-        const int rrow = gid + 32 * rr;
+      for (int rr = 0; rr < C::RPG; ++rr) {
+        const int rrow = gid + C::NGRP * rr;
         const int64_t i = i0 + rrow;
         const bool active = i < rend;
         const int64_t ij = ijn;
@@ -611,17 +632,17 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
         for (int q = 0; q < W; ++q) Xv[q] = Xn[q];
         int8_t xs = xsn;
         int64_t xe = xen;
-        if (rr < 3) {
-          const int64_t in2 = i0 + gid + 32 * (rr + 1);
+        if (rr + 1 < C::RPG) {
+          const int64_t in2 = i0 + gid + C::NGRP * (rr + 1);
           ijn = (in2 < rend ? in2 : i0) * N + j;
-          load_slice<W>(X.m + ijn * n + gp.g * W, Xn);
+          load_slice<W>(X.m + ijn * NL + gp.g * W, Xn);
           xsn = X.s[ijn];
           xen = X.e[ijn];
         }
         load_slice<W>(Tb + rrow * RSTR + gp.g * W, T);
-        sub_round<W, G>(gp, p, xs, xe, Xv, sTs[tb * M + rrow], sTe[tb * M + rrow], T, scr);
+        sub_round<W, GS>(gp, p, xs, xe, Xv, sTs[tb * M + rrow], sTe[tb * M + rrow], T, scr);
         if (active) {
-          store_slice<W>(X.m + ij * n + gp.g * W, Xv);
+          store_slice<W>(X.m + ij * NL + gp.g * W, Xv);
           if (gp.g == 0) {
             X.s[ij] = xs;
             X.e[ij] = xe;
@@ -634,8 +655,9 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
   if (tid == 0 && *eflag) atomicExch(status, 5);  // MPDET_ETIMEOUT
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TCOLS));
 }
+
 
 }  // namespace tc
 
@@ -652,14 +674,30 @@ cudaError_t update_tc_p2048(MpArr X, UpdArgs a, MpArr Z, int* status, int p, int
   bx = (ncols + chunk - 1) / chunk;
   dim3 grid((unsigned)bx, (unsigned)by);
   if (pipelined) {
-    cudaFuncSetAttribute(tc::k_update_tcp, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::pipe::SMEM);
-    tc::k_update_tcp<<<grid, tc::pipe::NTH, tc::pipe::SMEM, st>>>(X, a, Z, status, p, (int)chunk);
+    switch (p) {
+      case 512:
+        cudaFuncSetAttribute(tc::k_update_tcp<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::pipe::Cfg<64>::SMEM);
+        tc::k_update_tcp<64><<<grid, tc::pipe::NTH, tc::pipe::Cfg<64>::SMEM, st>>>(X, a, Z, status, p, (int)chunk);
+        break;
+      case 1024:
+        cudaFuncSetAttribute(tc::k_update_tcp<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::pipe::Cfg<128>::SMEM);
+        tc::k_update_tcp<128><<<grid, tc::pipe::NTH, tc::pipe::Cfg<128>::SMEM, st>>>(X, a, Z, status, p, (int)chunk);
+        break;
+      default:
+        cudaFuncSetAttribute(tc::k_update_tcp<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::pipe::Cfg<256>::SMEM);
+        tc::k_update_tcp<256><<<grid, tc::pipe::NTH, tc::pipe::Cfg<256>::SMEM, st>>>(X, a, Z, status, p, (int)chunk);
+        break;
+    }
   } else {
     cudaFuncSetAttribute(tc::k_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM);
     tc::k_update_tc<<<grid, 128, tc::SMEM, st>>>(X, a, Z, status, p, (int)chunk);
   }
   return cudaGetLastError();
 }
+
+// True when the tensor engine covers p (the warp-specialised kernel: p = 512,
+// 1024, 2048; the one-phase-at-a-time kernel: p = 2048).
+bool tc_supports(int p, int pipelined) { return pipelined ? (p == 512 || p == 1024 || p == 2048) : p == 2048; }
 
 // Schur update of step k (lastcol: every column but k) on the tensor cores.
 cudaError_t update_tc_p2048_step(MpArr X, int64_t N, int64_t k, MpArr Z, int* status, int p, int lastcol, int nsm,

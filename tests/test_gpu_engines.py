@@ -1,4 +1,5 @@
-"""The tensor-core engine (exact digit convolution on tcgen05, p = 2048) and
+"""The tensor-core engine (exact digit convolution on tcgen05, p = 512, 1024,
+2048) and
 the IMAD engine must give the same bits for the whole elimination, in both
 modes, for the adjoint's back substitution, and match the oracle."""
 import numpy as np
@@ -25,23 +26,24 @@ def run(mpdet, N, p, kind, data, engine, lastcol=True):
     return rc, zk, D, Xm
 
 
+@pytest.mark.parametrize("p", [512, 1024, 2048])
 @pytest.mark.parametrize("N", [1, 2, 5, 130, 300])
 @pytest.mark.parametrize("kind", ["cauchy", "int", "f64"])
-def test_tensor_engine_equals_imad_engine(mpdet, N, kind):
-    p = 2048
-    g = W.rng(N * 7 + len(kind))
+def test_tensor_engine_equals_imad_engine(mpdet, p, N, kind):
+    g = W.rng(N * 7 + len(kind) + p)
     data = W.cauchy_xy(N, N) if kind == "cauchy" else (W.int_matrix(N, N) if kind == "int" else g.standard_normal((N, N)))
     for lastcol in (False, True):
         b = run(mpdet, N, p, kind, data, 0, lastcol)
-        for engine in (1, 2):
+        for engine in ((1, 2) if p == 2048 else (1,)):
             a = run(mpdet, N, p, kind, data, engine, lastcol)
             assert a[:2] == b[:2]
             assert X.same(a[2], b[2]), f"leading minors differ between engines {engine} and 0"
             assert X.same(a[3], b[3]), f"in-place arrays differ between engines {engine} and 0"
 
 
-def test_tensor_engine_vs_oracle(mpdet, oracle_lib):
-    N, p = 150, 2048
+@pytest.mark.parametrize("p", [512, 1024, 2048])
+def test_tensor_engine_vs_oracle(mpdet, oracle_lib, p):
+    N = 150
     A = W.int_matrix(N, 3)
     rc, zk, D, Xm = run(mpdet, N, p, "int", A, 1)
     st, ozk, OD, OX = oracle_lib.ge(oracle_lib.from_int(A.reshape(-1), p), N, p, lastcol=True, nthreads=16)
