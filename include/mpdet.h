@@ -156,11 +156,14 @@ int64_t mpdet_steps_done(mpdet_t h);
  * IMAD Schur-update kernel: value v in 0..3 compiles it for at least 3 + v
  * resident 128-thread blocks per SM.  MPDET_TUNE_ENGINE selects how the
  * update forms its products: 1 (default) on the tensor cores as an exact
- * digit convolution where that engine exists (p = 2048), warp-specialised so
- * that the tensor core, the rounding and the subtraction overlap; 2 the same
- * one phase at a time; 0 with IMAD limb products everywhere.
+ * digit convolution where that engine exists (p = 512, 1024, 2048),
+ * warp-specialised so that the tensor core, the rounding and the subtraction
+ * overlap; 2 the same one phase at a time (p = 2048 only); 0 with IMAD limb
+ * products everywhere.  MPDET_TUNE_TC_MIN_ROWS (value >= 0): an update launch
+ * of fewer rows than this takes the IMAD kernel even when the tensor engine is
+ * selected (its tiles are 128 rows high; default 32).
  * Errors: MPDET_EINVAL. */
-enum { MPDET_TUNE_UPDATE_VARIANT = 1, MPDET_TUNE_ENGINE = 2 };
+enum { MPDET_TUNE_UPDATE_VARIANT = 1, MPDET_TUNE_ENGINE = 2, MPDET_TUNE_TC_MIN_ROWS = 3 };
 int mpdet_tune(mpdet_t h, int param, int value);
 
 /* Instrumentation (not part of the computation).  mpdet_profile(h, 1)

@@ -964,6 +964,19 @@ struct Launch {
     s.batch_blocks_per_sm = &batch_blocks_per_sm;
     return s;
   }
+  // The same set with the pivot and the single reciprocal taken from the
+  // family (PW, PG), PW * PG = n.  Both run one long division per launch on
+  // one group, a serial chain whose length per quotient limb grows with the
+  // slice width, so the narrowest slices (W = 4 while n <= 128) give the
+  // shortest step.
+  template <int PW, int PG>
+  static KernelSet make_with_pivot() {
+    static_assert(PW * PG == n, "the pivot family holds the same numbers");
+    KernelSet s = make();
+    s.pivot = &Launch<PW, PG>::pivot;
+    s.recip1 = &Launch<PW, PG>::recip1;
+    return s;
+  }
 };
 
 }  // namespace mpd

@@ -53,7 +53,8 @@ struct mpdet_ctx {
   size_t stage_bytes = 0;
   int64_t k_done = 0;
   int upd_variant = 1;
-  int engine = 1;  // 1: tensor cores, pipelined (p = 2048); 2: tensor cores, one role at a time; 0: IMAD
+  int engine = 1;  // 1: tensor cores, pipelined (p = 512..2048); 2: tensor cores, one role at a time; 0: IMAD
+  int64_t tc_min_rows = 32;  // shorter update launches take the IMAD kernel
   bool have_matrix = false;
   char err[512] = {0};
   // instrumentation: kernel launches enqueued, and optional event pairs
@@ -295,6 +296,11 @@ static int next_event(mpdet_t h, cudaEvent_t* ev) {
   return MPDET_OK;
 }
 
+// Tensor engine for an update launch of `rows` rows?
+static bool use_tc(mpdet_t h, int64_t rows) {
+  return h->engine >= 1 && mpd::tc_supports(h->p, h->engine == 1) && rows >= h->tc_min_rows;
+}
+
 // enqueue steps k (0-based) in [k0, k1)
 static int run_steps(mpdet_t h, int64_t k0, int64_t k1) {
   const int lastcol = (h->flags & MPDET_LASTCOL) ? 1 : 0;
@@ -311,7 +317,7 @@ static int run_steps(mpdet_t h, int64_t k0, int64_t k1) {
         if (rc) return rc;
         CU(h, cudaEventRecord(e0, h->stream));
       }
-      if (h->engine >= 1 && mpd::tc_supports(h->p, h->engine == 1))
+      if (use_tc(h, N - k - 1))
         CU(h, mpd::update_tc_p2048_step(h->X, N, k, h->Z, h->status, h->p, lastcol, h->nsm, h->stream,
                                         h->engine == 1 ? 1 : 0));
       else
@@ -338,6 +344,10 @@ extern "C" int mpdet_tune(mpdet_t h, int param, int value) {
     case MPDET_TUNE_ENGINE:
       if (value < 0 || value > 2) return fail(h, MPDET_EINVAL, "tune: engine %d", value);
       h->engine = value;
+      return MPDET_OK;
+    case MPDET_TUNE_TC_MIN_ROWS:
+      if (value < 0) return fail(h, MPDET_EINVAL, "tune: tc_min_rows %d", value);
+      h->tc_min_rows = value;
       return MPDET_OK;
     default:
       return fail(h, MPDET_EINVAL, "tune: unknown parameter %d", param);
@@ -536,7 +546,7 @@ extern "C" int mpdet_logabsdet_grad(mpdet_t h, const double* A, int64_t ld, doub
                               cudaMemcpyDeviceToDevice, h->stream));
       CU(h, cudaMemcpy2DAsync(h->Z.e, 8, h->X.e + k, (size_t)N * 8, 8, (size_t)k, cudaMemcpyDeviceToDevice, h->stream));
       CU(h, cudaMemcpy2DAsync(h->Z.s, 1, h->X.s + k, (size_t)N, 1, (size_t)k, cudaMemcpyDeviceToDevice, h->stream));
-      if (h->engine >= 1 && mpd::tc_supports(h->p, h->engine == 1))
+      if (use_tc(h, k))
         CU(h, mpd::usolve_tc_p2048(h->S, N, k, h->Z, h->status, h->p, h->nsm, h->stream, h->engine == 1 ? 1 : 0));
       else
         CU(h, h->ks->usolve_update(h->S, N, k, h->Z, h->status, h->p, h->nsm, h->stream));

@@ -505,6 +505,36 @@ __device__ __forceinline__ void sub_round(const Grp<G>& gp, int p, int8_t& xs, i
 }
 
 // ---------------------------------------------------------------------------
+// Division of the two-limb u1*2^32 + u0 (u1 < d) by a normalised limb d
+// (top bit set) with the precomputed reciprocal v = floor((2^64-1)/d) - 2^32,
+// after Moller and Granlund, "Improved division by invariant integers"
+// (IEEE Trans. Computers 60(2), 2011), Algorithm 4: one multiply, one
+// multiply-low and two rarely taken corrections instead of a 64-by-32-bit
+// software division.  Returns the quotient limb; r = the remainder.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint32_t div21_preinv(uint32_t u1, uint32_t u0, uint32_t d, uint32_t v,
+                                                          uint32_t& r) {
+  const uint64_t s = (uint64_t)v * u1 + (((uint64_t)u1 << 32) | u0);  // modulo 2^64
+  uint32_t q1 = (uint32_t)(s >> 32) + 1u;
+  const uint32_t q0 = (uint32_t)s;
+  uint32_t rr = u0 - q1 * d;
+  if (rr > q0) {
+    q1 -= 1u;
+    rr += d;
+  }
+  if (rr >= d) {
+    q1 += 1u;
+    rr -= d;
+  }
+  r = rr;
+  return q1;
+}
+
+__host__ __device__ __forceinline__ uint32_t div21_inverse(uint32_t d) {
+  return (uint32_t)(~0ull / d - (1ull << 32));
+}
+
+// ---------------------------------------------------------------------------
 // Correctly rounded reciprocal of a mantissa: RN_p(2^(2p-1) / m) scaled to
 // [2^(p-1), 2^p).  V: this lane's slice of m (normalised, top bit set).
 // qbuf: per-group shared scratch of >= n + 1 words.
@@ -512,67 +542,81 @@ __device__ __forceinline__ void sub_round(const Grp<G>& gp, int p, int8_t& xs, i
 //
 // Schoolbook long division in base 2^32 (Knuth, TAOCP vol. 2, 4.3.1,
 // Algorithm D) of 2^(2p) by m: one quotient limb per step from the top two
-// remainder limbs, a 2-limb test that leaves the estimate at most one too
-// large, a distributed multiply-subtract, and an add-back when the estimate
-// was too large.  Quotient Q = floor(2^(2p)/m) lies in (2^p, 2^(p+1)];
-// RN rounds Q/2 with Q's last bit as round bit and the remainder as sticky.
+// remainder limbs (Theorem B: the estimate is at most two too large for a
+// normalised divisor), a 2-limb test that leaves it at most one too large, a
+// multiply-subtract, and an add-back when the estimate was too large.
+// Quotient Q = floor(2^(2p)/m) lies in (2^p, 2^(p+1)]; RN rounds Q/2 with
+// Q's last bit as round bit and the remainder as sticky.
+//
+// Per step the group exchanges one word per lane: each lane subtracts q times
+// its slice of m from its slice of the shifted remainder with a word-sized
+// running borrow (at most 2^32 - 1), passes that borrow word one lane up, and
+// the one-bit borrows that remain are resolved with two ballots.  A lane whose
+// own subtraction borrowed is left with a non-zero slice (W >= 2), so no lane
+// passes on more than one bit.
 // ---------------------------------------------------------------------------
 template <int W, int G>
 __device__ __forceinline__ int recip_round(const Grp<G>& gp, const uint32_t (&V)[W], uint32_t* qbuf, uint32_t (&M)[W]) {
   constexpr int n = W * G;
-  static_assert(W >= 4, "the quotient test reads two limbs of the top slice");
+  static_assert(W >= 4, "the quotient test reads three limbs of the top slice");
   const int g = gp.g;
   uint32_t R[W];
 #pragma unroll
   for (int i = 0; i < W; ++i) R[i] = 0u;
   if (g == G - 1) R[W - 1] = 1u;  // R = 2^(32(n-1)); the first shift makes it 2^p
   const uint32_t v1 = gp.from(V[W - 1], G - 1), v0 = gp.from(V[W - 2], G - 1);
+  const uint32_t vinv = div21_inverse(v1);
 #pragma unroll 1
   for (int j = n; j >= 0; --j) {
-    // R' = R * 2^32 (n+1 limbs; limb n is rtop)
+    // R' = R * 2^32 (n+1 limbs; limb n is rtop, limbs n-1 and n-2 are r1, r0)
+    const uint32_t rtop = gp.from(R[W - 1], G - 1);
+    const uint32_t r1 = gp.from(R[W - 2], G - 1), r0 = gp.from(R[W - 3], G - 1);
     uint32_t up = __shfl_up_sync(FULL, R[W - 1], 1);
     if (g == 0) up = 0u;
-    const uint32_t rtop = gp.from(R[W - 1], G - 1);
 #pragma unroll
     for (int i = W - 1; i > 0; --i) R[i] = R[i - 1];
     R[0] = up;
-    const uint32_t r1 = gp.from(R[W - 1], G - 1), r0 = gp.from(R[W - 2], G - 1);
-    uint64_t num = ((uint64_t)rtop << 32) | r1;
-    uint64_t qh = num / v1, rh = num % v1;
-    // at most two corrections for a normalised divisor (v1 >= 2^31)
-    for (int it = 0; it < 2 && (qh >= (1ull << 32) || qh * v0 > ((rh << 32) | r0)); ++it) {
-      qh -= 1;
-      rh += v1;
-      if (rh >= (1ull << 32)) break;
+    // quotient limb estimate: min(floor((rtop, r1) / v1), 2^32 - 1); the
+    // remainder never exceeds m, so rtop <= v1
+    uint32_t q, rh;
+    bool rbig;
+    if (rtop >= v1) {
+      q = 0xffffffffu;
+      const uint64_t t = (uint64_t)r1 + v1;  // (rtop, r1) - q * v1 with rtop = v1
+      rh = (uint32_t)t;
+      rbig = (t >> 32) != 0u;
+    } else {
+      q = div21_preinv(rtop, r1, v1, vinv, rh);
+      rbig = false;
     }
-    uint32_t q = (uint32_t)qh;
-    // P = q * m (n+1 limbs)
-    uint32_t lo[W], hi[W];
+    for (int it = 0; it < 2 && !rbig && (uint64_t)q * v0 > (((uint64_t)rh << 32) | r0); ++it) {
+      q -= 1u;
+      const uint64_t t = (uint64_t)rh + v1;
+      rh = (uint32_t)t;
+      rbig = (t >> 32) != 0u;
+    }
+    // D = R' - q * m: this slice with a running borrow word ...
+    uint32_t D[W];
+    uint32_t acc = 0u;
 #pragma unroll
     for (int i = 0; i < W; ++i) {
-      uint64_t t = (uint64_t)q * V[i];
-      lo[i] = (uint32_t)t;
-      hi[i] = (uint32_t)(t >> 32);
+      const uint64_t t = (uint64_t)q * V[i] + acc;
+      const uint32_t lo = (uint32_t)t;
+      D[i] = R[i] - lo;
+      acc = (uint32_t)(t >> 32) + (R[i] < lo ? 1u : 0u);
     }
-    uint32_t hprev = __shfl_up_sync(FULL, hi[W - 1], 1);
-    if (g == 0) hprev = 0u;
-    uint32_t P[W];
-    P[0] = add_cc(lo[0], hprev);
+    // ... minus the borrow word of the slice below ...
+    uint32_t bin = __shfl_up_sync(FULL, acc, 1);
+    if (g == 0) bin = 0u;
+    const uint32_t atop = gp.from(acc, G - 1);
+    D[0] = sub_cc(D[0], bin);
 #pragma unroll
-    for (int i = 1; i < W; ++i) P[i] = addc_cc(lo[i], hi[i - 1]);
-    uint32_t pc = addc(0u, 0u);
-    uint64_t cm = carry_mask(gp.ballot(pc != 0u), gp.ballot(all_ones<W>(P)), 0u);
-    slice_inc<W>(P, (uint32_t)(cm >> g) & 1u);
-    const uint32_t ptop = gp.from(hi[W - 1], G - 1) + (uint32_t)((cm >> G) & 1u);
-    // D = R' - P
-    uint32_t D[W];
-    D[0] = sub_cc(R[0], P[0]);
-#pragma unroll
-    for (int i = 1; i < W; ++i) D[i] = subc_cc(R[i], P[i]);
-    uint32_t bo = borrow_out();
-    uint64_t bm = carry_mask(gp.ballot(bo != 0u), gp.ballot(all_zero<W>(D)), 0u);
+    for (int i = 1; i < W; ++i) D[i] = subc_cc(D[i], 0u);
+    const uint32_t bo = borrow_out();
+    // ... and the one-bit borrows rippling up through all-zero slices
+    const uint64_t bm = carry_mask(gp.ballot(bo != 0u), gp.ballot(all_zero<W>(D)), 0u);
     slice_dec<W>(D, (uint32_t)(bm >> g) & 1u);
-    const int64_t top = (int64_t)rtop - (int64_t)ptop - (int64_t)((bm >> G) & 1u);
+    const int64_t top = (int64_t)rtop - (int64_t)atop - (int64_t)((bm >> G) & 1u);
     const bool neg = top < 0;  // estimate one too large: add m back
     if (__any_sync(FULL, neg)) {
       uint32_t Vm[W];

@@ -11,9 +11,11 @@ from paper_1308_1536_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 
-def run(mpdet, N, p, kind, data, engine, lastcol=True):
+def run(mpdet, N, p, kind, data, engine, lastcol=True, tc_min_rows=0):
+    """tc_min_rows=0: the tensor engine takes every update launch, down to
+    one row (the default hands short launches to the IMAD kernel)."""
     h = mpdet.Mpdet(N, p, lastcol=lastcol)
-    h.tune(engine=engine)
+    h.tune(engine=engine, tc_min_rows=tc_min_rows)
     if kind == "cauchy":
         h.set_cauchy(*data)
     elif kind == "int":
@@ -57,9 +59,20 @@ def test_tensor_engine_adjoint(mpdet):
     out = []
     for engine in (1, 0):
         h = mpdet.Mpdet(N, p, lastcol=True)
-        h.tune(engine=engine)
+        h.tune(engine=engine, tc_min_rows=0)
         s, la, G = h.logabsdet_grad(A)
         out.append((s, la, G, h.get_inverse()))
         h.close()
     assert out[0][0] == out[1][0] and out[0][1] == out[1][1]
     assert np.array_equal(out[0][2], out[1][2]) and X.same(out[0][3], out[1][3])
+
+
+@pytest.mark.parametrize("tc_min_rows", [16, 64, 1 << 20])
+def test_engine_switch_by_rows(mpdet, tc_min_rows):
+    """Mixing the engines within one elimination (tensor cores for the long
+    launches, IMAD for the short ones) changes no bit."""
+    N, p = 200, 1024
+    data = W.int_matrix(N, 17)
+    ref = run(mpdet, N, p, "int", data, 0)
+    got = run(mpdet, N, p, "int", data, 1, tc_min_rows=tc_min_rows)
+    assert got[:2] == ref[:2] and X.same(got[2], ref[2]) and X.same(got[3], ref[3])

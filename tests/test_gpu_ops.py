@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import exactref as X
-from test_oracle_ops import rand_num, values_with_specials
+from test_oracle_ops import division_corner_mantissas, rand_num, values_with_specials
 
 pytestmark = pytest.mark.gpu
 
@@ -61,3 +61,38 @@ def test_ops_vs_oracle(mpdet, oracle_lib, p):
     Anz = tuple(t[nz] for t in A)
     got = mpdet.ops("recip", Anz, Anz, p)
     assert first_bad(got, oracle_lib.recip(Anz, p)) is None
+
+
+@pytest.mark.parametrize("p", [128, 256, 512, 1024, 2048, 4096, 8192, 32768])
+def test_recip_division_corners(mpdet, oracle_lib, p):
+    vals = []
+    for m in division_corner_mantissas(p):
+        for e in (0, 5, -3):
+            vals.append(Fraction(m) * Fraction(2) ** (e - p))
+            vals.append(-Fraction(m) * Fraction(2) ** (e - p))
+    A = X.pack(vals, p)
+    got = mpdet.ops("recip", A, A, p)
+    i = first_bad(got, oracle_lib.recip(A, p))
+    assert i is None, f"p={p}: first mismatch at {i}"
+    want = X.pack([1 / v for v in vals], p)
+    assert first_bad(got, want) is None
+
+
+@pytest.mark.parametrize("p", [128, 256, 512, 1024, 2048, 4096, 8192])
+def test_pivot_reciprocal_corners(mpdet, oracle_lib, p):
+    """The pivot kernel's reciprocal (its own lane grouping) on the same
+    divisors: a_00 is the corner mantissa, the multipliers of column 0 expose
+    r_1 in lastcol mode and must equal the oracle's bit for bit."""
+    g = np.random.Generator(np.random.PCG64(900 + p))
+    for m in division_corner_mantissas(p):
+        vals = [Fraction(m) * Fraction(2) ** (-p)] + [rand_num(g, p) for _ in range(8)]
+        A = X.pack(vals, p)
+        h = mpdet.Mpdet(3, p, lastcol=True)
+        h.set_mp(A)
+        rc, zk, D = h.factor()
+        Xg = h.get_mp()
+        h.close()
+        st, ozk, OD, OX = oracle_lib.ge(A, 3, p, lastcol=True)
+        assert rc == st and zk == ozk
+        assert first_bad(D, OD) is None
+        assert first_bad(Xg, OX) is None, f"p={p} m={hex(m)[:20]}"

@@ -39,6 +39,24 @@ def special_mantissas(p):
     ]
 
 
+def division_corner_mantissas(p):
+    """Divisors that drive every branch of a base-2^32 long division of
+    2^(2p): one and two decrements of the quotient-limb estimate by the
+    two-limb test, the add-back (2^(p-1) + 1 and top limbs 2^31 over
+    all-ones), the estimate clamped to 2^32 - 1 when the remainder's top limb
+    equals the divisor's (every limb 2^31), and the power-of-two case."""
+    top = 1 << (p - 1)
+    return special_mantissas(p) + [
+        top | ((1 << (p - 64)) - 1),          # v1 = 2^31, v0 = 0, lower limbs all ones
+        top | (1 << (p - 64)),                # lowest bit of the second limb
+        top | ((1 << (p - 32)) - 1),          # v1 = 2^31, everything below all ones
+        (1 << p) - (1 << (p - 32)),           # top limb all ones, the rest zero
+        ((1 << p) - 1) ^ ((1 << (p - 33)) | 1),
+        sum(0x80000000 << (32 * i) for i in range(p // 32)) + 1,  # remainder top limb = v1: clamped estimate
+        top | (0x7FFFFFFF << (p - 64)) | ((1 << (p - 64)) - (1 << 32)) | 0x80000000,
+    ]
+
+
 def values_with_specials(g, p, count):
     vals = [rand_num(g, p) for _ in range(count)]
     for m in special_mantissas(p):
@@ -142,6 +160,13 @@ def test_recip(oracle_lib, p):
     got = oracle_lib.recip(A, p)
     want = X.pack([1 / v for v in X.unpack(A, p)], p)
     assert X.same(got, want)
+
+
+@pytest.mark.parametrize("p", [128, 256, 2048])
+def test_recip_division_corners(oracle_lib, p):
+    vals = [Fraction(m) * Fraction(2) ** (e - p) for m in division_corner_mantissas(p) for e in (0, -3)]
+    A = X.pack(vals, p)
+    assert X.same(oracle_lib.recip(A, p), X.pack([1 / v for v in vals], p))
 
 
 def test_recip_of_zero_is_an_error(oracle_lib):
