@@ -465,7 +465,7 @@ def run_gpu(args):
         upd_launches = pc["update_launches"] + pi["update_launches"]
         achieved = upd_macs / (upd_ms / 1e3)
         tr = recorded_traffic()
-        tensor = (p == 2048 and args.engine != 0)
+        tensor = (p in (1024, 2048) and args.engine != 0)
         if tensor:
             # exact digit convolution on the tensor cores: one limb-MAC is 16 products of 8-bit digits,
             # 32 flops; peak = measured bf16 dense throughput (sustained: the kernel runs inside a long step)

@@ -161,9 +161,23 @@ int64_t mpdet_steps_done(mpdet_t h);
  * overlap; 2 the same one phase at a time (p = 2048 only); 0 with IMAD limb
  * products everywhere.  MPDET_TUNE_TC_MIN_ROWS (value >= 0): an update launch
  * of fewer rows than this takes the IMAD kernel even when the tensor engine is
- * selected (its tiles are 128 rows high; default 32).
+ * selected (its tiles are 128 rows high).  By default the threshold follows the
+ * precision: 64 rows at p = 2048, 128 at p = 1024, and the IMAD kernel always
+ * at p = 512, where it measured faster at every size.  MPDET_TUNE_LOOKAHEAD:
+ * 1 (default) overlaps the pivot and multipliers of step k+1 with the update
+ * of step k: a second stream owned by the handle updates column k+1 first and
+ * runs them while the handle's stream updates the other columns; 0 runs each
+ * step's kernels one after another on the handle's stream.
+ * MPDET_TUNE_LOOKAHEAD_RESERVE (0..64, default 4): SMs the update of the
+ * other columns leaves free for that second stream.
  * Errors: MPDET_EINVAL. */
-enum { MPDET_TUNE_UPDATE_VARIANT = 1, MPDET_TUNE_ENGINE = 2, MPDET_TUNE_TC_MIN_ROWS = 3 };
+enum {
+  MPDET_TUNE_UPDATE_VARIANT = 1,
+  MPDET_TUNE_ENGINE = 2,
+  MPDET_TUNE_TC_MIN_ROWS = 3,
+  MPDET_TUNE_LOOKAHEAD = 4,
+  MPDET_TUNE_LOOKAHEAD_RESERVE = 5
+};
 int mpdet_tune(mpdet_t h, int param, int value);
 
 /* Instrumentation (not part of the computation).  mpdet_profile(h, 1)

@@ -231,7 +231,8 @@ __global__ void k_pivot(MpArr X, int64_t N, int64_t k, MpArr D, MpArr R, int* st
   if (ae == ZEXP && !already) {
     if (mine && gp.g == 0) {
       if (*zero_k == 0) *zero_k = k + 1;
-      if (k < N - 1) *status = 4;  // MPDET_EZEROPIVOT
+      // MPDET_EZEROPIVOT with the 1-based step in the upper half, one store
+      if (k < N - 1) *reinterpret_cast<volatile unsigned long long*>(status) = ((unsigned long long)(k + 1) << 32) | 4u;
     }
     return;
   }
@@ -295,21 +296,25 @@ __global__ void k_mult(MpArr X, int64_t N, int64_t k, MpArr R, MpArr Z, const in
 // ---------------------------------------------------------------------------
 // a4/a5 (and the adjoint's back substitution): rank-1 update
 //   x_ij = RN(x_ij - RN(z_i * x_{brow,j}))
-// for rows i in [row0, row0 + nrows) and the columns j selected by cmode:
-//   0: j > kcol (Schur update of step kcol)
-//   1: j != kcol (lastcol mode: also L's row segment j < kcol)
-//   2: every j (back substitution)
+// for the rows and columns of an UpdArgs (kernelset.h).
 // z_i is Z[i].  Block: GPB groups, each owning one column j and holding the
 // pivot-row element x_{brow,j}'s slice in registers; the block walks rows
 // [i0, i1) with the multipliers staged in shared memory (broadcast reads).
 // ---------------------------------------------------------------------------
-struct UpdArgs {
-  int64_t N, brow, row0, nrows, kcol;
-  int cmode;
-};
+// An update launch stops once the elimination has: on any error, and on a
+// zero pivot found at its own step or before.  A zero pivot of a later step
+// does not stop it: with look-ahead the next step's pivot runs while this
+// step's update does.  The pivot stores its 1-based step in the status word's
+// upper half together with the code (one 64-bit store).
+__device__ __forceinline__ bool upd_stopped(const int* status, const UpdArgs& a) {
+  const unsigned long long w = *reinterpret_cast<volatile const unsigned long long*>(status);
+  const int code = (int)(uint32_t)w;
+  if (code == 0) return false;
+  if (code != 4 || a.step < 0) return true;  // MPDET_EZEROPIVOT
+  return (int64_t)(w >> 32) <= a.step + 1;
+}
 
-// tensor-core engine for p = 2048 (tc_update.cu)
-cudaError_t update_tc_p2048(MpArr X, UpdArgs a, MpArr Z, int* status, int p, int nsm, cudaStream_t st);
+__device__ __forceinline__ int64_t upd_col(const UpdArgs& a, int64_t c) { return a.j0 + c + (c >= a.hole ? a.hw : 0); }
 
 template <int W, int G, int MINB>
 __global__ void __launch_bounds__(128, MINB) k_update(MpArr X, UpdArgs a, MpArr Z, const int* status, int p,
@@ -317,7 +322,7 @@ __global__ void __launch_bounds__(128, MINB) k_update(MpArr X, UpdArgs a, MpArr 
   constexpr int n = W * G;
   constexpr int SW = Scratch<W, G>::words;
   extern __shared__ __align__(16) uint32_t smem[];
-  if (status_set(status)) return;
+  if (upd_stopped(status, a)) return;
   Grp<G> gp;
   const int64_t N = a.N;
   const int gpb = blockDim.x / G;
@@ -328,7 +333,7 @@ __global__ void __launch_bounds__(128, MINB) k_update(MpArr X, UpdArgs a, MpArr 
   int64_t* ze_s = reinterpret_cast<int64_t*>(smem + rows_per_cta * n);
   int8_t* zs_s = reinterpret_cast<int8_t*>(smem + rows_per_cta * n + upd_pad4(2 * rows_per_cta));
   uint32_t* buf = smem + rows_per_cta * n + upd_pad4(2 * rows_per_cta) + upd_pad4((rows_per_cta + 3) / 4) + gib * SW;
-  const int64_t ncols = a.cmode == 0 ? N - a.kcol - 1 : (a.cmode == 1 ? N - 1 : N);
+  const int64_t ncols = a.ncols;
   const int64_t i0 = a.row0 + (int64_t)blockIdx.y * rows_per_cta;
   const int64_t rend = a.row0 + a.nrows;
   const int64_t i1 = (i0 + rows_per_cta < rend) ? i0 + rows_per_cta : rend;
@@ -344,7 +349,7 @@ __global__ void __launch_bounds__(128, MINB) k_update(MpArr X, UpdArgs a, MpArr 
   int64_t c = (int64_t)blockIdx.x * gpb + gib;
   const bool active = c < ncols;
   if (!active) c = ncols - 1;
-  const int64_t j = a.cmode == 0 ? a.kcol + 1 + c : (a.cmode == 1 ? (c < a.kcol ? c : c + 1) : c);
+  const int64_t j = upd_col(a, c);
   // pivot-row element x_{brow,j}
   const int64_t kj = a.brow * N + j;
   uint32_t Bk[W];
@@ -374,6 +379,52 @@ __global__ void __launch_bounds__(128, MINB) k_update(MpArr X, UpdArgs a, MpArr 
         X.s[ij] = xs;
         X.e[ij] = xe;
       }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The same update for a single column (a.ncols == 1): one group per row, so
+// that the column k+1 of a look-ahead step spreads over as many groups as it
+// has rows instead of occupying one group per block.
+// ---------------------------------------------------------------------------
+template <int W, int G>
+__global__ void k_update_col(MpArr X, UpdArgs a, MpArr Z, const int* status, int p) {
+  constexpr int n = W * G;
+  constexpr int SW = Scratch<W, G>::words;
+  __shared__ __align__(16) uint32_t sbuf[(128 / G) * SW];
+  if (upd_stopped(status, a)) return;
+  Grp<G> gp;
+  const int64_t N = a.N;
+  const int64_t j = upd_col(a, 0);
+  int64_t r = (int64_t)blockIdx.x * (blockDim.x / G) + threadIdx.x / G;
+  const bool active = r < a.nrows;
+  if (!active) r = a.nrows - 1;
+  const int64_t i = a.row0 + r;
+  const int64_t kj = a.brow * N + j, ij = i * N + j;
+  uint32_t Bk[W], Xv[W], T[W];
+  load_slice<W>(X.m + kj * n + gp.g * W, Bk);
+  const int8_t bs = X.s[kj];
+  const int64_t be = X.e[kj];
+  int8_t xs = X.s[ij];
+  int64_t xe = X.e[ij];
+  const int64_t zer = Z.e[i];
+  const int8_t zs = Z.s[i];
+  const int adj = mul_round<W, G>(gp, Bk, Z.m + i * n, T);
+  load_slice<W>(X.m + ij * n + gp.g * W, Xv);
+  const bool tz = (zer == ZEXP) || (be == ZEXP);
+  const int8_t ts = tz ? 0 : (int8_t)(zs ^ bs);
+  const int64_t te = tz ? ZEXP : zer + be + adj;
+  if (tz) {
+#pragma unroll
+    for (int q = 0; q < W; ++q) T[q] = 0u;
+  }
+  sub_round<W, G>(gp, p, xs, xe, Xv, ts, te, T, sbuf + (threadIdx.x / G) * SW);
+  if (active) {
+    store_slice<W>(X.m + ij * n + gp.g * W, Xv);
+    if (gp.g == 0) {
+      X.s[ij] = xs;
+      X.e[ij] = xe;
     }
   }
 }
@@ -861,8 +912,8 @@ struct Launch {
     return (size_t)(rows_per_cta * n + upd_pad4(2 * rows_per_cta) + upd_pad4((rows_per_cta + 3) / 4) + (NT / G) * SW) * 4;
   }
   template <int MINB>
-  static cudaError_t update_any(MpArr X, UpdArgs a, MpArr Z, const int* status, int p, int nsm, cudaStream_t st) {
-    const int64_t ncols = a.cmode == 0 ? a.N - a.kcol - 1 : (a.cmode == 1 ? a.N - 1 : a.N);
+  static cudaError_t update(MpArr X, const UpdArgs& a, MpArr Z, const int* status, int p, int nsm, cudaStream_t st) {
+    const int64_t ncols = a.ncols;
     const int64_t rows = a.nrows;
     if (rows <= 0 || ncols <= 0) return cudaSuccess;
     const int gpb = NT / G;
@@ -882,16 +933,12 @@ struct Launch {
     k_update<W, G, MINB><<<grid, NT, sm, st>>>(X, a, Z, status, p, (int)rpc);
     return cudaGetLastError();
   }
-  template <int MINB>
-  static cudaError_t update(MpArr X, int64_t N, int64_t k, MpArr Z, const int* status, int p, int lastcol, int nsm,
-                            cudaStream_t st) {
-    UpdArgs a{N, k, k + 1, N - k - 1, k, lastcol ? 1 : 0};
-    return update_any<MINB>(X, a, Z, status, p, nsm, st);
-  }
-  static cudaError_t usolve_update(MpArr S, int64_t N, int64_t k, MpArr Z, const int* status, int p, int nsm,
-                                   cudaStream_t st) {
-    UpdArgs a{N, k, 0, k, 0, 2};
-    return update_any<4>(S, a, Z, status, p, nsm, st);
+  static cudaError_t update_col(MpArr X, const UpdArgs& a, MpArr Z, const int* status, int p, cudaStream_t st) {
+    if (a.ncols != 1) return cudaErrorInvalidValue;
+    if (a.nrows <= 0) return cudaSuccess;
+    const int64_t blocks = (a.nrows + NT / G - 1) / (NT / G);
+    k_update_col<W, G><<<(unsigned)blocks, NT, 0, st>>>(X, a, Z, status, p);
+    return cudaGetLastError();
   }
   static cudaError_t init_s(MpArr X, int64_t N, MpArr S, int nsm, cudaStream_t st) {
     int64_t blocks = (N * N + NT / G - 1) / (NT / G);
@@ -953,10 +1000,10 @@ struct Launch {
     s.update[1] = &update<4>;
     s.update[2] = &update<5>;
     s.update[3] = &update<6>;
+    s.update_col = &update_col;
     s.lastcol = &lastcol;
     s.recip1 = &recip1;
     s.batch = &batch;
-    s.usolve_update = &usolve_update;
     s.ops = &ops;
     s.init_s = &init_s;
     s.rowscale = &rowscale;

@@ -25,6 +25,38 @@ struct BatchDescHost {
   int64_t max_n;
 };
 
+// One rank-1 update launch (Alg. 1 step 2.2.2, and the adjoint's back
+// substitution):
+//   x_ij = RN(x_ij - RN(z_i * x_{brow,j})),   i in [row0, row0 + nrows),
+// over the columns j = j0 + c + (c >= hole ? hw : 0), c in [0, ncols): a run
+// of columns with at most one gap of hw columns (the pivot column in lastcol
+// mode, and with look-ahead also column k+1, which a separate launch updates
+// first).  z_i is Z[i].  step: the 0-based elimination step of the launch,
+// or -1 for the back substitution.
+struct UpdArgs {
+  int64_t N, brow, row0, nrows;
+  int64_t j0, hole, ncols;
+  int64_t step;
+  int hw;
+};
+
+// Every column of step k's Schur update: j > k, or j != k in lastcol mode
+// (which also carries L's row segment j < k).
+inline UpdArgs upd_step(int64_t N, int64_t k, int lastcol) {
+  return lastcol ? UpdArgs{N, k, k + 1, N - k - 1, 0, k, N - 1, k, 1}
+                 : UpdArgs{N, k, k + 1, N - k - 1, k + 1, INT64_MAX, N - k - 1, k, 0};
+}
+// Column k+1 of step k alone (k + 1 < N): all the next pivot and the next
+// multipliers need.
+inline UpdArgs upd_next(int64_t N, int64_t k) { return UpdArgs{N, k, k + 1, N - k - 1, k + 1, INT64_MAX, 1, k, 0}; }
+// The rest of step k: j > k + 1, or j not in {k, k + 1} in lastcol mode.
+inline UpdArgs upd_rest(int64_t N, int64_t k, int lastcol) {
+  return lastcol ? UpdArgs{N, k, k + 1, N - k - 1, 0, k, N - 2, k, 2}
+                 : UpdArgs{N, k, k + 1, N - k - 1, k + 2, INT64_MAX, N - k - 2, k, 0};
+}
+// Back substitution of the adjoint: rows [0, k), every column, pivot row k.
+inline UpdArgs upd_back(int64_t N, int64_t k) { return UpdArgs{N, k, 0, k, 0, INT64_MAX, N, -1, 0}; }
+
 struct KernelSet {
   int W, G;
   // kind 0: double entries, 1: int32 entries
@@ -37,8 +69,10 @@ struct KernelSet {
   // Schur update, one entry per register budget: variant v is compiled for
   // at least 3 + v resident 128-thread blocks per SM
   static constexpr int kUpdateVariants = 4;
-  cudaError_t (*update[kUpdateVariants])(MpArr X, int64_t N, int64_t k, MpArr Z, const int* status, int p,
-                                         int lastcol, int nsm, cudaStream_t st);
+  cudaError_t (*update[kUpdateVariants])(MpArr X, const UpdArgs& a, MpArr Z, const int* status, int p, int nsm,
+                                         cudaStream_t st);
+  // single-column launch (a.ncols == 1), one group per row
+  cudaError_t (*update_col)(MpArr X, const UpdArgs& a, MpArr Z, const int* status, int p, cudaStream_t st);
   cudaError_t (*lastcol)(MpArr X, int64_t N, MpArr F, MpArr out, int normalised, const int* status,
                          cudaStream_t st);
   cudaError_t (*recip1)(MpArr src, int64_t idx, MpArr dst, int* status, int code, cudaStream_t st);
@@ -47,24 +81,21 @@ struct KernelSet {
   int (*batch_blocks_per_sm)();
   // element-wise arithmetic (diagnostics)
   cudaError_t (*ops)(int op, int64_t count, MpArr A, MpArr B, MpArr O, int p, int nsm, cudaStream_t st);
-  // adjoint (back substitution X = U^-1 L and the binary64 gradient)
-  cudaError_t (*usolve_update)(MpArr S, int64_t N, int64_t k, MpArr Z, const int* status, int p, int nsm,
-                               cudaStream_t st);
+  // adjoint (X = U^-1 L by back substitution with update[], and the binary64 gradient)
   cudaError_t (*init_s)(MpArr X, int64_t N, MpArr S, int nsm, cudaStream_t st);
   cudaError_t (*rowscale)(MpArr S, int64_t N, int64_t k, MpArr R, cudaStream_t st);
   cudaError_t (*to_f64)(MpArr X, int64_t N, double* out, double scale, int p, int transpose, int nsm,
                         cudaStream_t st);
 };
 
-struct UpdArgs;  // kernels.cuh
 
-// Tensor-core engine of the rank-1 update, p = 2048 only (tc_update.cu).
+// Tensor-core engine of the rank-1 update (tc_update.cu): p = 512, 1024, 2048
+// with the warp-specialised kernel (pipelined = 1: tensor core, epilogue and
+// subtraction overlap), p = 2048 one role at a time (pipelined = 0).  nsm: the
+// SMs the launch may fill (one block each).
 bool tc_supports(int p, int pipelined);
-// pipelined = 1: warp-specialised kernel (tensor core, epilogue and subtraction overlap); 0: one role at a time
-cudaError_t update_tc_p2048_step(MpArr X, int64_t N, int64_t k, MpArr Z, int* status, int p, int lastcol, int nsm,
-                                 cudaStream_t st, int pipelined);
-cudaError_t usolve_tc_p2048(MpArr S, int64_t N, int64_t k, MpArr Z, int* status, int p, int nsm, cudaStream_t st,
-                            int pipelined);
+cudaError_t update_tc(MpArr X, const UpdArgs& a, MpArr Z, int* status, int p, int nsm, cudaStream_t st,
+                      int pipelined);
 
 // Kernel set for n = p/32 limbs, or nullptr if this n is not instantiated.
 const KernelSet* kernel_set_for(int n);

@@ -14,6 +14,7 @@
 
 using mpd::KernelSet;
 using mpd::MpArr;
+using mpd::UpdArgs;
 
 namespace mpd {
 const KernelSet* kernel_set_for(int n) {
@@ -46,6 +47,7 @@ struct mpdet_ctx {
   int device = 0, nsm = 0;
   const KernelSet* ks = nullptr;
   MpArr X{}, D{}, Z{}, R{}, T{};  // matrix, minors, multipliers, reciprocal, temp (N numbers)
+  MpArr Z2{};                     // multipliers of odd steps under look-ahead (N numbers)
   MpArr S{};                      // adjoint: S = L, then X = A^-1 (N*N numbers, allocated on first use)
   int* status = nullptr;          // [0] code
   int64_t* zero_k = nullptr;
@@ -54,7 +56,14 @@ struct mpdet_ctx {
   int64_t k_done = 0;
   int upd_variant = 1;
   int engine = 1;  // 1: tensor cores, pipelined (p = 512..2048); 2: tensor cores, one role at a time; 0: IMAD
-  int64_t tc_min_rows = 32;  // shorter update launches take the IMAD kernel
+  int64_t tc_min_rows = -1;  // shorter update launches take the IMAD kernel; -1: per precision
+  // look-ahead: the side stream updates column k+1 and runs the pivot and the
+  // multipliers of step k+1 while the handle's stream updates the rest of
+  // step k on all SMs but la_reserve
+  int lookahead = 1;
+  int la_reserve = 4;
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_mult = nullptr, ev_rest = nullptr;
   bool have_matrix = false;
   char err[512] = {0};
   // instrumentation: kernel launches enqueued, and optional event pairs
@@ -146,6 +155,15 @@ extern "C" int mpdet_create(int64_t N, int32_t p_bits, uint32_t flags, void* cud
   if (rc == MPDET_OK) rc = alloc_arr(h, &h->X, N * N);
   if (rc == MPDET_OK) rc = alloc_arr(h, &h->D, N);
   if (rc == MPDET_OK) rc = alloc_arr(h, &h->Z, N);
+  if (rc == MPDET_OK) rc = alloc_arr(h, &h->Z2, N);
+  if (rc == MPDET_OK) {
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, greatest) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_mult, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_rest, cudaEventDisableTiming) != cudaSuccess)
+      rc = MPDET_ECUDA;
+  }
   if (rc == MPDET_OK) rc = alloc_arr(h, &h->T, N);
   if (rc == MPDET_OK) rc = alloc_arr(h, &h->R, 1);
   if (rc == MPDET_OK && cudaMalloc(&h->status, 16) != cudaSuccess) rc = MPDET_ENOMEM;
@@ -169,6 +187,7 @@ extern "C" int mpdet_free(mpdet_t h) {
   free_arr(&h->X);
   free_arr(&h->D);
   free_arr(&h->Z);
+  free_arr(&h->Z2);
   free_arr(&h->T);
   free_arr(&h->R);
   free_arr(&h->S);
@@ -176,6 +195,12 @@ extern "C" int mpdet_free(mpdet_t h) {
   if (h->zero_k) cudaFree(h->zero_k);
   if (h->stage) cudaFree(h->stage);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  if (h->ev_mult) cudaEventDestroy(h->ev_mult);
+  if (h->ev_rest) cudaEventDestroy(h->ev_rest);
+  if (h->side) {
+    cudaStreamSynchronize(h->side);
+    cudaStreamDestroy(h->side);
+  }
   delete h;
   return MPDET_OK;
 }
@@ -296,13 +321,57 @@ static int next_event(mpdet_t h, cudaEvent_t* ev) {
   return MPDET_OK;
 }
 
+// Default shortest launch (rows) for the tensor engine, from GB300
+// measurements of whole eliminations: at p = 2048 it is twice as fast as the
+// IMAD kernel from about 64 rows on, at p = 1024 some 12 % faster from about
+// 128 rows on, and at p = 512 slower at every size measured (N <= 2048).
+static int64_t tc_default_min_rows(int p) { return p == 2048 ? 64 : (p == 1024 ? 128 : INT64_MAX); }
+
 // Tensor engine for an update launch of `rows` rows?
 static bool use_tc(mpdet_t h, int64_t rows) {
-  return h->engine >= 1 && mpd::tc_supports(h->p, h->engine == 1) && rows >= h->tc_min_rows;
+  const int64_t thr = h->tc_min_rows >= 0 ? h->tc_min_rows : tc_default_min_rows(h->p);
+  return h->engine >= 1 && mpd::tc_supports(h->p, h->engine == 1) && rows >= thr;
 }
 
-// enqueue steps k (0-based) in [k0, k1)
-static int run_steps(mpdet_t h, int64_t k0, int64_t k1) {
+// Enqueue one rank-1 update launch of the array A on stream st: single
+// columns on the column kernel, long launches on the tensor engine where it
+// exists, the rest on the IMAD kernel.  nsm: SMs the launch may fill.
+static int launch_update(mpdet_t h, MpArr A, const UpdArgs& a, MpArr Z, int nsm, cudaStream_t st) {
+  if (a.nrows <= 0 || a.ncols <= 0) return MPDET_OK;
+  if (a.ncols == 1)
+    CU(h, h->ks->update_col(A, a, Z, h->status, h->p, st));
+  else if (use_tc(h, a.nrows))
+    CU(h, mpd::update_tc(A, a, Z, h->status, h->p, nsm, st, h->engine == 1 ? 1 : 0));
+  else
+    CU(h, h->ks->update[h->upd_variant](A, a, Z, h->status, h->p, nsm, st));
+  h->launches += 1;
+  return MPDET_OK;
+}
+
+// The same, bracketed by a profiling event pair when profiling is on (the
+// Schur update is the dominant kernel; its algorithmic work is counted).
+static int timed_update(mpdet_t h, const UpdArgs& a, MpArr Z, int nsm, cudaStream_t st) {
+  if (a.nrows <= 0 || a.ncols <= 0) return MPDET_OK;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (h->profile) {
+    int rc = next_event(h, &e0);
+    if (!rc) rc = next_event(h, &e1);
+    if (rc) return rc;
+    CU(h, cudaEventRecord(e0, st));
+  }
+  int rc = launch_update(h, h->X, a, Z, nsm, st);
+  if (rc) return rc;
+  if (h->profile) {
+    CU(h, cudaEventRecord(e1, st));
+    h->upd_launches += 1;
+    h->upd_products += (double)a.nrows * (double)a.ncols;
+  }
+  return MPDET_OK;
+}
+
+// Steps k (0-based) in [k0, k1), one after the other on the handle's stream:
+// pivot, multipliers, update.
+static int run_steps_serial(mpdet_t h, int64_t k0, int64_t k1) {
   const int lastcol = (h->flags & MPDET_LASTCOL) ? 1 : 0;
   const int64_t N = h->N;
   for (int64_t k = k0; k < k1; ++k) {
@@ -310,26 +379,73 @@ static int run_steps(mpdet_t h, int64_t k0, int64_t k1) {
     h->launches += 1;
     if (k < N - 1) {
       CU(h, h->ks->mult(h->X, N, k, h->R, h->Z, h->status, h->p, lastcol, h->stream));
-      cudaEvent_t e0 = nullptr, e1 = nullptr;
-      if (h->profile) {
-        int rc = next_event(h, &e0);
-        if (!rc) rc = next_event(h, &e1);
-        if (rc) return rc;
-        CU(h, cudaEventRecord(e0, h->stream));
-      }
-      if (use_tc(h, N - k - 1))
-        CU(h, mpd::update_tc_p2048_step(h->X, N, k, h->Z, h->status, h->p, lastcol, h->nsm, h->stream,
-                                        h->engine == 1 ? 1 : 0));
-      else
-        CU(h, h->ks->update[h->upd_variant](h->X, N, k, h->Z, h->status, h->p, lastcol, h->nsm, h->stream));
-      if (h->profile) {
-        CU(h, cudaEventRecord(e1, h->stream));
-        h->upd_launches += 1;
-        h->upd_products += (double)(N - k - 1) * (double)(lastcol ? N - 1 : N - k - 1);
-      }
-      h->launches += 2;
+      h->launches += 1;
+      int rc = timed_update(h, mpd::upd_step(N, k, lastcol), h->Z, h->nsm, h->stream);
+      if (rc) return rc;
     }
   }
+  return MPDET_OK;
+}
+
+// Steps k in [k0, k1) with look-ahead.  Step k+1 needs only column k+1 of
+// step k's update before its pivot and multipliers, so the side stream T
+// updates that column first and runs pivot and multipliers of step k+1 while
+// the handle's stream S updates the rest of step k.  Order:
+//   T: [rest of k-1 done] column k+1 of step k, pivot k+1, multipliers k+1
+//   S: [multipliers k done] the rest of step k
+// Multipliers alternate between Z (even steps) and Z2 (odd steps), since
+// those of step k+1 are written while the rest of step k still reads step
+// k's.  The last step of the window updates all its columns on S, so a
+// window ends in the same state as without look-ahead; so do the results,
+// which are the same operations on the same operands.
+static int run_steps_lookahead(mpdet_t h, int64_t k0, int64_t k1) {
+  const int lastcol = (h->flags & MPDET_LASTCOL) ? 1 : 0;
+  const int64_t N = h->N;
+  cudaStream_t S = h->stream, T = h->side;
+  const MpArr Zb[2] = {h->Z, h->Z2};
+  const int nsm_rest = h->nsm > 4 * h->la_reserve ? h->nsm - h->la_reserve : h->nsm;
+  int rc = MPDET_OK;
+  CU(h, cudaEventRecord(h->ev_rest, S));  // T starts after everything enqueued so far
+  CU(h, cudaStreamWaitEvent(T, h->ev_rest, 0));
+  CU(h, h->ks->pivot(h->X, N, k0, h->D, h->R, h->status, h->zero_k, h->p, T));
+  h->launches += 1;
+  if (k0 < N - 1) {
+    CU(h, h->ks->mult(h->X, N, k0, h->R, Zb[k0 & 1], h->status, h->p, lastcol, T));
+    h->launches += 1;
+  }
+  CU(h, cudaEventRecord(h->ev_mult, T));
+  for (int64_t k = k0; k < k1 && k < N - 1; ++k) {
+    const MpArr Zk = Zb[k & 1];
+    CU(h, cudaStreamWaitEvent(S, h->ev_mult, 0));  // multipliers of step k
+    if (k + 1 < k1) {
+      CU(h, cudaStreamWaitEvent(T, h->ev_rest, 0));  // rest of step k-1
+      rc = launch_update(h, h->X, mpd::upd_next(N, k), Zk, h->nsm, T);
+      if (rc) return rc;
+      CU(h, h->ks->pivot(h->X, N, k + 1, h->D, h->R, h->status, h->zero_k, h->p, T));
+      h->launches += 1;
+      if (k + 1 < N - 1) {
+        CU(h, h->ks->mult(h->X, N, k + 1, h->R, Zb[(k + 1) & 1], h->status, h->p, lastcol, T));
+        h->launches += 1;
+      }
+      CU(h, cudaEventRecord(h->ev_mult, T));
+      rc = timed_update(h, mpd::upd_rest(N, k, lastcol), Zk, nsm_rest, S);
+      if (rc) return rc;
+      CU(h, cudaEventRecord(h->ev_rest, S));
+    } else {
+      rc = timed_update(h, mpd::upd_step(N, k, lastcol), Zk, h->nsm, S);
+      if (rc) return rc;
+    }
+  }
+  CU(h, cudaEventRecord(h->ev_mult, T));  // S continues after all of T's work
+  CU(h, cudaStreamWaitEvent(S, h->ev_mult, 0));
+  return MPDET_OK;
+}
+
+// enqueue steps k (0-based) in [k0, k1)
+static int run_steps(mpdet_t h, int64_t k0, int64_t k1) {
+  if (k1 <= k0) return MPDET_OK;
+  int rc = h->lookahead ? run_steps_lookahead(h, k0, k1) : run_steps_serial(h, k0, k1);
+  if (rc) return rc;
   h->k_done = k1;
   return MPDET_OK;
 }
@@ -348,6 +464,14 @@ extern "C" int mpdet_tune(mpdet_t h, int param, int value) {
     case MPDET_TUNE_TC_MIN_ROWS:
       if (value < 0) return fail(h, MPDET_EINVAL, "tune: tc_min_rows %d", value);
       h->tc_min_rows = value;
+      return MPDET_OK;
+    case MPDET_TUNE_LOOKAHEAD:
+      if (value < 0 || value > 1) return fail(h, MPDET_EINVAL, "tune: lookahead %d", value);
+      h->lookahead = value;
+      return MPDET_OK;
+    case MPDET_TUNE_LOOKAHEAD_RESERVE:
+      if (value < 0 || value > 64) return fail(h, MPDET_EINVAL, "tune: lookahead reserve %d", value);
+      h->la_reserve = value;
       return MPDET_OK;
     default:
       return fail(h, MPDET_EINVAL, "tune: unknown parameter %d", param);
@@ -546,11 +670,8 @@ extern "C" int mpdet_logabsdet_grad(mpdet_t h, const double* A, int64_t ld, doub
                               cudaMemcpyDeviceToDevice, h->stream));
       CU(h, cudaMemcpy2DAsync(h->Z.e, 8, h->X.e + k, (size_t)N * 8, 8, (size_t)k, cudaMemcpyDeviceToDevice, h->stream));
       CU(h, cudaMemcpy2DAsync(h->Z.s, 1, h->X.s + k, (size_t)N, 1, (size_t)k, cudaMemcpyDeviceToDevice, h->stream));
-      if (use_tc(h, k))
-        CU(h, mpd::usolve_tc_p2048(h->S, N, k, h->Z, h->status, h->p, h->nsm, h->stream, h->engine == 1 ? 1 : 0));
-      else
-        CU(h, h->ks->usolve_update(h->S, N, k, h->Z, h->status, h->p, h->nsm, h->stream));
-      h->launches += 1;
+      const int rc = launch_update(h, h->S, mpd::upd_back(N, k), h->Z, h->nsm, h->stream);
+      if (rc) return rc;
     }
   }
   double* g = grad;

@@ -124,7 +124,7 @@ extern "C" int mpdet_factor_noalloc(int64_t N, int32_t p_bits, uint32_t flags, m
   for (int64_t k = 0; k < N && e == cudaSuccess; ++k) {
     e = ks->pivot(X, N, k, D, R, status, zero_k, p_bits, st);
     if (e == cudaSuccess && k < N - 1) e = ks->mult(X, N, k, R, Z, status, p_bits, lc, st);
-    if (e == cudaSuccess && k < N - 1) e = ks->update[1](X, N, k, Z, status, p_bits, lc, nsm, st);
+    if (e == cudaSuccess && k < N - 1) e = ks->update[1](X, mpd::upd_step(N, k, lc), Z, status, p_bits, nsm, st);
   }
   if (e == cudaSuccess && want_lastcol) {
     mpd::MpArr C{lastcol.sign, lastcol.exp, lastcol.limbs};

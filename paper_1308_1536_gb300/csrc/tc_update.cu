@@ -89,7 +89,7 @@ __device__ __forceinline__ uint16_t dbf(uint32_t d) { return (uint16_t)(__float_
 
 __global__ void __launch_bounds__(128, 1) k_update_tc(MpArr X, UpdArgs a, MpArr Z, int* status, int p, int col_chunk) {
   extern __shared__ __align__(1024) unsigned char sm[];
-  if (status_set(status)) return;
+  if (upd_stopped(status, a)) return;
   const int tid = threadIdx.x, warp = tid >> 5;
   unsigned char* sA = sm + OFF_A;
   unsigned char* sH = sm + OFF_H;
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(128, 1) k_update_tc(MpArr X, UpdArgs a, MpArr 
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + OFF_BAR);  // 4 tile barriers
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + OFF_BAR + 64);
   const int64_t N = a.N;
-  const int64_t ncols = a.cmode == 0 ? N - a.kcol - 1 : (a.cmode == 1 ? N - 1 : N);
+  const int64_t ncols = a.ncols;
   const int64_t i0 = a.row0 + (int64_t)blockIdx.y * M;
   const int64_t rend = a.row0 + a.nrows;
   const int64_t c0 = (int64_t)blockIdx.x * col_chunk;
@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(128, 1) k_update_tc(MpArr X, UpdArgs a, MpArr 
   bool ok = true;
 
   for (int64_t c = c0; c < c1 && ok; ++c) {
-    const int64_t j = a.cmode == 0 ? a.kcol + 1 + c : (a.cmode == 1 ? (c < a.kcol ? c : c + 1) : c);
+    const int64_t j = upd_col(a, c);
     const int64_t kj = a.brow * N + j;
     const int64_t be = X.e[kj];
     const int8_t bs = X.s[kj];
@@ -387,7 +387,7 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
   using C = pipe::Cfg<KD>;
   constexpr int NL = C::NL, TILES = C::TILES, NCORE = C::NCORE, RSTR = C::RSTR, GS = C::G, SWS = C::SW;
   extern __shared__ __align__(1024) unsigned char sm[];
-  if (status_set(status)) return;
+  if (upd_stopped(status, a)) return;
   const int tid = threadIdx.x, warp = tid >> 5;
   unsigned char* sA = sm + C::OFF_A;
   uint32_t* sBl = reinterpret_cast<uint32_t*>(sm + C::OFF_B);
@@ -402,7 +402,7 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
   const uint32_t b_full = su32(&bars[0]), b_empty = su32(&bars[4]), b_hfree = su32(&bars[8]);
   const uint32_t b_tfull = su32(&bars[10]), b_tfree = su32(&bars[12]);
   const int64_t N = a.N;
-  const int64_t ncols = a.cmode == 0 ? N - a.kcol - 1 : (a.cmode == 1 ? N - 1 : N);
+  const int64_t ncols = a.ncols;
   const int64_t i0 = a.row0 + (int64_t)blockIdx.y * M;
   const int64_t rend = a.row0 + a.nrows;
   const int64_t c0 = (int64_t)blockIdx.x * col_chunk;
@@ -410,7 +410,7 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
   const int nc = (int)(c1 > c0 ? c1 - c0 : 0);
   auto colj = [&](int c) -> int64_t {
     const int64_t cc = c0 + c;
-    return a.cmode == 0 ? a.kcol + 1 + cc : (a.cmode == 1 ? (cc < a.kcol ? cc : cc + 1) : cc);
+    return upd_col(a, cc);
   };
 
   // ---- set-up: A (rows by warps 0-3), barriers, tensor memory ------------
@@ -662,9 +662,9 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
 }  // namespace tc
 
 // Launch: 128-row blocks x column chunks sized to fill the SMs once.
-cudaError_t update_tc_p2048(MpArr X, UpdArgs a, MpArr Z, int* status, int p, int nsm, cudaStream_t st,
-                            int pipelined) {
-  const int64_t ncols = a.cmode == 0 ? a.N - a.kcol - 1 : (a.cmode == 1 ? a.N - 1 : a.N);
+cudaError_t update_tc(MpArr X, const UpdArgs& a, MpArr Z, int* status, int p, int nsm, cudaStream_t st,
+                      int pipelined) {
+  const int64_t ncols = a.ncols;
   if (a.nrows <= 0 || ncols <= 0) return cudaSuccess;
   const int64_t by = (a.nrows + tc::M - 1) / tc::M;
   int64_t bx = nsm / by;  // one wave: at most one block per SM
@@ -683,12 +683,15 @@ cudaError_t update_tc_p2048(MpArr X, UpdArgs a, MpArr Z, int* status, int p, int
         cudaFuncSetAttribute(tc::k_update_tcp<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::pipe::Cfg<128>::SMEM);
         tc::k_update_tcp<128><<<grid, tc::pipe::NTH, tc::pipe::Cfg<128>::SMEM, st>>>(X, a, Z, status, p, (int)chunk);
         break;
-      default:
+      case 2048:
         cudaFuncSetAttribute(tc::k_update_tcp<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::pipe::Cfg<256>::SMEM);
         tc::k_update_tcp<256><<<grid, tc::pipe::NTH, tc::pipe::Cfg<256>::SMEM, st>>>(X, a, Z, status, p, (int)chunk);
         break;
+      default:
+        return cudaErrorInvalidValue;
     }
   } else {
+    if (p != 2048) return cudaErrorInvalidValue;
     cudaFuncSetAttribute(tc::k_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM);
     tc::k_update_tc<<<grid, 128, tc::SMEM, st>>>(X, a, Z, status, p, (int)chunk);
   }
@@ -698,19 +701,5 @@ cudaError_t update_tc_p2048(MpArr X, UpdArgs a, MpArr Z, int* status, int p, int
 // True when the tensor engine covers p (the warp-specialised kernel: p = 512,
 // 1024, 2048; the one-phase-at-a-time kernel: p = 2048).
 bool tc_supports(int p, int pipelined) { return pipelined ? (p == 512 || p == 1024 || p == 2048) : p == 2048; }
-
-// Schur update of step k (lastcol: every column but k) on the tensor cores.
-cudaError_t update_tc_p2048_step(MpArr X, int64_t N, int64_t k, MpArr Z, int* status, int p, int lastcol, int nsm,
-                                 cudaStream_t st, int pipelined) {
-  UpdArgs a{N, k, k + 1, N - k - 1, k, lastcol ? 1 : 0};
-  return update_tc_p2048(X, a, Z, status, p, nsm, st, pipelined);
-}
-
-// Back-substitution update of the adjoint (rows [0, k), every column).
-cudaError_t usolve_tc_p2048(MpArr S, int64_t N, int64_t k, MpArr Z, int* status, int p, int nsm, cudaStream_t st,
-                            int pipelined) {
-  UpdArgs a{N, k, 0, k, 0, 2};
-  return update_tc_p2048(S, a, Z, status, p, nsm, st, pipelined);
-}
 
 }  // namespace mpd
