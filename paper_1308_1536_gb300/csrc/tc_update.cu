@@ -308,6 +308,183 @@ __global__ void __launch_bounds__(128, 1) k_update_tc(MpArr X, UpdArgs a, MpArr 
 
 
 // ---------------------------------------------------------------------------
+// x_ij = RN(x_ij - t) for one row by one thread, the same rounding as
+// sub_round: the larger magnitude A sits in a frame of NL + 2 limbs above two
+// guard limbs, the smaller B is aligned into it (bits below the frame jammed
+// into a sticky bit), then normalisation and round to nearest even.  No data
+// crosses lanes.  Register path when the exponent gap is below 64 and at
+// most 32 bits cancel (the usual case); otherwise the frame goes through
+// scr (NL + 3 words of shared memory, this row's own).
+//   xm, tm: x's and t's mantissas (shared memory, 16-byte aligned)
+//   out:    the row's destination mantissa (global, 16-byte aligned)
+// Returns the result's sign and exponent in rs, re.
+// ---------------------------------------------------------------------------
+template <int NL>
+__device__ __forceinline__ void copy_row(const uint32_t* src, uint32_t* out) {
+#pragma unroll
+  for (int q = 0; q < NL; q += 4) *reinterpret_cast<uint4*>(out + q) = *reinterpret_cast<const uint4*>(src + q);
+}
+
+template <int NL>
+__device__ __forceinline__ void sub_row(const uint32_t* xm, int8_t xs, int64_t xe, const uint32_t* tm, int8_t ts,
+                                        int64_t te, uint32_t* out, uint32_t* scr, int8_t& rs, int64_t& re) {
+  constexpr int p = 32 * NL;
+  if (te == ZEXP) {  // x - 0
+    copy_row<NL>(xm, out);
+    rs = xs;
+    re = xe;
+    return;
+  }
+  const int8_t tsn = (int8_t)(ts ^ 1);
+  if (xe == ZEXP) {  // 0 - t
+    copy_row<NL>(tm, out);
+    rs = tsn;
+    re = te;
+    return;
+  }
+  int cmp = (xe != te) ? (xe > te ? 1 : -1) : 0;
+  if (cmp == 0) {
+    for (int i = NL - 1; i >= 0; --i) {
+      const uint32_t a = xm[i], b = tm[i];
+      if (a != b) {
+        cmp = a > b ? 1 : -1;
+        break;
+      }
+    }
+  }
+  const bool swap = cmp < 0;
+  const uint32_t* Am = swap ? tm : xm;
+  const uint32_t* Bm = swap ? xm : tm;
+  const int64_t eA = swap ? te : xe, eB = swap ? xe : te;
+  const int8_t sA = swap ? tsn : xs, sB = swap ? xs : tsn;
+  const bool eff_sub = (sA != sB);
+  const int64_t dd = eA - eB;
+  if (dd >= p + 2) {  // B below a quarter ulp of A
+    copy_row<NL>(Am, out);
+    rs = sA;
+    re = eA;
+    return;
+  }
+  const uint32_t inv = eff_sub ? 0xffffffffu : 0u;
+  const int d = (int)dd;
+  // frame F = A * 2^64 +- (B aligned)
+  uint32_t F[NL + 2];
+  uint32_t sx;
+  if (d < 64) {
+    const int q = d >> 5, r = d & 31;
+    uint32_t Bv[NL];
+#pragma unroll
+    for (int k = 0; k < NL; k += 4) {
+      const uint4 v = *reinterpret_cast<const uint4*>(Bm + k);
+      Bv[k] = v.x;
+      Bv[k + 1] = v.y;
+      Bv[k + 2] = v.z;
+      Bv[k + 3] = v.w;
+    }
+    uint32_t Y[NL + 2];
+#pragma unroll
+    for (int f = 0; f < NL + 2; ++f) {
+      // bits [32 (f - 2) + d, +32) of B
+      const uint32_t b0 = (f - 2 >= 0 && f - 2 < NL) ? Bv[f - 2 < 0 ? 0 : (f - 2 < NL ? f - 2 : 0)] : 0u;
+      const uint32_t b1 = (f - 1 >= 0 && f - 1 < NL) ? Bv[f - 1 < 0 ? 0 : (f - 1 < NL ? f - 1 : 0)] : 0u;
+      const uint32_t b2 = (f < NL) ? Bv[f < NL ? f : 0] : 0u;
+      Y[f] = q ? __funnelshift_r(b1, b2, r) : __funnelshift_r(b0, b1, r);
+    }
+    F[0] = add_cc(Y[0] ^ inv, eff_sub ? 1u : 0u);
+    F[1] = addc_cc(Y[1] ^ inv, 0u);
+#pragma unroll
+    for (int k = 0; k < NL; k += 4) {
+      const uint4 a = *reinterpret_cast<const uint4*>(Am + k);
+      F[k + 2] = addc_cc(a.x, Y[k + 2] ^ inv);
+      F[k + 3] = addc_cc(a.y, Y[k + 3] ^ inv);
+      F[k + 4] = addc_cc(a.z, Y[k + 4] ^ inv);
+      F[k + 5] = addc_cc(a.w, Y[k + 5] ^ inv);
+    }
+    sx = addc(0u, 0u);
+  } else {
+    // bits of B below the frame (index d - 64 of B) go into the sticky bit
+    const int q = (d - 64) >> 5, r = (d - 64) & 31;
+    bool lost = false;
+    for (int k = 0; k < q && k < NL; ++k) lost = lost || Bm[k] != 0u;
+    if (q < NL && r) lost = lost || (Bm[q] & ((1u << r) - 1u)) != 0u;
+    uint32_t Y[NL + 2];
+#pragma unroll
+    for (int f = 0; f < NL + 2; ++f) {
+      const int k = f + q;  // frame limb f holds bits [32 (f + q) + r, +32) of B
+      const uint32_t lo = (k < NL) ? Bm[k < NL ? k : 0] : 0u;
+      const uint32_t hi = (k + 1 < NL) ? Bm[k + 1 < NL ? k + 1 : 0] : 0u;
+      Y[f] = __funnelshift_r(lo, hi, r);
+    }
+    Y[0] |= lost ? 1u : 0u;
+    F[0] = add_cc(Y[0] ^ inv, eff_sub ? 1u : 0u);
+    F[1] = addc_cc(Y[1] ^ inv, 0u);
+#pragma unroll
+    for (int k = 0; k < NL; ++k) F[k + 2] = addc_cc(Am[k], Y[k + 2] ^ inv);
+    sx = addc(0u, 0u);
+  }
+  if (eff_sub) sx = 0u;  // the carry out of A*2^64 + ~Y + 1
+  // top bit of the frame value (usual case: in the top two limbs or sx)
+  int topbit = -1;
+  if (sx) topbit = 32 * (NL + 2);
+  else if (F[NL + 1]) topbit = 32 * (NL + 1) + 31 - __clz(F[NL + 1]);
+  else if (F[NL]) topbit = 32 * NL + 31 - __clz(F[NL]);
+  int sh = topbit - (p - 1);
+  uint32_t M[NL];
+  uint32_t rbit, st;
+  if (topbit >= 0 && sh >= 32) {
+    // sh in [32, 65]: output limb l = frame bits [32 l + sh, +32)
+    const int q2 = sh >> 5, r2 = sh & 31;
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+      const uint32_t f3 = (l + 3 < NL + 2) ? F[l + 3 < NL + 2 ? l + 3 : 0] : sx;
+      M[l] = (q2 == 1) ? __funnelshift_r(F[l + 1], F[l + 2], r2) : __funnelshift_r(F[l + 2], f3, r2);
+    }
+    const uint64_t g64 = ((uint64_t)F[1] << 32) | F[0];
+    const int rb = sh - 1;  // 31..64
+    rbit = (rb < 64) ? (uint32_t)((g64 >> rb) & 1ull) : (F[2] & 1u);
+    st = (rb < 64) ? (uint32_t)((g64 & ((1ull << rb) - 1ull)) != 0ull) : (uint32_t)(g64 != 0ull);
+  } else {
+    // more than 32 bits cancelled: the frame through shared memory
+#pragma unroll
+    for (int k = 0; k < NL + 2; ++k) scr[k] = F[k];
+    scr[NL + 2] = sx;
+    topbit = -1;
+    for (int k = NL + 2; k >= 0 && topbit < 0; --k)
+      if (scr[k]) topbit = 32 * k + 31 - __clz(scr[k]);
+    if (topbit < 0) {  // exact cancellation
+#pragma unroll
+      for (int q = 0; q < NL; q += 4) *reinterpret_cast<uint4*>(out + q) = make_uint4(0u, 0u, 0u, 0u);
+      rs = 0;
+      re = ZEXP;
+      return;
+    }
+    sh = topbit - (p - 1);
+#pragma unroll
+    for (int l = 0; l < NL; ++l) M[l] = funnel(scr, 32 * l + sh, NL + 3);
+    rbit = (sh >= 1) ? (funnel(scr, sh - 1, NL + 3) & 1u) : 0u;
+    bool stl = false;
+    if (sh >= 2) {
+      const int cut = sh - 1;  // bits [0, cut)
+      for (int k = 0; 32 * k < cut; ++k) {
+        const uint32_t m = (cut >= 32 * k + 32) ? 0xffffffffu : ((1u << (cut - 32 * k)) - 1u);
+        stl = stl || (scr[k] & m) != 0u;
+      }
+    }
+    st = stl ? 1u : 0u;
+  }
+  const uint32_t inc = rbit & (st | (M[0] & 1u));
+  M[0] = add_cc(M[0], inc);
+#pragma unroll
+  for (int l = 1; l < NL; ++l) M[l] = addc_cc(M[l], 0u);
+  const uint32_t ovf = addc(0u, 0u);
+  if (ovf) M[NL - 1] = 0x80000000u;  // every limb wrapped to 0
+#pragma unroll
+  for (int q = 0; q < NL; q += 4) *reinterpret_cast<uint4*>(out + q) = make_uint4(M[q], M[q + 1], M[q + 2], M[q + 3]);
+  rs = sA;
+  re = (int64_t)topbit + 1 + eA - p - 64 + (int64_t)ovf;
+}
+
+// ---------------------------------------------------------------------------
 // Pipelined version: 12 warps in three roles so that the tensor core, the
 // epilogue and the subtraction of consecutive columns overlap.
 //   warps 0-3  (E): one thread per row; drain the four tensor-memory tiles of
@@ -334,11 +511,7 @@ struct Cfg {
   static constexpr int TCOLS = TILES * 128;         // allocated columns (a power of two >= 32)
   static constexpr int NCORE = 16 * TILES + KD / 8 - 1;  // Hankel cores
   static constexpr int HBYTES = (NCORE * 128 + 1023) / 1024 * 1024;
-  static constexpr int G = NL / 16;                 // lanes per number in the subtraction (W = 16)
-  static constexpr int NGRP = 128 / G;              // subtraction groups
-  static constexpr int RPG = M / NGRP;              // rows per group
-  static constexpr int RSTR = NL + 4;               // words per staged row
-  static constexpr int SW = Scratch<16, G>::words;
+  static constexpr int RSTR = NL + 4;               // words per staged row (uint4 rows hit distinct bank quads)
   static constexpr int OFF_A = 0;                           // M x KD bf16
   static constexpr int OFF_H = OFF_A + M * KD * 2;          // 2 Hankel buffers
   static constexpr int OFF_B = OFF_H + 2 * HBYTES;          // 2 x NL limbs of b_j
@@ -346,11 +519,12 @@ struct Cfg {
   static constexpr int OFF_TE = OFF_T + 2 * M * RSTR * 4;   // 2 x M int64
   static constexpr int OFF_TS = OFF_TE + 2 * M * 8;         // 2 x M int8
   static constexpr int OFF_FL = OFF_TS + 2 * M;             // M multiplier flags
-  static constexpr int OFF_SCR = OFF_FL + M;                // NGRP groups x SW words
-  static constexpr int OFF_BAR = OFF_SCR + NGRP * SW * 4;   // barriers
+  static constexpr int OFF_X = (OFF_FL + M + 15) / 16 * 16;  // M x RSTR words: x_ij of the next column
+  static constexpr int OFF_BAR = OFF_X + M * RSTR * 4;      // barriers
   static constexpr int SMEM = OFF_BAR + 256;
-  static_assert(NL % 16 == 0 && G >= 1 && G <= 4, "tensor engine covers p = 512, 1024, 2048");
-  static_assert(OFF_SCR % 16 == 0 && OFF_BAR % 8 == 0 && OFF_T % 16 == 0, "alignment");
+  static_assert(NL % 16 == 0 && NL <= 64, "tensor engine covers p = 512, 1024, 2048");
+  static_assert(OFF_X % 16 == 0 && OFF_BAR % 8 == 0 && OFF_T % 16 == 0, "alignment");
+  static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
 __device__ __forceinline__ void arrive(uint32_t bar) {
@@ -385,7 +559,7 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
   using pipe::arrive;
   using pipe::wait_bar;
   using C = pipe::Cfg<KD>;
-  constexpr int NL = C::NL, TILES = C::TILES, NCORE = C::NCORE, RSTR = C::RSTR, GS = C::G, SWS = C::SW;
+  constexpr int NL = C::NL, TILES = C::TILES, NCORE = C::NCORE, RSTR = C::RSTR;
   extern __shared__ __align__(1024) unsigned char sm[];
   if (upd_stopped(status, a)) return;
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -599,14 +773,29 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
       arrive(b_tfull + 8 * tb);
     }
   } else {
-    // ================= S: subtraction by lane groups ======================
-    Grp<GS> gp;
-    const int st_ = tid - 128;
-    const int gid = st_ / GS;  // C::NGRP groups
-    uint32_t* scr = reinterpret_cast<uint32_t*>(sm + C::OFF_SCR) + gid * SWS;
+    // ================= S: one thread per row subtracts ====================
+    const int r = tid - 128;
+    const int64_t i = i0 + r;
+    const bool active = i < rend;
+    const int64_t irow = active ? i : i0;
+    uint32_t* xrow = reinterpret_cast<uint32_t*>(sm + C::OFF_X) + r * RSTR;
+    // x_ij of the next column: mantissa by cp.async into this row's buffer,
+    // sign and exponent into registers
+    int8_t xs_n = 0;
+    int64_t xe_n = ZEXP;
+    if (nc > 0) {
+      const int64_t ij = irow * N + colj(0);
+#pragma unroll
+      for (int q = 0; q < NL; q += 4) cp16(su32(xrow + q), X.m + ij * NL + q);
+      asm volatile("cp.async.commit_group;" ::: "memory");
+      xs_n = X.s[ij];
+      xe_n = X.e[ij];
+    }
     for (int c = 0; c < nc; ++c) {
       const int tb = c & 1;
-      const int64_t j = colj(c);
+      const int64_t ij = irow * N + colj(c);
+      const int8_t xs = xs_n;
+      const int64_t xe = xe_n;
       bool okc = wait_bar(b_tfull + 8 * tb, (c >> 1) & 1);
       okc = __all_sync(0xffffffffu, okc) && !*eflag;
       okc = __all_sync(0xffffffffu, okc);
@@ -614,43 +803,27 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
         *eflag = 1;
         break;
       }
-      const uint32_t* Tb = sT + tb * (M * RSTR);
-      // software-pipelined loads of x_ij for the group's four rows
-      uint32_t Xn[W];
-      int64_t ijn = ((i0 + gid < rend) ? i0 + gid : i0) * N + j;
-      load_slice<W>(X.m + ijn * NL + gp.g * W, Xn);
-      int8_t xsn = X.s[ijn];
-      int64_t xen = X.e[ijn];
-#pragma unroll 1
-      for (int rr = 0; rr < C::RPG; ++rr) {
-        const int rrow = gid + C::NGRP * rr;
-        const int64_t i = i0 + rrow;
-        const bool active = i < rend;
-        const int64_t ij = ijn;
-        uint32_t Xv[W], T[W];
-#pragma unroll
-        for (int q = 0; q < W; ++q) Xv[q] = Xn[q];
-        int8_t xs = xsn;
-        int64_t xe = xen;
-        if (rr + 1 < C::RPG) {
-          const int64_t in2 = i0 + gid + C::NGRP * (rr + 1);
-          ijn = (in2 < rend ? in2 : i0) * N + j;
-          load_slice<W>(X.m + ijn * NL + gp.g * W, Xn);
-          xsn = X.s[ijn];
-          xen = X.e[ijn];
-        }
-        load_slice<W>(Tb + rrow * RSTR + gp.g * W, T);
-        sub_round<W, GS>(gp, p, xs, xe, Xv, sTs[tb * M + rrow], sTe[tb * M + rrow], T, scr);
-        if (active) {
-          store_slice<W>(X.m + ij * NL + gp.g * W, Xv);
-          if (gp.g == 0) {
-            X.s[ij] = xs;
-            X.e[ij] = xe;
-          }
-        }
-      }
+      asm volatile("cp.async.wait_all;" ::: "memory");
+      int8_t rs = 0;
+      int64_t re = ZEXP;
+      if (active)
+        sub_row<NL>(xrow, xs, xe, sT + tb * (M * RSTR) + r * RSTR, sTs[tb * M + r], sTe[tb * M + r], X.m + ij * NL,
+                    xrow, rs, re);
       arrive(b_tfree + 8 * tb);
+      if (active) {
+        X.s[ij] = rs;
+        X.e[ij] = re;
+      }
+      if (c + 1 < nc) {
+        const int64_t ij2 = irow * N + colj(c + 1);
+#pragma unroll
+        for (int q = 0; q < NL; q += 4) cp16(su32(xrow + q), X.m + ij2 * NL + q);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        xs_n = X.s[ij2];
+        xe_n = X.e[ij2];
+      }
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
   }
   if (tid == 0 && *eflag) atomicExch(status, 5);  // MPDET_ETIMEOUT
   asm volatile("tcgen05.fence::before_thread_sync;");

@@ -76,3 +76,28 @@ def test_engine_switch_by_rows(mpdet, tc_min_rows):
     ref = run(mpdet, N, p, "int", data, 0)
     got = run(mpdet, N, p, "int", data, 1, tc_min_rows=tc_min_rows)
     assert got[:2] == ref[:2] and X.same(got[2], ref[2]) and X.same(got[3], ref[3])
+
+
+@pytest.mark.parametrize("p", [512, 1024, 2048])
+def test_tensor_engine_rare_subtraction_paths(mpdet, oracle_lib, p):
+    """Inputs that drive the subtraction's rare paths in the tensor engine's
+    row subtraction: entries spread over 2^-300..2^300 (exponent gaps of 64
+    and more between x_ij and the product), rank-deficient integer matrices
+    (exact cancellation to zero), and near-duplicate rows (cancellation of
+    more than 32 bits).  Bit-identical to the IMAD engine and the oracle."""
+    g = W.rng(500 + p)
+    N = 140
+    spread = g.standard_normal((N, N)) * np.exp2(g.integers(-300, 300, (N, N)).astype(np.float64))
+    B = g.integers(-5, 6, (N, 3))
+    lowrank = (B @ g.integers(-5, 6, (3, N))).astype(np.int64)
+    near = g.standard_normal((N, N))
+    near[1::2] = near[0::2] + g.standard_normal((N // 2, N)) * 2.0 ** -40
+    for kind, data in (("f64", spread), ("int", lowrank), ("f64", near)):
+        a = run(mpdet, N, p, kind, data, 1)
+        b = run(mpdet, N, p, kind, data, 0)
+        assert a[:2] == b[:2]
+        assert X.same(a[2], b[2]) and X.same(a[3], b[3])
+    A = oracle_lib.from_f64(near.reshape(-1), p)
+    st, zk, D, OX = oracle_lib.ge(A, N, p, lastcol=True, nthreads=16)
+    a = run(mpdet, N, p, "f64", near, 1)
+    assert a[:2] == (st, zk) and X.same(a[2], D) and X.same(a[3], OX)
