@@ -72,6 +72,38 @@ __device__ __forceinline__ bool bar_wait(uint32_t addr, uint32_t phase) {
   return done != 0;
 }
 
+// 32 columns of this warp's 32 lanes, without waiting: the registers are
+// valid after tmem_wait(v).
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+        "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+}
+// Wait for this thread's tensor-memory loads; v is named so that no use of
+// it moves above the wait.
+__device__ __forceinline__ void tmem_wait(uint32_t (&v)[32]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]),
+                 "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15]),
+                 "+r"(v[16]), "+r"(v[17]), "+r"(v[18]), "+r"(v[19]), "+r"(v[20]), "+r"(v[21]), "+r"(v[22]),
+                 "+r"(v[23]), "+r"(v[24]), "+r"(v[25]), "+r"(v[26]), "+r"(v[27]), "+r"(v[28]), "+r"(v[29]),
+                 "+r"(v[30]), "+r"(v[31]));
+}
+
+// 8 columns of this warp's 32 lanes, waited for.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]));
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
@@ -319,6 +351,45 @@ __global__ void __launch_bounds__(128, 1) k_update_tc(MpArr X, UpdArgs a, MpArr 
 //   out:    the row's destination mantissa (global, 16-byte aligned)
 // Returns the result's sign and exponent in rs, re.
 // ---------------------------------------------------------------------------
+// Round a staged exact product to p = 32 NL bits in place: T[0..NL) its
+// upper NL limbs, T[NL] limb NL - 1, T[NL + 1] the OR of the limbs below.  The
+// product of two normalised mantissas has 2p or 2p - 1 bits; returns the
+// exponent adjustment (-1, 0 or +1) as mul_round does.
+template <int NL>
+__device__ __forceinline__ int round_product(uint32_t* T) {
+  uint32_t up[NL];
+#pragma unroll
+  for (int q = 0; q < NL; q += 4) {
+    const uint4 v = *reinterpret_cast<const uint4*>(T + q);
+    up[q] = v.x;
+    up[q + 1] = v.y;
+    up[q + 2] = v.z;
+    up[q + 3] = v.w;
+  }
+  const uint32_t l63 = T[NL], sticky = T[NL + 1];
+  const uint32_t top = up[NL - 1] >> 31;
+  uint32_t rbit, st;
+  if (top) {
+    rbit = l63 >> 31;
+    st = (l63 & 0x7fffffffu) | sticky;
+  } else {
+#pragma unroll
+    for (int q = NL - 1; q > 0; --q) up[q] = (up[q] << 1) | (up[q - 1] >> 31);
+    up[0] = (up[0] << 1) | (l63 >> 31);
+    rbit = (l63 >> 30) & 1u;
+    st = (l63 & 0x3fffffffu) | sticky;
+  }
+  const uint32_t inc = rbit & ((st != 0u) | (up[0] & 1u));
+  up[0] = add_cc(up[0], inc);
+#pragma unroll
+  for (int q = 1; q < NL; ++q) up[q] = addc_cc(up[q], 0u);
+  const uint32_t ovf = addc(0u, 0u);
+  if (ovf) up[NL - 1] = 0x80000000u;
+#pragma unroll
+  for (int q = 0; q < NL; q += 4) *reinterpret_cast<uint4*>(T + q) = make_uint4(up[q], up[q + 1], up[q + 2], up[q + 3]);
+  return (top ? 0 : -1) + (int)ovf;
+}
+
 template <int NL>
 __device__ __forceinline__ void copy_row(const uint32_t* src, uint32_t* out) {
 #pragma unroll
@@ -326,13 +397,17 @@ __device__ __forceinline__ void copy_row(const uint32_t* src, uint32_t* out) {
 }
 
 template <int NL>
-__device__ __forceinline__ void sub_row(const uint32_t* xm, int8_t xs, int64_t xe, const uint32_t* tm, int8_t ts,
-                                        int64_t te, uint32_t* out, uint32_t* scr, int8_t& rs, int64_t& re) {
+__device__ __noinline__ void sub_row_general(const uint32_t* xm, int8_t xs, int64_t xe, const uint32_t* tm, int8_t ts,
+                                             int64_t te, uint32_t* out, uint32_t* scr, int8_t* rs_, int64_t* re_) {
+  int8_t rs;
+  int64_t re;
   constexpr int p = 32 * NL;
   if (te == ZEXP) {  // x - 0
     copy_row<NL>(xm, out);
     rs = xs;
     re = xe;
+    *rs_ = rs;
+    *re_ = re;
     return;
   }
   const int8_t tsn = (int8_t)(ts ^ 1);
@@ -340,6 +415,8 @@ __device__ __forceinline__ void sub_row(const uint32_t* xm, int8_t xs, int64_t x
     copy_row<NL>(tm, out);
     rs = tsn;
     re = te;
+    *rs_ = rs;
+    *re_ = re;
     return;
   }
   int cmp = (xe != te) ? (xe > te ? 1 : -1) : 0;
@@ -363,6 +440,8 @@ __device__ __forceinline__ void sub_row(const uint32_t* xm, int8_t xs, int64_t x
     copy_row<NL>(Am, out);
     rs = sA;
     re = eA;
+    *rs_ = rs;
+    *re_ = re;
     return;
   }
   const uint32_t inv = eff_sub ? 0xffffffffu : 0u;
@@ -456,7 +535,9 @@ __device__ __forceinline__ void sub_row(const uint32_t* xm, int8_t xs, int64_t x
       for (int q = 0; q < NL; q += 4) *reinterpret_cast<uint4*>(out + q) = make_uint4(0u, 0u, 0u, 0u);
       rs = 0;
       re = ZEXP;
-      return;
+      *rs_ = rs;
+    *re_ = re;
+    return;
     }
     sh = topbit - (p - 1);
 #pragma unroll
@@ -480,6 +561,112 @@ __device__ __forceinline__ void sub_row(const uint32_t* xm, int8_t xs, int64_t x
   if (ovf) M[NL - 1] = 0x80000000u;  // every limb wrapped to 0
 #pragma unroll
   for (int q = 0; q < NL; q += 4) *reinterpret_cast<uint4*>(out + q) = make_uint4(M[q], M[q + 1], M[q + 2], M[q + 3]);
+  *rs_ = sA;
+  *re_ = (int64_t)topbit + 1 + eA - p - 64 + (int64_t)ovf;
+}
+
+// The usual case inline (exponent gap below 64, at most 32 bits cancelled,
+// frame in registers); everything else goes to sub_row_general, which
+// recomputes from the unchanged operands.
+template <int NL>
+__device__ __forceinline__ void sub_row(const uint32_t* xm, int8_t xs, int64_t xe, const uint32_t* tm, int8_t ts,
+                                        int64_t te, uint32_t* out, uint32_t* scr, int8_t& rs, int64_t& re) {
+  constexpr int p = 32 * NL;
+  const int8_t tsn = (int8_t)(ts ^ 1);
+  const bool tzero = te == ZEXP, xzero = xe == ZEXP;
+  int cmp = (xe != te) ? (xe > te ? 1 : -1) : 0;
+  if (!tzero && !xzero && cmp == 0) {
+    for (int i = NL - 1; i >= 0; --i) {
+      const uint32_t a = xm[i], b = tm[i];
+      if (a != b) {
+        cmp = a > b ? 1 : -1;
+        break;
+      }
+    }
+  }
+  const bool swap = cmp < 0;
+  const int64_t dd = swap ? te - xe : xe - te;
+  if (tzero || xzero || dd >= p + 2) {  // x - 0, 0 - t, or the smaller below a quarter ulp of the larger
+    const bool keep_x = tzero || (!xzero && !swap);
+    copy_row<NL>(keep_x ? xm : tm, out);
+    rs = keep_x ? xs : tsn;
+    re = keep_x ? xe : te;
+    return;
+  }
+  if (dd >= 64) {
+    sub_row_general<NL>(xm, xs, xe, tm, ts, te, out, scr, &rs, &re);
+    return;
+  }
+  const uint32_t* Am = swap ? tm : xm;
+  const uint32_t* Bm = swap ? xm : tm;
+  const int64_t eA = swap ? te : xe;
+  const int8_t sA = swap ? tsn : xs, sB = swap ? xs : tsn;
+  const bool eff_sub = (sA != sB);
+  const uint32_t inv = eff_sub ? 0xffffffffu : 0u;
+  const int d = (int)dd;
+  const int q = d >> 5, r = d & 31;
+  uint32_t F[NL + 2];
+  {
+    uint32_t Bv[NL];
+#pragma unroll
+    for (int k = 0; k < NL; k += 4) {
+      const uint4 v = *reinterpret_cast<const uint4*>(Bm + k);
+      Bv[k] = v.x;
+      Bv[k + 1] = v.y;
+      Bv[k + 2] = v.z;
+      Bv[k + 3] = v.w;
+    }
+    uint32_t Y[NL + 2];
+#pragma unroll
+    for (int f = 0; f < NL + 2; ++f) {
+      // bits [32 (f - 2) + d, +32) of B
+      const uint32_t b0 = (f - 2 >= 0 && f - 2 < NL) ? Bv[f - 2 < 0 ? 0 : (f - 2 < NL ? f - 2 : 0)] : 0u;
+      const uint32_t b1 = (f - 1 >= 0 && f - 1 < NL) ? Bv[f - 1 < 0 ? 0 : (f - 1 < NL ? f - 1 : 0)] : 0u;
+      const uint32_t b2 = (f < NL) ? Bv[f < NL ? f : 0] : 0u;
+      Y[f] = q ? __funnelshift_r(b1, b2, r) : __funnelshift_r(b0, b1, r);
+    }
+    F[0] = add_cc(Y[0] ^ inv, eff_sub ? 1u : 0u);
+    F[1] = addc_cc(Y[1] ^ inv, 0u);
+#pragma unroll
+    for (int k = 0; k < NL; k += 4) {
+      const uint4 a = *reinterpret_cast<const uint4*>(Am + k);
+      F[k + 2] = addc_cc(a.x, Y[k + 2] ^ inv);
+      F[k + 3] = addc_cc(a.y, Y[k + 3] ^ inv);
+      F[k + 4] = addc_cc(a.z, Y[k + 4] ^ inv);
+      F[k + 5] = addc_cc(a.w, Y[k + 5] ^ inv);
+    }
+  }
+  uint32_t sx = addc(0u, 0u);
+  if (eff_sub) sx = 0u;  // the carry out of A*2^64 + ~Y + 1
+  int topbit = -1;
+  if (sx) topbit = 32 * (NL + 2);
+  else if (F[NL + 1]) topbit = 32 * (NL + 1) + 31 - __clz(F[NL + 1]);
+  else if (F[NL]) topbit = 32 * NL + 31 - __clz(F[NL]);
+  const int sh = topbit - (p - 1);
+  if (topbit < 0 || sh < 32) {  // more than 32 bits cancelled
+    sub_row_general<NL>(xm, xs, xe, tm, ts, te, out, scr, &rs, &re);
+    return;
+  }
+  // sh in [32, 65]: output limb l = frame bits [32 l + sh, +32)
+  const int q2 = sh >> 5, r2 = sh & 31;
+  uint32_t M[NL];
+#pragma unroll
+  for (int l = 0; l < NL; ++l) {
+    const uint32_t f3 = (l + 3 < NL + 2) ? F[l + 3 < NL + 2 ? l + 3 : 0] : sx;
+    M[l] = (q2 == 1) ? __funnelshift_r(F[l + 1], F[l + 2], r2) : __funnelshift_r(F[l + 2], f3, r2);
+  }
+  const uint64_t g64 = ((uint64_t)F[1] << 32) | F[0];
+  const int rb = sh - 1;  // 31..64
+  const uint32_t rbit = (rb < 64) ? (uint32_t)((g64 >> rb) & 1ull) : (F[2] & 1u);
+  const uint32_t st = (rb < 64) ? (uint32_t)((g64 & ((1ull << rb) - 1ull)) != 0ull) : (uint32_t)(g64 != 0ull);
+  const uint32_t inc = rbit & (st | (M[0] & 1u));
+  M[0] = add_cc(M[0], inc);
+#pragma unroll
+  for (int l = 1; l < NL; ++l) M[l] = addc_cc(M[l], 0u);
+  const uint32_t ovf = addc(0u, 0u);
+  if (ovf) M[NL - 1] = 0x80000000u;  // every limb wrapped to 0
+#pragma unroll
+  for (int k = 0; k < NL; k += 4) *reinterpret_cast<uint4*>(out + k) = make_uint4(M[k], M[k + 1], M[k + 2], M[k + 3]);
   rs = sA;
   re = (int64_t)topbit + 1 + eA - p - 64 + (int64_t)ovf;
 }
@@ -502,6 +689,28 @@ namespace pipe {
 constexpr int NTH = 384;
 constexpr int LIMIT = 1 << 22;
 
+// Balanced digits.  The warp-specialised kernel writes both mantissas in
+// digits e in [-128, 127] (e_s = d_s + c_s - 256 c_{s+1}, c_{s+1} = 1 when
+// d_s + c_s >= 128); a normalised mantissa m then equals sum_s e_s 256^s +
+// 256^KD.  With m' = m - 2^p for the multiplier z and b~ = b's balanced
+// digits followed by the carry digit 1 at position KD (the value b itself),
+//     z * b = z' * b~ + 2^p * b,
+// the first term a digit convolution of KD + 1 positions per output, the
+// second added to the upper limbs in the carry chain.  Every column sum lies
+// in [-4161536, 4194304]: at most 256 products in [-16256, 16384], or 255 of
+// them and one with the carry digit when that digit is in the window.  Adding
+// kMagic puts it in [2^23, 2^24), where the fp32 spacing is 1, so the sum
+// plus kMagic - 2^23 (kOff) is the low 23 bits of the fp32 result: one FADD
+// instead of a conversion on the XU pipe.  Four consecutive outputs form a
+// limb, less kOff * 0x01010101 (kC).
+constexpr float kMagic = 12566528.0f;  // 2^23 + kOff
+constexpr uint32_t kOff = 4177920u;
+constexpr int64_t kC = 70368744161280ll;  // kOff * 0x01010101
+static_assert((int64_t)kOff * 0x01010101ll == kC, "digit offset per limb");
+
+// bf16 bits of a small integer (|e| <= 256: exact)
+__device__ __forceinline__ uint32_t dbfs(int e) { return __float_as_uint((float)e) >> 16; }
+
 // Geometry for mantissas of KD 8-bit digits (NL = KD/4 limbs; p = 8 KD).
 template <int KD_>
 struct Cfg {
@@ -512,6 +721,16 @@ struct Cfg {
   static constexpr int NCORE = 16 * TILES + KD / 8 - 1;  // Hankel cores
   static constexpr int HBYTES = (NCORE * 128 + 1023) / 1024 * 1024;
   static constexpr int RSTR = NL + 4;               // words per staged row (uint4 rows hit distinct bank quads)
+  // Output tile t (positions [128 t, 128 t + 128)) receives products only
+  // from reversed K positions k' in [KD - 128 (t + 1), 2 KD - 1 - 128 t]
+  // (b~ has digits 0..KD): the K steps outside are all-zero Hankel corners and
+  // are not issued.  Neighbouring tiles with the same K range form one
+  // M = 128, N = 256 MMA (half the operand reads per product of two N = 128).
+  __host__ __device__ static constexpr int ks_lo(int t) { return (KD - 128 * (t + 1)) > 0 ? (KD - 128 * (t + 1)) / 16 : 0; }
+  __host__ __device__ static constexpr int ks_hi(int t) { return (2 * KD - 128 * t) < KD ? (2 * KD - 128 * t) / 16 : KD / 16; }
+  __host__ __device__ static constexpr bool merge(int t) {  // tile t and t + 1 in one MMA group
+    return t + 1 < TILES && ks_lo(t) == ks_lo(t + 1) && ks_hi(t) == ks_hi(t + 1);
+  }
   static constexpr int OFF_A = 0;                           // M x KD bf16
   static constexpr int OFF_H = OFF_A + M * KD * 2;          // 2 Hankel buffers
   static constexpr int OFF_B = OFF_H + 2 * HBYTES;          // 2 x NL limbs of b_j
@@ -520,28 +739,30 @@ struct Cfg {
   static constexpr int OFF_TS = OFF_TE + 2 * M * 8;         // 2 x M int8
   static constexpr int OFF_FL = OFF_TS + 2 * M;             // M multiplier flags
   static constexpr int OFF_X = (OFF_FL + M + 15) / 16 * 16;  // M x RSTR words: x_ij of the next column
-  static constexpr int OFF_BAR = OFF_X + M * RSTR * 4;      // barriers
+  static constexpr int OFF_EB = OFF_X + M * RSTR * 4;       // bf16 balanced digits of b, KD + 1 (+ pad)
+  static constexpr int OFF_BK = OFF_EB + (KD + 8) * 2;      // 3 x NL int64: b's limbs minus the digit offset
+  static constexpr int OFF_BAR = OFF_BK + 3 * NL * 8;       // barriers
   static constexpr int SMEM = OFF_BAR + 256;
   static_assert(NL % 16 == 0 && NL <= 64, "tensor engine covers p = 512, 1024, 2048");
-  static_assert(OFF_X % 16 == 0 && OFF_BAR % 8 == 0 && OFF_T % 16 == 0, "alignment");
+  static_assert(OFF_X % 16 == 0 && OFF_BK % 8 == 0 && OFF_BAR % 8 == 0 && OFF_T % 16 == 0, "alignment");
   static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
 __device__ __forceinline__ void arrive(uint32_t bar) {
   asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(bar));
 }
-// barrier 1 over the 128 producer threads, returning the OR of q over them
+// barrier 1 over the 96 Hankel builder threads, returning the OR of q over them
 __device__ __forceinline__ bool pbar_or(bool q) {
   uint32_t r;
   __syncwarp();
-  asm volatile("{\n .reg .pred a, b;\n setp.ne.u32 a, %1, 0;\n bar.red.or.pred b, 1, 128, a;\n selp.u32 %0, 1, 0, b;\n}"
+  asm volatile("{\n .reg .pred a, b;\n setp.ne.u32 a, %1, 0;\n bar.red.or.pred b, 1, 96, a;\n selp.u32 %0, 1, 0, b;\n}"
                : "=r"(r)
                : "r"((uint32_t)q));
   return r != 0;
 }
 __device__ __forceinline__ void pbar() {
   __syncwarp();
-  asm volatile("bar.sync 1, 128;");
+  asm volatile("bar.sync 1, 96;");
 }
 __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity) {
   uint32_t done = 0;
@@ -570,11 +791,15 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
   int8_t* sTs = reinterpret_cast<int8_t*>(sm + C::OFF_TS);
   int8_t* sFl = reinterpret_cast<int8_t*>(sm + C::OFF_FL);
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + C::OFF_BAR);
-  // bars: 0-3 full, 4-7 empty, 8-9 hfree, 10-11 tfull, 12-13 tfree; slot 14: tmem address; 15: error flag
+  // bars: 0-3 full, 4-7 empty, 8-9 hfree, 10-11 tfull, 12-13 tfree; slot 14: tmem address; 15: error
+  // flag; 16-18 bkrdy (B -> E: the per-limb constants of a column are in sBk); 19-20 hready (B -> I:
+  // a column's Hankel cores are built)
   uint32_t* tslot = reinterpret_cast<uint32_t*>(&bars[14]);
   volatile int* eflag = reinterpret_cast<volatile int*>(&bars[15]);
   const uint32_t b_full = su32(&bars[0]), b_empty = su32(&bars[4]), b_hfree = su32(&bars[8]);
-  const uint32_t b_tfull = su32(&bars[10]), b_tfree = su32(&bars[12]);
+  const uint32_t b_tfull = su32(&bars[10]), b_tfree = su32(&bars[12]), b_bkrdy = su32(&bars[16]), b_hready = su32(&bars[19]);
+  int64_t* const sBk = reinterpret_cast<int64_t*>(sm + C::OFF_BK);
+  uint16_t* const sEb = reinterpret_cast<uint16_t*>(sm + C::OFF_EB);
   const int64_t N = a.N;
   const int64_t ncols = a.ncols;
   const int64_t i0 = a.row0 + (int64_t)blockIdx.y * M;
@@ -593,13 +818,21 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
     const bool have = i < rend && Z.e[i < rend ? i : i0] != ZEXP;
     const uint32_t* zm = Z.m + (i < rend ? i : i0) * NL;
     unsigned char* rowbase = sA + (tid >> 3) * (KD * 16) + (tid & 7) * 16;
-    for (int c = 0; c < KD / 8; ++c) {
-      uint32_t hi = have ? zm[NL - 1 - 2 * c] : 0u, lo = have ? zm[NL - 2 - 2 * c] : 0u;
-      uint32_t w0 = dbf(hi >> 24) | ((uint32_t)dbf((hi >> 16) & 255) << 16);
-      uint32_t w1 = dbf((hi >> 8) & 255) | ((uint32_t)dbf(hi & 255) << 16);
-      uint32_t w2 = dbf(lo >> 24) | ((uint32_t)dbf((lo >> 16) & 255) << 16);
-      uint32_t w3 = dbf((lo >> 8) & 255) | ((uint32_t)dbf(lo & 255) << 16);
-      *reinterpret_cast<uint4*>(rowbase + c * 128) = make_uint4(w0, w1, w2, w3);
+    // balanced digits of z (the top carry is the 2^p of z = z' + 2^p), digit
+    // s at k' = KD - 1 - s: limb L's four digits fill k' = KD - 4 - 4L .. KD - 1 - 4L
+    int cy = 0;
+    for (int L = 0; L < NL; ++L) {
+      const uint32_t w = have ? zm[L] : 0u;
+      int e[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int t = (int)((w >> (8 * q)) & 255u) + cy;
+        cy = t >= 128 ? 1 : 0;
+        e[q] = t - (cy << 8);
+      }
+      const int k0 = KD - 4 - 4 * L;
+      *reinterpret_cast<uint2*>(rowbase + (k0 >> 3) * 128 + (k0 & 7) * 2) =
+          make_uint2(pipe::dbfs(e[3]) | (pipe::dbfs(e[2]) << 16), pipe::dbfs(e[1]) | (pipe::dbfs(e[0]) << 16));
     }
     sFl[tid] = have ? 1 : 0;
   }
@@ -613,6 +846,8 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(b_tfull + 8 * b), "r"(M));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(b_tfree + 8 * b), "r"(M));
     }
+    for (int b = 0; b < 3; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b_bkrdy + 8 * b));
+    for (int b = 0; b < 2; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b_hready + 8 * b));
     *eflag = 0;
   }
   if (warp == 0) {
@@ -625,26 +860,101 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = *tslot;
 
-  if (warp >= 8) {
-    // ================= P: Hankel producer and MMA issuer =================
-    const int pt = tid - 256;
-    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+  if (warp == 8) {
+    // ================= I: MMA issuer, one thread =========================
+    // waits until the builders have a column's Hankel cores in shared memory,
+    // then issues its MMAs tile group by tile group as the epilogue releases
+    // the tensor-memory tiles; tcgen05.commit signals each tile (full) and the
+    // Hankel buffer (hfree)
+    if ((tid & 31) == 0) {
+      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+      const uint32_t idesc2 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((2 * NT) >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+      for (int c = 0; c < nc; ++c) {
+        const int hb = c & 1;
+        unsigned char* sH = sm + C::OFF_H + hb * C::HBYTES;
+        if (!wait_bar(b_hready + 8 * hb, (c >> 1) & 1) || *eflag) {
+          *eflag = 1;
+          break;
+        }
+        bool okm = true;
+        for (int t = 0; t < TILES && okm; ++t) {
+          const bool two = C::merge(t);
+          for (int u = t; u <= (two ? t + 1 : t) && okm; ++u)
+            if (c >= 1 && !wait_bar(b_empty + 8 * u, (c - 1) & 1)) okm = false;
+          if (!okm) {
+            *eflag = 1;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t id = two ? idesc2 : idesc;
+          for (int ks = C::ks_lo(t); ks < C::ks_hi(t); ++ks) {
+            const uint64_t ad = desc(su32(sA) + ks * 256, 128, KD * 16);
+            const uint64_t bd = desc(su32(sH) + (16 * t + 2 * ks) * 128, 128, 128);
+            const uint32_t acc = ks > C::ks_lo(t) ? 1u : 0u;
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+                    tmem + (uint32_t)(t * NT)),
+                "l"(ad), "l"(bd), "r"(id), "r"(acc));
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(b_full + 8 * t));
+          if (two) {
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(b_full + 8 * (t + 1)));
+            ++t;
+          }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(b_hfree + 8 * hb));
+        if (!okm) break;
+      }
+    }
+    __syncwarp();
+  } else if (warp > 8) {
+    // ================= B: Hankel builders, warps 9-11 ====================
+    // per column: b's limbs (sB; sBk for the epilogue), b's balanced digits
+    // (warp 9), the Hankel cores of b~ into the free buffer, then hready
+    const int bt = tid - 288;
     for (int c = 0; c < nc; ++c) {
       const int hb = c & 1;
       unsigned char* sH = sm + C::OFF_H + hb * C::HBYTES;
       uint32_t* sB = sBl + hb * NL;
       bool bad = false;
-      if (pt == 0 && c >= 2 && !wait_bar(b_hfree + 8 * hb, ((c - 2) >> 1) & 1)) bad = true;
+      if (bt == 0 && c >= 2 && !wait_bar(b_hfree + 8 * hb, ((c - 2) >> 1) & 1)) bad = true;
       if (pipe::pbar_or(bad || *eflag != 0)) {
         *eflag = 1;
         break;
       }
       const int64_t kj = a.brow * N + colj(c);
       const bool bz = X.e[kj] == ZEXP;
-      if (pt < NL) sB[pt] = X.m[kj * NL + pt];
+      if (bt < NL) {
+        const uint32_t bl = X.m[kj * NL + bt];
+        sB[bt] = bl;
+        sBk[(c % 3) * NL + bt] = (int64_t)bl - pipe::kC;  // limb NL + bt of 2^p * b, less the digit offset
+      }
       pipe::pbar();
-      const unsigned char* bb = reinterpret_cast<const unsigned char*>(sB);
-      for (int q = pt; q < NCORE * 8; q += 128) {
+      if (bt == 0) arrive(b_bkrdy + 8 * (c % 3));
+      if (warp == 9) {
+        // balanced digits of b: carries across lanes by carry lookahead (lane l
+        // holds digits [l * DPL, (l + 1) * DPL)); the top carry is digit KD
+        constexpr int DPL = KD / 32;
+        const unsigned char* bb = reinterpret_cast<const unsigned char*>(sB);
+        int f0 = 0, f1 = 1;
+#pragma unroll
+        for (int q = 0; q < DPL; ++q) {
+          const int d = bb[bt * DPL + q];
+          f0 = (d + f0) >= 128 ? 1 : 0;
+          f1 = (d + f1) >= 128 ? 1 : 0;
+        }
+        const uint64_t cm = carry_mask(__ballot_sync(FULL, f0 != 0), __ballot_sync(FULL, f1 != 0 && f0 == 0), 0u);
+        int cy = (int)((cm >> bt) & 1u);
+#pragma unroll
+        for (int q = 0; q < DPL; ++q) {
+          const int t = (int)bb[bt * DPL + q] + cy;
+          cy = t >= 128 ? 1 : 0;
+          sEb[bt * DPL + q] = bz ? (uint16_t)0 : (uint16_t)pipe::dbfs(t - (cy << 8));
+        }
+        if (bt == 31) sEb[KD] = bz ? (uint16_t)0 : (uint16_t)pipe::dbfs((int)((cm >> 32) & 1u));
+      }
+      pipe::pbar();
+      for (int q = bt; q < NCORE * 8; q += 96) {
         const int d = q >> 3, nn = q & 7;
         const int base = 8 * d + nn - (KD - 1);
         uint32_t w[4];
@@ -654,7 +964,7 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
 #pragma unroll
           for (int u = 0; u < 2; ++u) {
             const int idx = base + 2 * e + u;
-            h2[u] = dbf((idx >= 0 && idx < KD && !bz) ? bb[idx] : 0u);
+            h2[u] = (idx >= 0 && idx <= KD) ? (uint32_t)sEb[idx] : 0u;
           }
           w[e] = h2[0] | (h2[1] << 16);
         }
@@ -662,113 +972,155 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
       }
       asm volatile("fence.proxy.async.shared::cta;");
       pipe::pbar();
-      if (pt == 0) {
-        for (int t = 0; t < TILES; ++t) {
-          if (c >= 1 && !wait_bar(b_empty + 8 * t, (c - 1) & 1)) {
-            *eflag = 1;
-            break;
-          }
-          asm volatile("tcgen05.fence::after_thread_sync;");
-          for (int ks = 0; ks < KD / 16; ++ks) {
-            const uint64_t ad = desc(su32(sA) + ks * 256, 128, KD * 16);
-            const uint64_t bd = desc(su32(sH) + (16 * t + 2 * ks) * 128, 128, 128);
-            const uint32_t acc = ks > 0 ? 1u : 0u;
-            asm volatile(
-                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
-                    tmem + (uint32_t)(t * NT)),
-                "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-          }
-          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(b_full + 8 * t));
-        }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(b_hfree + 8 * hb));
-      }
+      if (bt == 0) arrive(b_hready + 8 * hb);
     }
   } else if (warp < 4) {
     // ================= E: epilogue, one thread per row ====================
+    // Forms each row's 2n-limb product z' * b~ + 2^p * b from the column's
+    // 2 KD exact sums (32-column chunks, the next chunk loading while this
+    // one is processed) and stages for the subtraction role its upper n
+    // limbs, limb n - 1 and the OR of the limbs below (it rounds there).
+    // Lazy low half: the carry chain starts at limb NL - 8 with a zero carry.
+    // The sums below contribute less than 2^(32 (NL - 8) + 14) in magnitude,
+    // so when bits [14, 224) of limbs NL-8 .. NL-2 hold both a one and a zero
+    // they change neither those limbs' carry out nor the sticky bit (which is
+    // then set); otherwise the warp reads the low chunks and adds their exact
+    // carry.  The low tiles are released only after that decision.
     const int r = tid;
     const int8_t zsign = (i0 + r < rend) ? Z.s[i0 + r] : 0;
     const int64_t zexp = (i0 + r < rend) ? Z.e[i0 + r] : ZEXP;
     const bool have = sFl[r] != 0;
+    constexpr int NCH = 4 * TILES;    // chunks of 32 sums (8 limbs)
+    constexpr int K0 = NL / 8 - 1;     // first chunk read: limbs NL - 8 .. NL - 1
+    constexpr int T0 = K0 >> 2;        // its tile
+    const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
     for (int c = 0; c < nc; ++c) {
       const int tb = c & 1;
       const int64_t kj = a.brow * N + colj(c);
       const int64_t be = X.e[kj];
       const int8_t bs = X.s[kj];
-      uint32_t up[NL];
-      uint32_t l63 = 0, sticky = 0;  // limb NL-1 and the OR of limbs 0..NL-2
-      uint64_t acc = 0;
+      const bool used = have && be != ZEXP;  // the row's product is used
+      const int64_t* bk = sBk + (c % 3) * NL;
+      uint32_t* Trow = sT + tb * (M * RSTR) + r * RSTR;
+      uint32_t l63 = 0, sticky = 0;
+      int64_t acc = 0;
       bool okc = true;
+      uint32_t va[32], vb[32];
+      // tiles complete in issue order: tile T0 done means the ones below are too
+      if (!wait_bar(b_full + 8 * T0, c & 1)) okc = false;
+      okc = __all_sync(0xffffffffu, okc) && !*eflag;
+      okc = __all_sync(0xffffffffu, okc);
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      if (okc) tmem_ld32_async(tl + 32 * K0, va);
+      auto limbs8 = [&](const uint32_t* v, const int64_t* kv, uint32_t(&lim)[8], int64_t& ac) {
 #pragma unroll
-      for (int t = 0; t < TILES; ++t) {
-        if (okc && !wait_bar(b_full + 8 * t, c & 1)) okc = false;
-        okc = __all_sync(0xffffffffu, okc) && !*eflag;
-        okc = __all_sync(0xffffffffu, okc);
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        if (okc) {
+        for (int q = 0; q < 8; ++q) {
+          uint32_t u[4];
 #pragma unroll
-          for (int ch = 0; ch < 4; ++ch) {
-            uint32_t v[32];
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * NT + ch * 32), v);
+          for (int j = 0; j < 4; ++j)
+            u[j] = __float_as_uint(__fadd_rn(__uint_as_float(v[4 * q + j]), pipe::kMagic)) & 0x7FFFFFu;
+          const uint32_t xl = u[0] + (u[1] << 8), yl = u[2] + (u[3] << 8);
+          ac += (int64_t)((uint64_t)yl * 65536u + xl) + kv[q];
+          lim[q] = (uint32_t)ac;
+          ac >>= 32;
+        }
+      };
+      auto release_low = [&]() {  // tiles below T0, and T0 when K0 is its last chunk
+        asm volatile("tcgen05.fence::before_thread_sync;");
+#pragma unroll
+        for (int t = 0; t < T0; ++t) arrive(b_empty + 8 * t);
+        if ((K0 & 3) == 3) arrive(b_empty + 8 * T0);
+      };
+      auto chunk = [&](const int k, uint32_t(&cur)[32], uint32_t(&nxt)[32]) {
+        const bool upper = 8 * k >= NL;
+        if (8 * k == NL && okc) {
+          // first upper chunk: the staging buffer is free and sBk holds b
+          bool okw = (c < 2) || wait_bar(b_tfree + 8 * tb, ((c - 2) >> 1) & 1);
+          okw = okw && wait_bar(b_bkrdy + 8 * (c % 3), (c / 3) & 1);
+          okc = __all_sync(0xffffffffu, okw);
+        }
+        int64_t kv[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) kv[q] = (upper && okc) ? bk[8 * k - NL + q] : -pipe::kC;
+        if (okc) tmem_wait(cur);
+        if (okc && (k & 3) == 3 && k != K0) {  // the tile's last chunk is in registers: release it
+          asm volatile("tcgen05.fence::before_thread_sync;");
+          arrive(b_empty + 8 * (k >> 2));
+        }
+        if (k + 1 < NCH && okc) {
+          if (((k + 1) & 3) == 0) {
+            bool okt = wait_bar(b_full + 8 * ((k + 1) >> 2), c & 1);
+            okt = __all_sync(0xffffffffu, okt) && !*eflag;
+            okc = __all_sync(0xffffffffu, okt);
+            asm volatile("tcgen05.fence::after_thread_sync;");
+          }
+          if (okc) tmem_ld32_async(tl + (uint32_t)(32 * (k + 1)), nxt);
+        }
+        if (!okc) return;
+        uint32_t lim[8];
+        limbs8(cur, kv, lim, acc);
+        if (upper) {
+          *reinterpret_cast<uint4*>(Trow + 8 * k - NL) = make_uint4(lim[0], lim[1], lim[2], lim[3]);
+          *reinterpret_cast<uint4*>(Trow + 8 * k - NL + 4) = make_uint4(lim[4], lim[5], lim[6], lim[7]);
+          return;
+        }
+        // k == K0: limbs NL - 8 .. NL - 1 with a zero carry in
+        const uint32_t lo7 = lim[1] | lim[2] | lim[3] | lim[4] | lim[5] | lim[6];
+        const uint32_t hi7 = lim[1] & lim[2] & lim[3] & lim[4] & lim[5] & lim[6];
+        const bool any1 = ((lim[0] >> 14) | lo7) != 0u;
+        const bool any0 = ((~lim[0] >> 14) | ~hi7) != 0u;
+        const bool unsafe = used && !(any1 && any0);
+        l63 = lim[7];
+        sticky = 1u;
+        if (__any_sync(0xffffffffu, unsafe)) {
+          // exact low part: limbs 0 .. NL - 9 and its carry into limb NL - 8
+          int64_t ac2 = 0;
+          uint32_t slo = 0;
+          const int64_t kvl[8] = {-pipe::kC, -pipe::kC, -pipe::kC, -pipe::kC,
+                                  -pipe::kC, -pipe::kC, -pipe::kC, -pipe::kC};
+#pragma unroll 1
+          for (int kk = 0; kk < K0; ++kk) {
+            uint32_t w[32];
+#pragma unroll
+            for (int part = 0; part < 4; ++part) {
+              uint32_t w8[8];
+              tmem_ld8(tl + (uint32_t)(32 * kk + 8 * part), w8);
+#pragma unroll
+              for (int e = 0; e < 8; ++e) w[8 * part + e] = w8[e];
+            }
+            uint32_t l8[8];
+            limbs8(w, kvl, l8, ac2);
+            slo |= l8[0] | l8[1] | l8[2] | l8[3] | l8[4] | l8[5] | l8[6] | l8[7];
+          }
+          if (unsafe) {
+            int64_t t = ac2;
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-              const uint64_t c0v = __float2uint_rz(__uint_as_float(v[4 * q]));
-              const uint64_t c1v = __float2uint_rz(__uint_as_float(v[4 * q + 1]));
-              const uint64_t c2v = __float2uint_rz(__uint_as_float(v[4 * q + 2]));
-              const uint64_t c3v = __float2uint_rz(__uint_as_float(v[4 * q + 3]));
-              acc += c0v + (c1v << 8) + (c2v << 16) + (c3v << 24);
-              const uint32_t limb = (uint32_t)acc;
-              acc >>= 32;
-              const int L = t * 32 + ch * 8 + q;
-              if (L >= NL) up[L >= NL ? L - NL : 0] = limb;
-              else if (L == NL - 1) l63 = limb;
-              else sticky |= limb;
+              t += (int64_t)lim[q];
+              lim[q] = (uint32_t)t;
+              t >>= 32;
             }
+            acc += t;
+            l63 = lim[7];
+            sticky = slo | lim[0] | lim[1] | lim[2] | lim[3] | lim[4] | lim[5] | lim[6];
           }
-          asm volatile("tcgen05.fence::before_thread_sync;");
-          arrive(b_empty + 8 * t);
         }
+        release_low();
+      };
+#pragma unroll 1
+      for (int k = K0; k + 1 < NCH; k += 2) {
+        chunk(k, va, vb);
+        chunk(k + 1, vb, va);
       }
+      chunk(NCH - 1, va, vb);  // NCH - K0 is odd: the last chunk is in va
       if (!okc) {  // warp-uniform
         *eflag = 1;
         break;
       }
-      const uint32_t top = up[NL - 1] >> 31;
-      uint32_t rbit, st;
-      if (top) {
-        rbit = l63 >> 31;
-        st = (l63 & 0x7fffffffu) | sticky;
-      } else {
-#pragma unroll
-        for (int q = NL - 1; q > 0; --q) up[q] = (up[q] << 1) | (up[q - 1] >> 31);
-        up[0] = (up[0] << 1) | (l63 >> 31);
-        rbit = (l63 >> 30) & 1u;
-        st = (l63 & 0x3fffffffu) | sticky;
-      }
-      uint32_t carry = rbit & ((st != 0u) | (up[0] & 1u));
-#pragma unroll
-      for (int q = 0; q < NL; ++q) {
-        const uint64_t s2 = (uint64_t)up[q] + carry;
-        up[q] = (uint32_t)s2;
-        carry = (uint32_t)(s2 >> 32);
-      }
-      int adj = top ? 0 : -1;
-      if (carry) {
-        up[NL - 1] = 0x80000000u;
-        adj += 1;
-      }
       const bool tz = !have || be == ZEXP;
-      bool okw = (c < 2) || wait_bar(b_tfree + 8 * tb, ((c - 2) >> 1) & 1);
-      okw = __all_sync(0xffffffffu, okw);
-      if (!okw) {
-        *eflag = 1;
-        break;
-      }
-      uint32_t* T = sT + tb * (M * RSTR);
-#pragma unroll
-      for (int q = 0; q < NL; q += 4)
-        *reinterpret_cast<uint4*>(T + r * RSTR + q) =
-            tz ? make_uint4(0u, 0u, 0u, 0u) : make_uint4(up[q], up[q + 1], up[q + 2], up[q + 3]);
-      sTe[tb * M + r] = tz ? ZEXP : zexp + be + adj;
+      Trow[NL] = l63;
+      Trow[NL + 1] = sticky;
+      sTe[tb * M + r] = tz ? ZEXP : zexp + be;  // before rounding
       sTs[tb * M + r] = tz ? (int8_t)0 : (int8_t)(zsign ^ bs);
       arrive(b_tfull + 8 * tb);
     }
@@ -806,9 +1158,12 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
       asm volatile("cp.async.wait_all;" ::: "memory");
       int8_t rs = 0;
       int64_t re = ZEXP;
-      if (active)
-        sub_row<NL>(xrow, xs, xe, sT + tb * (M * RSTR) + r * RSTR, sTs[tb * M + r], sTe[tb * M + r], X.m + ij * NL,
-                    xrow, rs, re);
+      if (active) {
+        uint32_t* Tr = sT + tb * (M * RSTR) + r * RSTR;
+        int64_t te = sTe[tb * M + r];
+        if (te != ZEXP) te += round_product<NL>(Tr);
+        sub_row<NL>(xrow, xs, xe, Tr, sTs[tb * M + r], te, X.m + ij * NL, xrow, rs, re);
+      }
       arrive(b_tfree + 8 * tb);
       if (active) {
         X.s[ij] = rs;
