@@ -780,7 +780,7 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
   using pipe::arrive;
   using pipe::wait_bar;
   using C = pipe::Cfg<KD>;
-  constexpr int NL = C::NL, TILES = C::TILES, NCORE = C::NCORE, RSTR = C::RSTR;
+  constexpr int NL = C::NL, TILES = C::TILES, RSTR = C::RSTR;
   extern __shared__ __align__(1024) unsigned char sm[];
   if (upd_stopped(status, a)) return;
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -836,6 +836,9 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
     }
     sFl[tid] = have ? 1 : 0;
   }
+  // the Hankel cores outside the digit window are zero for every column
+  for (int q = tid; q < 2 * C::HBYTES / 16; q += pipe::NTH)
+    reinterpret_cast<uint4*>(sm + C::OFF_H)[q] = make_uint4(0u, 0u, 0u, 0u);
   if (tid == 0) {
     for (int t = 0; t < 4; ++t) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b_full + 8 * t));
@@ -912,20 +915,32 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
     // per column: b's limbs (sB; sBk for the epilogue), b's balanced digits
     // (warp 9), the Hankel cores of b~ into the free buffer, then hready
     const int bt = tid - 288;
+    // b of the next column (limb bt and the exponent), loaded one column ahead
+    uint32_t bl_n = 0u;
+    int64_t be_n = ZEXP;
+    if (nc > 0) {
+      const int64_t kj = a.brow * N + colj(0);
+      if (bt < NL) bl_n = X.m[kj * NL + bt];
+      be_n = X.e[kj];
+    }
     for (int c = 0; c < nc; ++c) {
       const int hb = c & 1;
       unsigned char* sH = sm + C::OFF_H + hb * C::HBYTES;
       uint32_t* sB = sBl + hb * NL;
+      const uint32_t bl = bl_n;
+      const bool bz = be_n == ZEXP;
+      if (c + 1 < nc) {
+        const int64_t kj = a.brow * N + colj(c + 1);
+        if (bt < NL) bl_n = X.m[kj * NL + bt];
+        be_n = X.e[kj];
+      }
       bool bad = false;
       if (bt == 0 && c >= 2 && !wait_bar(b_hfree + 8 * hb, ((c - 2) >> 1) & 1)) bad = true;
       if (pipe::pbar_or(bad || *eflag != 0)) {
         *eflag = 1;
         break;
       }
-      const int64_t kj = a.brow * N + colj(c);
-      const bool bz = X.e[kj] == ZEXP;
       if (bt < NL) {
-        const uint32_t bl = X.m[kj * NL + bt];
         sB[bt] = bl;
         sBk[(c % 3) * NL + bt] = (int64_t)bl - pipe::kC;  // limb NL + bt of 2^p * b, less the digit offset
       }
@@ -954,8 +969,10 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
         if (bt == 31) sEb[KD] = bz ? (uint16_t)0 : (uint16_t)pipe::dbfs((int)((cm >> 32) & 1u));
       }
       pipe::pbar();
-      for (int q = bt; q < NCORE * 8; q += 96) {
-        const int d = q >> 3, nn = q & 7;
+      // core d, row nn holds b~[8 (d - KD/8) + nn + 1 .. + 8]: only cores
+      // KD/8 - 1 .. KD/4 - 1 meet digits 0..KD; the others stay zero
+      for (int q = bt; q < (KD / 8 + 1) * 8; q += 96) {
+        const int d = KD / 8 - 1 + (q >> 3), nn = q & 7;
         const int base = 8 * d + nn - (KD - 1);
         uint32_t w[4];
 #pragma unroll
@@ -994,11 +1011,21 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
     constexpr int K0 = NL / 8 - 1;     // first chunk read: limbs NL - 8 .. NL - 1
     constexpr int T0 = K0 >> 2;        // its tile
     const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+    // b's exponent and sign, loaded one column ahead
+    int64_t be_n = ZEXP;
+    int8_t bs_n = 0;
+    if (nc > 0) {
+      be_n = X.e[a.brow * N + colj(0)];
+      bs_n = X.s[a.brow * N + colj(0)];
+    }
     for (int c = 0; c < nc; ++c) {
       const int tb = c & 1;
-      const int64_t kj = a.brow * N + colj(c);
-      const int64_t be = X.e[kj];
-      const int8_t bs = X.s[kj];
+      const int64_t be = be_n;
+      const int8_t bs = bs_n;
+      if (c + 1 < nc) {
+        be_n = X.e[a.brow * N + colj(c + 1)];
+        bs_n = X.s[a.brow * N + colj(c + 1)];
+      }
       const bool used = have && be != ZEXP;  // the row's product is used
       const int64_t* bk = sBk + (c % 3) * NL;
       uint32_t* Trow = sT + tb * (M * RSTR) + r * RSTR;
