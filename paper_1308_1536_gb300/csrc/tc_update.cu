@@ -699,14 +699,18 @@ constexpr int LIMIT = 1 << 22;
 // second added to the upper limbs in the carry chain.  Every column sum lies
 // in [-4161536, 4194304]: at most 256 products in [-16256, 16384], or 255 of
 // them and one with the carry digit when that digit is in the window.  Adding
-// kMagic puts it in [2^23, 2^24), where the fp32 spacing is 1, so the sum
-// plus kMagic - 2^23 (kOff) is the low 23 bits of the fp32 result: one FADD
-// instead of a conversion on the XU pipe.  Four consecutive outputs form a
-// limb, less kOff * 0x01010101 (kC).
+// kMagic puts it in [2^23, 2^24), where the fp32 spacing is 1, so the fp32
+// result's bits are 0x4B000000 + u with u = sum + kMagic - 2^23 (kOff) in
+// [0, 2^23): one FADD instead of a conversion on the XU pipe.  Four
+// consecutive outputs w0..w3 (raw bits) form a limb as
+//     (w0 + (w1 << 8)) + (w2 + (w3 << 8)) * 2^16        (32-bit inner sums)
+// where w << 8 drops the exponent field mod 2^32 and neither inner sum wraps
+// (u < 2^23), so the limb is sum_q u_q 2^(8q) + 0x4B000000 * 0x10001 and,
+// less kOff * 0x01010101, the four sums' weighted total: kC removes both.
 constexpr float kMagic = 12566528.0f;  // 2^23 + kOff
 constexpr uint32_t kOff = 4177920u;
-constexpr int64_t kC = 70368744161280ll;  // kOff * 0x01010101
-static_assert((int64_t)kOff * 0x01010101ll == kC, "digit offset per limb");
+constexpr int64_t kC = 152833374535680ll;  // kOff * 0x01010101 + 0x4B000000 * 0x10001
+static_assert((int64_t)kOff * 0x01010101ll + 0x4B000000ll * 0x10001ll == kC, "per-limb constant");
 
 // bf16 bits of a small integer (|e| <= 256: exact)
 __device__ __forceinline__ uint32_t dbfs(int e) { return __float_as_uint((float)e) >> 16; }
@@ -942,7 +946,7 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
       }
       if (bt < NL) {
         sB[bt] = bl;
-        sBk[(c % 3) * NL + bt] = (int64_t)bl - pipe::kC;  // limb NL + bt of 2^p * b, less the digit offset
+        sBk[(c % 3) * NL + bt] = (int64_t)bl - pipe::kC;  // limb NL + bt of 2^p * b, less the per-limb constant
       }
       pipe::pbar();
       if (bt == 0) arrive(b_bkrdy + 8 * (c % 3));
@@ -1045,7 +1049,7 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
           uint32_t u[4];
 #pragma unroll
           for (int j = 0; j < 4; ++j)
-            u[j] = __float_as_uint(__fadd_rn(__uint_as_float(v[4 * q + j]), pipe::kMagic)) & 0x7FFFFFu;
+            u[j] = __float_as_uint(__fadd_rn(__uint_as_float(v[4 * q + j]), pipe::kMagic));  // 0x4B000000 + u
           const uint32_t xl = u[0] + (u[1] << 8), yl = u[2] + (u[3] << 8);
           ac += (int64_t)((uint64_t)yl * 65536u + xl) + kv[q];
           lim[q] = (uint32_t)ac;
