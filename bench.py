@@ -140,16 +140,19 @@ def measured_peaks():
         return {}
 
 
-def recorded_traffic():
-    """dram bytes per Schur-update launch from the committed ncu summary, valid
-    only for the kernel sources it was measured on."""
+def recorded_traffic(products_per_launch: float):
+    """DRAM bytes per Schur-update launch: the bytes per product of one ncu
+    capture (profiles/k_update_traffic.json, dram__bytes_read.sum +
+    dram__bytes_write.sum of a launch of known size) times this run's average
+    products per timed launch.  None unless the capture was taken on the
+    current kernel sources."""
     try:
         t = json.load(open(os.path.join(ROOT, "profiles", "k_update_traffic.json")))
     except Exception:
         return None
     if t.get("source_sha") != kernel_source_sha():
         return None
-    return t.get("bytes_per_launch")
+    return t["bytes_per_product"] * products_per_launch
 
 
 # ---------------------------------------------------------------------------
@@ -464,7 +467,7 @@ def run_gpu(args):
         upd_macs = pc["update_limb_macs"] + pi["update_limb_macs"]
         upd_launches = pc["update_launches"] + pi["update_launches"]
         achieved = upd_macs / (upd_ms / 1e3)
-        tr = recorded_traffic()
+        tr = recorded_traffic(upd_macs / (n * n) / max(upd_launches, 1))
         tensor = (p in (1024, 2048) and args.engine != 0)
         if tensor:
             # exact digit convolution on the tensor cores: one limb-MAC is 16 products of 8-bit digits,
