@@ -696,9 +696,11 @@ constexpr int LIMIT = 1 << 22;
 // digits followed by the carry digit 1 at position KD (the value b itself),
 //     z * b = z' * b~ + 2^p * b,
 // the first term a digit convolution of KD + 1 positions per output, the
-// second added to the upper limbs in the carry chain.  Every column sum lies
-// in [-4161536, 4194304]: at most 256 products in [-16256, 16384], or 255 of
-// them and one with the carry digit when that digit is in the window.  Adding
+// second one more MMA K step per upper tile: a column of ones in A times b's
+// raw digits d_j at output position KD + j.  Every column sum lies
+// in [-4161536, 4194559]: at most 256 products in [-16256, 16384], or 255 of
+// them and one with the carry digit when that digit is in the window, plus a
+// raw digit of b (0..255) above position KD.  Adding
 // kMagic puts it in [2^23, 2^24), where the fp32 spacing is 1, so the fp32
 // result's bits are 0x4B000000 + u with u = sum + kMagic - 2^23 (kOff) in
 // [0, 2^23): one FADD instead of a conversion on the XU pipe.  Four
@@ -735,20 +737,27 @@ struct Cfg {
   __host__ __device__ static constexpr bool merge(int t) {  // tile t and t + 1 in one MMA group
     return t + 1 < TILES && ks_lo(t) == ks_lo(t + 1) && ks_hi(t) == ks_hi(t + 1);
   }
-  static constexpr int OFF_A = 0;                           // M x KD bf16
-  static constexpr int OFF_H = OFF_A + M * KD * 2;          // 2 Hankel buffers
-  static constexpr int OFF_B = OFF_H + 2 * HBYTES;          // 2 x NL limbs of b_j
+  // A holds KA = KD + 16 digits per row: z's KD balanced digits (K reversed)
+  // and one K step whose first position is 1, which multiplies b's raw
+  // digits in the BX region (the 2^p * b term, one extra MMA per upper tile)
+  static constexpr int KA = KD + 16;
+  static constexpr int XT0 = KD / 128;                      // first tile holding positions >= KD
+  static constexpr int XTN = TILES - XT0;                   // tiles with the extra MMA
+  static constexpr int XBYTES = XTN * 16 * 256;             // per buffer: 16 n-cores x 2 k-cores per tile
+  static constexpr int OFF_A = 0;                           // M x KA bf16
+  static constexpr int OFF_H = OFF_A + M * KA * 2;          // 2 Hankel buffers
+  static constexpr int OFF_BX = OFF_H + 2 * HBYTES;         // 2 extra-K B buffers
+  static constexpr int OFF_B = OFF_BX + 2 * XBYTES;         // 2 x NL limbs of b_j
   static constexpr int OFF_T = OFF_B + 2 * NL * 4;          // 2 x M x RSTR words staged products
   static constexpr int OFF_TE = OFF_T + 2 * M * RSTR * 4;   // 2 x M int64
   static constexpr int OFF_TS = OFF_TE + 2 * M * 8;         // 2 x M int8
   static constexpr int OFF_FL = OFF_TS + 2 * M;             // M multiplier flags
   static constexpr int OFF_X = (OFF_FL + M + 15) / 16 * 16;  // M x RSTR words: x_ij of the next column
   static constexpr int OFF_EB = OFF_X + M * RSTR * 4;       // bf16 balanced digits of b, KD + 1 (+ pad)
-  static constexpr int OFF_BK = OFF_EB + (KD + 8) * 2;      // 3 x NL int64: b's limbs minus the digit offset
-  static constexpr int OFF_BAR = OFF_BK + 3 * NL * 8;       // barriers
+  static constexpr int OFF_BAR = OFF_EB + (KD + 8) * 2;     // barriers
   static constexpr int SMEM = OFF_BAR + 256;
   static_assert(NL % 16 == 0 && NL <= 64, "tensor engine covers p = 512, 1024, 2048");
-  static_assert(OFF_X % 16 == 0 && OFF_BK % 8 == 0 && OFF_BAR % 8 == 0 && OFF_T % 16 == 0, "alignment");
+  static_assert(OFF_X % 16 == 0 && OFF_BX % 16 == 0 && OFF_BAR % 8 == 0 && OFF_T % 16 == 0, "alignment");
   static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
@@ -796,13 +805,11 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
   int8_t* sFl = reinterpret_cast<int8_t*>(sm + C::OFF_FL);
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + C::OFF_BAR);
   // bars: 0-3 full, 4-7 empty, 8-9 hfree, 10-11 tfull, 12-13 tfree; slot 14: tmem address; 15: error
-  // flag; 16-18 bkrdy (B -> E: the per-limb constants of a column are in sBk); 19-20 hready (B -> I:
-  // a column's Hankel cores are built)
+  // flag; 19-20 hready (B -> I: a column's Hankel cores and extra-K digits are built)
   uint32_t* tslot = reinterpret_cast<uint32_t*>(&bars[14]);
   volatile int* eflag = reinterpret_cast<volatile int*>(&bars[15]);
   const uint32_t b_full = su32(&bars[0]), b_empty = su32(&bars[4]), b_hfree = su32(&bars[8]);
-  const uint32_t b_tfull = su32(&bars[10]), b_tfree = su32(&bars[12]), b_bkrdy = su32(&bars[16]), b_hready = su32(&bars[19]);
-  int64_t* const sBk = reinterpret_cast<int64_t*>(sm + C::OFF_BK);
+  const uint32_t b_tfull = su32(&bars[10]), b_tfree = su32(&bars[12]), b_hready = su32(&bars[19]);
   uint16_t* const sEb = reinterpret_cast<uint16_t*>(sm + C::OFF_EB);
   const int64_t N = a.N;
   const int64_t ncols = a.ncols;
@@ -821,7 +828,7 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
     const int64_t i = i0 + tid;
     const bool have = i < rend && Z.e[i < rend ? i : i0] != ZEXP;
     const uint32_t* zm = Z.m + (i < rend ? i : i0) * NL;
-    unsigned char* rowbase = sA + (tid >> 3) * (KD * 16) + (tid & 7) * 16;
+    unsigned char* rowbase = sA + (tid >> 3) * (C::KA * 16) + (tid & 7) * 16;
     // balanced digits of z (the top carry is the 2^p of z = z' + 2^p), digit
     // s at k' = KD - 1 - s: limb L's four digits fill k' = KD - 4 - 4L .. KD - 1 - 4L
     int cy = 0;
@@ -838,10 +845,14 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
       *reinterpret_cast<uint2*>(rowbase + (k0 >> 3) * 128 + (k0 & 7) * 2) =
           make_uint2(pipe::dbfs(e[3]) | (pipe::dbfs(e[2]) << 16), pipe::dbfs(e[1]) | (pipe::dbfs(e[0]) << 16));
     }
+    // the extra K step: 1 at k' = KD, zeros after it
+    *reinterpret_cast<uint4*>(rowbase + (KD / 8) * 128) = make_uint4(0x3F80u, 0u, 0u, 0u);
+    *reinterpret_cast<uint4*>(rowbase + (KD / 8 + 1) * 128) = make_uint4(0u, 0u, 0u, 0u);
     sFl[tid] = have ? 1 : 0;
   }
   // the Hankel cores outside the digit window are zero for every column
-  for (int q = tid; q < 2 * C::HBYTES / 16; q += pipe::NTH)
+  static_assert(C::OFF_BX == C::OFF_H + 2 * C::HBYTES, "Hankel and extra-K buffers are contiguous");
+  for (int q = tid; q < (2 * C::HBYTES + 2 * C::XBYTES) / 16; q += pipe::NTH)
     reinterpret_cast<uint4*>(sm + C::OFF_H)[q] = make_uint4(0u, 0u, 0u, 0u);
   if (tid == 0) {
     for (int t = 0; t < 4; ++t) {
@@ -853,7 +864,6 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(b_tfull + 8 * b), "r"(M));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(b_tfree + 8 * b), "r"(M));
     }
-    for (int b = 0; b < 3; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b_bkrdy + 8 * b));
     for (int b = 0; b < 2; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b_hready + 8 * b));
     *eflag = 0;
   }
@@ -895,13 +905,23 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
           asm volatile("tcgen05.fence::after_thread_sync;");
           const uint32_t id = two ? idesc2 : idesc;
           for (int ks = C::ks_lo(t); ks < C::ks_hi(t); ++ks) {
-            const uint64_t ad = desc(su32(sA) + ks * 256, 128, KD * 16);
+            const uint64_t ad = desc(su32(sA) + ks * 256, 128, C::KA * 16);
             const uint64_t bd = desc(su32(sH) + (16 * t + 2 * ks) * 128, 128, 128);
             const uint32_t acc = ks > C::ks_lo(t) ? 1u : 0u;
             asm volatile(
                 "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
                     tmem + (uint32_t)(t * NT)),
                 "l"(ad), "l"(bd), "r"(id), "r"(acc));
+          }
+          // 2^p * b: the extra K step for the tiles at or above position KD
+          for (int u = t; u <= (two ? t + 1 : t); ++u) {
+            if (u < C::XT0) continue;
+            const uint64_t ad = desc(su32(sA) + (KD / 16) * 256, 128, C::KA * 16);
+            const uint64_t bd = desc(su32(sm + C::OFF_BX + hb * C::XBYTES) + (u - C::XT0) * 4096, 128, 256);
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+                    tmem + (uint32_t)(u * NT)),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(1u));
           }
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(b_full + 8 * t));
           if (two) {
@@ -916,8 +936,9 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
     __syncwarp();
   } else if (warp > 8) {
     // ================= B: Hankel builders, warps 9-11 ====================
-    // per column: b's limbs (sB; sBk for the epilogue), b's balanced digits
-    // (warp 9), the Hankel cores of b~ into the free buffer, then hready
+    // per column: b's limbs (sB), b's balanced digits (warp 9), the Hankel
+    // cores of b~ and b's raw digits for the extra K step into the free
+    // buffers, then hready
     const int bt = tid - 288;
     // b of the next column (limb bt and the exponent), loaded one column ahead
     uint32_t bl_n = 0u;
@@ -944,12 +965,19 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
         *eflag = 1;
         break;
       }
-      if (bt < NL) {
-        sB[bt] = bl;
-        sBk[(c % 3) * NL + bt] = (int64_t)bl - pipe::kC;  // limb NL + bt of 2^p * b, less the per-limb constant
-      }
+      if (bt < NL) sB[bt] = bl;
       pipe::pbar();
-      if (bt == 0) arrive(b_bkrdy + 8 * (c % 3));
+      // raw digit d_{r - KD} at output position r of the upper tiles: core
+      // (n-core (r % 128) / 8 of tile r / 128, k-core 0), row r % 8, element 0
+      {
+        unsigned char* bx = sm + C::OFF_BX + hb * C::XBYTES;
+        const unsigned char* bb = reinterpret_cast<const unsigned char*>(sB);
+        for (int r = 128 * C::XT0 + bt; r < 128 * TILES; r += 96) {
+          const int j = r - KD;
+          const uint16_t v = (j >= 0 && j < KD && !bz) ? (uint16_t)pipe::dbfs((int)bb[j]) : (uint16_t)0;
+          *reinterpret_cast<uint16_t*>(bx + (r / 128 - C::XT0) * 4096 + ((r % 128) / 8) * 256 + (r % 8) * 16) = v;
+        }
+      }
       if (warp == 9) {
         // balanced digits of b: carries across lanes by carry lookahead (lane l
         // holds digits [l * DPL, (l + 1) * DPL)); the top carry is digit KD
@@ -1031,7 +1059,6 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
         bs_n = X.s[a.brow * N + colj(c + 1)];
       }
       const bool used = have && be != ZEXP;  // the row's product is used
-      const int64_t* bk = sBk + (c % 3) * NL;
       uint32_t* Trow = sT + tb * (M * RSTR) + r * RSTR;
       uint32_t l63 = 0, sticky = 0;
       int64_t acc = 0;
@@ -1064,15 +1091,12 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
       };
       auto chunk = [&](const int k, uint32_t(&cur)[32], uint32_t(&nxt)[32]) {
         const bool upper = 8 * k >= NL;
-        if (8 * k == NL && okc) {
-          // first upper chunk: the staging buffer is free and sBk holds b
-          bool okw = (c < 2) || wait_bar(b_tfree + 8 * tb, ((c - 2) >> 1) & 1);
-          okw = okw && wait_bar(b_bkrdy + 8 * (c % 3), (c / 3) & 1);
+        if (8 * k == NL && okc) {  // first upper chunk: the staging buffer must be free
+          const bool okw = (c < 2) || wait_bar(b_tfree + 8 * tb, ((c - 2) >> 1) & 1);
           okc = __all_sync(0xffffffffu, okw);
         }
-        int64_t kv[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) kv[q] = (upper && okc) ? bk[8 * k - NL + q] : -pipe::kC;
+        const int64_t kv[8] = {-pipe::kC, -pipe::kC, -pipe::kC, -pipe::kC,
+                               -pipe::kC, -pipe::kC, -pipe::kC, -pipe::kC};
         if (okc) tmem_wait(cur);
         if (okc && (k & 3) == 3 && k != K0) {  // the tile's last chunk is in registers: release it
           asm volatile("tcgen05.fence::before_thread_sync;");
