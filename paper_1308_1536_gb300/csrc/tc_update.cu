@@ -368,17 +368,12 @@ __device__ __forceinline__ int round_product(uint32_t* T) {
   }
   const uint32_t l63 = T[NL], sticky = T[NL + 1];
   const uint32_t top = up[NL - 1] >> 31;
-  uint32_t rbit, st;
-  if (top) {
-    rbit = l63 >> 31;
-    st = (l63 & 0x7fffffffu) | sticky;
-  } else {
+  const uint32_t sft = 1u - top;  // a 2p - 1 bit product moves up one bit (no branch: lanes differ)
 #pragma unroll
-    for (int q = NL - 1; q > 0; --q) up[q] = (up[q] << 1) | (up[q - 1] >> 31);
-    up[0] = (up[0] << 1) | (l63 >> 31);
-    rbit = (l63 >> 30) & 1u;
-    st = (l63 & 0x3fffffffu) | sticky;
-  }
+  for (int q = NL - 1; q > 0; --q) up[q] = __funnelshift_l(up[q - 1], up[q], sft);
+  up[0] = __funnelshift_l(l63, up[0], sft);
+  const uint32_t rbit = (l63 >> (31u - sft)) & 1u;
+  const uint32_t st = (l63 & (0x7fffffffu >> sft)) | sticky;
   const uint32_t inc = rbit & ((st != 0u) | (up[0] & 1u));
   up[0] = add_cc(up[0], inc);
 #pragma unroll
@@ -616,15 +611,18 @@ __device__ __forceinline__ void sub_row(const uint32_t* xm, int8_t xs, int64_t x
       Bv[k + 2] = v.z;
       Bv[k + 3] = v.w;
     }
+    // bits [32 (f - 2) + d, +32) of B: limb f - 2 + q shifted right by r with
+    // the next one; Bq[i] = limb i - 2 + q of B (zero outside 0..NL-1)
+    uint32_t Bq[NL + 3];
+#pragma unroll
+    for (int i = 0; i < NL + 3; ++i) {
+      const uint32_t lo = (i - 2 >= 0 && i - 2 < NL) ? Bv[i - 2 >= 0 && i - 2 < NL ? i - 2 : 0] : 0u;
+      const uint32_t hi = (i - 1 >= 0 && i - 1 < NL) ? Bv[i - 1 >= 0 && i - 1 < NL ? i - 1 : 0] : 0u;
+      Bq[i] = q ? hi : lo;
+    }
     uint32_t Y[NL + 2];
 #pragma unroll
-    for (int f = 0; f < NL + 2; ++f) {
-      // bits [32 (f - 2) + d, +32) of B
-      const uint32_t b0 = (f - 2 >= 0 && f - 2 < NL) ? Bv[f - 2 < 0 ? 0 : (f - 2 < NL ? f - 2 : 0)] : 0u;
-      const uint32_t b1 = (f - 1 >= 0 && f - 1 < NL) ? Bv[f - 1 < 0 ? 0 : (f - 1 < NL ? f - 1 : 0)] : 0u;
-      const uint32_t b2 = (f < NL) ? Bv[f < NL ? f : 0] : 0u;
-      Y[f] = q ? __funnelshift_r(b1, b2, r) : __funnelshift_r(b0, b1, r);
-    }
+    for (int f = 0; f < NL + 2; ++f) Y[f] = __funnelshift_r(Bq[f], Bq[f + 1], r);
     F[0] = add_cc(Y[0] ^ inv, eff_sub ? 1u : 0u);
     F[1] = addc_cc(Y[1] ^ inv, 0u);
 #pragma unroll
@@ -648,13 +646,17 @@ __device__ __forceinline__ void sub_row(const uint32_t* xm, int8_t xs, int64_t x
     return;
   }
   // sh in [32, 65]: output limb l = frame bits [32 l + sh, +32)
+  // frame limb l + q2 shifted right by r2 with the next one (limb NL + 2 is sx)
   const int q2 = sh >> 5, r2 = sh & 31;
+  uint32_t Fq[NL + 1];
+#pragma unroll
+  for (int i = 0; i < NL + 1; ++i) {
+    const uint32_t f3 = (i + 2 < NL + 2) ? F[i + 2 < NL + 2 ? i + 2 : 0] : sx;
+    Fq[i] = (q2 == 1) ? F[i + 1] : f3;
+  }
   uint32_t M[NL];
 #pragma unroll
-  for (int l = 0; l < NL; ++l) {
-    const uint32_t f3 = (l + 3 < NL + 2) ? F[l + 3 < NL + 2 ? l + 3 : 0] : sx;
-    M[l] = (q2 == 1) ? __funnelshift_r(F[l + 1], F[l + 2], r2) : __funnelshift_r(F[l + 2], f3, r2);
-  }
+  for (int l = 0; l < NL; ++l) M[l] = __funnelshift_r(Fq[l], Fq[l + 1], r2);
   const uint64_t g64 = ((uint64_t)F[1] << 32) | F[0];
   const int rb = sh - 1;  // 31..64
   const uint32_t rbit = (rb < 64) ? (uint32_t)((g64 >> rb) & 1ull) : (F[2] & 1u);
