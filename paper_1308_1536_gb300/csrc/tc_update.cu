@@ -807,11 +807,13 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
   int8_t* sFl = reinterpret_cast<int8_t*>(sm + C::OFF_FL);
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + C::OFF_BAR);
   // bars: 0-3 full, 4-7 empty, 8-9 hfree, 10-11 tfull, 12-13 tfree; slot 14: tmem address; 15: error
-  // flag; 19-20 hready (B -> I: a column's Hankel cores and extra-K digits are built)
+  // flag; 19-20 hready (B -> I: a column's Hankel cores and extra-K digits are built); 21-24 xfull
+  // (one per subtraction warp: its rows' x_ij have arrived by bulk copy)
   uint32_t* tslot = reinterpret_cast<uint32_t*>(&bars[14]);
   volatile int* eflag = reinterpret_cast<volatile int*>(&bars[15]);
   const uint32_t b_full = su32(&bars[0]), b_empty = su32(&bars[4]), b_hfree = su32(&bars[8]);
-  const uint32_t b_tfull = su32(&bars[10]), b_tfree = su32(&bars[12]), b_hready = su32(&bars[19]);
+  const uint32_t b_tfull = su32(&bars[10]), b_tfree = su32(&bars[12]), b_hready = su32(&bars[19]),
+                 b_xfull = su32(&bars[21]);
   uint16_t* const sEb = reinterpret_cast<uint16_t*>(sm + C::OFF_EB);
   const int64_t N = a.N;
   const int64_t ncols = a.ncols;
@@ -867,6 +869,7 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(b_tfree + 8 * b), "r"(M));
     }
     for (int b = 0; b < 2; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b_hready + 8 * b));
+    for (int b = 0; b < 4; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b_xfull + 8 * b));
     *eflag = 0;
   }
   if (warp == 0) {
@@ -1188,15 +1191,27 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
     const bool active = i < rend;
     const int64_t irow = active ? i : i0;
     uint32_t* xrow = reinterpret_cast<uint32_t*>(sm + C::OFF_X) + r * RSTR;
-    // x_ij of the next column: mantissa by cp.async into this row's buffer,
-    // sign and exponent into registers
+    const uint32_t xbar = b_xfull + 8 * (warp - 4);
+    // x_ij of a column: the mantissa by one bulk copy per row into this
+    // row's buffer (completing on the warp's xfull barrier), sign and
+    // exponent into registers
+    auto fetch_x = [&](const int64_t ij) {
+      if ((tid & 31) == 0)
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(xbar), "r"(32 * NL * 4) : "memory");
+      __syncwarp();
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // this row's generic accesses come first
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                       su32(xrow)),
+                   "l"(X.m + ij * NL), "r"(NL * 4), "r"(xbar)
+                   : "memory");
+    };
     int8_t xs_n = 0;
     int64_t xe_n = ZEXP;
+    int pending = -1;  // column whose bulk copy is issued and not yet waited for
     if (nc > 0) {
       const int64_t ij = irow * N + colj(0);
-#pragma unroll
-      for (int q = 0; q < NL; q += 4) cp16(su32(xrow + q), X.m + ij * NL + q);
-      asm volatile("cp.async.commit_group;" ::: "memory");
+      fetch_x(ij);
+      pending = 0;
       xs_n = X.s[ij];
       xe_n = X.e[ij];
     }
@@ -1206,13 +1221,14 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
       const int8_t xs = xs_n;
       const int64_t xe = xe_n;
       bool okc = wait_bar(b_tfull + 8 * tb, (c >> 1) & 1);
+      okc = okc && wait_bar(xbar, c & 1);
       okc = __all_sync(0xffffffffu, okc) && !*eflag;
       okc = __all_sync(0xffffffffu, okc);
       if (!okc) {
         *eflag = 1;
         break;
       }
-      asm volatile("cp.async.wait_all;" ::: "memory");
+      pending = -1;
       int8_t rs = 0;
       int64_t re = ZEXP;
       if (active) {
@@ -1228,14 +1244,15 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
       }
       if (c + 1 < nc) {
         const int64_t ij2 = irow * N + colj(c + 1);
-#pragma unroll
-        for (int q = 0; q < NL; q += 4) cp16(su32(xrow + q), X.m + ij2 * NL + q);
-        asm volatile("cp.async.commit_group;" ::: "memory");
+        fetch_x(ij2);
+        pending = c + 1;
         xs_n = X.s[ij2];
         xe_n = X.e[ij2];
       }
     }
-    asm volatile("cp.async.wait_all;" ::: "memory");
+    // no bulk copy may still be writing this block's shared memory at exit
+    // (after an early stop); column c's copy completes the barrier's phase c
+    if (pending >= 0) wait_bar(xbar, pending & 1);
   }
   if (tid == 0 && *eflag) atomicExch(status, 5);  // MPDET_ETIMEOUT
   asm volatile("tcgen05.fence::before_thread_sync;");
