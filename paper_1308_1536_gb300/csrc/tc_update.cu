@@ -403,6 +403,7 @@ __device__ __noinline__ void sub_row_general(const uint32_t* xm, int8_t xs, int6
     re = xe;
     *rs_ = rs;
     *re_ = re;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     return;
   }
   const int8_t tsn = (int8_t)(ts ^ 1);
@@ -412,6 +413,7 @@ __device__ __noinline__ void sub_row_general(const uint32_t* xm, int8_t xs, int6
     re = te;
     *rs_ = rs;
     *re_ = re;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     return;
   }
   int cmp = (xe != te) ? (xe > te ? 1 : -1) : 0;
@@ -437,6 +439,7 @@ __device__ __noinline__ void sub_row_general(const uint32_t* xm, int8_t xs, int6
     re = eA;
     *rs_ = rs;
     *re_ = re;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     return;
   }
   const uint32_t inv = eff_sub ? 0xffffffffu : 0u;
@@ -532,6 +535,7 @@ __device__ __noinline__ void sub_row_general(const uint32_t* xm, int8_t xs, int6
       re = ZEXP;
       *rs_ = rs;
     *re_ = re;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     return;
     }
     sh = topbit - (p - 1);
@@ -558,6 +562,8 @@ __device__ __noinline__ void sub_row_general(const uint32_t* xm, int8_t xs, int6
   for (int q = 0; q < NL; q += 4) *reinterpret_cast<uint4*>(out + q) = make_uint4(M[q], M[q + 1], M[q + 2], M[q + 3]);
   *rs_ = sA;
   *re_ = (int64_t)topbit + 1 + eA - p - 64 + (int64_t)ovf;
+  // scr is the caller's x buffer, refilled next by a bulk copy (async proxy)
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 // The usual case inline (exponent gap below 64, at most 32 bits cancelled,
@@ -1199,7 +1205,8 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
       if ((tid & 31) == 0)
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(xbar), "r"(32 * NL * 4) : "memory");
       __syncwarp();
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // this row's generic accesses come first
+      // the buffer's earlier generic reads have returned their values; the
+      // general subtraction path, which also writes it, fences before returning
       asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                        su32(xrow)),
                    "l"(X.m + ij * NL), "r"(NL * 4), "r"(xbar)
