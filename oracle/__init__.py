@@ -64,10 +64,13 @@ def build(force: bool = False) -> str:
 
 
 def _load():
+    """Load the oracle library.  MPDET_ORACLE_LIB, when set, names another
+    build of it to load instead: the mutation tests point it at copies with a
+    planted mistake to show that the pins catch them."""
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
+            lib = ctypes.CDLL(os.environ.get("MPDET_ORACLE_LIB") or build())
             P = ctypes.c_void_p
             i64, i32 = ctypes.c_int64, ctypes.c_int
             lib.or_mul_v.argtypes = [i64, i32, P, P, P, P, P, P, P, P, P]

@@ -101,3 +101,50 @@ def test_tensor_engine_rare_subtraction_paths(mpdet, oracle_lib, p):
     st, zk, D, OX = oracle_lib.ge(A, N, p, lastcol=True, nthreads=16)
     a = run(mpdet, N, p, "f64", near, 1)
     assert a[:2] == (st, zk) and X.same(a[2], D) and X.same(a[3], OX)
+
+
+@pytest.mark.parametrize("p", [512, 1024, 2048])
+def test_tensor_engine_lazy_drain_fallback(mpdet, oracle_lib, p):
+    """The epilogue reads the low half of a product only when limbs n-8..n-2
+    of its upper part are all zeros or all ones above bit 14.  With a_00 = 1
+    the first step's multipliers are column 0 exactly, so column 0 and row 0
+    choose the products: (2^(p-1) + 1)(2^p - 1) has a low half of all ones,
+    (2^p - 1)^2 and products with a power of two have (almost) all zeros, the
+    random entries take the fast path.  Bit-identical to the IMAD engine and
+    the oracle."""
+    from fractions import Fraction
+
+    from test_oracle_ops import rand_num
+
+    g = np.random.Generator(np.random.PCG64(4242 + p))
+    N = 40
+    half, ones, top = (1 << (p - 1)) + 1, (1 << p) - 1, 1 << (p - 1)
+    col0 = [half, ones, top, None]
+    row0 = [ones, top, half, None]
+    vals = []
+    for i in range(N):
+        for j in range(N):
+            if i == 0 and j == 0:
+                v = Fraction(1)
+            elif j == 0:
+                m = col0[i % 4]
+                v = rand_num(g, p) if m is None else Fraction(m) * Fraction(2) ** (int(g.integers(-3, 4)) - p)
+            elif i == 0:
+                m = row0[j % 4]
+                v = rand_num(g, p) if m is None else Fraction(m) * Fraction(2) ** (int(g.integers(-3, 4)) - p)
+            else:
+                v = rand_num(g, p)
+            vals.append(v)
+    A = X.pack(vals, p)
+    out = []
+    for engine in (1, 0):
+        h = mpdet.Mpdet(N, p, lastcol=True)
+        h.tune(engine=engine, tc_min_rows=0)
+        h.set_mp(A)
+        rc, zk, D = h.factor()
+        out.append((rc, zk, D, h.get_mp()))
+        h.close()
+    assert out[0][:2] == out[1][:2]
+    assert X.same(out[0][2], out[1][2]) and X.same(out[0][3], out[1][3])
+    st, ozk, OD, OX = oracle_lib.ge(A, N, p, lastcol=True, nthreads=8)
+    assert out[0][:2] == (st, ozk) and X.same(out[0][2], OD) and X.same(out[0][3], OX)

@@ -132,6 +132,24 @@ def test_addsub_exponent_gaps(oracle_lib, p, kind):
 
 
 @pytest.mark.parametrize("p", PS)
+def test_addsub_power_of_two_far_operand(oracle_lib, p):
+    """A = +-1 (a power of two) minus or plus B at exponent gaps p-1 .. p+3.
+    Below a power of two the spacing halves, so at gap p+1 a B above half
+    that spacing moves A - B to the grid point under A: an exact-gap shortcut
+    that returns A one bit too early fails here."""
+    g = np.random.Generator(np.random.PCG64(77 + p))
+    a, b = [], []
+    ulp = Fraction(2) ** (-p + 1)  # ulp of A = 1 (mantissa 2^(p-1), value 1)
+    for d in (p - 1, p, p + 1, p + 2, p + 3):
+        for mb in ((1 << (p - 1)) + 1, 3 << (p - 2), (1 << p) - 1, int(g.integers(1 << 62, 1 << 63)) << (p - 63)):
+            y = Fraction(mb) * Fraction(2) ** (-p) * 2 * ulp * Fraction(2) ** (p - 1 - d)
+            a += [Fraction(1), Fraction(-1), Fraction(1)]
+            b += [y, -y, -y]
+    check_binary(oracle_lib, oracle_lib.sub, p, a, b, lambda x, y: x - y)
+    check_binary(oracle_lib, oracle_lib.add, p, a, b, lambda x, y: x + y)
+
+
+@pytest.mark.parametrize("p", PS)
 def test_sub_cancellation_ties_and_binade_drop(oracle_lib, p):
     g = np.random.Generator(np.random.PCG64(5 + p))
     a, b = [], []
