@@ -20,6 +20,7 @@
 // accumulate, M = 128, N = 128, K = 16), tcgen05.commit signals an mbarrier
 // per tile; every wait is bounded and reports MPDET_ETIMEOUT through the
 // status word; the block always frees its tensor memory.
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include "kernels.cuh"
@@ -340,33 +341,48 @@ __global__ void __launch_bounds__(128, 1) k_update_tc(MpArr X, UpdArgs a, MpArr 
 
 
 // ---------------------------------------------------------------------------
-// x_ij = RN(x_ij - t) for one row by one thread, the same rounding as
-// sub_round: the larger magnitude A sits in a frame of NL + 2 limbs above two
-// guard limbs, the smaller B is aligned into it (bits below the frame jammed
-// into a sticky bit), then normalisation and round to nearest even.  No data
-// crosses lanes.  Register path when the exponent gap is below 64 and at
-// most 32 bits cancel (the usual case); otherwise the frame goes through
-// scr (NL + 3 words of shared memory, this row's own).
-//   xm, tm: x's and t's mantissas (shared memory, 16-byte aligned)
-//   out:    the row's destination mantissa (global, 16-byte aligned)
-// Returns the result's sign and exponent in rs, re.
+// Row tiles.  The subtraction role's operands, x_ij of the next column and the
+// staged product t, sit per warp of 32 rows in the layout a TMA copy with
+// 128-byte swizzle writes: for NL >= 32 limbs [half of the row (128 bytes)]
+// [row r of the warp][32 words], the 16-byte chunk c of each 128-byte line
+// stored at chunk c ^ (r & 7); for NL = 16 [row][16 words] with 64-byte
+// swizzle, chunk c at c ^ ((r >> 1) & 3).  Eight consecutive rows then hit
+// eight different bank quads, so one thread per row reads or writes its row
+// 16 bytes at a time without bank conflicts.  Tiles are 1024-byte aligned.
 // ---------------------------------------------------------------------------
-// Round a staged exact product to p = 32 NL bits in place: T[0..NL) its
-// upper NL limbs, T[NL] limb NL - 1, T[NL + 1] the OR of the limbs below.  The
-// product of two normalised mantissas has 2p or 2p - 1 bits; returns the
-// exponent adjustment (-1, 0 or +1) as mul_round does.
 template <int NL>
-__device__ __forceinline__ int round_product(uint32_t* T) {
+struct RowT {
+  static constexpr int TILE = 32 * NL * 4;  // bytes per warp tile
+  unsigned char* tile;
+  uint32_t r;  // row within the warp, 0..31
+  __device__ __forceinline__ uint32_t off(int kk) const {  // byte offset of the row's 16-byte chunk kk
+    if constexpr (NL >= 32)
+      return (uint32_t)(kk >> 3) * 4096u + r * 128u + ((((uint32_t)kk & 7u) ^ (r & 7u)) << 4);
+    else
+      return r * 64u + ((((uint32_t)kk) ^ ((r >> 1) & 3u)) << 4);
+  }
+  __device__ __forceinline__ uint4 ld16(int kk) const { return *reinterpret_cast<const uint4*>(tile + off(kk)); }
+  __device__ __forceinline__ void st16(int kk, uint4 v) const { *reinterpret_cast<uint4*>(tile + off(kk)) = v; }
+  __device__ __forceinline__ uint32_t ld32(int i) const {
+    return *reinterpret_cast<const uint32_t*>(tile + off(i >> 2) + ((uint32_t)(i & 3) << 2));
+  }
+};
+
+// Round a staged exact product to p = 32 NL bits in place: T holds its upper NL
+// limbs, l63 its limb NL - 1 and sticky the OR of the limbs below.  The product
+// of two normalised mantissas has 2p or 2p - 1 bits; returns the exponent
+// adjustment (-1, 0 or +1) as mul_round does.
+template <int NL>
+__device__ __forceinline__ int round_product(const RowT<NL>& T, uint32_t l63, uint32_t sticky) {
   uint32_t up[NL];
 #pragma unroll
   for (int q = 0; q < NL; q += 4) {
-    const uint4 v = *reinterpret_cast<const uint4*>(T + q);
+    const uint4 v = T.ld16(q >> 2);
     up[q] = v.x;
     up[q + 1] = v.y;
     up[q + 2] = v.z;
     up[q + 3] = v.w;
   }
-  const uint32_t l63 = T[NL], sticky = T[NL + 1];
   const uint32_t top = up[NL - 1] >> 31;
   const uint32_t sft = 1u - top;  // a 2p - 1 bit product moves up one bit (no branch: lanes differ)
 #pragma unroll
@@ -381,45 +397,49 @@ __device__ __forceinline__ int round_product(uint32_t* T) {
   const uint32_t ovf = addc(0u, 0u);
   if (ovf) up[NL - 1] = 0x80000000u;
 #pragma unroll
-  for (int q = 0; q < NL; q += 4) *reinterpret_cast<uint4*>(T + q) = make_uint4(up[q], up[q + 1], up[q + 2], up[q + 3]);
+  for (int q = 0; q < NL; q += 4) T.st16(q >> 2, make_uint4(up[q], up[q + 1], up[q + 2], up[q + 3]));
   return (top ? 0 : -1) + (int)ovf;
 }
 
 template <int NL>
-__device__ __forceinline__ void copy_row(const uint32_t* src, uint32_t* out) {
+__device__ __forceinline__ void copy_row(const RowT<NL>& src, uint32_t* out) {
 #pragma unroll
-  for (int q = 0; q < NL; q += 4) *reinterpret_cast<uint4*>(out + q) = *reinterpret_cast<const uint4*>(src + q);
+  for (int q = 0; q < NL; q += 4) *reinterpret_cast<uint4*>(out + q) = src.ld16(q >> 2);
 }
 
+// ---------------------------------------------------------------------------
+// x_ij = RN(x_ij - t) for one row by one thread, the same rounding as
+// sub_round: the larger magnitude A sits in a frame of NL + 2 limbs above two
+// guard limbs, the smaller B is aligned into it (bits below the frame jammed
+// into a sticky bit), then normalisation and round to nearest even.  No data
+// crosses lanes.  sub_row handles the usual case in registers (exponent gap
+// below 64, at most 32 bits cancelled) and hands the rest to
+// sub_row_general, which recomputes from the unchanged operands with the
+// frame in thread-local memory.
+//   x, t: the row's x and t tiles;  out: the row's destination (global,
+//   16-byte aligned).  Returns the result's sign and exponent in rs, re.
+// ---------------------------------------------------------------------------
 template <int NL>
-__device__ __noinline__ void sub_row_general(const uint32_t* xm, int8_t xs, int64_t xe, const uint32_t* tm, int8_t ts,
-                                             int64_t te, uint32_t* out, uint32_t* scr, int8_t* rs_, int64_t* re_) {
-  int8_t rs;
-  int64_t re;
+__device__ __noinline__ void sub_row_general(RowT<NL> xr, int8_t xs, int64_t xe, RowT<NL> tr, int8_t ts, int64_t te,
+                                             uint32_t* out, int8_t* rs_, int64_t* re_) {
   constexpr int p = 32 * NL;
   if (te == ZEXP) {  // x - 0
-    copy_row<NL>(xm, out);
-    rs = xs;
-    re = xe;
-    *rs_ = rs;
-    *re_ = re;
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    copy_row<NL>(xr, out);
+    *rs_ = xs;
+    *re_ = xe;
     return;
   }
   const int8_t tsn = (int8_t)(ts ^ 1);
   if (xe == ZEXP) {  // 0 - t
-    copy_row<NL>(tm, out);
-    rs = tsn;
-    re = te;
-    *rs_ = rs;
-    *re_ = re;
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    copy_row<NL>(tr, out);
+    *rs_ = tsn;
+    *re_ = te;
     return;
   }
   int cmp = (xe != te) ? (xe > te ? 1 : -1) : 0;
   if (cmp == 0) {
     for (int i = NL - 1; i >= 0; --i) {
-      const uint32_t a = xm[i], b = tm[i];
+      const uint32_t a = xr.ld32(i), b = tr.ld32(i);
       if (a != b) {
         cmp = a > b ? 1 : -1;
         break;
@@ -427,132 +447,67 @@ __device__ __noinline__ void sub_row_general(const uint32_t* xm, int8_t xs, int6
     }
   }
   const bool swap = cmp < 0;
-  const uint32_t* Am = swap ? tm : xm;
-  const uint32_t* Bm = swap ? xm : tm;
+  const RowT<NL> A = swap ? tr : xr;
+  const RowT<NL> B = swap ? xr : tr;
   const int64_t eA = swap ? te : xe, eB = swap ? xe : te;
   const int8_t sA = swap ? tsn : xs, sB = swap ? xs : tsn;
   const bool eff_sub = (sA != sB);
   const int64_t dd = eA - eB;
   if (dd >= p + 2) {  // B below a quarter ulp of A
-    copy_row<NL>(Am, out);
-    rs = sA;
-    re = eA;
-    *rs_ = rs;
-    *re_ = re;
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    copy_row<NL>(A, out);
+    *rs_ = sA;
+    *re_ = eA;
     return;
   }
   const uint32_t inv = eff_sub ? 0xffffffffu : 0u;
   const int d = (int)dd;
-  // frame F = A * 2^64 +- (B aligned)
-  uint32_t F[NL + 2];
-  uint32_t sx;
-  if (d < 64) {
-    const int q = d >> 5, r = d & 31;
-    uint32_t Bv[NL];
-#pragma unroll
-    for (int k = 0; k < NL; k += 4) {
-      const uint4 v = *reinterpret_cast<const uint4*>(Bm + k);
-      Bv[k] = v.x;
-      Bv[k + 1] = v.y;
-      Bv[k + 2] = v.z;
-      Bv[k + 3] = v.w;
-    }
-    uint32_t Y[NL + 2];
-#pragma unroll
-    for (int f = 0; f < NL + 2; ++f) {
-      // bits [32 (f - 2) + d, +32) of B
-      const uint32_t b0 = (f - 2 >= 0 && f - 2 < NL) ? Bv[f - 2 < 0 ? 0 : (f - 2 < NL ? f - 2 : 0)] : 0u;
-      const uint32_t b1 = (f - 1 >= 0 && f - 1 < NL) ? Bv[f - 1 < 0 ? 0 : (f - 1 < NL ? f - 1 : 0)] : 0u;
-      const uint32_t b2 = (f < NL) ? Bv[f < NL ? f : 0] : 0u;
-      Y[f] = q ? __funnelshift_r(b1, b2, r) : __funnelshift_r(b0, b1, r);
-    }
-    F[0] = add_cc(Y[0] ^ inv, eff_sub ? 1u : 0u);
-    F[1] = addc_cc(Y[1] ^ inv, 0u);
-#pragma unroll
-    for (int k = 0; k < NL; k += 4) {
-      const uint4 a = *reinterpret_cast<const uint4*>(Am + k);
-      F[k + 2] = addc_cc(a.x, Y[k + 2] ^ inv);
-      F[k + 3] = addc_cc(a.y, Y[k + 3] ^ inv);
-      F[k + 4] = addc_cc(a.z, Y[k + 4] ^ inv);
-      F[k + 5] = addc_cc(a.w, Y[k + 5] ^ inv);
-    }
-    sx = addc(0u, 0u);
-  } else {
-    // bits of B below the frame (index d - 64 of B) go into the sticky bit
-    const int q = (d - 64) >> 5, r = (d - 64) & 31;
+  // frame F = A * 2^64 +- (B aligned): frame limb f holds bits
+  // [32 (f - 2) + d, +32) of B; the bits of B below the frame (index d - 64)
+  // are jammed into the lowest frame bit
+  uint32_t F[NL + 3];
+  {
+    const int q = (d - 64) >> 5, r = (d - 64) & 31;  // frame limb f holds B bits from 32 (f + q) + r
     bool lost = false;
-    for (int k = 0; k < q && k < NL; ++k) lost = lost || Bm[k] != 0u;
-    if (q < NL && r) lost = lost || (Bm[q] & ((1u << r) - 1u)) != 0u;
+    for (int k = 0; k < q && k < NL; ++k) lost = lost || B.ld32(k) != 0u;
+    if (q >= 0 && q < NL && r) lost = lost || (B.ld32(q) & ((1u << r) - 1u)) != 0u;
     uint32_t Y[NL + 2];
-#pragma unroll
     for (int f = 0; f < NL + 2; ++f) {
-      const int k = f + q;  // frame limb f holds bits [32 (f + q) + r, +32) of B
-      const uint32_t lo = (k < NL) ? Bm[k < NL ? k : 0] : 0u;
-      const uint32_t hi = (k + 1 < NL) ? Bm[k + 1 < NL ? k + 1 : 0] : 0u;
+      const int k = f + q;
+      const uint32_t lo = (k >= 0 && k < NL) ? B.ld32(k) : 0u;
+      const uint32_t hi = (k + 1 >= 0 && k + 1 < NL) ? B.ld32(k + 1) : 0u;
       Y[f] = __funnelshift_r(lo, hi, r);
     }
     Y[0] |= lost ? 1u : 0u;
     F[0] = add_cc(Y[0] ^ inv, eff_sub ? 1u : 0u);
     F[1] = addc_cc(Y[1] ^ inv, 0u);
 #pragma unroll
-    for (int k = 0; k < NL; ++k) F[k + 2] = addc_cc(Am[k], Y[k + 2] ^ inv);
-    sx = addc(0u, 0u);
+    for (int k = 0; k < NL; ++k) F[k + 2] = addc_cc(A.ld32(k), Y[k + 2] ^ inv);
+    F[NL + 2] = addc(0u, 0u);
+    if (eff_sub) F[NL + 2] = 0u;  // the carry out of A*2^64 + ~Y + 1
   }
-  if (eff_sub) sx = 0u;  // the carry out of A*2^64 + ~Y + 1
-  // top bit of the frame value (usual case: in the top two limbs or sx)
   int topbit = -1;
-  if (sx) topbit = 32 * (NL + 2);
-  else if (F[NL + 1]) topbit = 32 * (NL + 1) + 31 - __clz(F[NL + 1]);
-  else if (F[NL]) topbit = 32 * NL + 31 - __clz(F[NL]);
-  int sh = topbit - (p - 1);
-  uint32_t M[NL];
-  uint32_t rbit, st;
-  if (topbit >= 0 && sh >= 32) {
-    // sh in [32, 65]: output limb l = frame bits [32 l + sh, +32)
-    const int q2 = sh >> 5, r2 = sh & 31;
+  for (int k = NL + 2; k >= 0 && topbit < 0; --k)
+    if (F[k]) topbit = 32 * k + 31 - __clz(F[k]);
+  if (topbit < 0) {  // exact cancellation
 #pragma unroll
-    for (int l = 0; l < NL; ++l) {
-      const uint32_t f3 = (l + 3 < NL + 2) ? F[l + 3 < NL + 2 ? l + 3 : 0] : sx;
-      M[l] = (q2 == 1) ? __funnelshift_r(F[l + 1], F[l + 2], r2) : __funnelshift_r(F[l + 2], f3, r2);
-    }
-    const uint64_t g64 = ((uint64_t)F[1] << 32) | F[0];
-    const int rb = sh - 1;  // 31..64
-    rbit = (rb < 64) ? (uint32_t)((g64 >> rb) & 1ull) : (F[2] & 1u);
-    st = (rb < 64) ? (uint32_t)((g64 & ((1ull << rb) - 1ull)) != 0ull) : (uint32_t)(g64 != 0ull);
-  } else {
-    // more than 32 bits cancelled: the frame through shared memory
-#pragma unroll
-    for (int k = 0; k < NL + 2; ++k) scr[k] = F[k];
-    scr[NL + 2] = sx;
-    topbit = -1;
-    for (int k = NL + 2; k >= 0 && topbit < 0; --k)
-      if (scr[k]) topbit = 32 * k + 31 - __clz(scr[k]);
-    if (topbit < 0) {  // exact cancellation
-#pragma unroll
-      for (int q = 0; q < NL; q += 4) *reinterpret_cast<uint4*>(out + q) = make_uint4(0u, 0u, 0u, 0u);
-      rs = 0;
-      re = ZEXP;
-      *rs_ = rs;
-    *re_ = re;
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    for (int q = 0; q < NL; q += 4) *reinterpret_cast<uint4*>(out + q) = make_uint4(0u, 0u, 0u, 0u);
+    *rs_ = 0;
+    *re_ = ZEXP;
     return;
-    }
-    sh = topbit - (p - 1);
-#pragma unroll
-    for (int l = 0; l < NL; ++l) M[l] = funnel(scr, 32 * l + sh, NL + 3);
-    rbit = (sh >= 1) ? (funnel(scr, sh - 1, NL + 3) & 1u) : 0u;
-    bool stl = false;
-    if (sh >= 2) {
-      const int cut = sh - 1;  // bits [0, cut)
-      for (int k = 0; 32 * k < cut; ++k) {
-        const uint32_t m = (cut >= 32 * k + 32) ? 0xffffffffu : ((1u << (cut - 32 * k)) - 1u);
-        stl = stl || (scr[k] & m) != 0u;
-      }
-    }
-    st = stl ? 1u : 0u;
   }
-  const uint32_t inc = rbit & (st | (M[0] & 1u));
+  const int sh = topbit - (p - 1);
+  uint32_t M[NL];
+  for (int l = 0; l < NL; ++l) M[l] = funnel(F, 32 * l + sh, NL + 3);
+  const uint32_t rbit = (sh >= 1) ? (funnel(F, sh - 1, NL + 3) & 1u) : 0u;
+  bool stl = false;
+  if (sh >= 2) {
+    const int cut = sh - 1;  // bits [0, cut)
+    for (int k = 0; 32 * k < cut; ++k) {
+      const uint32_t m = (cut >= 32 * k + 32) ? 0xffffffffu : ((1u << (cut - 32 * k)) - 1u);
+      stl = stl || (F[k] & m) != 0u;
+    }
+  }
+  const uint32_t inc = rbit & ((stl ? 1u : 0u) | (M[0] & 1u));
   M[0] = add_cc(M[0], inc);
 #pragma unroll
   for (int l = 1; l < NL; ++l) M[l] = addc_cc(M[l], 0u);
@@ -562,23 +517,18 @@ __device__ __noinline__ void sub_row_general(const uint32_t* xm, int8_t xs, int6
   for (int q = 0; q < NL; q += 4) *reinterpret_cast<uint4*>(out + q) = make_uint4(M[q], M[q + 1], M[q + 2], M[q + 3]);
   *rs_ = sA;
   *re_ = (int64_t)topbit + 1 + eA - p - 64 + (int64_t)ovf;
-  // scr is the caller's x buffer, refilled next by a bulk copy (async proxy)
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// The usual case inline (exponent gap below 64, at most 32 bits cancelled,
-// frame in registers); everything else goes to sub_row_general, which
-// recomputes from the unchanged operands.
 template <int NL>
-__device__ __forceinline__ void sub_row(const uint32_t* xm, int8_t xs, int64_t xe, const uint32_t* tm, int8_t ts,
-                                        int64_t te, uint32_t* out, uint32_t* scr, int8_t& rs, int64_t& re) {
+__device__ __forceinline__ void sub_row(const RowT<NL>& xr, int8_t xs, int64_t xe, const RowT<NL>& tr, int8_t ts,
+                                        int64_t te, uint32_t* out, int8_t& rs, int64_t& re) {
   constexpr int p = 32 * NL;
   const int8_t tsn = (int8_t)(ts ^ 1);
   const bool tzero = te == ZEXP, xzero = xe == ZEXP;
   int cmp = (xe != te) ? (xe > te ? 1 : -1) : 0;
   if (!tzero && !xzero && cmp == 0) {
     for (int i = NL - 1; i >= 0; --i) {
-      const uint32_t a = xm[i], b = tm[i];
+      const uint32_t a = xr.ld32(i), b = tr.ld32(i);
       if (a != b) {
         cmp = a > b ? 1 : -1;
         break;
@@ -589,17 +539,17 @@ __device__ __forceinline__ void sub_row(const uint32_t* xm, int8_t xs, int64_t x
   const int64_t dd = swap ? te - xe : xe - te;
   if (tzero || xzero || dd >= p + 2) {  // x - 0, 0 - t, or the smaller below a quarter ulp of the larger
     const bool keep_x = tzero || (!xzero && !swap);
-    copy_row<NL>(keep_x ? xm : tm, out);
+    copy_row<NL>(keep_x ? xr : tr, out);
     rs = keep_x ? xs : tsn;
     re = keep_x ? xe : te;
     return;
   }
   if (dd >= 64) {
-    sub_row_general<NL>(xm, xs, xe, tm, ts, te, out, scr, &rs, &re);
+    sub_row_general<NL>(xr, xs, xe, tr, ts, te, out, &rs, &re);
     return;
   }
-  const uint32_t* Am = swap ? tm : xm;
-  const uint32_t* Bm = swap ? xm : tm;
+  const RowT<NL> A = swap ? tr : xr;
+  const RowT<NL> B = swap ? xr : tr;
   const int64_t eA = swap ? te : xe;
   const int8_t sA = swap ? tsn : xs, sB = swap ? xs : tsn;
   const bool eff_sub = (sA != sB);
@@ -611,7 +561,7 @@ __device__ __forceinline__ void sub_row(const uint32_t* xm, int8_t xs, int64_t x
     uint32_t Bv[NL];
 #pragma unroll
     for (int k = 0; k < NL; k += 4) {
-      const uint4 v = *reinterpret_cast<const uint4*>(Bm + k);
+      const uint4 v = B.ld16(k >> 2);
       Bv[k] = v.x;
       Bv[k + 1] = v.y;
       Bv[k + 2] = v.z;
@@ -633,7 +583,7 @@ __device__ __forceinline__ void sub_row(const uint32_t* xm, int8_t xs, int64_t x
     F[1] = addc_cc(Y[1] ^ inv, 0u);
 #pragma unroll
     for (int k = 0; k < NL; k += 4) {
-      const uint4 a = *reinterpret_cast<const uint4*>(Am + k);
+      const uint4 a = A.ld16(k >> 2);
       F[k + 2] = addc_cc(a.x, Y[k + 2] ^ inv);
       F[k + 3] = addc_cc(a.y, Y[k + 3] ^ inv);
       F[k + 4] = addc_cc(a.z, Y[k + 4] ^ inv);
@@ -648,11 +598,11 @@ __device__ __forceinline__ void sub_row(const uint32_t* xm, int8_t xs, int64_t x
   else if (F[NL]) topbit = 32 * NL + 31 - __clz(F[NL]);
   const int sh = topbit - (p - 1);
   if (topbit < 0 || sh < 32) {  // more than 32 bits cancelled
-    sub_row_general<NL>(xm, xs, xe, tm, ts, te, out, scr, &rs, &re);
+    sub_row_general<NL>(xr, xs, xe, tr, ts, te, out, &rs, &re);
     return;
   }
-  // sh in [32, 65]: output limb l = frame bits [32 l + sh, +32)
-  // frame limb l + q2 shifted right by r2 with the next one (limb NL + 2 is sx)
+  // sh in [32, 65]: output limb l = frame bits [32 l + sh, +32), i.e. frame
+  // limb l + q2 shifted right by r2 with the next one (limb NL + 2 is sx)
   const int q2 = sh >> 5, r2 = sh & 31;
   uint32_t Fq[NL + 1];
 #pragma unroll
@@ -734,7 +684,7 @@ struct Cfg {
   static constexpr int TCOLS = TILES * 128;         // allocated columns (a power of two >= 32)
   static constexpr int NCORE = 16 * TILES + KD / 8 - 1;  // Hankel cores
   static constexpr int HBYTES = (NCORE * 128 + 1023) / 1024 * 1024;
-  static constexpr int RSTR = NL + 4;               // words per staged row (uint4 rows hit distinct bank quads)
+  static constexpr int TILE = RowT<NL>::TILE;       // bytes per 32-row tile (swizzled rows)
   // Output tile t (positions [128 t, 128 t + 128)) receives products only
   // from reversed K positions k' in [KD - 128 (t + 1), 2 KD - 1 - 128 t]
   // (b~ has digits 0..KD): the K steps outside are all-zero Hankel corners and
@@ -756,16 +706,17 @@ struct Cfg {
   static constexpr int OFF_H = OFF_A + M * KA * 2;          // 2 Hankel buffers
   static constexpr int OFF_BX = OFF_H + 2 * HBYTES;         // 2 extra-K B buffers
   static constexpr int OFF_B = OFF_BX + 2 * XBYTES;         // 2 x NL limbs of b_j
-  static constexpr int OFF_T = OFF_B + 2 * NL * 4;          // 2 x M x RSTR words staged products
-  static constexpr int OFF_TE = OFF_T + 2 * M * RSTR * 4;   // 2 x M int64
+  static constexpr int OFF_T = (OFF_B + 2 * NL * 4 + 1023) / 1024 * 1024;  // 2 x 4 tiles: staged products
+  static constexpr int OFF_TA = OFF_T + 2 * 4 * TILE;       // 2 x M x 2 words: limb NL - 1 and sticky
+  static constexpr int OFF_TE = OFF_TA + 2 * M * 8;          // 2 x M int64
   static constexpr int OFF_TS = OFF_TE + 2 * M * 8;         // 2 x M int8
   static constexpr int OFF_FL = OFF_TS + 2 * M;             // M multiplier flags
-  static constexpr int OFF_X = (OFF_FL + M + 15) / 16 * 16;  // M x RSTR words: x_ij of the next column
-  static constexpr int OFF_EB = OFF_X + M * RSTR * 4;       // bf16 balanced digits of b, KD + 1 (+ pad)
+  static constexpr int OFF_X = (OFF_FL + M + 1023) / 1024 * 1024;  // 4 tiles: x_ij of the current column
+  static constexpr int OFF_EB = OFF_X + 4 * TILE;            // bf16 balanced digits of b, KD + 1 (+ pad)
   static constexpr int OFF_BAR = OFF_EB + (KD + 8) * 2;     // barriers
   static constexpr int SMEM = OFF_BAR + 256;
   static_assert(NL % 16 == 0 && NL <= 64, "tensor engine covers p = 512, 1024, 2048");
-  static_assert(OFF_X % 16 == 0 && OFF_BX % 16 == 0 && OFF_BAR % 8 == 0 && OFF_T % 16 == 0, "alignment");
+  static_assert(OFF_X % 1024 == 0 && OFF_T % 1024 == 0 && OFF_BX % 16 == 0 && OFF_BAR % 8 == 0, "alignment");
   static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
@@ -797,17 +748,25 @@ __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity) {
 
 template <int KD>
 __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a, MpArr Z, int* status, int p,
-                                                            int col_chunk) {
+                                                            int col_chunk, const __grid_constant__ CUtensorMap tmx0,
+                                                            const __grid_constant__ CUtensorMap tmx1) {
   using pipe::arrive;
   using pipe::wait_bar;
   using C = pipe::Cfg<KD>;
-  constexpr int NL = C::NL, TILES = C::TILES, RSTR = C::RSTR;
+  constexpr int NL = C::NL, TILES = C::TILES, TILE = C::TILE;
   extern __shared__ __align__(1024) unsigned char sm[];
   if (upd_stopped(status, a)) return;
   const int tid = threadIdx.x, warp = tid >> 5;
+  // the swizzled x tiles need a 1024-byte aligned window: refuse (MPDET_ECUDA)
+  // rather than copy with a layout the readers do not expect
+  if (su32(sm) & 1023u) {
+    if (tid == 0) atomicExch(status, 3);
+    return;
+  }
   unsigned char* sA = sm + C::OFF_A;
   uint32_t* sBl = reinterpret_cast<uint32_t*>(sm + C::OFF_B);
-  uint32_t* sT = reinterpret_cast<uint32_t*>(sm + C::OFF_T);
+  unsigned char* const sT = sm + C::OFF_T;  // [buffer][warp] tiles of staged products
+  uint32_t* const sTa = reinterpret_cast<uint32_t*>(sm + C::OFF_TA);  // [buffer][row]: limb NL - 1, sticky
   int64_t* sTe = reinterpret_cast<int64_t*>(sm + C::OFF_TE);
   int8_t* sTs = reinterpret_cast<int8_t*>(sm + C::OFF_TS);
   int8_t* sFl = reinterpret_cast<int8_t*>(sm + C::OFF_FL);
@@ -1070,7 +1029,7 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
         bs_n = X.s[a.brow * N + colj(c + 1)];
       }
       const bool used = have && be != ZEXP;  // the row's product is used
-      uint32_t* Trow = sT + tb * (M * RSTR) + r * RSTR;
+      const RowT<NL> Tw{sT + (tb * 4 + warp) * TILE, (uint32_t)(tid & 31)};
       uint32_t l63 = 0, sticky = 0;
       int64_t acc = 0;
       bool okc = true;
@@ -1126,8 +1085,8 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
         uint32_t lim[8];
         limbs8(cur, kv, lim, acc);
         if (upper) {
-          *reinterpret_cast<uint4*>(Trow + 8 * k - NL) = make_uint4(lim[0], lim[1], lim[2], lim[3]);
-          *reinterpret_cast<uint4*>(Trow + 8 * k - NL + 4) = make_uint4(lim[4], lim[5], lim[6], lim[7]);
+          Tw.st16(2 * k - NL / 4, make_uint4(lim[0], lim[1], lim[2], lim[3]));
+          Tw.st16(2 * k - NL / 4 + 1, make_uint4(lim[4], lim[5], lim[6], lim[7]));
           return;
         }
         // k == K0: limbs NL - 8 .. NL - 1 with a zero carry in
@@ -1184,8 +1143,8 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
         break;
       }
       const bool tz = !have || be == ZEXP;
-      Trow[NL] = l63;
-      Trow[NL + 1] = sticky;
+      sTa[(tb * M + r) * 2] = l63;
+      sTa[(tb * M + r) * 2 + 1] = sticky;
       sTe[tb * M + r] = tz ? ZEXP : zexp + be;  // before rounding
       sTs[tb * M + r] = tz ? (int8_t)0 : (int8_t)(zsign ^ bs);
       arrive(b_tfull + 8 * tb);
@@ -1196,31 +1155,41 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
     const int64_t i = i0 + r;
     const bool active = i < rend;
     const int64_t irow = active ? i : i0;
-    uint32_t* xrow = reinterpret_cast<uint32_t*>(sm + C::OFF_X) + r * RSTR;
-    const uint32_t xbar = b_xfull + 8 * (warp - 4);
-    // x_ij of a column: the mantissa by one bulk copy per row into this
-    // row's buffer (completing on the warp's xfull barrier), sign and
-    // exponent into registers
-    auto fetch_x = [&](const int64_t ij) {
-      if ((tid & 31) == 0)
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(xbar), "r"(32 * NL * 4) : "memory");
+    const int w = warp - 4;
+    unsigned char* const xtile = sm + C::OFF_X + w * TILE;
+    const RowT<NL> Xr{xtile, (uint32_t)(tid & 31)};
+    const uint32_t xbar = b_xfull + 8 * w;
+    // x_ij of a column for the warp's 32 rows: one TMA copy per 128-byte half
+    // of the rows (rows beyond N read as zero), completing on the warp's xfull
+    // barrier; sign and exponent into registers.  The tile's earlier generic
+    // reads have returned their values before the warp reaches this point.
+    auto fetch_x = [&](const int64_t j) {
       __syncwarp();
-      // the buffer's earlier generic reads have returned their values; the
-      // general subtraction path, which also writes it, fences before returning
-      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                       su32(xrow)),
-                   "l"(X.m + ij * NL), "r"(NL * 4), "r"(xbar)
-                   : "memory");
+      if ((tid & 31) == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(xbar), "r"(TILE) : "memory");
+        const int row0 = (int)(i0 + 32 * w), col = (int)j;
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+                su32(xtile)),
+            "l"(reinterpret_cast<uint64_t>(&tmx0)), "r"(0), "r"(col), "r"(row0), "r"(xbar)
+            : "memory");
+        if (NL > 32)
+          asm volatile(
+              "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+                  su32(xtile + 4096)),
+              "l"(reinterpret_cast<uint64_t>(&tmx1)), "r"(0), "r"(col), "r"(row0), "r"(xbar)
+              : "memory");
+      }
     };
     int8_t xs_n = 0;
     int64_t xe_n = ZEXP;
-    int pending = -1;  // column whose bulk copy is issued and not yet waited for
+    int pending = -1;  // column whose copy is issued and not yet waited for
     if (nc > 0) {
-      const int64_t ij = irow * N + colj(0);
-      fetch_x(ij);
+      const int64_t j = colj(0);
+      fetch_x(j);
       pending = 0;
-      xs_n = X.s[ij];
-      xe_n = X.e[ij];
+      xs_n = X.s[irow * N + j];
+      xe_n = X.e[irow * N + j];
     }
     for (int c = 0; c < nc; ++c) {
       const int tb = c & 1;
@@ -1239,10 +1208,10 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
       int8_t rs = 0;
       int64_t re = ZEXP;
       if (active) {
-        uint32_t* Tr = sT + tb * (M * RSTR) + r * RSTR;
+        const RowT<NL> Tr{sT + (tb * 4 + w) * TILE, (uint32_t)(tid & 31)};
         int64_t te = sTe[tb * M + r];
-        if (te != ZEXP) te += round_product<NL>(Tr);
-        sub_row<NL>(xrow, xs, xe, Tr, sTs[tb * M + r], te, X.m + ij * NL, xrow, rs, re);
+        if (te != ZEXP) te += round_product<NL>(Tr, sTa[(tb * M + r) * 2], sTa[(tb * M + r) * 2 + 1]);
+        sub_row<NL>(Xr, xs, xe, Tr, sTs[tb * M + r], te, X.m + ij * NL, rs, re);
       }
       arrive(b_tfree + 8 * tb);
       if (active) {
@@ -1250,15 +1219,15 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
         X.e[ij] = re;
       }
       if (c + 1 < nc) {
-        const int64_t ij2 = irow * N + colj(c + 1);
-        fetch_x(ij2);
+        const int64_t j2 = colj(c + 1);
+        fetch_x(j2);
         pending = c + 1;
-        xs_n = X.s[ij2];
-        xe_n = X.e[ij2];
+        xs_n = X.s[irow * N + j2];
+        xe_n = X.e[irow * N + j2];
       }
     }
-    // no bulk copy may still be writing this block's shared memory at exit
-    // (after an early stop); column c's copy completes the barrier's phase c
+    // no copy may still be writing this block's shared memory at exit (after
+    // an early stop); column c's copy completes the barrier's phase c
     if (pending >= 0) wait_bar(xbar, pending & 1);
   }
   if (tid == 0 && *eflag) atomicExch(status, 5);  // MPDET_ETIMEOUT
@@ -1269,6 +1238,45 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
 
 
 }  // namespace tc
+
+// cuTensorMapEncodeTiled from the driver, through the runtime's entry-point
+// query (no link against the driver library).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled() {
+  static const EncodeTiledFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<EncodeTiledFn>(f);
+  }();
+  return fn;
+}
+
+// Tensor maps for the subtraction role's x copies: half h (128 bytes, or the
+// whole 64-byte row at n = 16) of every number of the N x N array as a 3-D
+// tensor (words, column, row); a box is 1 column x 32 rows, written with the
+// swizzle RowT reads.
+static cudaError_t x_tensor_maps(MpArr X, int64_t N, int nl, CUtensorMap (&tm)[2]) {
+  const EncodeTiledFn enc = encode_tiled();
+  if (!enc) return cudaErrorNotSupported;
+  const int d0 = nl < 32 ? nl : 32;
+  for (int h = 0; h < 2; ++h) {
+    const int hh = nl > 32 ? h : 0;
+    const cuuint64_t dims[3] = {(cuuint64_t)d0, (cuuint64_t)N, (cuuint64_t)N};
+    const cuuint64_t strides[2] = {(cuuint64_t)nl * 4, (cuuint64_t)N * nl * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)d0, 1, 32};
+    const cuuint32_t es[3] = {1, 1, 1};
+    const CUresult r = enc(&tm[h], CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, X.m + 32 * hh, dims, strides, box, es,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, nl >= 32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                           CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  }
+  return cudaSuccess;
+}
 
 // Launch: 128-row blocks x column chunks sized to fill the SMs once.
 cudaError_t update_tc(MpArr X, const UpdArgs& a, MpArr Z, int* status, int p, int nsm, cudaStream_t st,
@@ -1283,18 +1291,24 @@ cudaError_t update_tc(MpArr X, const UpdArgs& a, MpArr Z, int* status, int p, in
   bx = (ncols + chunk - 1) / chunk;
   dim3 grid((unsigned)bx, (unsigned)by);
   if (pipelined) {
+    CUtensorMap tm[2];
+    const cudaError_t e = x_tensor_maps(X, a.N, p / 32, tm);
+    if (e != cudaSuccess) return e;
     switch (p) {
       case 512:
         cudaFuncSetAttribute(tc::k_update_tcp<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::pipe::Cfg<64>::SMEM);
-        tc::k_update_tcp<64><<<grid, tc::pipe::NTH, tc::pipe::Cfg<64>::SMEM, st>>>(X, a, Z, status, p, (int)chunk);
+        tc::k_update_tcp<64><<<grid, tc::pipe::NTH, tc::pipe::Cfg<64>::SMEM, st>>>(X, a, Z, status, p, (int)chunk, tm[0],
+                                                                                       tm[1]);
         break;
       case 1024:
         cudaFuncSetAttribute(tc::k_update_tcp<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::pipe::Cfg<128>::SMEM);
-        tc::k_update_tcp<128><<<grid, tc::pipe::NTH, tc::pipe::Cfg<128>::SMEM, st>>>(X, a, Z, status, p, (int)chunk);
+        tc::k_update_tcp<128><<<grid, tc::pipe::NTH, tc::pipe::Cfg<128>::SMEM, st>>>(X, a, Z, status, p, (int)chunk, tm[0],
+                                                                                       tm[1]);
         break;
       case 2048:
         cudaFuncSetAttribute(tc::k_update_tcp<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::pipe::Cfg<256>::SMEM);
-        tc::k_update_tcp<256><<<grid, tc::pipe::NTH, tc::pipe::Cfg<256>::SMEM, st>>>(X, a, Z, status, p, (int)chunk);
+        tc::k_update_tcp<256><<<grid, tc::pipe::NTH, tc::pipe::Cfg<256>::SMEM, st>>>(X, a, Z, status, p, (int)chunk, tm[0],
+                                                                                       tm[1]);
         break;
       default:
         return cudaErrorInvalidValue;
