@@ -407,6 +407,14 @@ __device__ __forceinline__ void copy_row(const RowT<NL>& src, uint32_t* out) {
   for (int q = 0; q < NL; q += 4) *reinterpret_cast<uint4*>(out + q) = src.ld16(q >> 2);
 }
 
+// The row of src into the row of out (nothing to do when they are the same).
+template <int NL>
+__device__ __forceinline__ void put_row(const RowT<NL>& src, const RowT<NL>& out) {
+  if (src.tile == out.tile) return;
+#pragma unroll
+  for (int q = 0; q < NL; q += 4) out.st16(q >> 2, src.ld16(q >> 2));
+}
+
 // ---------------------------------------------------------------------------
 // x_ij = RN(x_ij - t) for one row by one thread, the same rounding as
 // sub_round: the larger magnitude A sits in a frame of NL + 2 limbs above two
@@ -416,22 +424,23 @@ __device__ __forceinline__ void copy_row(const RowT<NL>& src, uint32_t* out) {
 // below 64, at most 32 bits cancelled) and hands the rest to
 // sub_row_general, which recomputes from the unchanged operands with the
 // frame in thread-local memory.
-//   x, t: the row's x and t tiles;  out: the row's destination (global,
-//   16-byte aligned).  Returns the result's sign and exponent in rs, re.
+//   x, t: the row's x and t tiles;  out: the row's destination tile (t's
+//   own: every read of an operand comes before the first write of the
+//   result).  Returns the result's sign and exponent in rs, re.
 // ---------------------------------------------------------------------------
 template <int NL>
 __device__ __noinline__ void sub_row_general(RowT<NL> xr, int8_t xs, int64_t xe, RowT<NL> tr, int8_t ts, int64_t te,
-                                             uint32_t* out, int8_t* rs_, int64_t* re_) {
+                                             RowT<NL> out, int8_t* rs_, int64_t* re_) {
   constexpr int p = 32 * NL;
   if (te == ZEXP) {  // x - 0
-    copy_row<NL>(xr, out);
+    put_row<NL>(xr, out);
     *rs_ = xs;
     *re_ = xe;
     return;
   }
   const int8_t tsn = (int8_t)(ts ^ 1);
   if (xe == ZEXP) {  // 0 - t
-    copy_row<NL>(tr, out);
+    put_row<NL>(tr, out);
     *rs_ = tsn;
     *re_ = te;
     return;
@@ -454,7 +463,7 @@ __device__ __noinline__ void sub_row_general(RowT<NL> xr, int8_t xs, int64_t xe,
   const bool eff_sub = (sA != sB);
   const int64_t dd = eA - eB;
   if (dd >= p + 2) {  // B below a quarter ulp of A
-    copy_row<NL>(A, out);
+    put_row<NL>(A, out);
     *rs_ = sA;
     *re_ = eA;
     return;
@@ -490,7 +499,7 @@ __device__ __noinline__ void sub_row_general(RowT<NL> xr, int8_t xs, int64_t xe,
     if (F[k]) topbit = 32 * k + 31 - __clz(F[k]);
   if (topbit < 0) {  // exact cancellation
 #pragma unroll
-    for (int q = 0; q < NL; q += 4) *reinterpret_cast<uint4*>(out + q) = make_uint4(0u, 0u, 0u, 0u);
+    for (int q = 0; q < NL; q += 4) out.st16(q >> 2, make_uint4(0u, 0u, 0u, 0u));
     *rs_ = 0;
     *re_ = ZEXP;
     return;
@@ -514,14 +523,14 @@ __device__ __noinline__ void sub_row_general(RowT<NL> xr, int8_t xs, int64_t xe,
   const uint32_t ovf = addc(0u, 0u);
   if (ovf) M[NL - 1] = 0x80000000u;  // every limb wrapped to 0
 #pragma unroll
-  for (int q = 0; q < NL; q += 4) *reinterpret_cast<uint4*>(out + q) = make_uint4(M[q], M[q + 1], M[q + 2], M[q + 3]);
+  for (int q = 0; q < NL; q += 4) out.st16(q >> 2, make_uint4(M[q], M[q + 1], M[q + 2], M[q + 3]));
   *rs_ = sA;
   *re_ = (int64_t)topbit + 1 + eA - p - 64 + (int64_t)ovf;
 }
 
 template <int NL>
 __device__ __forceinline__ void sub_row(const RowT<NL>& xr, int8_t xs, int64_t xe, const RowT<NL>& tr, int8_t ts,
-                                        int64_t te, uint32_t* out, int8_t& rs, int64_t& re) {
+                                        int64_t te, const RowT<NL>& out, int8_t& rs, int64_t& re) {
   constexpr int p = 32 * NL;
   const int8_t tsn = (int8_t)(ts ^ 1);
   const bool tzero = te == ZEXP, xzero = xe == ZEXP;
@@ -539,7 +548,7 @@ __device__ __forceinline__ void sub_row(const RowT<NL>& xr, int8_t xs, int64_t x
   const int64_t dd = swap ? te - xe : xe - te;
   if (tzero || xzero || dd >= p + 2) {  // x - 0, 0 - t, or the smaller below a quarter ulp of the larger
     const bool keep_x = tzero || (!xzero && !swap);
-    copy_row<NL>(keep_x ? xr : tr, out);
+    put_row<NL>(keep_x ? xr : tr, out);
     rs = keep_x ? xs : tsn;
     re = keep_x ? xe : te;
     return;
@@ -624,7 +633,7 @@ __device__ __forceinline__ void sub_row(const RowT<NL>& xr, int8_t xs, int64_t x
   const uint32_t ovf = addc(0u, 0u);
   if (ovf) M[NL - 1] = 0x80000000u;  // every limb wrapped to 0
 #pragma unroll
-  for (int k = 0; k < NL; k += 4) *reinterpret_cast<uint4*>(out + k) = make_uint4(M[k], M[k + 1], M[k + 2], M[k + 3]);
+  for (int k = 0; k < NL; k += 4) out.st16(k >> 2, make_uint4(M[k], M[k + 1], M[k + 2], M[k + 3]));
   rs = sA;
   re = (int64_t)topbit + 1 + eA - p - 64 + (int64_t)ovf;
 }
@@ -710,8 +719,7 @@ struct Cfg {
   static constexpr int OFF_TA = OFF_T + 2 * 4 * TILE;       // 2 x M x 2 words: limb NL - 1 and sticky
   static constexpr int OFF_TE = OFF_TA + 2 * M * 8;          // 2 x M int64
   static constexpr int OFF_TS = OFF_TE + 2 * M * 8;         // 2 x M int8
-  static constexpr int OFF_FL = OFF_TS + 2 * M;             // M multiplier flags
-  static constexpr int OFF_X = (OFF_FL + M + 1023) / 1024 * 1024;  // 4 tiles: x_ij of the current column
+  static constexpr int OFF_X = (OFF_TS + 2 * M + 1023) / 1024 * 1024;  // 4 tiles: x_ij of the current column
   static constexpr int OFF_EB = OFF_X + 4 * TILE;            // bf16 balanced digits of b, KD + 1 (+ pad)
   static constexpr int OFF_BAR = OFF_EB + (KD + 8) * 2;     // barriers
   static constexpr int SMEM = OFF_BAR + 256;
@@ -769,16 +777,16 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
   uint32_t* const sTa = reinterpret_cast<uint32_t*>(sm + C::OFF_TA);  // [buffer][row]: limb NL - 1, sticky
   int64_t* sTe = reinterpret_cast<int64_t*>(sm + C::OFF_TE);
   int8_t* sTs = reinterpret_cast<int8_t*>(sm + C::OFF_TS);
-  int8_t* sFl = reinterpret_cast<int8_t*>(sm + C::OFF_FL);
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + C::OFF_BAR);
   // bars: 0-3 full, 4-7 empty, 8-9 hfree, 10-11 tfull, 12-13 tfree; slot 14: tmem address; 15: error
-  // flag; 19-20 hready (B -> I: a column's Hankel cores and extra-K digits are built); 21-24 xfull
-  // (one per subtraction warp: its rows' x_ij have arrived by bulk copy)
+  // flag; 16 aready (E -> I: the multipliers' digits are in A); 19-20 hready (B -> I: a column's
+  // Hankel cores and extra-K digits are built); 21-24 xfull (one per subtraction warp: its rows'
+  // x_ij have arrived)
   uint32_t* tslot = reinterpret_cast<uint32_t*>(&bars[14]);
   volatile int* eflag = reinterpret_cast<volatile int*>(&bars[15]);
   const uint32_t b_full = su32(&bars[0]), b_empty = su32(&bars[4]), b_hfree = su32(&bars[8]);
   const uint32_t b_tfull = su32(&bars[10]), b_tfree = su32(&bars[12]), b_hready = su32(&bars[19]),
-                 b_xfull = su32(&bars[21]);
+                 b_xfull = su32(&bars[21]), b_aready = su32(&bars[16]);
   uint16_t* const sEb = reinterpret_cast<uint16_t*>(sm + C::OFF_EB);
   const int64_t N = a.N;
   const int64_t ncols = a.ncols;
@@ -792,33 +800,7 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
     return upd_col(a, cc);
   };
 
-  // ---- set-up: A (rows by warps 0-3), barriers, tensor memory ------------
-  if (tid < M) {
-    const int64_t i = i0 + tid;
-    const bool have = i < rend && Z.e[i < rend ? i : i0] != ZEXP;
-    const uint32_t* zm = Z.m + (i < rend ? i : i0) * NL;
-    unsigned char* rowbase = sA + (tid >> 3) * (C::KA * 16) + (tid & 7) * 16;
-    // balanced digits of z (the top carry is the 2^p of z = z' + 2^p), digit
-    // s at k' = KD - 1 - s: limb L's four digits fill k' = KD - 4 - 4L .. KD - 1 - 4L
-    int cy = 0;
-    for (int L = 0; L < NL; ++L) {
-      const uint32_t w = have ? zm[L] : 0u;
-      int e[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int t = (int)((w >> (8 * q)) & 255u) + cy;
-        cy = t >= 128 ? 1 : 0;
-        e[q] = t - (cy << 8);
-      }
-      const int k0 = KD - 4 - 4 * L;
-      *reinterpret_cast<uint2*>(rowbase + (k0 >> 3) * 128 + (k0 & 7) * 2) =
-          make_uint2(pipe::dbfs(e[3]) | (pipe::dbfs(e[2]) << 16), pipe::dbfs(e[1]) | (pipe::dbfs(e[0]) << 16));
-    }
-    // the extra K step: 1 at k' = KD, zeros after it
-    *reinterpret_cast<uint4*>(rowbase + (KD / 8) * 128) = make_uint4(0x3F80u, 0u, 0u, 0u);
-    *reinterpret_cast<uint4*>(rowbase + (KD / 8 + 1) * 128) = make_uint4(0u, 0u, 0u, 0u);
-    sFl[tid] = have ? 1 : 0;
-  }
+  // ---- set-up: barriers, tensor memory, zero Hankel corners ----------------
   // the Hankel cores outside the digit window are zero for every column
   static_assert(C::OFF_BX == C::OFF_H + 2 * C::HBYTES, "Hankel and extra-K buffers are contiguous");
   for (int q = tid; q < (2 * C::HBYTES + 2 * C::XBYTES) / 16; q += pipe::NTH)
@@ -835,6 +817,7 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
     }
     for (int b = 0; b < 2; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b_hready + 8 * b));
     for (int b = 0; b < 4; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b_xfull + 8 * b));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(b_aready), "r"(M));
     *eflag = 0;
   }
   if (warp == 0) {
@@ -856,7 +839,9 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
     if ((tid & 31) == 0) {
       const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
       const uint32_t idesc2 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((2 * NT) >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-      for (int c = 0; c < nc; ++c) {
+      const bool aok = nc <= 0 || wait_bar(b_aready, 0);
+      if (!aok) *eflag = 1;
+      for (int c = 0; c < nc && aok; ++c) {
         const int hb = c & 1;
         unsigned char* sH = sm + C::OFF_H + hb * C::HBYTES;
         if (!wait_bar(b_hready + 8 * hb, (c >> 1) & 1) || *eflag) {
@@ -1008,7 +993,40 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
     const int r = tid;
     const int8_t zsign = (i0 + r < rend) ? Z.s[i0 + r] : 0;
     const int64_t zexp = (i0 + r < rend) ? Z.e[i0 + r] : ZEXP;
-    const bool have = sFl[r] != 0;
+    const bool have = zexp != ZEXP;
+    {
+      // A: the balanced digits of this row's multiplier (the top carry is the
+      // 2^p of z = z' + 2^p), digit s at k' = KD - 1 - s: limb L's four digits
+      // fill k' = KD - 4 - 4L .. KD - 1 - 4L; then the extra K step's 1 at
+      // k' = KD and zeros after it.  The row's limbs arrive by vector loads
+      // issued together.
+      const uint32_t* zm = Z.m + (have ? i0 + r : i0) * NL;
+      unsigned char* rowbase = sA + (r >> 3) * (C::KA * 16) + (r & 7) * 16;
+      uint4 zv[NL / 4];
+#pragma unroll
+      for (int q = 0; q < NL / 4; ++q)
+        zv[q] = have ? *reinterpret_cast<const uint4*>(zm + 4 * q) : make_uint4(0u, 0u, 0u, 0u);
+      int cy = 0;
+#pragma unroll
+      for (int L = 0; L < NL; ++L) {
+        const uint4 v4 = zv[L >> 2];
+        const uint32_t w = (L & 3) == 0 ? v4.x : (L & 3) == 1 ? v4.y : (L & 3) == 2 ? v4.z : v4.w;
+        int e[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int t = (int)((w >> (8 * q)) & 255u) + cy;
+          cy = t >= 128 ? 1 : 0;
+          e[q] = t - (cy << 8);
+        }
+        const int k0 = KD - 4 - 4 * L;
+        *reinterpret_cast<uint2*>(rowbase + (k0 >> 3) * 128 + (k0 & 7) * 2) =
+            make_uint2(pipe::dbfs(e[3]) | (pipe::dbfs(e[2]) << 16), pipe::dbfs(e[1]) | (pipe::dbfs(e[0]) << 16));
+      }
+      *reinterpret_cast<uint4*>(rowbase + (KD / 8) * 128) = make_uint4(0x3F80u, 0u, 0u, 0u);
+      *reinterpret_cast<uint4*>(rowbase + (KD / 8 + 1) * 128) = make_uint4(0u, 0u, 0u, 0u);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // A is read by the tensor core
+      arrive(b_aready);
+    }
     constexpr int NCH = 4 * TILES;    // chunks of 32 sums (8 limbs)
     constexpr int K0 = NL / 8 - 1;     // first chunk read: limbs NL - 8 .. NL - 1
     constexpr int T0 = K0 >> 2;        // its tile
@@ -1159,6 +1177,24 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
     unsigned char* const xtile = sm + C::OFF_X + w * TILE;
     const RowT<NL> Xr{xtile, (uint32_t)(tid & 31)};
     const uint32_t xbar = b_xfull + 8 * w;
+    // The results replace the staged products in the warp's T tile and leave
+    // by one TMA store per 128-byte half, unless the tile holds rows in
+    // [rend, N) (back substitution), which are not this launch's to write:
+    // then each thread stores its own row.
+    const bool tma_out = rend >= N || i0 + 32 * w + 32 <= rend;
+    auto store_tile = [&](const unsigned char* tile, const int64_t j) {
+      const int row0 = (int)(i0 + 32 * w), col = (int)j;
+      asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+                       reinterpret_cast<uint64_t>(&tmx0)),
+                   "r"(0), "r"(col), "r"(row0), "r"(su32(tile))
+                   : "memory");
+      if (NL > 32)
+        asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+                         reinterpret_cast<uint64_t>(&tmx1)),
+                     "r"(0), "r"(col), "r"(row0), "r"(su32(tile + 4096))
+                     : "memory");
+      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    };
     // x_ij of a column for the warp's 32 rows: one TMA copy per 128-byte half
     // of the rows (rows beyond N read as zero), completing on the warp's xfull
     // barrier; sign and exponent into registers.  The tile's earlier generic
@@ -1205,15 +1241,28 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
         break;
       }
       pending = -1;
+      // the previous column's store has read its tile: the epilogue may
+      // stage into that buffer again
+      if (c > 0) {
+        if ((tid & 31) == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+        __syncwarp();
+        arrive(b_tfree + 8 * (tb ^ 1));
+      }
       int8_t rs = 0;
       int64_t re = ZEXP;
+      const RowT<NL> Tr{sT + (tb * 4 + w) * TILE, (uint32_t)(tid & 31)};
       if (active) {
-        const RowT<NL> Tr{sT + (tb * 4 + w) * TILE, (uint32_t)(tid & 31)};
         int64_t te = sTe[tb * M + r];
         if (te != ZEXP) te += round_product<NL>(Tr, sTa[(tb * M + r) * 2], sTa[(tb * M + r) * 2 + 1]);
-        sub_row<NL>(Xr, xs, xe, Tr, sTs[tb * M + r], te, X.m + ij * NL, rs, re);
+        sub_row<NL>(Xr, xs, xe, Tr, sTs[tb * M + r], te, Tr, rs, re);
       }
-      arrive(b_tfree + 8 * tb);
+      if (tma_out) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the results, to the TMA store
+        __syncwarp();
+        if ((tid & 31) == 0) store_tile(Tr.tile, colj(c));
+      } else if (active) {
+        copy_row<NL>(Tr, X.m + ij * NL);
+      }
       if (active) {
         X.s[ij] = rs;
         X.e[ij] = re;
@@ -1226,8 +1275,10 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
         xe_n = X.e[irow * N + j2];
       }
     }
-    // no copy may still be writing this block's shared memory at exit (after
-    // an early stop); column c's copy completes the barrier's phase c
+    // no copy may still be writing this block's shared memory, and no store
+    // reading it, at exit (after an early stop too); column c's copy
+    // completes the barrier's phase c
+    if ((tid & 31) == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
     if (pending >= 0) wait_bar(xbar, pending & 1);
   }
   if (tid == 0 && *eflag) atomicExch(status, 5);  // MPDET_ETIMEOUT
