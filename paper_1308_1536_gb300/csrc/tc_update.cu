@@ -1256,6 +1256,14 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
         if (te != ZEXP) te += round_product<NL>(Tr, sTa[(tb * M + r) * 2], sTa[(tb * M + r) * 2 + 1]);
         sub_row<NL>(Xr, xs, xe, Tr, sTs[tb * M + r], te, Tr, rs, re);
       }
+      // x is no longer read: the next column's copy may start
+      if (c + 1 < nc) {
+        const int64_t j2 = colj(c + 1);
+        fetch_x(j2);
+        pending = c + 1;
+        xs_n = X.s[irow * N + j2];
+        xe_n = X.e[irow * N + j2];
+      }
       if (tma_out) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the results, to the TMA store
         __syncwarp();
@@ -1266,13 +1274,6 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
       if (active) {
         X.s[ij] = rs;
         X.e[ij] = re;
-      }
-      if (c + 1 < nc) {
-        const int64_t j2 = colj(c + 1);
-        fetch_x(j2);
-        pending = c + 1;
-        xs_n = X.s[irow * N + j2];
-        xe_n = X.e[irow * N + j2];
       }
     }
     // no copy may still be writing this block's shared memory, and no store
