@@ -839,51 +839,54 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
     if ((tid & 31) == 0) {
       const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
       const uint32_t idesc2 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((2 * NT) >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+      // descriptors of the first K step; a K step adds 256 bytes to A's start
+      // address and two cores (256 bytes) to the Hankel operand's, a tile 16
+      // cores (the address field counts 16-byte units and never carries out)
+      const uint64_t ad0 = desc(su32(sA), 128, C::KA * 16);
+      const uint64_t hd0 = desc(su32(sm + C::OFF_H), 128, 128);
+      const uint64_t xd0 = desc(su32(sm + C::OFF_BX), 128, 256);
+      const uint64_t adx = ad0 + (uint64_t)((KD / 16) * 16);  // the extra K step
       const bool aok = nc <= 0 || wait_bar(b_aready, 0);
       if (!aok) *eflag = 1;
       for (int c = 0; c < nc && aok; ++c) {
         const int hb = c & 1;
-        unsigned char* sH = sm + C::OFF_H + hb * C::HBYTES;
+        const uint64_t hd = hd0 + (uint64_t)(hb * (C::HBYTES >> 4));
+        const uint64_t xd = xd0 + (uint64_t)(hb * (C::XBYTES >> 4));
         if (!wait_bar(b_hready + 8 * hb, (c >> 1) & 1) || *eflag) {
           *eflag = 1;
           break;
         }
         bool okm = true;
-        for (int t = 0; t < TILES && okm; ++t) {
+#pragma unroll
+        for (int t = 0; t < TILES; ++t) {
+          if (t > 0 && C::merge(t - 1)) continue;  // issued with tile t - 1
           const bool two = C::merge(t);
-          for (int u = t; u <= (two ? t + 1 : t) && okm; ++u)
-            if (c >= 1 && !wait_bar(b_empty + 8 * u, (c - 1) & 1)) okm = false;
-          if (!okm) {
-            *eflag = 1;
-            break;
+          if (okm && c >= 1) {
+            okm = wait_bar(b_empty + 8 * t, (c - 1) & 1);
+            if (two) okm = okm && wait_bar(b_empty + 8 * (t + 1), (c - 1) & 1);
           }
+          if (!okm) continue;
           asm volatile("tcgen05.fence::after_thread_sync;");
-          const uint32_t id = two ? idesc2 : idesc;
-          for (int ks = C::ks_lo(t); ks < C::ks_hi(t); ++ks) {
-            const uint64_t ad = desc(su32(sA) + ks * 256, 128, C::KA * 16);
-            const uint64_t bd = desc(su32(sH) + (16 * t + 2 * ks) * 128, 128, 128);
-            const uint32_t acc = ks > C::ks_lo(t) ? 1u : 0u;
+#pragma unroll
+          for (int ks = C::ks_lo(t); ks < C::ks_hi(t); ++ks)
             asm volatile(
                 "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
                     tmem + (uint32_t)(t * NT)),
-                "l"(ad), "l"(bd), "r"(id), "r"(acc));
-          }
+                "l"(ad0 + (uint64_t)(ks * 16)), "l"(hd + (uint64_t)((16 * t + 2 * ks) * 8)), "r"(two ? idesc2 : idesc),
+                "r"(ks > C::ks_lo(t) ? 1u : 0u));
           // 2^p * b: the extra K step for the tiles at or above position KD
-          for (int u = t; u <= (two ? t + 1 : t); ++u) {
-            if (u < C::XT0) continue;
-            const uint64_t ad = desc(su32(sA) + (KD / 16) * 256, 128, C::KA * 16);
-            const uint64_t bd = desc(su32(sm + C::OFF_BX + hb * C::XBYTES) + (u - C::XT0) * 4096, 128, 256);
-            asm volatile(
-                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
-                    tmem + (uint32_t)(u * NT)),
-                "l"(ad), "l"(bd), "r"(idesc), "r"(1u));
-          }
+#pragma unroll
+          for (int u = t; u <= (two ? t + 1 : t); ++u)
+            if (u >= C::XT0)
+              asm volatile(
+                  "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+                      tmem + (uint32_t)(u * NT)),
+                  "l"(adx), "l"(xd + (uint64_t)((u - C::XT0) * 256)), "r"(idesc), "r"(1u));
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(b_full + 8 * t));
-          if (two) {
+          if (two)
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(b_full + 8 * (t + 1)));
-            ++t;
-          }
         }
+        if (!okm) *eflag = 1;
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(b_hfree + 8 * hb));
         if (!okm) break;
       }
