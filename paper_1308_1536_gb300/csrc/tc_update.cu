@@ -677,6 +677,15 @@ constexpr int LIMIT = 1 << 22;
 // (u < 2^23), so the limb is sum_q u_q 2^(8q) + 0x4B000000 * 0x10001 and,
 // less kOff * 0x01010101, the four sums' weighted total: kC removes both.
 constexpr float kMagic = 12566528.0f;  // 2^23 + kOff
+// The upper tiles (positions >= KD) receive kMagic from the MMA itself: the
+// extra K step has ones in A's columns KD + 1 and KD + 2 and the bf16
+// constants 2^23 and kOff = 255 * 2^14 (both exact) in B's rows 1 and 2.
+// The extra K step is issued last, so the partial sums before it are below
+// 2^23 in magnitude and the final one lies in [2^23, 2^24): all are exact
+// fp32 integers, the accumulator holds the exact biased sum and the epilogue
+// reads its bits without the FADD.
+constexpr uint32_t kBias23 = 0x4B00u;   // bf16 2^23
+constexpr uint32_t kBiasOff = 0x4A7Fu;  // bf16 4177920 = kOff
 constexpr uint32_t kOff = 4177920u;
 constexpr int64_t kC = 152833374535680ll;  // kOff * 0x01010101 + 0x4B000000 * 0x10001
 static_assert((int64_t)kOff * 0x01010101ll + 0x4B000000ll * 0x10001ll == kC, "per-limb constant");
@@ -803,8 +812,14 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
   // ---- set-up: barriers, tensor memory, zero Hankel corners ----------------
   // the Hankel cores outside the digit window are zero for every column
   static_assert(C::OFF_BX == C::OFF_H + 2 * C::HBYTES, "Hankel and extra-K buffers are contiguous");
-  for (int q = tid; q < (2 * C::HBYTES + 2 * C::XBYTES) / 16; q += pipe::NTH)
-    reinterpret_cast<uint4*>(sm + C::OFF_H)[q] = make_uint4(0u, 0u, 0u, 0u);
+  // ... and the extra K step's rows 1 and 2 hold 2^23 and kOff at every
+  // position (its row 0, b's raw digits, is written per column)
+  for (int q = tid; q < (2 * C::HBYTES + 2 * C::XBYTES) / 16; q += pipe::NTH) {
+    const int o = q * 16 - 2 * C::HBYTES;  // byte offset in the extra-K buffers
+    const bool krow = o >= 0 && (o & 255) < 128;  // a row of k-core 0
+    reinterpret_cast<uint4*>(sm + C::OFF_H)[q] =
+        krow ? make_uint4((uint32_t)pipe::kBias23 << 16, pipe::kBiasOff, 0u, 0u) : make_uint4(0u, 0u, 0u, 0u);
+  }
   if (tid == 0) {
     for (int t = 0; t < 4; ++t) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b_full + 8 * t));
@@ -1025,7 +1040,7 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
         *reinterpret_cast<uint2*>(rowbase + (k0 >> 3) * 128 + (k0 & 7) * 2) =
             make_uint2(pipe::dbfs(e[3]) | (pipe::dbfs(e[2]) << 16), pipe::dbfs(e[1]) | (pipe::dbfs(e[0]) << 16));
       }
-      *reinterpret_cast<uint4*>(rowbase + (KD / 8) * 128) = make_uint4(0x3F80u, 0u, 0u, 0u);
+      *reinterpret_cast<uint4*>(rowbase + (KD / 8) * 128) = make_uint4(0x3F803F80u, 0x3F80u, 0u, 0u);
       *reinterpret_cast<uint4*>(rowbase + (KD / 8 + 1) * 128) = make_uint4(0u, 0u, 0u, 0u);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // A is read by the tensor core
       arrive(b_aready);
@@ -1061,13 +1076,15 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
       okc = __all_sync(0xffffffffu, okc);
       asm volatile("tcgen05.fence::after_thread_sync;");
       if (okc) tmem_ld32_async(tl + 32 * K0, va);
-      auto limbs8 = [&](const uint32_t* v, const int64_t* kv, uint32_t(&lim)[8], int64_t& ac) {
+      // biased: the sums already carry kMagic (tiles from XT0 up)
+      auto limbs8 = [&](const uint32_t* v, const int64_t* kv, uint32_t(&lim)[8], int64_t& ac, const bool biased) {
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           uint32_t u[4];
 #pragma unroll
           for (int j = 0; j < 4; ++j)
-            u[j] = __float_as_uint(__fadd_rn(__uint_as_float(v[4 * q + j]), pipe::kMagic));  // 0x4B000000 + u
+            u[j] = biased ? v[4 * q + j]
+                          : __float_as_uint(__fadd_rn(__uint_as_float(v[4 * q + j]), pipe::kMagic));  // 0x4B000000 + u
           const uint32_t xl = u[0] + (u[1] << 8), yl = u[2] + (u[3] << 8);
           ac += (int64_t)((uint64_t)yl * 65536u + xl) + kv[q];
           lim[q] = (uint32_t)ac;
@@ -1104,7 +1121,10 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
         }
         if (!okc) return;
         uint32_t lim[8];
-        limbs8(cur, kv, lim, acc);
+        if ((k >> 2) >= C::XT0)
+          limbs8(cur, kv, lim, acc, true);
+        else
+          limbs8(cur, kv, lim, acc, false);
         if (upper) {
           Tw.st16(2 * k - NL / 4, make_uint4(lim[0], lim[1], lim[2], lim[3]));
           Tw.st16(2 * k - NL / 4 + 1, make_uint4(lim[4], lim[5], lim[6], lim[7]));
@@ -1135,7 +1155,7 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
               for (int e = 0; e < 8; ++e) w[8 * part + e] = w8[e];
             }
             uint32_t l8[8];
-            limbs8(w, kvl, l8, ac2);
+            limbs8(w, kvl, l8, ac2, (kk >> 2) >= C::XT0);
             slo |= l8[0] | l8[1] | l8[2] | l8[3] | l8[4] | l8[5] | l8[6] | l8[7];
           }
           if (unsafe) {
