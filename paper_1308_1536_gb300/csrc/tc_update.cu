@@ -1016,29 +1016,33 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
       // A: the balanced digits of this row's multiplier (the top carry is the
       // 2^p of z = z' + 2^p), digit s at k' = KD - 1 - s: limb L's four digits
       // fill k' = KD - 4 - 4L .. KD - 1 - 4L; then the extra K step's 1 at
-      // k' = KD and zeros after it.  The row's limbs arrive by vector loads
-      // issued together.
+      // k' = KD and zeros after it.  Digits in [-128, 127] are unique, so they
+      // are the bytes of z + (128, 128, ..., 128) in base 256, less 128: one
+      // carry chain over the limbs instead of one over the digits.  The row's
+      // limbs arrive by vector loads issued together.
       const uint32_t* zm = Z.m + (have ? i0 + r : i0) * NL;
       unsigned char* rowbase = sA + (r >> 3) * (C::KA * 16) + (r & 7) * 16;
-      uint4 zv[NL / 4];
+      uint32_t f[NL];
 #pragma unroll
-      for (int q = 0; q < NL / 4; ++q)
-        zv[q] = have ? *reinterpret_cast<const uint4*>(zm + 4 * q) : make_uint4(0u, 0u, 0u, 0u);
-      int cy = 0;
+      for (int q = 0; q < NL / 4; ++q) {
+        const uint4 v = have ? *reinterpret_cast<const uint4*>(zm + 4 * q) : make_uint4(0u, 0u, 0u, 0u);
+        f[4 * q] = v.x;
+        f[4 * q + 1] = v.y;
+        f[4 * q + 2] = v.z;
+        f[4 * q + 3] = v.w;
+      }
+      f[0] = add_cc(f[0], 0x80808080u);
+#pragma unroll
+      for (int L = 1; L < NL; ++L) f[L] = addc_cc(f[L], 0x80808080u);
 #pragma unroll
       for (int L = 0; L < NL; ++L) {
-        const uint4 v4 = zv[L >> 2];
-        const uint32_t w = (L & 3) == 0 ? v4.x : (L & 3) == 1 ? v4.y : (L & 3) == 2 ? v4.z : v4.w;
-        int e[4];
+        uint32_t h[4];  // bf16 of byte q - 128: exact through fp32 (2^23 + byte, less 2^23 + 128)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int t = (int)((w >> (8 * q)) & 255u) + cy;
-          cy = t >= 128 ? 1 : 0;
-          e[q] = t - (cy << 8);
-        }
+        for (int q = 0; q < 4; ++q)
+          h[q] = __float_as_uint(__uint_as_float(0x4B000000u | ((f[L] >> (8 * q)) & 255u)) - 8388736.0f) >> 16;
         const int k0 = KD - 4 - 4 * L;
         *reinterpret_cast<uint2*>(rowbase + (k0 >> 3) * 128 + (k0 & 7) * 2) =
-            make_uint2(pipe::dbfs(e[3]) | (pipe::dbfs(e[2]) << 16), pipe::dbfs(e[1]) | (pipe::dbfs(e[0]) << 16));
+            make_uint2(h[3] | (h[2] << 16), h[1] | (h[0] << 16));
       }
       *reinterpret_cast<uint4*>(rowbase + (KD / 8) * 128) = make_uint4(0x3F803F80u, 0x3F80u, 0u, 0u);
       *reinterpret_cast<uint4*>(rowbase + (KD / 8 + 1) * 128) = make_uint4(0u, 0u, 0u, 0u);
