@@ -134,6 +134,33 @@ int mpdet_status(mpdet_t h, int64_t* zero_pivot_k);
  * (MPDET_EZEROPIVOT or MPDET_EZERODIV). */
 int mpdet_lastcol_minors(mpdet_t h, mpdet_numv out, int normalised, int device_ptr);
 
+/* Signed minors of the last column for every leading size n = 1..N from one
+ * elimination: the series of minor arrays for N = 2, 3, ... that the paper's
+ * application needs (Sec. 3: at step n, row n of L holds the minors of the
+ * leading n x n matrix's last column up to a factor, so the series costs no
+ * extra elimination work).  Row n of L is final after step n-1 and the
+ * leading n x n block goes through the same rounded operations as a
+ * standalone n x n matrix, so series n is bit-identical to
+ * mpdet_lastcol_minors of that block:
+ *     C^(n)_jn = RN(D_{n-1} * l_nj),  j < n;    C^(n)_nn = D_{n-1}  (D_0 = 1),
+ * or with normalised != 0 the delta of eq. (minors) for every n:
+ *     delta^(n)_j = RN(l_nj * RN(1/l_n1)),  1 < j < n;   delta^(n)_1 = 1;
+ *     delta^(n)_n = RN(1/l_n1);   delta^(1)_1 = 1,
+ * where a series with l_n1 = 0 (C_1n = 0, delta undefined) comes out all +0.
+ * out: N(N+1)/2 numbers, series n at offset n(n-1)/2 (entries j = 1..n).
+ * Needs MPDET_LASTCOL and a completed factorisation.  After a zero pivot at
+ * step kz (D_kz = 0) the series 1..kz are valid; later unnormalised series
+ * are +0 and later normalised ones undefined.
+ * With device_ptr = 0 the call allocates a device buffer of the triangle for
+ * its duration.  Errors: MPDET_EINVAL, MPDET_ESTATE, MPDET_ENOMEM, MPDET_ECUDA. */
+int mpdet_minor_series(mpdet_t h, mpdet_numv out, int normalised, int device_ptr);
+
+/* Copy count entries of the in-place N x N array (flat row-major indices
+ * idx[q] = i*N + j, host array, 0 <= idx < N^2) into out (count numbers):
+ * sampled reads of a large factorisation without copying it whole.
+ * Errors: MPDET_EINVAL (bad index or pointer), MPDET_ECUDA. */
+int mpdet_get_entries(mpdet_t h, int64_t count, const int64_t* idx, mpdet_numv out, int device_ptr);
+
 /* Copy out the leading minors computed so far (D_1..D_N; entries of steps not
  * yet run are +0). */
 int mpdet_get_minors(mpdet_t h, mpdet_numv out, int device_ptr);
@@ -279,6 +306,33 @@ int mpdet_batch_set_cauchy(mpdet_batch_t b, int64_t m, const double* x, const do
 int mpdet_batch_set_mp(mpdet_batch_t b, int64_t m, mpdet_numv A, int device_ptr);
 int mpdet_batch_factor(mpdet_batch_t b, mpdet_numv minors, int64_t* zero_k, int device_ptr);
 int64_t mpdet_batch_launches(mpdet_batch_t b);
+
+/* Batch tuning (results are bit-identical for every setting; only speed
+ * changes).  The persistent kernel exists in several lane geometries per
+ * precision: variant v runs the multipliers and the Schur update with W
+ * limbs per lane and G lanes per number, the pivot with PW x PG
+ * (mpdet_batch_variant_info; variant 0 is the default), and is launched with
+ * a chosen number of resident blocks per SM (1 .. the occupancy limit).
+ * mpdet_batch_tune params:
+ *   MPDET_BATCH_VARIANT        value = variant index;
+ *   MPDET_BATCH_BLOCKS_PER_SM  value = resident blocks per SM;
+ *   MPDET_BATCH_GRAPH          1: mpdet_batch_factor with device outputs
+ *     replays a CUDA graph of the whole factorisation (working copy, the
+ *     persistent launch, the output copies), captured on the first call and
+ *     again whenever the output pointers or the launch shape change; 0 (the
+ *     default) enqueues the operations one by one.
+ * mpdet_batch_autotune times every variant at its occupancy limit and at half
+ * of it (reps factorisations each after one warm-up, CUDA events on the
+ * batch's stream, on the stored inputs; synchronous), keeps the fastest and
+ * returns it (any output pointer may be NULL): the variant, the blocks per
+ * SM, its time per factorisation in ms and the number of candidates timed.
+ * Every matrix must be set first.  Errors: MPDET_EINVAL, MPDET_ECUDA. */
+enum { MPDET_BATCH_VARIANT = 1, MPDET_BATCH_BLOCKS_PER_SM = 2, MPDET_BATCH_GRAPH = 3 };
+int mpdet_batch_tune(mpdet_batch_t b, int param, int value);
+int mpdet_batch_variant_info(mpdet_batch_t b, int32_t variant, int32_t* W, int32_t* G, int32_t* PW, int32_t* PG,
+                             int32_t* max_blocks_per_sm);
+int mpdet_batch_autotune(mpdet_batch_t b, int reps, int32_t* variant, int32_t* blocks_per_sm, double* best_ms,
+                         int32_t* candidates);
 int mpdet_batch_free(mpdet_batch_t b);
 
 /* Element-wise arithmetic of the kernels on device arrays of count numbers

@@ -27,6 +27,8 @@ Functions and the passages they follow:
   identity block of [A I] stored in A's strict lower triangle.
 * ``lastcol_minors``: C_jN = D_{N-1} * l_Nj (eq. minorsdef) and the
   normalised minors of eq. (minors).
+* ``minor_series``: the last-column minors of every leading size n = 1..N
+  (the series of minor arrays for N = 2, 3, ... of Sec. 3).
 * ``usolve``: X = A^-1 = U^-1 L from a lastcol elimination, the adjoint of
   log|det| (d log|det| / dA = A^-T; all minors are partial derivatives of
   the determinant, Sec. 3), by right-looking back substitution.
@@ -205,6 +207,35 @@ def lastcol_minors(X, D, N: int, p: int, normalised: bool = False):
                             *map(_ptr, o))
     _check(st, "lastcol")
     return o
+
+
+def minor_series(X, D, N: int, p: int, normalised: bool = False):
+    """Last-column minors of every leading size n = 1..N from one lastcol-mode
+    elimination (Sec. 3: at step n, row n of L holds the minors of the leading
+    n x n matrix, up to the factor D_{n-1}).  Series n, at offset n(n-1)/2 of
+    the packed result, is ``lastcol_minors`` of the leading n x n block of X
+    with D_1..D_n; a normalised series whose l_n1 is zero (C_1n = 0, delta
+    undefined) is left all +0."""
+    S, E, M = _norm(X, p)
+    Ds, De, Dm = _norm(D, p)
+    out = empty(N * (N + 1) // 2, p)
+    for r in range(N):
+        nn = r + 1
+        rows = np.arange(nn)[:, None] * N + np.arange(nn)[None, :]
+        blk = (S[rows].reshape(-1), E[rows].reshape(-1), M[rows.reshape(-1)])
+        if normalised:
+            o = empty(nn, p)
+            st = _load().or_lastcol(nn, p, 1, *map(_ptr, map(np.ascontiguousarray, blk)), 0, 1, _ptr(o[2][0]),
+                                    *map(_ptr, o))
+            if st == EZERODIV:
+                continue
+            _check(st, "lastcol")
+        else:
+            o = lastcol_minors(blk, (Ds[:nn], De[:nn], Dm[:nn]), nn, p)
+        off = r * (r + 1) // 2
+        for t, u in zip(out, o):
+            t[off:off + nn] = u
+    return out
 
 
 def usolve(X, N: int, p: int, nthreads: int = 1):

@@ -67,6 +67,8 @@ def load(build_if_missing: bool = True):
         "mpdet_lastcol_minors": ([P, NumV, ctypes.c_int, ctypes.c_int], ctypes.c_int),
         "mpdet_get_minors": ([P, NumV, ctypes.c_int], ctypes.c_int),
         "mpdet_get_mp": ([P, NumV, ctypes.c_int], ctypes.c_int),
+        "mpdet_minor_series": ([P, NumV, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+        "mpdet_get_entries": ([P, i64, P, NumV, ctypes.c_int], ctypes.c_int),
         "mpdet_resume": ([P, NumV, NumV, i64, ctypes.c_int], ctypes.c_int),
         "mpdet_steps_done": ([P], i64),
         "mpdet_free": ([P], ctypes.c_int),
@@ -81,6 +83,11 @@ def load(build_if_missing: bool = True):
         "mpdet_batch_set_mp": ([P, i64, NumV, ctypes.c_int], ctypes.c_int),
         "mpdet_batch_factor": ([P, NumV, P, ctypes.c_int], ctypes.c_int),
         "mpdet_batch_launches": ([P], i64),
+        "mpdet_batch_tune": ([P, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+        "mpdet_batch_variant_info": ([P, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                      ctypes.POINTER(i32), ctypes.POINTER(i32)], ctypes.c_int),
+        "mpdet_batch_autotune": ([P, ctypes.c_int, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                  ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)], ctypes.c_int),
         "mpdet_batch_free": ([P], ctypes.c_int),
         "mpdet_logabsdet_grad": ([P, P, i64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), P,
                                   ctypes.c_double, ctypes.c_int], ctypes.c_int),
@@ -282,6 +289,24 @@ class Mpdet:
         self._check(self.lib.mpdet_lastcol_minors(self.h, _numv(C), int(normalised), 0), "lastcol_minors")
         return C
 
+    def minor_series(self, normalised: bool = False, out=None):
+        """Last-column minors of every leading size n = 1..N (packed: series n
+        at offset n(n-1)/2)."""
+        if out is not None:
+            self._check(self.lib.mpdet_minor_series(self.h, _numv(out), int(normalised), 1), "minor_series")
+            return None
+        S = empty(self.N * (self.N + 1) // 2, self.p)
+        self._check(self.lib.mpdet_minor_series(self.h, _numv(S), int(normalised), 0), "minor_series")
+        return S
+
+    def get_entries(self, idx):
+        """Entries idx (flat row-major indices) of the in-place array."""
+        idx = np.ascontiguousarray(np.asarray(idx, dtype=np.int64))
+        out = empty(len(idx), self.p)
+        self._check(self.lib.mpdet_get_entries(self.h, len(idx), idx.ctypes.data_as(ctypes.c_void_p), _numv(out), 0),
+                    "get_entries")
+        return out
+
     def get_minors(self):
         D = empty(self.N, self.p)
         self._check(self.lib.mpdet_get_minors(self.h, _numv(D), 0), "get_minors")
@@ -424,6 +449,35 @@ class Batch:
         self._check(self.lib.mpdet_batch_factor(self.h, _numv(D), zk.ctypes.data_as(ctypes.c_void_p), 0),
                     "batch_factor")
         return zk, D
+
+    def tune(self, variant: int | None = None, blocks_per_sm: int | None = None, graph: bool | None = None):
+        """Lane-geometry variant, resident blocks per SM and CUDA-graph replay
+        of the persistent launch (results are identical for every setting)."""
+        if variant is not None:
+            self._check(self.lib.mpdet_batch_tune(self.h, 1, int(variant)), "batch_tune(variant)")
+        if blocks_per_sm is not None:
+            self._check(self.lib.mpdet_batch_tune(self.h, 2, int(blocks_per_sm)), "batch_tune(blocks_per_sm)")
+        if graph is not None:
+            self._check(self.lib.mpdet_batch_tune(self.h, 3, int(bool(graph))), "batch_tune(graph)")
+
+    def variants(self):
+        """[(W, G, PW, PG, max_blocks_per_sm)] of every lane-geometry variant."""
+        out, v = [], 0
+        while True:
+            a = [ctypes.c_int32() for _ in range(5)]
+            if self.lib.mpdet_batch_variant_info(self.h, v, *map(ctypes.byref, a)):
+                return out
+            out.append(tuple(int(x.value) for x in a))
+            v += 1
+
+    def autotune(self, reps: int = 1):
+        """Time every variant (occupancy limit and half of it), keep the
+        fastest: dict(variant, blocks_per_sm, ms, candidates)."""
+        v, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        ms = ctypes.c_double()
+        self._check(self.lib.mpdet_batch_autotune(self.h, int(reps), ctypes.byref(v), ctypes.byref(b),
+                                                  ctypes.byref(ms), ctypes.byref(c)), "batch_autotune")
+        return dict(variant=v.value, blocks_per_sm=b.value, ms=ms.value, candidates=c.value)
 
     def minors_of(self, D, m):
         a, b = int(self.offsets[m]), int(self.offsets[m + 1])

@@ -9,15 +9,61 @@
 #include <vector>
 
 #include "../../include/mpdet.h"
+#include "batch_variants.h"
 #include "kernelset.h"
 
 using mpd::MpArr;
 
+namespace mpd {
+int batch_variants(int n, const BatchVariant** out) {
+  // entry 0: the kernel set's own kernel; then the extra geometries for n
+  static BatchVariant lists[4][8];
+  static int counts[4] = {0, 0, 0, 0};
+  static const int ns[4] = {16, 32, 64, 128};
+  static bool init = false;
+  if (!init) {
+    for (int q = 0; q < 4; ++q) {
+      const KernelSet* ks = kernel_set_for(ns[q]);
+      lists[q][0] = BatchVariant{ks->W, ks->G, ks->PW, ks->PG, ks->batch, ks->batch_blocks_per_sm};
+      int c = 0;
+      const BatchVariant* v = q == 0 ? batch_variants_n16(&c)
+                              : q == 1 ? batch_variants_n32(&c)
+                              : q == 2 ? batch_variants_n64(&c)
+                                       : batch_variants_n128(&c);
+      for (int i = 0; i < c && i < 7; ++i) lists[q][1 + i] = v[i];
+      counts[q] = 1 + (c < 7 ? c : 7);
+    }
+    init = true;
+  }
+  for (int q = 0; q < 4; ++q)
+    if (ns[q] == n) {
+      *out = lists[q];
+      return counts[q];
+    }
+  static BatchVariant single;
+  const KernelSet* ks = kernel_set_for(n);
+  single = BatchVariant{ks->W, ks->G, ks->PW, ks->PG, ks->batch, ks->batch_blocks_per_sm};
+  *out = &single;
+  return 1;
+}
+}  // namespace mpd
+
 struct mpdet_batch_ctx {
   int64_t count = 0, total = 0, total_d = 0, max_n = 0;
-  int p = 0, n = 0, nsm = 0, blocks = 0;
+  int p = 0, n = 0, nsm = 0;
+  int max_blocks = 0;  // blocks the per-block multiplier scratch Z is sized for
   cudaStream_t stream = nullptr;
   const mpd::KernelSet* ks = nullptr;
+  // lane-geometry variant and resident blocks per SM of the persistent launch
+  const mpd::BatchVariant* variants = nullptr;
+  int nvariants = 0, variant = 0, bpsm = 0;
+  std::vector<int> bpsm_max;  // occupancy limit per variant
+  // CUDA graph of one factorisation (device outputs): captured on cap, replayed on stream
+  bool graph = false;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  const void* gkey[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  int gkey_variant = -1, gkey_bpsm = -1;
   std::vector<int64_t> Ns, xoff, doff;
   MpArr X0{}, X{}, D{}, Z{};  // inputs as set, working copy, minors, per-block multipliers
   int64_t *dN = nullptr, *dxoff = nullptr, *ddoff = nullptr, *dzero = nullptr;
@@ -54,6 +100,8 @@ extern "C" int mpdet_batch_free(mpdet_batch_t b) {
   cudaFree(b->dorder);
   cudaFree(b->dqueue);
   if (b->stage) cudaFree(b->stage);
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->cap) cudaStreamDestroy(b->cap);
   delete b;
   return MPDET_OK;
 }
@@ -89,9 +137,18 @@ extern "C" int mpdet_batch_create(int64_t count, const int64_t* Ns, int32_t p_bi
   int dev = 0;
   bool ok = cudaGetDevice(&dev) == cudaSuccess &&
             cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess;
-  b->blocks = b->nsm * b->ks->batch_blocks_per_sm();
+  if (ok) {
+    b->nvariants = mpd::batch_variants(n, &b->variants);
+    int mx = 1;
+    for (int v = 0; v < b->nvariants; ++v) {
+      b->bpsm_max.push_back(b->variants[v].blocks_per_sm());
+      mx = std::max(mx, b->bpsm_max.back());
+    }
+    b->bpsm = b->bpsm_max[0];
+    b->max_blocks = b->nsm * mx;
+  }
   ok = ok && alloc_arr(&b->X0, b->total, n) && alloc_arr(&b->X, b->total, n) && alloc_arr(&b->D, b->total_d, n) &&
-       alloc_arr(&b->Z, (int64_t)b->blocks * b->max_n, n);
+       alloc_arr(&b->Z, (int64_t)b->max_blocks * b->max_n, n);
   ok = ok && cudaMalloc(&b->dN, count * 8) == cudaSuccess && cudaMalloc(&b->dxoff, count * 8) == cudaSuccess &&
        cudaMalloc(&b->ddoff, count * 8) == cudaSuccess && cudaMalloc(&b->dzero, count * 8) == cudaSuccess &&
        cudaMalloc(&b->dorder, count * 4) == cudaSuccess && cudaMalloc(&b->dqueue, 16) == cudaSuccess;
@@ -188,10 +245,10 @@ extern "C" int mpdet_batch_set_mp(mpdet_batch_t b, int64_t m, mpdet_numv A, int 
   return finish(b, device_ptr);
 }
 
-extern "C" int mpdet_batch_factor(mpdet_batch_t b, mpdet_numv minors, int64_t* zero_k, int device_ptr) {
-  if (!b) return MPDET_EINVAL;
+// One factorisation of the stored inputs: working copy, cleared queue and
+// statuses, the persistent launch, and the outputs (kind: copy direction).
+static int enqueue_factor(mpdet_batch_t b, cudaStream_t st, mpdet_numv minors, int64_t* zero_k, cudaMemcpyKind k) {
   const int n = b->n;
-  cudaStream_t st = b->stream;
   // the stored inputs stay intact: eliminate a working copy
   if (cudaMemcpyAsync(b->X.m, b->X0.m, (size_t)b->total * n * 4, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
       cudaMemcpyAsync(b->X.e, b->X0.e, (size_t)b->total * 8, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
@@ -199,16 +256,143 @@ extern "C" int mpdet_batch_factor(mpdet_batch_t b, mpdet_numv minors, int64_t* z
       cudaMemsetAsync(b->dqueue, 0, 16, st) != cudaSuccess || cudaMemsetAsync(b->dzero, 0, b->count * 8, st) != cudaSuccess)
     return MPDET_ECUDA;
   mpd::BatchDescHost bd{b->dN, b->dxoff, b->ddoff, b->dorder, b->dzero, b->dqueue, b->count, b->max_n};
-  int blocks = (int)std::min<int64_t>(b->blocks, b->count);
-  if (b->ks->batch(b->X, b->D, b->Z, bd, b->p, blocks, st) != cudaSuccess) return MPDET_ECUDA;
-  b->launches += 1;
-  const cudaMemcpyKind k = device_ptr ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  const int blocks = (int)std::min<int64_t>((int64_t)b->nsm * b->bpsm, b->count);
+  if (b->variants[b->variant].launch(b->X, b->D, b->Z, bd, b->p, blocks, st) != cudaSuccess) return MPDET_ECUDA;
   if ((minors.limbs && cudaMemcpyAsync(minors.limbs, b->D.m, (size_t)b->total_d * n * 4, k, st) != cudaSuccess) ||
       (minors.exp && cudaMemcpyAsync(minors.exp, b->D.e, (size_t)b->total_d * 8, k, st) != cudaSuccess) ||
       (minors.sign && cudaMemcpyAsync(minors.sign, b->D.s, (size_t)b->total_d, k, st) != cudaSuccess) ||
       (zero_k && cudaMemcpyAsync(zero_k, b->dzero, b->count * 8, k, st) != cudaSuccess))
     return MPDET_ECUDA;
+  return MPDET_OK;
+}
+
+// Replay (capturing first when the outputs or the launch shape changed) the
+// graph of one factorisation with device outputs.
+static int graph_factor(mpdet_batch_t b, mpdet_numv minors, int64_t* zero_k) {
+  const void* key[5] = {minors.limbs, minors.exp, minors.sign, zero_k, b->stream};
+  bool same = b->gexec && b->gkey_variant == b->variant && b->gkey_bpsm == b->bpsm;
+  for (int q = 0; q < 5 && same; ++q) same = key[q] == b->gkey[q];
+  if (!same) {
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+    if (!b->cap && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) return MPDET_ECUDA;
+    if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return MPDET_ECUDA;
+    int rc = enqueue_factor(b, b->cap, minors, zero_k, cudaMemcpyDeviceToDevice);
+    cudaGraph_t g = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(b->cap, &g);
+    if (rc || ce != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return MPDET_ECUDA;
+    }
+    ce = cudaGraphInstantiate(&b->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) {
+      b->gexec = nullptr;
+      return MPDET_ECUDA;
+    }
+    for (int q = 0; q < 5; ++q) b->gkey[q] = key[q];
+    b->gkey_variant = b->variant;
+    b->gkey_bpsm = b->bpsm;
+  }
+  return cudaGraphLaunch(b->gexec, b->stream) == cudaSuccess ? MPDET_OK : MPDET_ECUDA;
+}
+
+extern "C" int mpdet_batch_factor(mpdet_batch_t b, mpdet_numv minors, int64_t* zero_k, int device_ptr) {
+  if (!b) return MPDET_EINVAL;
+  int rc = (b->graph && device_ptr)
+               ? graph_factor(b, minors, zero_k)
+               : enqueue_factor(b, b->stream, minors, zero_k, device_ptr ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost);
+  if (rc) return rc;
+  b->launches += 1;
   return finish(b, device_ptr);
+}
+
+extern "C" int mpdet_batch_tune(mpdet_batch_t b, int param, int value) {
+  if (!b) return MPDET_EINVAL;
+  switch (param) {
+    case MPDET_BATCH_VARIANT:
+      if (value < 0 || value >= b->nvariants) return MPDET_EINVAL;
+      b->variant = value;
+      b->bpsm = std::min(b->bpsm, b->bpsm_max[value]);
+      return MPDET_OK;
+    case MPDET_BATCH_BLOCKS_PER_SM:
+      if (value < 1 || value > b->bpsm_max[b->variant]) return MPDET_EINVAL;
+      b->bpsm = value;
+      return MPDET_OK;
+    case MPDET_BATCH_GRAPH:
+      if (value != 0 && value != 1) return MPDET_EINVAL;
+      b->graph = value == 1;
+      return MPDET_OK;
+    default:
+      return MPDET_EINVAL;
+  }
+}
+
+extern "C" int mpdet_batch_variant_info(mpdet_batch_t b, int32_t variant, int32_t* W, int32_t* G, int32_t* PW,
+                                        int32_t* PG, int32_t* max_blocks_per_sm) {
+  if (!b || variant < 0 || variant >= b->nvariants) return MPDET_EINVAL;
+  const mpd::BatchVariant& v = b->variants[variant];
+  if (W) *W = v.W;
+  if (G) *G = v.G;
+  if (PW) *PW = v.PW;
+  if (PG) *PG = v.PG;
+  if (max_blocks_per_sm) *max_blocks_per_sm = b->bpsm_max[variant];
+  return MPDET_OK;
+}
+
+extern "C" int mpdet_batch_autotune(mpdet_batch_t b, int reps, int32_t* variant, int32_t* blocks_per_sm,
+                                    double* best_ms, int32_t* candidates) {
+  if (!b || reps < 1) return MPDET_EINVAL;
+  const int v0 = b->variant, p0 = b->bpsm;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return MPDET_ECUDA;
+  }
+  double best = 1e300;
+  int bv = v0, bp = p0, ncand = 0, rc = MPDET_OK;
+  mpdet_numv none{nullptr, nullptr, nullptr};
+  for (int v = 0; v < b->nvariants && !rc; ++v) {
+    // resident blocks per SM: the occupancy limit and its half (more blocks
+    // hide latency, fewer balance the tail of uneven jobs better)
+    const int mx = b->bpsm_max[v];
+    const int cand[2] = {mx, std::max(1, mx / 2)};
+    for (int c = 0; c < (cand[1] == cand[0] ? 1 : 2) && !rc; ++c) {
+      b->variant = v;
+      b->bpsm = cand[c];
+      float ms = 0.f;
+      if ((rc = enqueue_factor(b, b->stream, none, nullptr, cudaMemcpyDeviceToDevice))) break;  // warm-up
+      if (cudaEventRecord(e0, b->stream) != cudaSuccess) { rc = MPDET_ECUDA; break; }
+      for (int r = 0; r < reps && !rc; ++r) rc = enqueue_factor(b, b->stream, none, nullptr, cudaMemcpyDeviceToDevice);
+      if (rc || cudaEventRecord(e1, b->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        rc = rc ? rc : MPDET_ECUDA;
+        break;
+      }
+      b->launches += 1 + reps;
+      ++ncand;
+      if (ms / reps < best) {
+        best = ms / reps;
+        bv = v;
+        bp = cand[c];
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) {
+    b->variant = v0;
+    b->bpsm = p0;
+    return rc;
+  }
+  b->variant = bv;
+  b->bpsm = bp;
+  if (variant) *variant = bv;
+  if (blocks_per_sm) *blocks_per_sm = bp;
+  if (best_ms) *best_ms = best;
+  if (candidates) *candidates = ncand;
+  return MPDET_OK;
 }
 
 extern "C" int64_t mpdet_batch_launches(mpdet_batch_t b) { return b ? b->launches : -1; }

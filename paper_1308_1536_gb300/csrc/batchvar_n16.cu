@@ -1,0 +1,15 @@
+// Extra lane geometries of the batch kernel for n = 16 limbs (the batch
+// autotuner's candidates beside the kernel set's own).
+#include "kernels.cuh"
+#include "batch_variants.h"
+
+namespace mpd {
+const BatchVariant* batch_variants_n16(int* count) {
+  static const BatchVariant v[] = {
+      {8, 2, 4, 4, &Launch<8, 2>::batch_p<4, 4>, &Launch<8, 2>::batch_blocks_per_sm_p<4, 4>},
+      {4, 4, 4, 4, &Launch<4, 4>::batch_p<4, 4>, &Launch<4, 4>::batch_blocks_per_sm_p<4, 4>},
+  };
+  *count = (int)(sizeof v / sizeof v[0]);
+  return v;
+}
+}  // namespace mpd

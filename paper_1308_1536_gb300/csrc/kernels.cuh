@@ -602,6 +602,75 @@ __global__ void k_lastcol(MpArr X, int64_t N, MpArr F, MpArr out, int normalised
   }
 }
 
+// Series of last-column minors for every leading size (Sec. 3: the series
+// of minor arrays for N = 2, 3, ...; at step n row n of L holds the minors of
+// the n x n leading matrix up to a factor).  Row r of L (0-based) is final
+// after step r, and the elimination of the leading (r+1) x (r+1) block is the
+// same rounded sequence, so series r holds
+//   C^(r+1)_{j,r} = RN(D_r * l_rj),  j < r;   C^(r+1)_{r,r} = D_r,
+// with D_r the leading minor of size r (D[r-1]; D_0 = 1), or, normalised,
+//   delta_j = RN(l_rj * R[r]),  0 < j < r;   delta_0 = 1;   delta_r = R[r],
+// with R[r] = RN(1/l_r0) (+0 when l_r0 = 0: that series is then all +0).
+// out is the packed triangle: series r at offset r(r+1)/2.  A zero pivot at
+// step kz leaves D_kz.. = +0, so every later unnormalised series is +0.
+// Grid-stride over the triangle; the trip count is uniform per block, so
+// every lane takes part in the group shuffles of mul_round.
+template <int W, int G>
+__global__ void k_series(MpArr X, int64_t N, MpArr F, int normalised, MpArr out) {
+  constexpr int n = W * G;
+  Grp<G> gp;
+  const int64_t total = N * (N + 1) / 2;
+  const int gpb = blockDim.x / G;
+  for (int64_t t0 = (int64_t)blockIdx.x * gpb; t0 < total; t0 += (int64_t)gridDim.x * gpb) {
+    int64_t t = t0 + threadIdx.x / G;
+    const bool active = t < total;
+    if (!active) t = total - 1;
+    int64_t r = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while (r > 0 && r * (r + 1) / 2 > t) --r;
+    while ((r + 1) * (r + 2) / 2 <= t) ++r;
+    const int64_t j = t - r * (r + 1) / 2;
+    const int64_t fi = normalised ? r : (r > 0 ? r - 1 : 0);
+    const int64_t xj = r * N + j;
+    uint32_t L[W], M[W];
+    load_slice<W>(X.m + xj * n + gp.g * W, L);
+    const int8_t ls = X.s[xj];
+    const int64_t le = X.e[xj];
+    const int8_t fs = F.s[fi];
+    const int64_t fe = F.e[fi];
+    const int adj = mul_round<W, G>(gp, L, F.m + fi * n, M);
+    int8_t os;
+    int64_t oe;
+    if (le == ZEXP || fe == ZEXP) {
+      os = 0;
+      oe = ZEXP;
+#pragma unroll
+      for (int q = 0; q < W; ++q) M[q] = 0u;
+    } else {
+      os = (int8_t)(ls ^ fs);
+      oe = le + fe + adj;
+    }
+    const bool one = r == 0 || (normalised && j == 0 && fe != ZEXP);
+    if (one) {  // C^(1)_{1,1} = D_0 = 1; delta_0 = 1
+#pragma unroll
+      for (int q = 0; q < W; ++q) M[q] = 0u;
+      if (gp.g == G - 1) M[W - 1] = 0x80000000u;
+      os = 0;
+      oe = 1;
+    } else if (j == r) {  // C^(r+1)_{r,r} = D_r; delta_r = RN(1/l_r0)
+      load_slice<W>(F.m + fi * n + gp.g * W, M);
+      os = fs;
+      oe = fe;
+    }
+    if (active) {
+      store_slice<W>(out.m + t * n + gp.g * W, M);
+      if (gp.g == 0) {
+        out.s[t] = os;
+        out.e[t] = oe;
+      }
+    }
+  }
+}
+
 // RN(1/src[idx]) into dst[0]; one warp, group 0.  Sets *status = code when
 // src[idx] is zero.
 template <int W, int G>
@@ -649,12 +718,17 @@ struct BatchDesc {
   int64_t max_n;
 };
 
-template <int W, int G>
+// The pivot phase (one warp) runs in its own lane geometry (PW limbs per lane,
+// PG lanes per number, PW * PG = n): the long division's serial chain per
+// quotient limb shortens with the slice width, as in the single-matrix path.
+template <int W, int G, int PW, int PG>
 __global__ void __launch_bounds__(128, 4) k_batch(MpArr Xall, MpArr Dall, MpArr Zall, BatchDesc bd, int p) {
   constexpr int n = W * G;
+  static_assert(PW * PG == n, "the pivot geometry holds the same numbers");
   constexpr int SW = Scratch<W, G>::words;
   constexpr int NG = 128 / G;  // groups per block
-  __shared__ __align__(16) uint32_t sbuf[NG * SW];
+  constexpr int SBUF = NG * SW > (32 / PG) * SW ? NG * SW : (32 / PG) * SW;
+  __shared__ __align__(16) uint32_t sbuf[SBUF];
   __shared__ __align__(16) uint32_t r_m[n];
   __shared__ int64_t r_e;
   __shared__ int8_t r_s;
@@ -676,43 +750,44 @@ __global__ void __launch_bounds__(128, 4) k_batch(MpArr Xall, MpArr Dall, MpArr 
     for (int64_t k = 0; k < N; ++k) {
       const int64_t kk = k * N + k;
       if (threadIdx.x < 32) {  // warp 0: pivot
-        uint32_t A[W], Dm[W];
-        load_slice<W>(X.m + kk * n + gp.g * W, A);
+        Grp<PG> pg;
+        uint32_t A[PW], Dm[PW];
+        load_slice<PW>(X.m + kk * n + pg.g * PW, A);
         const int8_t as = X.s[kk];
         const int64_t ae = X.e[kk];
         int8_t ds = as;
         int64_t de = ae;
         if (k == 0) {
 #pragma unroll
-          for (int q = 0; q < W; ++q) Dm[q] = A[q];
+          for (int q = 0; q < PW; ++q) Dm[q] = A[q];
         } else {
-          const int adj = mul_round<W, G>(gp, A, D.m + (k - 1) * n, Dm);
+          const int adj = mul_round<PW, PG>(pg, A, D.m + (k - 1) * n, Dm);
           const int8_t ps = D.s[k - 1];
           const int64_t pe = D.e[k - 1];
           if (pe == ZEXP || ae == ZEXP) {
             ds = 0;
             de = ZEXP;
 #pragma unroll
-            for (int q = 0; q < W; ++q) Dm[q] = 0u;
+            for (int q = 0; q < PW; ++q) Dm[q] = 0u;
           } else {
             ds = (int8_t)(ps ^ as);
             de = pe + ae + adj;
           }
         }
-        if (threadIdx.x < G) {
-          store_slice<W>(D.m + k * n + gp.g * W, Dm);
-          if (gp.g == 0) {
+        if (threadIdx.x < PG) {
+          store_slice<PW>(D.m + k * n + pg.g * PW, Dm);
+          if (pg.g == 0) {
             D.s[k] = ds;
             D.e[k] = de;
           }
         }
         if (threadIdx.x == 0) s_zero = (ae == ZEXP);
         if (ae != ZEXP && k < N - 1) {  // warp-uniform: every lane read the same pivot
-          uint32_t Mr[W];
-          const int adj = recip_round<W, G>(gp, A, buf, Mr);
-          if (threadIdx.x < G) {
-            store_slice<W>(r_m + gp.g * W, Mr);
-            if (gp.g == 0) {
+          uint32_t Mr[PW];
+          const int adj = recip_round<PW, PG>(pg, A, sbuf + (threadIdx.x / PG) * SW, Mr);
+          if (threadIdx.x < PG) {
+            store_slice<PW>(r_m + pg.g * PW, Mr);
+            if (pg.g == 0) {
               r_s = as;
               r_e = (int64_t)adj - ae;
             }
@@ -964,19 +1039,28 @@ struct Launch {
     k_lastcol<W, G><<<(unsigned)blocks, NT, 0, st>>>(X, N, F, out, normalised, status);
     return cudaGetLastError();
   }
+  static cudaError_t series(MpArr X, int64_t N, MpArr F, int normalised, MpArr out, int nsm, cudaStream_t st) {
+    const int64_t total = N * (N + 1) / 2;
+    int64_t blocks = (total + NT / G - 1) / (NT / G);
+    if (blocks > (int64_t)nsm * 16) blocks = (int64_t)nsm * 16;
+    k_series<W, G><<<(unsigned)blocks, NT, 0, st>>>(X, N, F, normalised, out);
+    return cudaGetLastError();
+  }
   static cudaError_t recip1(MpArr src, int64_t idx, MpArr dst, int* status, int code, cudaStream_t st) {
     k_recip1<W, G><<<1, 32, 0, st>>>(src, idx, dst, status, code);
     return cudaGetLastError();
   }
-  static cudaError_t batch(MpArr X, MpArr D, MpArr Z, const BatchDescHost& h, int p, int blocks,
-                           cudaStream_t st) {
+  template <int PW, int PG>
+  static cudaError_t batch_p(MpArr X, MpArr D, MpArr Z, const BatchDescHost& h, int p, int blocks,
+                             cudaStream_t st) {
     BatchDesc bd{h.N, h.xoff, h.doff, h.order, h.zero_k, h.queue, h.count, h.max_n};
-    k_batch<W, G><<<blocks, 128, 0, st>>>(X, D, Z, bd, p);
+    k_batch<W, G, PW, PG><<<blocks, 128, 0, st>>>(X, D, Z, bd, p);
     return cudaGetLastError();
   }
-  static int batch_blocks_per_sm() {
+  template <int PW, int PG>
+  static int batch_blocks_per_sm_p() {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<W, G>, 128, 0) != cudaSuccess) return 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<W, G, PW, PG>, 128, 0) != cudaSuccess) return 1;
     return nb > 0 ? nb : 1;
   }
   static cudaError_t ops(int op, int64_t count, MpArr A, MpArr B, MpArr O, int p, int nsm, cudaStream_t st) {
@@ -992,6 +1076,8 @@ struct Launch {
     KernelSet s;
     s.W = W;
     s.G = G;
+    s.PW = W;
+    s.PG = G;
     s.lift = &lift;
     s.cauchy = &cauchy;
     s.pivot = &pivot;
@@ -1003,12 +1089,13 @@ struct Launch {
     s.update_col = &update_col;
     s.lastcol = &lastcol;
     s.recip1 = &recip1;
-    s.batch = &batch;
+    s.series = &series;
+    s.batch = &batch_p<W, G>;
     s.ops = &ops;
     s.init_s = &init_s;
     s.rowscale = &rowscale;
     s.to_f64 = &to_f64;
-    s.batch_blocks_per_sm = &batch_blocks_per_sm;
+    s.batch_blocks_per_sm = &batch_blocks_per_sm_p<W, G>;
     return s;
   }
   // The same set with the pivot and the single reciprocal taken from the
@@ -1020,8 +1107,12 @@ struct Launch {
   static KernelSet make_with_pivot() {
     static_assert(PW * PG == n, "the pivot family holds the same numbers");
     KernelSet s = make();
+    s.PW = PW;
+    s.PG = PG;
     s.pivot = &Launch<PW, PG>::pivot;
     s.recip1 = &Launch<PW, PG>::recip1;
+    s.batch = &batch_p<PW, PG>;
+    s.batch_blocks_per_sm = &batch_blocks_per_sm_p<PW, PG>;
     return s;
   }
 };

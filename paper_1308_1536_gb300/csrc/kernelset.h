@@ -59,6 +59,7 @@ inline UpdArgs upd_back(int64_t N, int64_t k) { return UpdArgs{N, k, 0, k, 0, IN
 
 struct KernelSet {
   int W, G;
+  int PW, PG;  // lane geometry of the pivot and the single reciprocal (PW * PG = W * G)
   // kind 0: double entries, 1: int32 entries
   cudaError_t (*lift)(const void* src, int kind, int64_t ld, int64_t N, MpArr X, int p, int nsm, cudaStream_t st);
   cudaError_t (*cauchy)(const double* x, const double* y, int64_t N, MpArr X, int p, int nsm, cudaStream_t st);
@@ -76,6 +77,9 @@ struct KernelSet {
   cudaError_t (*lastcol)(MpArr X, int64_t N, MpArr F, MpArr out, int normalised, const int* status,
                          cudaStream_t st);
   cudaError_t (*recip1)(MpArr src, int64_t idx, MpArr dst, int* status, int code, cudaStream_t st);
+  // last-column minors of every leading size (packed triangle of N(N+1)/2
+  // numbers); F = D (unnormalised) or R[r] = RN(1/l_r0) (normalised)
+  cudaError_t (*series)(MpArr X, int64_t N, MpArr F, int normalised, MpArr out, int nsm, cudaStream_t st);
   // persistent batch kernel (blocks = resident blocks to launch)
   cudaError_t (*batch)(MpArr X, MpArr D, MpArr Z, const BatchDescHost& bd, int p, int blocks, cudaStream_t st);
   int (*batch_blocks_per_sm)();

@@ -605,6 +605,73 @@ extern "C" int mpdet_lastcol_minors(mpdet_t h, mpdet_numv out, int normalised, i
   return finish_call(h, device_ptr);
 }
 
+extern "C" int mpdet_minor_series(mpdet_t h, mpdet_numv out, int normalised, int device_ptr) {
+  if (!h || !out.sign || !out.exp || !out.limbs) return fail(h, MPDET_EINVAL, "minor_series: null pointer");
+  if (!(h->flags & MPDET_LASTCOL)) return fail(h, MPDET_ESTATE, "minor_series: handle created without MPDET_LASTCOL");
+  if (!h->have_matrix || h->k_done != h->N) return fail(h, MPDET_ESTATE, "minor_series: factorisation not complete");
+  const int64_t N = h->N, total = N * (N + 1) / 2;
+  MpArr dst{out.sign, out.exp, out.limbs};
+  MpArr tmp{};
+  if (!device_ptr) {  // host output: a device buffer of the packed triangle for this call
+    int rc = alloc_arr(h, &tmp, total);
+    if (rc) {
+      free_arr(&tmp);
+      return rc;
+    }
+    dst = tmp;
+  }
+  MpArr F = h->D;
+  cudaError_t ce = cudaSuccess;
+  if (normalised) {
+    // R[r] = RN(1/l_r0) for every row (1/0 gives +0): column 0 of the array
+    // gathered into T, reciprocals into Z2 (both free once the elimination is done)
+    const size_t nb = (size_t)h->n * 4;
+    ce = cudaMemcpy2DAsync(h->T.m, nb, h->X.m, (size_t)N * nb, nb, (size_t)N, cudaMemcpyDeviceToDevice, h->stream);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpy2DAsync(h->T.e, 8, h->X.e, (size_t)N * 8, 8, (size_t)N, cudaMemcpyDeviceToDevice, h->stream);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpy2DAsync(h->T.s, 1, h->X.s, (size_t)N, 1, (size_t)N, cudaMemcpyDeviceToDevice, h->stream);
+    if (ce == cudaSuccess) {
+      ce = h->ks->ops(3, N, h->T, h->T, h->Z2, h->p, h->nsm, h->stream);
+      h->launches += 1;
+    }
+    F = h->Z2;
+  }
+  if (ce == cudaSuccess) {
+    ce = h->ks->series(h->X, N, F, normalised ? 1 : 0, dst, h->nsm, h->stream);
+    h->launches += 1;
+  }
+  int rc = ce == cudaSuccess ? MPDET_OK : fail(h, MPDET_ECUDA, "k_series: %s", cudaGetErrorString(ce));
+  if (!rc && !device_ptr) {
+    rc = copy_arr(h, tmp, out, total, 0, false);
+    if (!rc) rc = finish_call(h, 0);
+  } else if (!rc) {
+    rc = finish_call(h, 1);
+  }
+  if (tmp.m || tmp.e || tmp.s) {
+    cudaStreamSynchronize(h->stream);
+    free_arr(&tmp);
+  }
+  return rc;
+}
+
+extern "C" int mpdet_get_entries(mpdet_t h, int64_t count, const int64_t* idx, mpdet_numv out, int device_ptr) {
+  if (!h || count < 0 || (count > 0 && (!idx || !out.sign || !out.exp || !out.limbs)))
+    return fail(h, MPDET_EINVAL, "get_entries: bad argument");
+  const int64_t NN = h->N * h->N;
+  for (int64_t q = 0; q < count; ++q)
+    if (idx[q] < 0 || idx[q] >= NN) return fail(h, MPDET_EINVAL, "get_entries: index %lld out of range", (long long)idx[q]);
+  const cudaMemcpyKind k = device_ptr ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  const size_t nb = (size_t)h->n * 4;
+  for (int64_t q = 0; q < count; ++q) {
+    const int64_t i = idx[q];
+    CU(h, cudaMemcpyAsync(out.limbs + (size_t)q * h->n, h->X.m + (size_t)i * h->n, nb, k, h->stream));
+    CU(h, cudaMemcpyAsync(out.exp + q, h->X.e + i, 8, k, h->stream));
+    CU(h, cudaMemcpyAsync(out.sign + q, h->X.s + i, 1, k, h->stream));
+  }
+  return finish_call(h, device_ptr);
+}
+
 extern "C" int mpdet_get_mp(mpdet_t h, mpdet_numv out, int device_ptr) {
   if (!h) return MPDET_EINVAL;
   int rc = copy_arr(h, h->X, out, h->N * h->N, device_ptr, false);

@@ -1,0 +1,49 @@
+"""Host-side logic of the benchmark (no GPU): the closed-form accuracy report
+of the Cauchy leading minors against exact rational arithmetic, and the
+work counts behind the limb-MAC/s figures."""
+from fractions import Fraction
+import math
+
+import pytest
+
+import exactref as X
+from paper_1308_1536_gb300 import workloads as W
+
+pytestmark = pytest.mark.usefixtures("oracle_lib")
+
+
+def test_cauchy_bit_loss_matches_exact_rationals(oracle_lib):
+    import bench
+
+    N, p = 40, 256
+    x, y = W.cauchy_xy(N, W.C1["seed"])
+    st, zk, D, _ = oracle_lib.ge(oracle_lib.cauchy(x, y, p), N, p)
+    r = bench.cauchy_bit_loss(x, y, D, p, every=1)
+    fx = [Fraction(float(v)) for v in x]
+    fy = [Fraction(float(v)) for v in y]
+    num = den = Fraction(1)
+    Dv = X.unpack(D, p)
+    got = {o["k"]: o["bits"] for o in r["per_k"]}
+    for k in range(1, N + 1):
+        i = k - 1
+        for j in range(i):
+            num *= (fx[i] - fx[j]) * (fy[i] - fy[j])
+        for j in range(k):
+            den *= (fx[i] + fy[j]) * ((fx[j] + fy[i]) if j != i else 1)
+        ex = num / den
+        rel = abs(Dv[i] - ex) / ex
+        bits = max(0.0, -(math.log2(rel.numerator) - math.log2(rel.denominator))) if rel else p + 1
+        if k in got:
+            assert abs(got[k] - bits) <= 0.11, (k, got[k], bits)
+    assert 2.0 < r["bits_per_row"] < 12.0
+
+
+def test_work_counts():
+    import bench
+
+    # plain elimination: S(N) = (N-1)N(2N-1)/6 Schur products, N(N-1)/2 multipliers, N-1 pivot products
+    for N in (1, 2, 5, 64):
+        assert bench.elim_products(N, False) == (N - 1) * N * (2 * N - 1) // 6 + N * (N - 1) // 2 + (N - 1)
+    # lastcol: full rows, (N-1)^2 N / 2 update products, plus the N-1 last-column products
+    for N in (2, 5, 64):
+        assert bench.elim_products(N, True) == (N - 1) ** 2 * N // 2 + N * (N - 1) // 2 + 2 * (N - 1)

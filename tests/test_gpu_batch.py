@@ -107,3 +107,72 @@ def test_batch_full_size_C3_sampled(mpdet, oracle_lib):
         ozk, OD = oracle_minors(oracle_lib, kinds[m], inputs[m], p)
         assert same(b.minors_of(D, m), OD)
     b.close()
+
+
+def _mixed_items(g, count, Nmax):
+    items = []
+    for m in range(count):
+        N = int(g.integers(1, Nmax + 1))
+        if m % 2 == 0:
+            items.append(("cauchy", W.cauchy_xy(N, int(g.integers(1 << 30)))))
+        else:
+            items.append(("int", W.int_matrix(N, int(g.integers(1 << 30)))))
+    items.append(("int", np.array([[1, 2, 3], [2, 4, 5], [1, 1, 1]])))  # zero pivot at k = 2
+    return items
+
+
+@pytest.mark.parametrize("p", [512, 1024, 2048, 4096])
+def test_batch_variants_and_blocks_per_sm_are_bit_identical(mpdet, oracle_lib, p):
+    """Every lane-geometry variant of the persistent kernel, at its occupancy
+    limit and at one block per SM, gives the oracle's bits."""
+    items = _mixed_items(W.rng(300 + p), 23, 70)
+    b = make_batch(mpdet, items, p)
+    ref = [oracle_minors(oracle_lib, k, d, p) for k, d in items]
+    variants = b.variants()
+    assert len(variants) >= 1 and all(v[0] * v[1] == p // 32 == v[2] * v[3] for v in variants)
+    for vi, (Wl, G, PW, PG, mx) in enumerate(variants):
+        for bp in sorted({1, mx}):
+            b.tune(variant=vi, blocks_per_sm=bp)
+            zk, D = b.factor()
+            for m in range(len(items)):
+                assert zk[m] == ref[m][0], (vi, bp, m)
+                assert same(b.minors_of(D, m), ref[m][1]), f"variant {vi} (W={Wl}, G={G}) x {bp} blocks: matrix {m}"
+    b.close()
+
+
+def test_batch_graph_replay_and_autotune(mpdet, oracle_lib):
+    """CUDA-graph replay of the whole factorisation (device outputs) equals
+    the plain enqueue, also after the outputs move (re-capture) and after the
+    autotuner changes the launch shape."""
+    import torch
+
+    p = 1024
+    n = p // 32
+    items = _mixed_items(W.rng(991), 40, 60)
+    b = make_batch(mpdet, items, p)
+    zk0, D0 = b.factor()
+    tot = int(b.offsets[-1])
+
+    def dev_out():
+        return (torch.empty(tot, dtype=torch.int8, device="cuda"), torch.empty(tot, dtype=torch.int64, device="cuda"),
+                torch.empty((tot, n), dtype=torch.int32, device="cuda"),
+                torch.empty(len(items), dtype=torch.int64, device="cuda"))
+
+    def host(o):
+        torch.cuda.synchronize()
+        return (o[0].cpu().numpy(), o[1].cpu().numpy(), o[2].cpu().numpy().view(np.uint32)), o[3].cpu().numpy()
+
+    b.tune(graph=True)
+    for rep in range(3):
+        o = dev_out() if rep != 1 else o
+        b.factor(out=o[:3], zero_k=o[3])
+        D, zk = host(o)
+        assert same(D, D0) and np.array_equal(zk, zk0), rep
+    r = b.autotune(reps=1)
+    assert 0 <= r["variant"] < len(b.variants()) and r["blocks_per_sm"] >= 1 and r["ms"] > 0
+    assert r["candidates"] >= len(b.variants())
+    o = dev_out()
+    b.factor(out=o[:3], zero_k=o[3])
+    D, zk = host(o)
+    assert same(D, D0) and np.array_equal(zk, zk0)
+    b.close()

@@ -261,3 +261,75 @@ def test_single_element(oracle_lib):
     st, zk, D, Xm = oracle_lib.ge(oracle_lib.from_f64([-3.5], p), 1, p, lastcol=True)
     assert st == 0 and X.unpack(D, p) == [Fraction(-7, 2)]
     assert X.unpack(oracle_lib.lastcol_minors(Xm, D, 1, p), p) == [1]  # C_11 = D_0 = 1
+
+
+def test_minor_series_integer_exact(oracle_lib):
+    """Series of last-column minors for every leading size (Sec. 3): series n
+    against exact cofactors of the leading n x n block's last column, its
+    normalised form against C_jn / C_1n, and the Laplace identity per n."""
+    N, p = 10, 512
+    M = W.int_matrix(N, 11)
+    Ml = M.tolist()
+    st, zk, D, Xm = oracle_lib.ge(lift_int(oracle_lib, Ml, p), N, p, lastcol=True)
+    assert st == 0
+    S = X.unpack(oracle_lib.minor_series(Xm, D, N, p), p)
+    Sd = X.unpack(oracle_lib.minor_series(Xm, D, N, p, normalised=True), p)
+    Dl = X.unpack(D, p)
+    tol = Fraction(1, 2 ** (p - 64))
+    for nn in range(1, N + 1):
+        off = nn * (nn - 1) // 2
+        blk = [row[:nn] for row in Ml[:nn]]
+        Cx = exact_lastcol_cofactors(blk)
+        C = S[off:off + nn]
+        for c, cx in zip(C, Cx):
+            assert abs(c - cx) <= abs(cx) * tol
+        # Laplace along the last column of the n x n block: D_n = sum_j a_jn C_jn
+        lap = sum(Fraction(blk[j][nn - 1]) * C[j] for j in range(nn))
+        assert abs(lap - Dl[nn - 1]) <= sum(abs(Fraction(blk[j][nn - 1]) * C[j]) for j in range(nn)) * tol
+        d = Sd[off:off + nn]
+        assert d[0] == 1
+        for j in range(nn):
+            assert abs(d[j] - Cx[j] / Cx[0]) <= abs(Cx[j] / Cx[0]) * tol
+
+
+def test_minor_series_equals_standalone_runs(oracle_lib):
+    """Series n is bit-identical to the last-column minors of a standalone
+    n x n elimination of the leading block (both modes), Cauchy input."""
+    N, p = 14, 256
+    x, y = W.cauchy_xy(N, 21)
+    _, _, D, Xm = oracle_lib.ge(oracle_lib.cauchy(x, y, p), N, p, lastcol=True)
+    for normalised in (False, True):
+        S = oracle_lib.minor_series(Xm, D, N, p, normalised=normalised)
+        for nn in (1, 2, 3, 7, N):
+            _, _, Dn, Xn = oracle_lib.ge(oracle_lib.cauchy(x[:nn], y[:nn], p), nn, p, lastcol=True)
+            Cn = oracle_lib.lastcol_minors(Xn, Dn, nn, p, normalised=normalised)
+            off = nn * (nn - 1) // 2
+            assert X.same(tuple(t[off:off + nn] for t in S), Cn)
+
+
+def test_minor_series_2x2_by_hand(oracle_lib):
+    """[[a, b], [c, d]]: series 1 is (1), series 2 the cofactors (-c, a)."""
+    p = 128
+    A = [[3, 5], [7, 2]]
+    _, _, D, Xm = oracle_lib.ge(lift_int(oracle_lib, A, p), 2, p, lastcol=True)
+    S = X.unpack(oracle_lib.minor_series(Xm, D, 2, p), p)
+    # C^(2)_22 = D_1 = a exactly; C^(2)_12 = RN(a * l_21) = -c within three roundings
+    assert S[0] == 1 and S[2] == 3 and abs(S[1] + 7) <= 7 * Fraction(1, 2 ** (p - 3))
+    Sd = X.unpack(oracle_lib.minor_series(Xm, D, 2, p, normalised=True), p)
+    # delta^(2) = (1, C_22 / C_12) = (1, RN(1/l_21)), l_21 = -RN(c RN(1/a))
+    assert Sd[:2] == [1, 1] and abs(Sd[2] - Fraction(3, -7)) <= Fraction(3, 7) * Fraction(1, 2 ** (p - 3))
+
+
+def test_minor_series_zero_l_n1(oracle_lib):
+    """A leading block whose C_1n is zero: its normalised series is all +0,
+    the unnormalised one holds the exact (zero) cofactor."""
+    p = 128
+    # leading 2x2 block [[1, 0], [0, 1]]: l_21 = 0, C^(2)_12 = 0
+    A = [[1, 0, 2], [0, 1, 3], [4, 5, 6]]
+    _, _, D, Xm = oracle_lib.ge(lift_int(oracle_lib, A, p), 3, p, lastcol=True)
+    S = X.unpack(oracle_lib.minor_series(Xm, D, 3, p), p)
+    Sd = X.unpack(oracle_lib.minor_series(Xm, D, 3, p, normalised=True), p)
+    assert S[1:3] == [0, 1]
+    assert Sd[1:3] == [0, 0]
+    Cx = exact_lastcol_cofactors(A)
+    assert S[3:6] == Cx
