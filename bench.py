@@ -38,6 +38,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_1308_1536_gb300 import shard  # noqa: E402
 from paper_1308_1536_gb300 import workloads as W  # noqa: E402
 
 METRIC = "mp elimination limb-MAC/s"
@@ -204,19 +205,23 @@ def run_reference(args):
     return 0
 
 
-def bench_batch(args, dev, m):
+def bench_batch(args, dev, m, rank=0, world=1):
     """Workload C3: 4096 matrices, N ~ U[8, 256], half Cauchy half integer,
     p = 1024, det and leading minors of each, one persistent launch per step
     (inputs resident in HBM as p-bit numbers; the timed step copies them to
     the working array and factors), replayed as a CUDA graph, with the lane
-    geometry and blocks per SM chosen by the batch autotuner.  The single-matrix path is timed on a
-    sample of the same matrices at the same p for comparison."""
+    geometry and blocks per SM chosen by the batch autotuner.  With several
+    ranks every rank factors its share of the 4096 matrices (no exchange;
+    time = max over ranks).  The single-matrix path is timed on a sample of
+    the same matrices at the same p for comparison."""
     import torch
 
     cfg = W.C3
     p = cfg["p"]
     n = p // 32
-    Ns, kinds, seeds = W.batch_sizes(cfg["count"], cfg["Nmin"], cfg["Nmax"], cfg["seed"])
+    Ns_all, kinds_all, seeds_all = W.batch_sizes(cfg["count"], cfg["Nmin"], cfg["Nmax"], cfg["seed"])
+    mine = shard.batch_shard(Ns_all, rank, world)
+    Ns, kinds, seeds = Ns_all[mine], kinds_all[mine], seeds_all[mine]
     b = m.Batch(Ns, p, stream=torch.cuda.current_stream(dev).cuda_stream)
     inputs = []
     for i in range(len(Ns)):
@@ -247,10 +252,10 @@ def bench_batch(args, dev, m):
         b.factor(out=out, zero_k=zk)
     e1.record()
     torch.cuda.synchronize(dev)
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = shard.reduce_over_ranks(e0.elapsed_time(e1) / args.steps, "max", device=dev)
     launches = (b.launches() - l0) // args.steps
     b.close()
-    macs = batch_products(Ns) * n * n
+    macs = batch_products(Ns_all) * n * n
     # single-matrix path on a sample (every 16th matrix), same p, same GPU
     sample = list(range(0, len(Ns), 16))
     handles = {}
@@ -274,7 +279,8 @@ def bench_batch(args, dev, m):
         h.close()
     single_dets = len(sample) / t_single
     return {"workload": "4096 matrices N~U[8,256], half Cauchy half integer, p=1024: det + leading minors",
-            "dets_per_s": len(Ns) / (ms / 1e3), "ms_per_step": ms, "limb_macs_per_s": macs / (ms / 1e3),
+            "ranks": world, "matrices_per_rank": int(len(Ns)),
+            "dets_per_s": len(Ns_all) / (ms / 1e3), "ms_per_step": ms, "limb_macs_per_s": macs / (ms / 1e3),
             "gpu_launches_per_step": int(launches),
             "autotuned": {"W": var[0], "G": var[1], "pivot_W": var[2], "pivot_G": var[3],
                           "blocks_per_sm": tuned["blocks_per_sm"], "candidates": tuned["candidates"],
@@ -555,12 +561,7 @@ def run_gpu(args):
     serial_ms = (time.perf_counter() - t_serial) * 1e3
     hc.profile(False)
     hi.profile(False)
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = shard.reduce_over_ranks(ms, "max", device=dev)
     macs = step_limb_macs(N, p, 2)
     value = macs * world / (ms / 1e3)
 
@@ -584,16 +585,12 @@ def run_gpu(args):
     for _ in range(args.steps):
         outs = step_e2e()
     barrier()
-    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = shard.reduce_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps, "max", device=dev)
     h2d = x.nbytes + y.nbytes + A.nbytes
     d2h = sum(a.nbytes for o in outs for a in o)
 
+    # the batch workload runs on every rank (its share of the matrices)
+    batch = None if args.no_extras else bench_batch(args, dev, m, rank, world)
     if rank == 0:
         props = torch.cuda.get_device_properties(dev)
         nsm = props.multi_processor_count
@@ -644,7 +641,7 @@ def run_gpu(args):
             out["accuracy"] = {"what": f"leading minors D_k of the N={N} Cauchy matrix (GPU results of the timed "
                                        "step) against the closed-form Cauchy determinant at every k",
                                **cauchy_bit_loss(x, y, Dh, p)}
-            out["batch"] = bench_batch(args, dev, m)
+            out["batch"] = batch
             out["adjoint"] = bench_adjoint(args, dev, m)
             out["large"] = bench_large(args, dev, m, peak)
         if world == 1 and not args.no_cpu_baseline:
