@@ -219,7 +219,8 @@ def bench_batch(args, dev, m, rank=0, world=1):
     cfg = W.C3
     p = cfg["p"]
     n = p // 32
-    Ns_all, kinds_all, seeds_all = W.batch_sizes(cfg["count"], cfg["Nmin"], cfg["Nmax"], cfg["seed"])
+    Ns_all, kinds_all, seeds_all = W.batch_sizes(args.batch_count or cfg["count"], cfg["Nmin"], cfg["Nmax"],
+                                                 cfg["seed"])
     mine = shard.batch_shard(Ns_all, rank, world)
     Ns, kinds, seeds = Ns_all[mine], kinds_all[mine], seeds_all[mine]
     b = m.Batch(Ns, p, stream=torch.cuda.current_stream(dev).cuda_stream)
@@ -278,7 +279,7 @@ def bench_batch(args, dev, m, rank=0, world=1):
     for h in handles.values():
         h.close()
     single_dets = len(sample) / t_single
-    return {"workload": "4096 matrices N~U[8,256], half Cauchy half integer, p=1024: det + leading minors",
+    return {"workload": f"{len(Ns_all)} matrices N~U[8,256], half Cauchy half integer, p=1024: det + leading minors",
             "ranks": world, "matrices_per_rank": int(len(Ns)),
             "dets_per_s": len(Ns_all) / (ms / 1e3), "ms_per_step": ms, "limb_macs_per_s": macs / (ms / 1e3),
             "gpu_launches_per_step": int(launches),
@@ -590,7 +591,8 @@ def run_gpu(args):
     d2h = sum(a.nbytes for o in outs for a in o)
 
     # the batch workload runs on every rank (its share of the matrices)
-    batch = None if args.no_extras else bench_batch(args, dev, m, rank, world)
+    extras = set() if args.no_extras else set(args.extras.split(","))
+    batch = bench_batch(args, dev, m, rank, world) if "batch" in extras or "all" in extras else None
     if rank == 0:
         props = torch.cuda.get_device_properties(dev)
         nsm = props.multi_processor_count
@@ -636,13 +638,17 @@ def run_gpu(args):
             "roofline": roof,
             "clocks": clocks,
         }
-        if not args.no_extras:
+        want = lambda k: "all" in extras or k in extras  # noqa: E731
+        if want("accuracy"):
             Dh = (Dc[0].cpu().numpy(), Dc[1].cpu().numpy(), Dc[2].cpu().numpy().view(np.uint32))
             out["accuracy"] = {"what": f"leading minors D_k of the N={N} Cauchy matrix (GPU results of the timed "
                                        "step) against the closed-form Cauchy determinant at every k",
                                **cauchy_bit_loss(x, y, Dh, p)}
+        if batch is not None:
             out["batch"] = batch
+        if want("adjoint"):
             out["adjoint"] = bench_adjoint(args, dev, m)
+        if want("large"):
             out["large"] = bench_large(args, dev, m, peak)
         if world == 1 and not args.no_cpu_baseline:
             cb = oracle_sample()
@@ -665,7 +671,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mpdet", choices=["mpdet", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the batch and adjoint workloads")
+    ap.add_argument("--no-extras", action="store_true", help="skip the accuracy, batch, adjoint and large workloads")
+    ap.add_argument("--extras", default="all",
+                    help="comma list of accuracy,batch,adjoint,large (default all)")
+    ap.add_argument("--batch-count", type=int, default=0,
+                    help="profiling aid: matrices in the batch workload (default: the workload's 4096)")
     ap.add_argument("--N", type=int, default=0, help="profiling aid: override N (default: the workload's 1024)")
     ap.add_argument("--p", type=int, default=0, help="profiling aid: override p (default: the workload's 2048)")
     ap.add_argument("--update-variant", type=int, default=-1, help="tuning aid: Schur-update register budget 0..3")
