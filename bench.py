@@ -454,13 +454,39 @@ def bench_large(args, dev, m, peak_macs):
     rate = prods * n * n / (ms / 1e3)
     upd = pr["update_limb_macs"] / (pr["update_ms"] / 1e3)
     total = elim_products(N, False) * n * n
+    # Whole-run projection: a step's cost depends on its trailing size R =
+    # N - k - 1 (and p), not on the steps before it, so steps of smaller
+    # leading blocks of the same matrix stand in for the late steps of the
+    # full run; the step time is interpolated linearly between the sampled R
+    # (in R^2, the work) and summed over R = 0..N-1.
+    samples = [(N - 2, ms / w)]
+    for Rs in (2048, 1024, 512, 256, 128, 64, 16):
+        Ns = Rs + 2
+        hs = m.Mpdet(Ns, p, lastcol=False, stream=st.cuda_stream)
+        hs.set_cauchy(x[:Ns], y[:Ns])
+        hs.factor_range(0, 1)
+        e0.record(st)
+        hs.factor_range(1, 1 + w)
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        samples.append((Rs, e0.elapsed_time(e1) / w))
+        hs.close()
+    samples.sort()
+    rs = np.array([s_[0] for s_ in samples], dtype=np.float64)
+    ts = np.array([s_[1] for s_ in samples], dtype=np.float64)
+    Rall = np.arange(N, dtype=np.float64)
+    t_all = np.interp(Rall ** 2, rs ** 2, ts, left=ts[0])  # ms per step at trailing size R
+    proj_s = float(t_all.sum()) / 1e3
     return {"workload": f"Cauchy N={N} p={p} (68.9 GB in HBM), det + leading minors: steps 2..{1 + w} "
                         "timed (the heaviest; one full run is about an hour)",
             "window_ms": ms, "limb_macs_per_s": rate, "frac_of_imad_peak": rate / peak_macs,
             "update_kernel": {"achieved": upd / 1e12, "peak": peak_macs / 1e12, "unit": "Tlimb-MAC/s",
                               "frac": upd / peak_macs, "launches": int(pr["update_launches"])},
             "cauchy_generation_s": t_gen,
-            "projected_full_factorisation_s": total / rate}
+            "step_ms_by_trailing_size": {str(int(a)): round(b, 3) for a, b in samples},
+            "projected_full_factorisation_s": proj_s,
+            "projected_full_limb_macs_per_s": total / proj_s,
+            "projected_full_frac_of_imad_peak": total / proj_s / peak_macs}
 
 
 # ---------------------------------------------------------------------------
@@ -604,8 +630,9 @@ def run_gpu(args):
         upd_macs = pc["update_limb_macs"] + pi["update_limb_macs"]
         upd_launches = pc["update_launches"] + pi["update_launches"]
         achieved = upd_macs / (upd_ms / 1e3)
-        tr = recorded_traffic(upd_macs / (n * n) / max(upd_launches, 1))
         tensor = (p in (1024, 2048) and args.engine != 0)
+        # the recorded bytes per product belong to the tensor-core kernel at p = 2048
+        tr = recorded_traffic(upd_macs / (n * n) / max(upd_launches, 1)) if tensor and p == 2048 else None
         if tensor:
             # exact digit convolution on the tensor cores: one limb-MAC is 16 products of 8-bit digits,
             # 32 flops; peak = measured bf16 dense throughput (sustained: the kernel runs inside a long step)
