@@ -187,8 +187,8 @@ __device__ __forceinline__ bool any_below(const uint32_t (&v)[W], int first, int
 // T[r+W] holds 0 or 1 on entry (a previous carry); T[r+W+1] is written (set
 // to the outgoing carry) when it lies inside the 2W-limb tile.
 // ---------------------------------------------------------------------------
-template <int W>
-__device__ __forceinline__ void mac_row(uint32_t (&T)[2 * W], const uint32_t (&b)[W], uint32_t x, const int r) {
+template <int W, int L>
+__device__ __forceinline__ void mac_row(uint32_t (&T)[L], const uint32_t (&b)[W], uint32_t x, const int r) {
   uint32_t lo[W], hi[W];
 #pragma unroll
   for (int i = 0; i < W; ++i) {
@@ -204,7 +204,7 @@ __device__ __forceinline__ void mac_row(uint32_t (&T)[2 * W], const uint32_t (&b
   T[r + 1] = add_cc(T[r + 1], hi[0]);
 #pragma unroll
   for (int i = 1; i < W; ++i) T[r + 1 + i] = addc_cc(T[r + 1 + i], hi[i]);
-  if (r + W + 1 < 2 * W) T[r + W + 1] = addc(0u, 0u);
+  if (r + W + 1 < L) T[r + W + 1] = addc(0u, 0u);
 }
 
 // ---------------------------------------------------------------------------
@@ -223,6 +223,62 @@ __device__ __forceinline__ void mac_row(uint32_t (&T)[2 * W], const uint32_t (&b
 // matter through the round bit and the sticky bit.  After G blocks lane g
 // holds product limbs [n + g*W, n + g*W + W).
 // ---------------------------------------------------------------------------
+// The block loop of mul_round for wide slices (W >= 32): the W x W tile is
+// formed S rows at a time in a window of W + S + 1 registers (absolute tile
+// limbs [sS, sS + W + S] during rows sS .. sS + S - 1).  After each group of
+// S rows the window's lowest S limbs are final: they go down one lane (into
+// R, filled by rotation) and into lane 0's sticky bit, and the window moves
+// up by S.  The unrolled body is S rows instead of W, which keeps the loop
+// inside the instruction cache; the limbs computed are those of the full
+// tile, in the same order.
+template <int W, int G, int S>
+__device__ __forceinline__ void mul_blocks_windowed(const Grp<G>& gp, const uint32_t (&b)[W], const uint32_t* z,
+                                                    uint32_t (&H)[W], uint32_t (&R)[W], uint32_t& sticky,
+                                                    uint32_t& ltop) {
+  static_assert(W % S == 0 && S % 4 == 0, "window of whole uint4 groups");
+#pragma unroll 1
+  for (int B = 0; B < G; ++B) {
+    uint32_t Tw[W + S + 1];
+    Tw[0] = add_cc(H[0], R[0]);
+#pragma unroll
+    for (int i = 1; i < W; ++i) Tw[i] = addc_cc(H[i], R[i]);
+    Tw[W] = addc(0u, 0u);
+    const uint32_t* zb = z + B * W;
+    uint32_t o = 0u;
+#pragma unroll 1
+    for (int s0 = 0; s0 < W; s0 += S) {
+#pragma unroll
+      for (int j = 0; j < S; j += 4) {
+        uint4 q = *reinterpret_cast<const uint4*>(zb + s0 + j);
+        mac_row<W>(Tw, b, q.x, j);
+        mac_row<W>(Tw, b, q.y, j + 1);
+        mac_row<W>(Tw, b, q.z, j + 2);
+        mac_row<W>(Tw, b, q.w, j + 3);
+      }
+      // limbs s0 .. s0 + S - 1 of the tile are final: down one lane into the
+      // top of R (R moves down by S), and into lane 0's sticky bit except
+      // limb n - 1 of the product (the last tile's limb W - 1), kept whole
+#pragma unroll
+      for (int i = 0; i < W - S; ++i) R[i] = R[i + S];
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        const uint32_t v = __shfl_down_sync(FULL, Tw[j], 1);
+        R[W - S + j] = (gp.g == G - 1) ? 0u : v;
+      }
+      const bool last = (B == G - 1) && (s0 == W - S);
+#pragma unroll
+      for (int j = 0; j < S - 1; ++j) o |= Tw[j];
+      if (last) ltop = Tw[S - 1];
+      else o |= Tw[S - 1];
+#pragma unroll
+      for (int i = 0; i <= W; ++i) Tw[i] = Tw[i + S];
+    }
+    sticky |= o;
+#pragma unroll
+    for (int i = 0; i < W; ++i) H[i] = Tw[i];
+  }
+}
+
 template <int W, int G>
 __device__ __forceinline__ int mul_round(const Grp<G>& gp, const uint32_t (&b)[W], const uint32_t* z,
                                          uint32_t (&M)[W]) {
@@ -233,6 +289,9 @@ __device__ __forceinline__ int mul_round(const Grp<G>& gp, const uint32_t (&b)[W
     R[i] = 0u;
   }
   uint32_t sticky = 0u, ltop = 0u;
+  if constexpr (W >= 32) {
+    mul_blocks_windowed<W, G, 8>(gp, b, z, H, R, sticky, ltop);
+  } else {
 #pragma unroll 1
   for (int B = 0; B < G; ++B) {
     uint32_t T[2 * W];
@@ -264,6 +323,7 @@ __device__ __forceinline__ int mul_round(const Grp<G>& gp, const uint32_t (&b)[W
     sticky |= o;
 #pragma unroll
     for (int i = 0; i < W; ++i) H[i] = T[W + i];
+  }
   }
   // upper half: F = H + R, carries across the slices
   uint32_t F[W];
