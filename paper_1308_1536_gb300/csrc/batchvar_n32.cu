@@ -8,6 +8,7 @@ const BatchVariant* batch_variants_n32(int* count) {
   static const BatchVariant v[] = {
       {8, 4, 4, 8, &Launch<8, 4>::batch_p<4, 8>, &Launch<8, 4>::batch_blocks_per_sm_p<4, 8>},
       {4, 8, 4, 8, &Launch<4, 8>::batch_p<4, 8>, &Launch<4, 8>::batch_blocks_per_sm_p<4, 8>},
+      {32, 1, 4, 8, &Launch<32, 1>::batch_p<4, 8>, &Launch<32, 1>::batch_blocks_per_sm_p<4, 8>},
   };
   *count = (int)(sizeof v / sizeof v[0]);
   return v;

@@ -833,13 +833,19 @@ __global__ void __launch_bounds__(128, 4) k_batch(MpArr Xall, MpArr Dall, MpArr 
         }
       }
       __syncthreads();
-      // Schur update of the trailing R x R block, items (i, j) flattened
+      // Schur update of the trailing R x R block, items (i, j) flattened; the
+      // group's item t = t0 + gid advances by NG, its row and column follow
+      // without a division per item
       const int64_t items = R * R;
+      int64_t ti = gid / R, tj = gid % R;
       for (int64_t t0 = 0; t0 < items; t0 += NG) {
-        int64_t t = t0 + gid;
-        const bool active = t < items;
-        if (!active) t = items - 1;
-        const int64_t i = k + 1 + t / R, j = k + 1 + t % R;
+        const bool active = t0 + gid < items;
+        const int64_t i = k + 1 + (active ? ti : R - 1), j = k + 1 + (active ? tj : R - 1);
+        tj += NG;
+        while (tj >= R) {
+          tj -= R;
+          ++ti;
+        }
         const int64_t kj = k * N + j, ij = i * N + j;
         uint32_t Bk[W], T[W], Xv[W];
         load_slice<W>(X.m + kj * n + gp.g * W, Bk);
