@@ -197,13 +197,18 @@ int64_t mpdet_steps_done(mpdet_t h);
  * step's kernels one after another on the handle's stream.
  * MPDET_TUNE_LOOKAHEAD_RESERVE (0..64, default 4): SMs the update of the
  * other columns leaves free for that second stream.
+ * MPDET_TUNE_UPDATE_GEOMETRY: lane geometry of the IMAD update kernel: 0 the
+ * precision's own (16 limbs per lane below p = 32768), 1 or 2 32 limbs per
+ * lane (p = 2048 .. 16384) compiled for 4 or 3 resident blocks per SM, -1
+ * (default) the one measured fastest for the precision.
  * Errors: MPDET_EINVAL. */
 enum {
   MPDET_TUNE_UPDATE_VARIANT = 1,
   MPDET_TUNE_ENGINE = 2,
   MPDET_TUNE_TC_MIN_ROWS = 3,
   MPDET_TUNE_LOOKAHEAD = 4,
-  MPDET_TUNE_LOOKAHEAD_RESERVE = 5
+  MPDET_TUNE_LOOKAHEAD_RESERVE = 5,
+  MPDET_TUNE_UPDATE_GEOMETRY = 6
 };
 int mpdet_tune(mpdet_t h, int param, int value);
 

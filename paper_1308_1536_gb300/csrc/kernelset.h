@@ -57,6 +57,19 @@ inline UpdArgs upd_rest(int64_t N, int64_t k, int lastcol) {
 // Back substitution of the adjoint: rows [0, k), every column, pivot row k.
 inline UpdArgs upd_back(int64_t N, int64_t k) { return UpdArgs{N, k, 0, k, 0, INT64_MAX, N, -1, 0}; }
 
+typedef cudaError_t (*UpdateFn)(MpArr X, const UpdArgs& a, MpArr Z, const int* status, int p, int nsm,
+                                cudaStream_t st);
+
+// Schur update with 32 limbs per lane for n = 64 .. 512 (updwide_*.cu),
+// compiled for at least minb (3 or 4) resident 128-thread blocks per SM, or
+// nullptr: the wide alternative to a kernel set's own update geometry.
+UpdateFn update_wide_a(int n, int minb);
+UpdateFn update_wide_b(int n, int minb);
+inline UpdateFn update_wide_for(int n, int minb) {
+  UpdateFn f = update_wide_a(n, minb);
+  return f ? f : update_wide_b(n, minb);
+}
+
 struct KernelSet {
   int W, G;
   int PW, PG;  // lane geometry of the pivot and the single reciprocal (PW * PG = W * G)

@@ -62,6 +62,9 @@ struct mpdet_ctx {
   // step k on all SMs but la_reserve
   int lookahead = 1;
   int la_reserve = 4;
+  // IMAD update geometry: 0 the kernel set's own, 1 / 2 32 limbs per lane
+  // compiled for 4 / 3 blocks per SM (n = 64 .. 512); -1 per precision
+  int upd_geom = -1;
   cudaStream_t side = nullptr;
   cudaEvent_t ev_mult = nullptr, ev_rest = nullptr;
   bool have_matrix = false;
@@ -333,6 +336,23 @@ static bool use_tc(mpdet_t h, int64_t rows) {
   return h->engine >= 1 && mpd::tc_supports(h->p, h->engine == 1) && rows >= thr;
 }
 
+// Default IMAD update geometry per limb count (-1 resolved): the kernel
+// set's own unless the wide one measured faster.
+static int default_upd_geom(int n) {
+  (void)n;
+  return 0;
+}
+
+// The IMAD Schur-update kernel the handle uses.
+static mpd::UpdateFn imad_update(mpdet_t h) {
+  const int g = h->upd_geom >= 0 ? h->upd_geom : default_upd_geom(h->n);
+  if (g > 0) {
+    mpd::UpdateFn f = mpd::update_wide_for(h->n, g == 1 ? 4 : 3);
+    if (f) return f;
+  }
+  return h->ks->update[h->upd_variant];
+}
+
 // Enqueue one rank-1 update launch of the array A on stream st: single
 // columns on the column kernel, long launches on the tensor engine where it
 // exists, the rest on the IMAD kernel.  nsm: SMs the launch may fill.
@@ -343,7 +363,7 @@ static int launch_update(mpdet_t h, MpArr A, const UpdArgs& a, MpArr Z, int nsm,
   else if (use_tc(h, a.nrows))
     CU(h, mpd::update_tc(A, a, Z, h->status, h->p, nsm, st, h->engine == 1 ? 1 : 0));
   else
-    CU(h, h->ks->update[h->upd_variant](A, a, Z, h->status, h->p, nsm, st));
+    CU(h, imad_update(h)(A, a, Z, h->status, h->p, nsm, st));
   h->launches += 1;
   return MPDET_OK;
 }
@@ -472,6 +492,10 @@ extern "C" int mpdet_tune(mpdet_t h, int param, int value) {
     case MPDET_TUNE_LOOKAHEAD_RESERVE:
       if (value < 0 || value > 64) return fail(h, MPDET_EINVAL, "tune: lookahead reserve %d", value);
       h->la_reserve = value;
+      return MPDET_OK;
+    case MPDET_TUNE_UPDATE_GEOMETRY:
+      if (value < -1 || value > 2) return fail(h, MPDET_EINVAL, "tune: update geometry %d", value);
+      h->upd_geom = value;
       return MPDET_OK;
     default:
       return fail(h, MPDET_EINVAL, "tune: unknown parameter %d", param);

@@ -148,3 +148,37 @@ def test_tensor_engine_lazy_drain_fallback(mpdet, oracle_lib, p):
     assert X.same(out[0][2], out[1][2]) and X.same(out[0][3], out[1][3])
     st, ozk, OD, OX = oracle_lib.ge(A, N, p, lastcol=True, nthreads=8)
     assert out[0][:2] == (st, ozk) and X.same(out[0][2], OD) and X.same(out[0][3], OX)
+
+
+@pytest.mark.parametrize("p", [2048, 4096, 8192, 16384])
+def test_imad_update_geometries_are_bit_identical(mpdet, oracle_lib, p):
+    """The IMAD update with 32 limbs per lane (both register budgets) gives
+    the bits of the precision's own geometry, in both modes and for the
+    adjoint's back substitution, and the oracle's."""
+    N = 37 if p <= 4096 else 21
+    data = W.cauchy_xy(N, p + 1)
+
+    def go(geom, lastcol):
+        h = mpdet.Mpdet(N, p, lastcol=lastcol)
+        h.tune(engine=0, update_geometry=geom)
+        h.set_cauchy(*data)
+        rc, zk, D = h.factor()
+        Xm = h.get_mp()
+        h.close()
+        return rc, zk, D, Xm
+
+    for lastcol in (False, True):
+        base = go(0, lastcol)
+        for geom in (1, 2, -1):
+            a = go(geom, lastcol)
+            assert a[:2] == base[:2] and X.same(a[2], base[2]) and X.same(a[3], base[3]), (geom, lastcol)
+    st, ozk, OD, OX = oracle_lib.ge(oracle_lib.cauchy(*data, p), N, p, lastcol=True, nthreads=8)
+    assert X.same(base[2], OD) and X.same(base[3], OX)
+    A = W.rng(p).standard_normal((N, N))
+    g = []
+    for geom in (0, 1):
+        h = mpdet.Mpdet(N, p, lastcol=True)
+        h.tune(engine=0, update_geometry=geom)
+        g.append(h.logabsdet_grad(A, grad=True))
+        h.close()
+    assert g[0][0] == g[1][0] and g[0][1] == g[1][1] and np.array_equal(g[0][2], g[1][2])
