@@ -489,6 +489,53 @@ def bench_large(args, dev, m, peak_macs):
             "projected_full_frac_of_imad_peak": total / proj_s / peak_macs}
 
 
+def bench_hostmem(args, dev, m, peak_macs):
+    """The N x N array in page-locked host memory that the GPU reads and
+    writes in place (MPDET_HOSTMEM), for matrices larger than HBM such as the
+    paper's N = 12000 at 32768 bits (590 GB).  Cauchy N = 2048, p = 32768
+    (17.2 GB): steps 2..3 timed with the array host-resident and
+    device-resident; the whole N = 12000 factorisation is projected from the
+    host-resident step time (a step's work grows as its trailing size
+    squared, measured down to R = 256 on the device-resident path)."""
+    import torch
+
+    N, p, w = 2048, 32768, 2
+    n = p // 32
+    need = N * N * (4 * n + 9)
+    try:
+        avail = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+    except (ValueError, OSError):
+        avail = 0
+    if avail < 3 * need:
+        return {"skipped": f"host memory: {avail / 1e9:.0f} GB free, {3 * need / 1e9:.0f} GB wanted"}
+    x, y = W.cauchy_xy(N, W.C5["seed"])
+    st = torch.cuda.current_stream(dev)
+    out = {"workload": f"Cauchy N={N} p={p} ({need / 1e9:.1f} GB), det + leading minors: steps 2..{1 + w} timed"}
+    for host in (True, False):
+        h = m.Mpdet(N, p, lastcol=False, stream=st.cuda_stream, hostmem=host)
+        h.set_cauchy(x, y)
+        h.factor_range(0, 1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(st)
+        h.factor_range(1, 1 + w)
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        assert h.status()[0] == 0
+        h.close()
+        out["host_ms" if host else "device_ms"] = e0.elapsed_time(e1)
+    prods = sum((N - k - 1) ** 2 + (N - k - 1) + 1 for k in range(1, 1 + w))
+    rate = prods * n * n / (out["host_ms"] / 1e3)
+    out["host_limb_macs_per_s"] = rate
+    out["host_frac_of_imad_peak"] = rate / peak_macs
+    out["host_vs_device"] = out["device_ms"] / out["host_ms"]
+    Nb = 12000
+    total = elim_products(Nb, False) * n * n
+    out["projected_N12000_p32768_s"] = total / rate
+    out["projected_N12000_p32768_array_bytes"] = Nb * Nb * (4 * n + 9)
+    return out
+
+
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
@@ -677,6 +724,8 @@ def run_gpu(args):
             out["adjoint"] = bench_adjoint(args, dev, m)
         if want("large"):
             out["large"] = bench_large(args, dev, m, peak)
+        if want("hostmem"):
+            out["hostmem"] = bench_hostmem(args, dev, m, peak)
         if world == 1 and not args.no_cpu_baseline:
             cb = oracle_sample()
             cb.pop("seconds", None)
@@ -700,7 +749,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the accuracy, batch, adjoint and large workloads")
     ap.add_argument("--extras", default="all",
-                    help="comma list of accuracy,batch,adjoint,large (default all)")
+                    help="comma list of accuracy,batch,adjoint,large,hostmem (default all)")
     ap.add_argument("--batch-count", type=int, default=0,
                     help="profiling aid: matrices in the batch workload (default: the workload's 4096)")
     ap.add_argument("--N", type=int, default=0, help="profiling aid: override N (default: the workload's 1024)")

@@ -72,7 +72,7 @@ enum {
   MPDET_ENOSCRATCH = 8   /* problem larger than mpdet_factor_noalloc's static working memory */
 };
 
-enum { MPDET_LASTCOL = 1 };
+enum { MPDET_LASTCOL = 1, MPDET_HOSTMEM = 2 };
 
 /* Create a handle for N x N matrices at p bits on the current CUDA device.
  * p must be a power of two with 128 <= p <= 32768 (n = p/32 limbs; the kernel
@@ -80,8 +80,19 @@ enum { MPDET_LASTCOL = 1 };
  * last-column minors, 1.5x the work: Sec. 3 counts it as twice the row
  * operations).  cuda_stream: a cudaStream_t (NULL = legacy default stream).
  * Allocates (4n + 9) * N^2 bytes of device memory plus O(N n).
- * Errors: MPDET_EINVAL (N < 1, unsupported p, out == NULL), MPDET_ENOMEM,
- * MPDET_ECUDA. */
+ * MPDET_HOSTMEM (may be combined with MPDET_LASTCOL): the N x N array lives
+ * in page-locked host memory mapped into the GPU's address space instead
+ * (cudaHostAlloc, mapped), which the kernels read and write in place; on a
+ * Grace-Blackwell node the GPU reaches it coherently over NVLink-C2C.  This
+ * is for matrices larger than the GPU's memory, such as the paper's
+ * production size N = 12000 at 32768 bits (590 GB, Sec. 4.2 pages blocks
+ * to disk for it).  Every update of a p-bit number reads and writes 8n + 18
+ * bytes for n^2 limb multiply-accumulates, so at p >= 8192 the link keeps
+ * up with the arithmetic.  The update then runs on the IMAD engine (the
+ * tensor-core engine's TMA copies address device memory only).  Results are
+ * bit-identical to the device-resident array.
+ * Errors: MPDET_EINVAL (N < 1, unsupported p, unknown flag, out == NULL),
+ * MPDET_ENOMEM, MPDET_ECUDA. */
 int mpdet_create(int64_t N, int32_t p_bits, uint32_t flags, void* cuda_stream, mpdet_t* out);
 
 /* Set A from an N x N row-major double matrix with leading dimension ld >= N

@@ -23,6 +23,7 @@ from . import build as _build
 ZEXP = np.iinfo(np.int64).min
 OK, EINVAL, ENOMEM, ECUDA, EZEROPIVOT, ETIMEOUT, ESTATE, EZERODIV, ENOSCRATCH = range(9)
 LASTCOL = 1
+HOSTMEM = 2
 _NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EZEROPIVOT", 5: "ETIMEOUT", 6: "ESTATE",
           7: "EZERODIV", 8: "ENOSCRATCH"}
 
@@ -185,9 +186,11 @@ class Mpdet:
 
     ``lastcol=True`` keeps L in A's strict lower triangle so that the signed
     minors of the last column are available after the factorisation.
+    ``hostmem=True`` keeps the N x N array in page-locked host memory that
+    the GPU reads and writes in place (matrices larger than HBM).
     """
 
-    def __init__(self, N: int, p: int, lastcol: bool = False, stream=None):
+    def __init__(self, N: int, p: int, lastcol: bool = False, stream=None, hostmem: bool = False):
         self.lib = load()
         self.N, self.p, self.n = int(N), int(p), int(p) // 32
         self.lastcol = bool(lastcol)
@@ -200,8 +203,8 @@ class Mpdet:
                 stream = None
         self.stream = stream
         h = ctypes.c_void_p()
-        rc = self.lib.mpdet_create(self.N, self.p, LASTCOL if lastcol else 0, ctypes.c_void_p(stream or 0),
-                                   ctypes.byref(h))
+        flags = (LASTCOL if lastcol else 0) | (HOSTMEM if hostmem else 0)
+        rc = self.lib.mpdet_create(self.N, self.p, flags, ctypes.c_void_p(stream or 0), ctypes.byref(h))
         if rc:
             raise MpdetError(rc, f"create(N={N}, p={p})")
         self.h = h

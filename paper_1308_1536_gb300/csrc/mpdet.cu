@@ -49,6 +49,7 @@ struct mpdet_ctx {
   MpArr X{}, D{}, Z{}, R{}, T{};  // matrix, minors, multipliers, reciprocal, temp (N numbers)
   MpArr Z2{};                     // multipliers of odd steps under look-ahead (N numbers)
   MpArr S{};                      // adjoint: S = L, then X = A^-1 (N*N numbers, allocated on first use)
+  void* xhost[3] = {nullptr, nullptr, nullptr};  // MPDET_HOSTMEM: host allocations behind X (limbs, exp, sign)
   int* status = nullptr;          // [0] code
   int64_t* zero_k = nullptr;
   void* stage = nullptr;  // device staging for host inputs
@@ -113,6 +114,28 @@ static void free_arr(MpArr* a) {
   *a = MpArr{};
 }
 
+// The in-place array in page-locked host memory mapped into the device's
+// address space (MPDET_HOSTMEM): the kernels read and write it in place.
+static int alloc_arr_host(mpdet_t h, MpArr* a, int64_t count) {
+  const size_t bytes[3] = {(size_t)count * h->n * 4, (size_t)count * 8, (size_t)count};
+  void* hp[3] = {nullptr, nullptr, nullptr};
+  void* dp[3] = {nullptr, nullptr, nullptr};
+  for (int q = 0; q < 3; ++q) {
+    if (cudaHostAlloc(&hp[q], bytes[q], cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess ||
+        cudaHostGetDevicePointer(&dp[q], hp[q], 0) != cudaSuccess) {
+      cudaGetLastError();
+      for (int r = 0; r <= q; ++r)
+        if (hp[r]) cudaFreeHost(hp[r]);
+      return fail(h, MPDET_ENOMEM, "cudaHostAlloc of %zu bytes", bytes[q]);
+    }
+  }
+  h->xhost[0] = hp[0];
+  h->xhost[1] = hp[1];
+  h->xhost[2] = hp[2];
+  *a = MpArr{(int8_t*)dp[2], (int64_t*)dp[1], (uint32_t*)dp[0]};
+  return MPDET_OK;
+}
+
 // zero (+0) numbers: sign 0, exp INT64_MIN, limbs 0
 static cudaError_t zero_arr(MpArr a, int64_t count, int n, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(a.m, 0, (size_t)count * n * 4, st);
@@ -139,7 +162,7 @@ extern "C" int mpdet_create(int64_t N, int32_t p_bits, uint32_t flags, void* cud
   if (!out) return MPDET_EINVAL;
   *out = nullptr;
   if (N < 1 || N > (int64_t)1 << 20) return MPDET_EINVAL;
-  if (flags & ~(uint32_t)MPDET_LASTCOL) return MPDET_EINVAL;
+  if (flags & ~(uint32_t)(MPDET_LASTCOL | MPDET_HOSTMEM)) return MPDET_EINVAL;
   if (mpdet_geometry(p_bits, nullptr, nullptr, nullptr) != MPDET_OK) return MPDET_EINVAL;
   mpdet_t h = new (std::nothrow) mpdet_ctx();
   if (!h) return MPDET_ENOMEM;
@@ -155,7 +178,7 @@ extern "C" int mpdet_create(int64_t N, int32_t p_bits, uint32_t flags, void* cud
       cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
     rc = MPDET_ECUDA;
   }
-  if (rc == MPDET_OK) rc = alloc_arr(h, &h->X, N * N);
+  if (rc == MPDET_OK) rc = (flags & MPDET_HOSTMEM) ? alloc_arr_host(h, &h->X, N * N) : alloc_arr(h, &h->X, N * N);
   if (rc == MPDET_OK) rc = alloc_arr(h, &h->D, N);
   if (rc == MPDET_OK) rc = alloc_arr(h, &h->Z, N);
   if (rc == MPDET_OK) rc = alloc_arr(h, &h->Z2, N);
@@ -187,6 +210,13 @@ extern "C" int mpdet_create(int64_t N, int32_t p_bits, uint32_t flags, void* cud
 
 extern "C" int mpdet_free(mpdet_t h) {
   if (!h) return MPDET_OK;
+  if (h->flags & MPDET_HOSTMEM) {
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->side) cudaStreamSynchronize(h->side);
+    for (void* hp : h->xhost)
+      if (hp) cudaFreeHost(hp);
+    h->X = MpArr{};
+  }
   free_arr(&h->X);
   free_arr(&h->D);
   free_arr(&h->Z);
@@ -332,6 +362,7 @@ static int64_t tc_default_min_rows(int p) { return p == 2048 ? 64 : (p == 1024 ?
 
 // Tensor engine for an update launch of `rows` rows?
 static bool use_tc(mpdet_t h, int64_t rows) {
+  if (h->flags & MPDET_HOSTMEM) return false;  // its TMA copies address device memory only
   const int64_t thr = h->tc_min_rows >= 0 ? h->tc_min_rows : tc_default_min_rows(h->p);
   return h->engine >= 1 && mpd::tc_supports(h->p, h->engine == 1) && rows >= thr;
 }

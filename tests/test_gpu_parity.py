@@ -208,3 +208,27 @@ def test_full_size_C2_sampled(mpdet, oracle_lib):
         o = oracle_run(oracle_lib, K, p, False, kind, lead)
         assert_same(tuple(t[:K] for t in D), o[2], f"{kind}: leading minors 1..{K}")
         assert C[0][N - 1] == D[0][N - 2] and C[1][N - 1] == D[1][N - 2] and np.array_equal(C[2][N - 1], D[2][N - 2])
+
+
+@pytest.mark.parametrize("N,p,lastcol", [(70, 1024, True), (33, 8192, True), (40, 4096, False)])
+def test_host_resident_array(mpdet, oracle_lib, N, p, lastcol):
+    """The N x N array in page-locked host memory (MPDET_HOSTMEM), read and
+    written in place by the kernels: bit-identical to the device-resident
+    array and to the oracle, windows and the last-column minors included."""
+    x, y = W.cauchy_xy(N, 4040 + N)
+    out = []
+    for host in (False, True):
+        h = mpdet.Mpdet(N, p, lastcol=lastcol, hostmem=host)
+        h.set_cauchy(x, y)
+        h.factor_range(0, N // 3)
+        rc, zk, D = h.factor()
+        Xm = h.get_mp()
+        C = h.lastcol_minors() if lastcol else None
+        h.close()
+        out.append((rc, zk, D, Xm, C))
+    assert out[0][:2] == out[1][:2] == (0, 0)
+    assert same(out[0][2], out[1][2]) and same(out[0][3], out[1][3])
+    if lastcol:
+        assert same(out[0][4], out[1][4])
+    st, ozk, OD, OX = oracle_lib.ge(oracle_lib.cauchy(x, y, p), N, p, lastcol=lastcol, nthreads=8)
+    assert_same(out[1][2], OD, "leading minors (host-resident)")
