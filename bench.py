@@ -677,7 +677,7 @@ def run_gpu(args):
         upd_macs = pc["update_limb_macs"] + pi["update_limb_macs"]
         upd_launches = pc["update_launches"] + pi["update_launches"]
         achieved = upd_macs / (upd_ms / 1e3)
-        tensor = (p in (1024, 2048) and args.engine != 0)
+        tensor = (p == 2048 and args.engine != 0)  # the default engine per precision
         # the recorded bytes per product belong to the tensor-core kernel at p = 2048
         tr = recorded_traffic(upd_macs / (n * n) / max(upd_launches, 1)) if tensor and p == 2048 else None
         if tensor:

@@ -358,7 +358,11 @@ static int next_event(mpdet_t h, cudaEvent_t* ev) {
 // measurements of whole eliminations: at p = 2048 it is twice as fast as the
 // IMAD kernel from about 64 rows on, at p = 1024 some 12 % faster from about
 // 128 rows on, and at p = 512 slower at every size measured (N <= 2048).
-static int64_t tc_default_min_rows(int p) { return p == 2048 ? 64 : (p == 1024 ? 128 : INT64_MAX); }
+// Default row threshold of the tensor engine per precision: 64 rows at
+// p = 2048; at p = 512 and 1024 the IMAD kernel measured faster at every
+// size (whole eliminations, lastcol mode, N = 256 .. 2048), so it takes all
+// launches there unless the threshold is set.
+static int64_t tc_default_min_rows(int p) { return p == 2048 ? 64 : INT64_MAX; }
 
 // Tensor engine for an update launch of `rows` rows?
 static bool use_tc(mpdet_t h, int64_t rows) {
