@@ -358,6 +358,18 @@ int mpdet_batch_free(mpdet_batch_t b);
  * Errors: MPDET_EINVAL, MPDET_ECUDA. */
 int mpdet_ops(int op, int64_t count, int32_t p_bits, mpdet_numv a, mpdet_numv b, mpdet_numv out, void* cuda_stream);
 
+/* Failure-detection self-test (the paper has no counterpart).  Every wait of
+ * the kernels' hand-offs polls an mbarrier a bounded number of times and, when
+ * the bound runs out, reports MPDET_ETIMEOUT through the handle's status word
+ * and returns instead of hanging the GPU.  This call runs one such bounded
+ * wait (at most `limit` polls, limit >= 1) in a one-block kernel on
+ * cuda_stream, on a barrier that nothing completes (arrive = 0) or that the
+ * block completes itself (arrive != 0, the control), and synchronises.
+ * Returns MPDET_ETIMEOUT when the wait ran out, MPDET_OK when it completed;
+ * the context stays usable either way.  Errors: MPDET_EINVAL, MPDET_ENOMEM,
+ * MPDET_ECUDA. */
+int mpdet_selftest_timeout(int32_t limit, int arrive, void* cuda_stream);
+
 /* Release the handle and its device memory (NULL is accepted). */
 int mpdet_free(mpdet_t h);
 

@@ -95,6 +95,7 @@ def load(build_if_missing: bool = True):
         "mpdet_get_inverse": ([P, NumV, ctypes.c_int], ctypes.c_int),
         "mpdet_ops": ([ctypes.c_int, i64, i32, NumV, NumV, NumV, P], ctypes.c_int),
         "mpdet_factor_noalloc": ([i64, i32, u32, NumV, NumV, NumV, ctypes.POINTER(i64), P], ctypes.c_int),
+        "mpdet_selftest_timeout": ([i32, ctypes.c_int, P], ctypes.c_int),
         "mpdet_profile_read": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)], ctypes.c_int),
     }
@@ -131,6 +132,21 @@ def factor_noalloc(A, N: int, p: int, minors, lastcol=None, stream=None):
     if rc not in (OK, EZEROPIVOT):
         raise MpdetError(rc, f"factor_noalloc(N={N}, p={p})")
     return rc, int(zk.value)
+
+
+def selftest_timeout(limit: int = 4096, arrive: bool = False, stream=None) -> int:
+    """Run one bounded mbarrier wait (at most ``limit`` polls) on a barrier
+    nothing completes (or, with ``arrive``, one the block completes itself);
+    returns the status code: ETIMEOUT when the wait ran out, OK otherwise."""
+    lib = load()
+    if stream is None:
+        import torch
+
+        stream = torch.cuda.current_stream().cuda_stream
+    rc = lib.mpdet_selftest_timeout(int(limit), int(bool(arrive)), ctypes.c_void_p(stream or 0))
+    if rc not in (OK, ETIMEOUT):
+        raise MpdetError(rc, "selftest_timeout")
+    return rc
 
 
 def ops(op: str, a, b, p: int):
