@@ -112,6 +112,9 @@ def test_to_f64_is_correctly_rounded(oracle_lib):
     # ties at the binary64 boundary, the smallest subnormal, the largest finite
     vals += [Fraction(1) + Fraction(1, 2 ** 53), Fraction(1) + Fraction(3, 2 ** 53), Fraction(1, 2 ** 1075),
              Fraction(3, 2 ** 1076), Fraction(2 ** 1024 - 2 ** 970), Fraction(1, 2 ** 1022) * (1 - Fraction(1, 2 ** 60))]
+    # just above half the smallest subnormal: one rounding gives 2^-1074; rounding to 53 bits first and
+    # then to the subnormal grid gives a tie and 0 (the subnormal quantum must be applied directly)
+    vals += [Fraction(1, 2 ** 1075) * (1 + Fraction(1, 2 ** 59)), Fraction(5, 2 ** 1060) * (1 + Fraction(1, 2 ** 70))]
     packed = X.pack(vals, p)
     got = oracle_lib.to_f64(packed, p)
     for v, gv in zip(X.unpack(packed, p), got):

@@ -32,6 +32,17 @@ MUTATIONS = [
      "int64_t ij = i * N + j, kj = (k + 1) * N + j;", ["test_oracle_ge.py::test_integer_minors_vs_exact"]),
     ("Cauchy entries from x - y", "op_add(&c, xs, xe, xm, ys, ye, ym, 0, &ts, &te, tm);",
      "op_add(&c, xs, xe, xm, ys, ye, ym, 1, &ts, &te, tm);", ["test_oracle_ops.py::test_cauchy_entries"]),
+    ("back substitution adds the update",
+     "op_add(&c, u->S[ic], u->E[ic], u->M + ic * n, ts, te, t, 1, u->S + ic, u->E + ic, u->M + ic * n);",
+     "op_add(&c, u->S[ic], u->E[ic], u->M + ic * n, ts, te, t, 0, u->S + ic, u->E + ic, u->M + ic * n);",
+     ["test_oracle_adjoint.py::test_usolve_is_the_inverse"]),
+    ("binary64 rounding ties away from zero", "if (rbit && (st || (K & 1))) K += 1;", "if (rbit) K += 1;",
+     ["test_oracle_adjoint.py::test_to_f64_is_correctly_rounded"]),
+    ("binary64 rounding without subnormals", "int64_t q = (e - 53 < -1074) ? -1074 : e - 53;",
+     "int64_t q = e - 53;", ["test_oracle_adjoint.py::test_to_f64_is_correctly_rounded"]),
+    ("normalised minors divide by l_N2", "st = op_recip(&c, S[row], E[row], M + row * n, &rs, &re, r);",
+     "st = op_recip(&c, S[row + 1], E[row + 1], M + (row + 1) * n, &rs, &re, r);",
+     ["test_oracle_ge.py::test_lastcol_integer_cofactors_and_laplace"]),
 ]
 
 
