@@ -418,6 +418,100 @@ def cauchy_bit_loss(x, y, D, p: int, every: int = 64):
             "fit_range": [ks[0], ks[-1]] if ks else None}
 
 
+def _primes_below(limit: int, count: int):
+    """The `count` largest primes below `limit` (trial division; limit ~ 2^31)."""
+    out, c = [], limit - 1
+    while len(out) < count:
+        if c % 2 and all(c % d for d in range(3, int(c ** 0.5) + 1, 2)):
+            out.append(c)
+        c -= 1
+    return out
+
+
+def exact_leading_minors_int(A, kmax: int):
+    """Exact leading minors D_1..D_kmax of an integer matrix by elimination
+    without pivoting modulo many 31-bit primes at once and Chinese remaindering
+    (enough primes for Hadamard's bound of the largest block, plus margin).
+    A prime under which some pivot vanishes is dropped for that minor and the
+    ones after it.  Returns Python ints."""
+    import math
+
+    A = np.asarray(A, dtype=np.int64)[:kmax, :kmax]
+    norms = np.sqrt((A.astype(np.float64) ** 2).sum(axis=1))
+    bound_bits = float(np.sum(np.log2(np.maximum(norms, 1.0)))) + 2
+    P = _primes_below(2 ** 31, int(bound_bits / 30.9) + 8)
+    Pv = np.array(P, dtype=np.int64)
+    M = np.mod(A[None, :, :], Pv[:, None, None])
+    ok = np.ones(len(P), dtype=bool)
+    dets = np.ones(len(P), dtype=np.int64)
+    residues = []
+    for k in range(kmax):
+        piv = M[:, k, k].copy()
+        ok &= piv != 0
+        dets = (dets * piv) % Pv
+        residues.append((dets.copy(), ok.copy()))
+        if k + 1 == kmax:
+            break
+        inv = np.array([pow(int(v), int(q) - 2, int(q)) if v else 0 for v, q in zip(piv, P)], dtype=np.int64)
+        f = (M[:, k + 1:, k] * inv[:, None]) % Pv[:, None]
+        M[:, k + 1:, k + 1:] = (M[:, k + 1:, k + 1:] - (f[:, :, None] * M[:, k, None, k + 1:]) % Pv[:, None, None]) % Pv[:, None, None]
+    out = []
+    for r, okk in residues:
+        x, mod = 0, 1
+        for v, q, good in zip(r.tolist(), P, okk.tolist()):
+            if not good:
+                continue
+            # x = x + mod * ((v - x) * mod^-1 mod q)
+            t = ((v - x) * pow(mod, -1, q)) % q
+            x += mod * t
+            mod *= q
+        out.append(x - mod if x > mod // 2 else x)
+    return out
+
+
+def integer_bit_loss(A, D, p: int, kmax: int = 256, every: int = 32):
+    """Correct bits of the leading minors D_k of an integer matrix against
+    their exact values (multi-modular), k = 1..kmax; bit loss L_k = p - bits
+    and its least-squares slope in bits per row."""
+    import math
+
+    exact = exact_leading_minors_int(A, kmax)
+    sgn, ex, limbs = D
+    n = p // 32
+    out, ks, ls = [], [], []
+    for i, e in enumerate(exact):
+        k = i + 1
+        if int(ex[i]) == np.iinfo(np.int64).min:
+            bits = float(p + 1) if e == 0 else 0.0
+        elif e == 0:
+            bits = 0.0
+        else:
+            gm = 0
+            for q in range(n - 1, -1, -1):
+                gm = (gm << 32) | int(np.uint32(limbs[i, q]))
+            ge = int(ex[i]) - p
+            g = -gm if int(sgn[i]) else gm
+            # |g 2^ge - e| / |e| with integers at a common scale
+            if ge >= 0:
+                diff = abs(g * (1 << ge) - e)
+                rel = (math.log2(diff) - math.log2(abs(e))) if diff else None
+            else:
+                diff = abs(g - e * (1 << -ge))
+                rel = (math.log2(diff) + ge - math.log2(abs(e))) if diff else None
+            bits = float(p + 1) if rel is None else max(0.0, -rel)
+        if k == 1 or k % every == 0 or k == len(exact):
+            out.append({"k": k, "bits": round(bits, 1), "loss": round(p - bits, 1)})
+        if bits > 16:
+            ks.append(k)
+            ls.append(p - bits)
+    slope = None
+    if len(ks) >= 2:
+        kb, lb = sum(ks) / len(ks), sum(ls) / len(ls)
+        sxx = sum((a - kb) ** 2 for a in ks)
+        slope = sum((a - kb) * (b - lb) for a, b in zip(ks, ls)) / sxx if sxx else None
+    return {"per_k": out, "bits_per_row": None if slope is None else round(slope, 3)}
+
+
 def bench_large(args, dev, m, peak_macs):
     """Workload C5 at full size: Cauchy N = 4096, p = 32768 (1024 limbs,
     68.9 GB in HBM), det and leading minors.  The whole factorisation takes
@@ -719,6 +813,10 @@ def run_gpu(args):
             out["accuracy"] = {"what": f"leading minors D_k of the N={N} Cauchy matrix (GPU results of the timed "
                                        "step) against the closed-form Cauchy determinant at every k",
                                **cauchy_bit_loss(x, y, Dh, p)}
+            Dih = (Di[0].cpu().numpy(), Di[1].cpu().numpy(), Di[2].cpu().numpy().view(np.uint32))
+            out["accuracy_int"] = {"what": "leading minors D_1..D_128 of the integer matrix (GPU results of the "
+                                           "timed step) against their exact values (multi-modular)",
+                                   **integer_bit_loss(A, Dih, p, kmax=128, every=16)}
         if batch is not None:
             out["batch"] = batch
         if want("adjoint"):

@@ -47,3 +47,21 @@ def test_work_counts():
     # lastcol: full rows, (N-1)^2 N / 2 update products, plus the N-1 last-column products
     for N in (2, 5, 64):
         assert bench.elim_products(N, True) == (N - 1) ** 2 * N // 2 + N * (N - 1) // 2 + 2 * (N - 1)
+
+
+def test_exact_integer_minors_and_bit_loss(oracle_lib):
+    """The multi-modular exact leading minors equal exact rational
+    determinants (condensation), and the oracle's minors of an integer matrix
+    keep almost all their bits against them."""
+    import bench
+    import test_oracle_ge as T
+
+    A = W.int_matrix(14, 21)
+    ex = bench.exact_leading_minors_int(A, 14)
+    assert [int(v) for v in ex] == [int(v) for v in T.exact_leading_minors(A.tolist())]
+    N, p = 48, 512
+    A = W.int_matrix(N, 22)
+    st, zk, D, _ = oracle_lib.ge(oracle_lib.from_int(A.reshape(-1), p), N, p)
+    r = bench.integer_bit_loss(A, D, p, kmax=N, every=8)
+    assert all(o["bits"] >= p - 40 for o in r["per_k"]), r
+    assert r["per_k"][0]["bits"] == p + 1  # D_1 = a_11 exactly
