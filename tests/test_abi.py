@@ -58,3 +58,36 @@ def test_create_rejects_bad_arguments_without_a_device(lib):
     assert lib.mpdet_create(8, 512, 0, None, None) == 1  # no output
     assert lib.mpdet_free(None) == 0
     assert lib.mpdet_last_error(None) == b"no handle"
+
+
+def test_more_entry_points_reject_bad_arguments_without_a_device(lib):
+    import paper_1308_1536_gb300 as m
+
+    h = ctypes.c_void_p()
+    ns = (ctypes.c_int64 * 2)(8, 0)
+    assert lib.mpdet_batch_create(2, ns, 512, None, ctypes.byref(h)) == m.EINVAL  # N = 0 in the batch
+    assert lib.mpdet_batch_create(0, ns, 512, None, ctypes.byref(h)) == m.EINVAL  # empty batch
+    assert lib.mpdet_batch_create(1, ns, 100, None, ctypes.byref(h)) == m.EINVAL  # bad precision
+    assert lib.mpdet_batch_free(None) == m.OK
+    assert lib.mpdet_batch_tune(None, 1, 0) == m.EINVAL
+    assert lib.mpdet_batch_autotune(None, 1, None, None, None, None) == m.EINVAL
+    assert lib.mpdet_batch_launches(None) == -1
+    assert lib.mpdet_selftest_timeout(0, 0, None) == m.EINVAL  # limit < 1
+    z = m.NumV(None, None, None)
+    assert lib.mpdet_factor_noalloc(0, 512, 0, z, z, z, None, None) == m.EINVAL
+    assert lib.mpdet_minor_series(None, z, 0, 0) == m.EINVAL
+    assert lib.mpdet_get_entries(None, 0, None, z, 0) == m.EINVAL
+    assert lib.mpdet_tune(None, 1, 0) == m.EINVAL
+    assert lib.mpdet_steps_done(None) == -1
+
+
+def test_noalloc_size_limit_without_a_device(lib):
+    """Sizes beyond the static working array are refused before any device
+    work: N^2 (4n + 9) alone exceeds 16 MiB at N = 1024, p = 2048."""
+    import paper_1308_1536_gb300 as m
+
+    s8, e64, l32 = ctypes.c_int8(), ctypes.c_int64(), ctypes.c_uint32()  # never dereferenced
+    v = m.NumV(ctypes.cast(ctypes.byref(s8), ctypes.c_void_p), ctypes.cast(ctypes.byref(e64), ctypes.c_void_p),
+               ctypes.cast(ctypes.byref(l32), ctypes.c_void_p))
+    assert lib.mpdet_factor_noalloc(1024, 2048, 0, v, v, v, None, None) == m.ENOSCRATCH
+    assert lib.mpdet_factor_noalloc(479, 512, 0, v, v, v, None, None) == m.ENOSCRATCH
