@@ -400,6 +400,46 @@ class Mpdet:
         return dict(update_ms=ms.value, update_launches=nl.value, update_limb_macs=macs.value, launches=total.value)
 
 
+def tune_cache_key(device: str, p: int, Ns) -> str:
+    """Key of a batch autotuner choice: the device, the precision and the
+    size mix (count, and the matrices per N bucket of width 32, which is what
+    the persistent kernel's load balance depends on)."""
+    Ns = np.asarray(Ns, dtype=np.int64)
+    hist = np.bincount(np.minimum(Ns // 32, 63), minlength=64)
+    return f"{device}|p={int(p)}|count={len(Ns)}|hist32=" + ",".join(str(int(v)) for v in hist)
+
+
+class TuneCache:
+    """A JSON file of autotuner choices: {key: {variant, blocks_per_sm, ms,
+    candidates}}.  Written whole to a temporary file and renamed."""
+
+    def __init__(self, path: str):
+        self.path = path
+
+    def _load(self) -> dict:
+        import json
+
+        try:
+            with open(self.path) as f:
+                d = json.load(f)
+            return d if isinstance(d, dict) else {}
+        except (OSError, ValueError):
+            return {}
+
+    def get(self, key: str):
+        return self._load().get(key)
+
+    def put(self, key: str, value: dict) -> None:
+        import json
+
+        d = self._load()
+        d[key] = value
+        tmp = f"{self.path}.tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(d, f, indent=1, sort_keys=True)
+        os.replace(tmp, self.path)
+
+
 class Batch:
     """Many independent matrices of sizes Ns at p bits, factored in one
     persistent launch (det and leading minors of each)."""
@@ -492,14 +532,37 @@ class Batch:
             out.append(tuple(int(x.value) for x in a))
             v += 1
 
-    def autotune(self, reps: int = 1):
+    def autotune(self, reps: int = 1, cache: str | None = None):
         """Time every variant (occupancy limit and half of it), keep the
-        fastest: dict(variant, blocks_per_sm, ms, candidates)."""
+        fastest: dict(variant, blocks_per_sm, ms, candidates).  With
+        ``cache`` (a JSON file path) a choice stored for the same device,
+        precision and size mix is applied without timing, and a new one is
+        stored."""
+        key = None
+        if cache is not None:
+            key = tune_cache_key(self._device_name(), self.p, self.Ns)
+            hit = TuneCache(cache).get(key)
+            if hit is not None and 0 <= hit.get("variant", -1) < len(self.variants()):
+                self.tune(variant=hit["variant"], blocks_per_sm=hit["blocks_per_sm"])
+                return dict(hit, cached=True)
         v, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
         ms = ctypes.c_double()
         self._check(self.lib.mpdet_batch_autotune(self.h, int(reps), ctypes.byref(v), ctypes.byref(b),
                                                   ctypes.byref(ms), ctypes.byref(c)), "batch_autotune")
-        return dict(variant=v.value, blocks_per_sm=b.value, ms=ms.value, candidates=c.value)
+        res = dict(variant=v.value, blocks_per_sm=b.value, ms=ms.value, candidates=c.value)
+        if key is not None:
+            TuneCache(cache).put(key, res)
+        return res
+
+    @staticmethod
+    def _device_name() -> str:
+        try:
+            import torch
+
+            props = torch.cuda.get_device_properties(torch.cuda.current_device())
+            return f"{props.name} sm_{props.major}{props.minor} x{props.multi_processor_count}"
+        except Exception:
+            return "unknown"
 
     def minors_of(self, D, m):
         a, b = int(self.offsets[m]), int(self.offsets[m + 1])

@@ -65,3 +65,23 @@ def test_exact_integer_minors_and_bit_loss(oracle_lib):
     r = bench.integer_bit_loss(A, D, p, kmax=N, every=8)
     assert all(o["bits"] >= p - 40 for o in r["per_k"]), r
     assert r["per_k"][0]["bits"] == p + 1  # D_1 = a_11 exactly
+
+
+def test_batch_tune_cache_roundtrip(tmp_path):
+    """The batch autotuner's choice cache: keys separate devices, precisions
+    and size mixes; a stored choice reads back; a damaged file reads as empty."""
+    from paper_1308_1536_gb300 import TuneCache, tune_cache_key
+
+    Ns, _, _ = W.batch_sizes(4096, 8, 256, 1311)
+    k1 = tune_cache_key("GB300 sm_103 x152", 1024, Ns)
+    assert k1 != tune_cache_key("GB300 sm_103 x152", 2048, Ns)
+    assert k1 != tune_cache_key("B200 sm_100 x148", 1024, Ns)
+    assert k1 != tune_cache_key("GB300 sm_103 x152", 1024, Ns[:4000])
+    assert k1 == tune_cache_key("GB300 sm_103 x152", 1024, list(Ns))
+    c = TuneCache(str(tmp_path / "tune.json"))
+    assert c.get(k1) is None
+    c.put(k1, {"variant": 3, "blocks_per_sm": 4, "ms": 1425.5, "candidates": 8})
+    c.put("other", {"variant": 0, "blocks_per_sm": 2, "ms": 1.0, "candidates": 1})
+    assert TuneCache(str(tmp_path / "tune.json")).get(k1)["variant"] == 3
+    (tmp_path / "bad.json").write_text("{not json")
+    assert TuneCache(str(tmp_path / "bad.json")).get(k1) is None
