@@ -333,3 +333,18 @@ def test_minor_series_zero_l_n1(oracle_lib):
     assert Sd[1:3] == [0, 0]
     Cx = exact_lastcol_cofactors(A)
     assert S[3:6] == Cx
+
+
+def test_oracle_reproduces_stored_values(oracle_lib):
+    """The oracle's results for workload C1 (leading and last-column minors)
+    equal the stored values written by tests/golden/make_golden.py, number for
+    number: any change to the oracle's arithmetic shows here."""
+    import os
+    import sys
+
+    sys.path.insert(0, os.path.join(os.path.dirname(__file__), "golden"))
+    import make_golden
+
+    want = open(make_golden.GOLDEN).read().splitlines()
+    got = make_golden.lines(*make_golden.compute())
+    assert got == want
