@@ -348,3 +348,23 @@ def test_oracle_reproduces_stored_values(oracle_lib):
     want = open(make_golden.GOLDEN).read().splitlines()
     got = make_golden.lines(*make_golden.compute())
     assert got == want
+
+
+def test_integer_minors_vs_multimodular_exact(oracle_lib):
+    """Every leading minor of a 96 x 96 integer matrix (entries in [-1000,
+    1000]) against its exact value from elimination modulo many primes and
+    Chinese remaindering (an exact route independent of the oracle): at most
+    40 bits lost at p = 512, i.e. relative error below 2^-(p-40)."""
+    from fractions import Fraction as F
+
+    import bench
+
+    N, p = 96, 512
+    A = W.int_matrix(N, 1396)
+    exact = bench.exact_leading_minors_int(A, N)
+    st, zk, D, _ = oracle_lib.ge(lift_int(oracle_lib, A, p), N, p, nthreads=4)
+    assert st == 0
+    got = X.unpack(D, p)
+    for k in range(N):
+        assert exact[k] != 0
+        assert abs(got[k] - exact[k]) <= abs(F(exact[k])) / 2 ** (p - 40), k
