@@ -85,3 +85,23 @@ def test_batch_tune_cache_roundtrip(tmp_path):
     assert TuneCache(str(tmp_path / "tune.json")).get(k1)["variant"] == 3
     (tmp_path / "bad.json").write_text("{not json")
     assert TuneCache(str(tmp_path / "bad.json")).get(k1) is None
+
+
+def test_recorded_traffic_scales_with_the_launch():
+    """The DRAM traffic recorded from one ncu capture of the tensor update
+    kernel is used only while the kernel's sources hash to the recorded value,
+    and then scales with the products of the launch."""
+    import json
+    import os
+
+    import bench
+
+    rec = json.load(open(os.path.join(bench.ROOT, "profiles", "k_update_traffic.json")))
+    cap = rec["capture"]
+    products = 765 * 766
+    assert abs(rec["bytes_per_product"] - (cap["dram_bytes_read"] + cap["dram_bytes_write"]) / products) < 0.1
+    t = bench.recorded_traffic(1000.0)
+    if rec["source_sha"] == bench.kernel_source_sha():
+        assert t == rec["bytes_per_product"] * 1000.0
+    else:
+        assert t is None
