@@ -133,3 +133,34 @@ def test_full_size_C5_first_steps_sampled(mpdet, oracle_lib):
         assert_same(tuple(t[:k] for t in D), OD2, "D_1, D_2")
     finally:
         h.close()
+
+
+def test_full_size_C2_series_sampled(mpdet, oracle_lib):
+    """Workload C2 at full size (N = 1024, p = 2048, last-column mode, the
+    benchmark's configuration): the series of last-column minors of the full
+    run, at sampled sizes n, equals the oracle's last-column minors of the
+    leading n x n block (bit for bit); this checks the L bookkeeping (a5) of
+    rows below n in the full-size launches."""
+    N, p = W.C2["N"], W.C2["p"]
+    x, y = W.cauchy_xy(N, W.C2["seed"])
+    A = W.int_matrix(N, W.C2["seed"] + 100)
+    for kind in ("cauchy", "int"):
+        h = mpdet.Mpdet(N, p, lastcol=True)
+        if kind == "cauchy":
+            h.set_cauchy(x, y)
+        else:
+            h.set_i32(A.astype(np.int32))
+        rc, zk, D = h.factor()
+        assert rc == 0
+        S = h.minor_series()
+        h.close()
+        for nn in (1, 2, 17, 64):
+            if kind == "cauchy":
+                M = oracle_lib.cauchy(x[:nn], y[:nn], p)
+            else:
+                M = oracle_lib.from_int(A[:nn, :nn].reshape(-1), p)
+            st, _, OD, OX = oracle_lib.ge(M, nn, p, lastcol=True, nthreads=8)
+            assert st == 0
+            off = nn * (nn - 1) // 2
+            assert_same(tuple(t[off:off + nn] for t in S), oracle_lib.lastcol_minors(OX, OD, nn, p),
+                        f"{kind}: series {nn}")
