@@ -16,35 +16,37 @@ using mpd::MpArr;
 
 namespace mpd {
 int batch_variants(int n, const BatchVariant** out) {
-  // entry 0: the kernel set's own kernel; then the extra geometries for n
-  static BatchVariant lists[4][8];
-  static int counts[4] = {0, 0, 0, 0};
-  static const int ns[4] = {16, 32, 64, 128};
-  static bool init = false;
-  if (!init) {
-    for (int q = 0; q < 4; ++q) {
-      const KernelSet* ks = kernel_set_for(ns[q]);
-      lists[q][0] = BatchVariant{ks->W, ks->G, ks->PW, ks->PG, ks->batch, ks->batch_blocks_per_sm};
-      int c = 0;
-      const BatchVariant* v = q == 0 ? batch_variants_n16(&c)
-                              : q == 1 ? batch_variants_n32(&c)
-                              : q == 2 ? batch_variants_n64(&c)
-                                       : batch_variants_n128(&c);
-      for (int i = 0; i < c && i < 7; ++i) lists[q][1 + i] = v[i];
-      counts[q] = 1 + (c < 7 ? c : 7);
+  // One list per supported limb count, built once (thread-safe static
+  // initialisation): entry 0 is the kernel set's own kernel, then the extra
+  // geometries compiled for that n.
+  struct Table {
+    int ns[9] = {4, 8, 16, 32, 64, 128, 256, 512, 1024};
+    BatchVariant lists[9][8];
+    int counts[9] = {0};
+    Table() {
+      for (int q = 0; q < 9; ++q) {
+        const KernelSet* ks = kernel_set_for(ns[q]);
+        if (!ks) continue;
+        lists[q][0] = BatchVariant{ks->W, ks->G, ks->PW, ks->PG, ks->batch, ks->batch_blocks_per_sm};
+        int c = 0;
+        const BatchVariant* v = ns[q] == 16    ? batch_variants_n16(&c)
+                                : ns[q] == 32  ? batch_variants_n32(&c)
+                                : ns[q] == 64  ? batch_variants_n64(&c)
+                                : ns[q] == 128 ? batch_variants_n128(&c)
+                                               : nullptr;
+        for (int i = 0; v && i < c && i < 7; ++i) lists[q][1 + i] = v[i];
+        counts[q] = 1 + (v ? (c < 7 ? c : 7) : 0);
+      }
     }
-    init = true;
-  }
-  for (int q = 0; q < 4; ++q)
-    if (ns[q] == n) {
-      *out = lists[q];
-      return counts[q];
+  };
+  static const Table t;
+  for (int q = 0; q < 9; ++q)
+    if (t.ns[q] == n && t.counts[q] > 0) {
+      *out = t.lists[q];
+      return t.counts[q];
     }
-  static BatchVariant single;
-  const KernelSet* ks = kernel_set_for(n);
-  single = BatchVariant{ks->W, ks->G, ks->PW, ks->PG, ks->batch, ks->batch_blocks_per_sm};
-  *out = &single;
-  return 1;
+  *out = nullptr;
+  return 0;
 }
 }  // namespace mpd
 
@@ -137,8 +139,9 @@ extern "C" int mpdet_batch_create(int64_t count, const int64_t* Ns, int32_t p_bi
   int dev = 0;
   bool ok = cudaGetDevice(&dev) == cudaSuccess &&
             cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess;
+  if (ok) b->nvariants = mpd::batch_variants(n, &b->variants);
+  ok = ok && b->nvariants >= 1;
   if (ok) {
-    b->nvariants = mpd::batch_variants(n, &b->variants);
     int mx = 1;
     for (int v = 0; v < b->nvariants; ++v) {
       b->bpsm_max.push_back(b->variants[v].blocks_per_sm());
