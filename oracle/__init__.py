@@ -82,11 +82,13 @@ def _load():
             lib.or_from_i64_v.argtypes = [i64, i32, P, P, P, P]
             lib.or_cauchy.argtypes = [i64, i32, P, P, P, P, P]
             lib.or_ge_range.argtypes = [i64, i32, i32, i32, i64, i64, P, P, P, P, P, P, P]
+            lib.or_ge_range_div.argtypes = [i64, i32, i32, i32, i64, i64, P, P, P, P, P, P, P]
+            lib.or_div_v.argtypes = [i64, i32, P, P, P, P, P, P, P, P, P]
             lib.or_lastcol.argtypes = [i64, i32, i32, P, P, P, ctypes.c_int8, i64, P, P, P, P]
             lib.or_usolve.argtypes = [i64, i32, i32, P, P, P, P, P, P]
             lib.or_to_f64_v.argtypes = [i64, i32, P, P, P, P]
             for f in ("or_mul_v", "or_add_v", "or_recip_v", "or_from_f64_v", "or_from_i64_v", "or_cauchy",
-                      "or_ge_range", "or_lastcol", "or_usolve", "or_to_f64_v"):
+                      "or_ge_range", "or_ge_range_div", "or_div_v", "or_lastcol", "or_usolve", "or_to_f64_v"):
                 getattr(lib, f).restype = i32
             _lib = lib
     return _lib
@@ -137,6 +139,16 @@ def sub(a, b, p: int):
     return add(a, b, p, negate_b=True)
 
 
+def div(a, b, p: int):
+    """RN(a/b) with one rounding (not the method's multiplier, which is
+    RN(a * RN(1/b)); an option for accuracy comparisons)."""
+    a, b = _norm(a, p), _norm(b, p)
+    c = a[0].shape[0]
+    o = empty(c, p)
+    _check(_load().or_div_v(c, p, *map(_ptr, a), *map(_ptr, b), *map(_ptr, o)), "div")
+    return o
+
+
 def recip(a, p: int):
     a = _norm(a, p)
     c = a[0].shape[0]
@@ -171,11 +183,13 @@ def cauchy(x, y, p: int):
 
 
 def ge(A, N: int, p: int, lastcol: bool = False, nthreads: int = 1, k0: int = 0, k_end: int | None = None,
-       D=None):
+       D=None, divide: bool = False):
     """Eliminate the row-major N x N matrix A (copied), returning
     ``(status, zero_k, D, X)``: D holds the leading minors D_1..D_N, X the
     in-place array after steps k0+1..k_end (U in the upper triangle; L's
-    strict lower part in lastcol mode)."""
+    strict lower part in lastcol mode).  ``divide=True`` forms the
+    multipliers as correctly rounded quotients RN(a_ik / a_kk) instead of
+    the method's RN(a_ik * RN(1/a_kk)) (accuracy comparisons only)."""
     S, E, M = (np.array(t, copy=True) for t in _norm(A, p))
     assert S.shape[0] == N * N
     if D is None:
@@ -184,7 +198,8 @@ def ge(A, N: int, p: int, lastcol: bool = False, nthreads: int = 1, k0: int = 0,
         D = tuple(np.array(t, copy=True) for t in _norm(D, p))
     zk = np.zeros(1, np.int64)
     k_end = N if k_end is None else k_end
-    st = _load().or_ge_range(N, p, int(lastcol), int(nthreads), k0, k_end, _ptr(S), _ptr(E), _ptr(M),
+    fn = _load().or_ge_range_div if divide else _load().or_ge_range
+    st = fn(N, p, int(lastcol), int(nthreads), k0, k_end, _ptr(S), _ptr(E), _ptr(M),
                              *map(_ptr, D), _ptr(zk))
     if st not in (OK, EZEROPIVOT):
         raise RuntimeError(f"oracle ge failed with status {st}")

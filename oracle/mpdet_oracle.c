@@ -293,6 +293,45 @@ static int op_recip(ctx_t *c, int8_t sa, int64_t ea, const uint32_t *ma, int8_t 
   return OR_OK;
 }
 
+/* RN(a / b) with one rounding (the correctly rounded division that the
+ * elimination's default two-rounding multiplier RN(a * RN(1/b)) stands in
+ * for); OR_EZERODIV for b == 0. */
+static int op_div(ctx_t *c, int8_t sa, int64_t ea, const uint32_t *ma, int8_t sb, int64_t eb, const uint32_t *mb,
+                  int8_t *os, int64_t *oe, uint32_t *om) {
+  int n = c->n, p = c->p;
+  if (iszero(eb)) return OR_EZERODIV;
+  if (iszero(ea)) {
+    setzero(os, oe, om, n);
+    return OR_OK;
+  }
+  /* ma * 2^(p+1) = q*mb + r by restoring binary long division, 2^p < q < 2^(p+2). */
+  int L = n + 2;
+  uint32_t *q = c->buf, *r = c->buf + L, *m = c->buf + 2 * L;
+  memset(q, 0, sizeof(uint32_t) * L);
+  memset(r, 0, sizeof(uint32_t) * L);
+  memset(m, 0, sizeof(uint32_t) * L);
+  memcpy(m, mb, sizeof(uint32_t) * n);
+  for (int64_t i = 2 * (int64_t)p; i >= 0; --i) {
+    /* r = 2r + (bit i of ma * 2^(p+1)), i.e. bit i - p - 1 of ma */
+    int64_t src = i - (int64_t)p - 1;
+    uint32_t carry = (src >= 0) ? ((ma[src >> 5] >> (src & 31)) & 1u) : 0u;
+    for (int w = 0; w < L; ++w) {
+      uint32_t nc = r[w] >> 31;
+      r[w] = (r[w] << 1) | carry;
+      carry = nc;
+    }
+    if (cmpn(r, m, L) >= 0) {
+      subn(r, m, L);
+      if (i < (int64_t)L * 32) q[i >> 5] |= 1u << (i & 31);
+    }
+  }
+  int rem_nz = bitlen(r, L) != 0;
+  /* a/b = (ma/mb) * 2^(ea-eb) = (q + r/mb) * 2^(ea - eb - p - 1) */
+  rnd(q, L, ea - eb - (int64_t)p - 1, rem_nz, p, n, (sa ^ sb) & 1, os, oe, om);
+  return OR_OK;
+}
+
+
 /* Exact lift of a double (finite) to p bits, p >= 64. */
 static void op_from_f64(ctx_t *c, double v, int8_t *os, int64_t *oe, uint32_t *om) {
   int n = c->n, p = c->p;
@@ -339,6 +378,18 @@ static int ctx_init(ctx_t *c, int p) {
   c->n = p / 32;
   c->buf = (uint32_t *)calloc((size_t)6 * c->n + 16, sizeof(uint32_t));
   return c->buf ? OR_OK : OR_ENOMEM;
+}
+
+int or_div_v(int64_t cnt, int p, const int8_t *as, const int64_t *ae, const uint32_t *am, const int8_t *bs,
+             const int64_t *be, const uint32_t *bm, int8_t *os, int64_t *oe, uint32_t *om) {
+  ctx_t c;
+  int st = ctx_init(&c, p);
+  if (st) return st;
+  int n = c.n;
+  for (int64_t i = 0; i < cnt && st == OR_OK; ++i)
+    st = op_div(&c, as[i], ae[i], am + i * n, bs[i], be[i], bm + i * n, os + i, oe + i, om + i * n);
+  free(c.buf);
+  return st;
 }
 
 int or_mul_v(int64_t cnt, int p, const int8_t *sa, const int64_t *ea, const uint32_t *ma, const int8_t *sb,
@@ -486,8 +537,8 @@ static void *update_rows(void *arg) {
  * are +0), else OR_OK.  k_end limits the steps run (k_end = N for all):
  * steps k0+1..k_end are run, with D holding D_1..D_k0 on entry.
  */
-int or_ge_range(int64_t N, int p, int lastcol, int nthreads, int64_t k0, int64_t k_end, int8_t *S, int64_t *E,
-                uint32_t *M, int8_t *Ds, int64_t *De, uint32_t *Dm, int64_t *zero_k) {
+static int ge_range(int64_t N, int p, int lastcol, int nthreads, int64_t k0, int64_t k_end, int8_t *S, int64_t *E,
+                    uint32_t *M, int8_t *Ds, int64_t *De, uint32_t *Dm, int64_t *zero_k, int divide) {
   ctx_t c;
   int st = ctx_init(&c, p);
   if (st) return st;
@@ -522,10 +573,14 @@ int or_ge_range(int64_t N, int p, int lastcol, int nthreads, int64_t k0, int64_t
     int8_t rs;
     int64_t re;
     op_recip(&c, S[kk], E[kk], M + kk * n, &rs, &re, r);
-    /* multipliers z_ik = RN(a_ik * r_k) */
+    /* multipliers z_ik = RN(a_ik * r_k) (or, as an option for accuracy
+     * comparisons, the correctly rounded RN(a_ik / a_kk)) */
     for (int64_t i = k + 1; i < N; ++i) {
       int64_t ik = i * N + k, zi = i - (k + 1);
-      op_mul(&c, S[ik], E[ik], M + ik * n, rs, re, r, g.zs + zi, g.ze + zi, g.zm + zi * n);
+      if (divide)
+        op_div(&c, S[ik], E[ik], M + ik * n, S[kk], E[kk], M + kk * n, g.zs + zi, g.ze + zi, g.zm + zi * n);
+      else
+        op_mul(&c, S[ik], E[ik], M + ik * n, rs, re, r, g.zs + zi, g.ze + zi, g.zm + zi * n);
     }
     g.k = k;
     int64_t rows = N - (k + 1);
@@ -555,6 +610,19 @@ int or_ge_range(int64_t N, int p, int lastcol, int nthreads, int64_t k0, int64_t
   free(g.zs);
   free(c.buf);
   return st;
+}
+
+int or_ge_range(int64_t N, int p, int lastcol, int nthreads, int64_t k0, int64_t k_end, int8_t *S, int64_t *E,
+                uint32_t *M, int8_t *Ds, int64_t *De, uint32_t *Dm, int64_t *zero_k) {
+  return ge_range(N, p, lastcol, nthreads, k0, k_end, S, E, M, Ds, De, Dm, zero_k, 0);
+}
+
+/* The same elimination with correctly rounded multipliers z_ik = RN(a_ik /
+ * a_kk) (one rounding) instead of RN(a_ik * RN(1/a_kk)): not the method's
+ * arithmetic, an option to measure what the two-rounding multiplier costs. */
+int or_ge_range_div(int64_t N, int p, int lastcol, int nthreads, int64_t k0, int64_t k_end, int8_t *S, int64_t *E,
+                    uint32_t *M, int8_t *Ds, int64_t *De, uint32_t *Dm, int64_t *zero_k) {
+  return ge_range(N, p, lastcol, nthreads, k0, k_end, S, E, M, Ds, De, Dm, zero_k, 1);
 }
 
 /*

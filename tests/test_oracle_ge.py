@@ -368,3 +368,24 @@ def test_integer_minors_vs_multimodular_exact(oracle_lib):
     for k in range(N):
         assert exact[k] != 0
         assert abs(got[k] - exact[k]) <= abs(F(exact[k])) / 2 ** (p - 40), k
+
+
+def test_two_rounding_multiplier_costs_no_accuracy(oracle_lib):
+    """Reading G3: the multipliers are RN(a_ik * RN(1/a_kk)), two roundings,
+    instead of the correctly rounded RN(a_ik / a_kk).  Against the Cauchy
+    closed form at every k the two choices lose the same number of bits per
+    row (the matrix's conditioning, about 5 bits per row, dominates one extra
+    rounding per multiplier)."""
+    import bench
+
+    N, p = W.C1["N"], W.C1["p"]
+    x, y = W.cauchy_xy(N, W.C1["seed"])
+    A = oracle_lib.cauchy(x, y, p)
+    r = {}
+    for divide in (False, True):
+        st, zk, D, _ = oracle_lib.ge(A, N, p, divide=divide)
+        assert st == 0
+        r[divide] = bench.cauchy_bit_loss(x, y, D, p, every=8)
+    assert abs(r[False]["bits_per_row"] - r[True]["bits_per_row"]) < 0.2
+    for a, b in zip(r[False]["per_k"], r[True]["per_k"]):
+        assert abs(a["bits"] - b["bits"]) < 12

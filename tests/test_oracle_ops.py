@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 import exactref as X
+from paper_1308_1536_gb300 import workloads as W
 
 pytestmark = pytest.mark.usefixtures("oracle_lib")
 
@@ -249,3 +250,24 @@ def test_cauchy_entries(oracle_lib, p):
     r = lambda q: X.to_fraction(*X.rn_tuple(q, p), p)
     want = X.pack([1 / r(Fraction(float(a)) + Fraction(float(b))) for a in x for b in y], p)
     assert X.same(got, want)
+
+
+@pytest.mark.parametrize("p", [64, 128, 512, 2048])
+def test_div_is_correctly_rounded(oracle_lib, p):
+    """The oracle's optional one-rounding division RN(a/b) (used only to
+    measure what the method's two-rounding multiplier costs) against the
+    exact rational quotient rounded by the independent reference."""
+    g = W.rng(500 + p)
+    va, vb = [], []
+    for _ in range(150):
+        for out in (va, vb):
+            m = (1 << (p - 1)) | int.from_bytes(g.bytes(p // 8), "little") & ((1 << (p - 1)) - 1)
+            out.append(Fraction(m) * Fraction(2) ** int(g.integers(-400, 400) - p) * (-1 if g.integers(0, 2) else 1))
+    va += [Fraction(3), Fraction(1), Fraction(-7, 2), Fraction(0)]
+    vb += [Fraction(3), Fraction(3), Fraction(5), Fraction(9)]
+    A, B = X.pack(va, p), X.pack(vb, p)
+    got = oracle_lib.div(A, B, p)
+    want = X.pack([a / b for a, b in zip(X.unpack(A, p), X.unpack(B, p))], p)
+    assert X.same(got, want)
+    with pytest.raises(RuntimeError):
+        oracle_lib.div(X.pack([Fraction(1)], p), X.pack([Fraction(0)], p), p)
