@@ -631,6 +631,15 @@ def bench_hostmem(args, dev, m, peak_macs):
     return out
 
 
+def guarded(fn, *a):
+    """Run one optional part of the benchmark; an exception is reported in
+    the JSON line (as {"error": ...}) instead of losing the whole line."""
+    try:
+        return fn(*a)
+    except Exception as e:  # noqa: BLE001
+        return {"error": f"{type(e).__name__}: {e}"[:300]}
+
+
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
@@ -760,7 +769,7 @@ def run_gpu(args):
 
     # the batch workload runs on every rank (its share of the matrices)
     extras = set() if args.no_extras else set(args.extras.split(","))
-    batch = bench_batch(args, dev, m, rank, world) if "batch" in extras or "all" in extras else None
+    batch = guarded(bench_batch, args, dev, m, rank, world) if "batch" in extras or "all" in extras else None
     if rank == 0:
         props = torch.cuda.get_device_properties(dev)
         nsm = props.multi_processor_count
@@ -809,24 +818,29 @@ def run_gpu(args):
         }
         want = lambda k: "all" in extras or k in extras  # noqa: E731
         if want("accuracy"):
-            Dh = (Dc[0].cpu().numpy(), Dc[1].cpu().numpy(), Dc[2].cpu().numpy().view(np.uint32))
-            out["accuracy"] = {"what": f"leading minors D_k of the N={N} Cauchy matrix (GPU results of the timed "
-                                       "step) against the closed-form Cauchy determinant at every k",
-                               **cauchy_bit_loss(x, y, Dh, p)}
-            Dih = (Di[0].cpu().numpy(), Di[1].cpu().numpy(), Di[2].cpu().numpy().view(np.uint32))
-            out["accuracy_int"] = {"what": "leading minors D_1..D_128 of the integer matrix (GPU results of the "
-                                           "timed step) against their exact values (multi-modular)",
-                                   **integer_bit_loss(A, Dih, p, kmax=128, every=16)}
+            def acc_cauchy():
+                Dh = (Dc[0].cpu().numpy(), Dc[1].cpu().numpy(), Dc[2].cpu().numpy().view(np.uint32))
+                return {"what": f"leading minors D_k of the N={N} Cauchy matrix (GPU results of the timed step) "
+                                "against the closed-form Cauchy determinant at every k", **cauchy_bit_loss(x, y, Dh, p)}
+
+            def acc_int():
+                Dih = (Di[0].cpu().numpy(), Di[1].cpu().numpy(), Di[2].cpu().numpy().view(np.uint32))
+                return {"what": "leading minors D_1..D_128 of the integer matrix (GPU results of the timed step) "
+                                "against their exact values (multi-modular)",
+                        **integer_bit_loss(A, Dih, p, kmax=128, every=16)}
+
+            out["accuracy"] = guarded(acc_cauchy)
+            out["accuracy_int"] = guarded(acc_int)
         if batch is not None:
             out["batch"] = batch
         if want("adjoint"):
-            out["adjoint"] = bench_adjoint(args, dev, m)
+            out["adjoint"] = guarded(bench_adjoint, args, dev, m)
         if want("large"):
-            out["large"] = bench_large(args, dev, m, peak)
+            out["large"] = guarded(bench_large, args, dev, m, peak)
         if want("hostmem"):
-            out["hostmem"] = bench_hostmem(args, dev, m, peak)
+            out["hostmem"] = guarded(bench_hostmem, args, dev, m, peak)
         if world == 1 and not args.no_cpu_baseline:
-            cb = oracle_sample()
+            cb = guarded(oracle_sample)
             cb.pop("seconds", None)
             out["cpu_baseline"] = cb
         print(json.dumps(out))

@@ -105,3 +105,11 @@ def test_recorded_traffic_scales_with_the_launch():
         assert t == rec["bytes_per_product"] * 1000.0
     else:
         assert t is None
+
+
+def test_guarded_optional_parts():
+    import bench
+
+    assert bench.guarded(lambda a, b: a + b, 2, 3) == 5
+    r = bench.guarded(lambda: {}["missing"])
+    assert set(r) == {"error"} and r["error"].startswith("KeyError")
