@@ -323,6 +323,20 @@ int mpdet_batch_set_mp(mpdet_batch_t b, int64_t m, mpdet_numv A, int device_ptr)
 int mpdet_batch_factor(mpdet_batch_t b, mpdet_numv minors, int64_t* zero_k, int device_ptr);
 int64_t mpdet_batch_launches(mpdet_batch_t b);
 
+/* One-shot batch: create, set, factor and free in one call.  count matrices
+ * of sizes Ns[0..count) at p bits, matrix m given as N_m * N_m numbers in[m]
+ * (row-major, canonical); its leading minors D_1..D_{N_m} go to minors_out[m]
+ * (N_m numbers) and the 1-based index of its first zero pivot (0 if none) to
+ * status_out[m] (count int64, may be NULL).  device_ptr applies to every
+ * buffer (all host or all device memory of the current device).  The device
+ * memory of the batch is allocated and freed inside the call, which
+ * synchronises cuda_stream; repeated factorisations of the same sizes should
+ * keep a handle from mpdet_batch_create instead.  Results equal
+ * mpdet_batch_factor's (and mpdet_factor's) bit for bit.
+ * Errors: MPDET_EINVAL, MPDET_ENOMEM, MPDET_ECUDA. */
+int mpdet_batch(int64_t count, const int64_t* Ns, int32_t p_bits, const mpdet_numv* in, mpdet_numv* minors_out,
+                int64_t* status_out, int device_ptr, void* cuda_stream);
+
 /* Batch tuning (results are bit-identical for every setting; only speed
  * changes).  The persistent kernel exists in several lane geometries per
  * precision: variant v runs the multipliers and the Schur update with W

@@ -90,6 +90,7 @@ def load(build_if_missing: bool = True):
         "mpdet_batch_autotune": ([P, ctypes.c_int, ctypes.POINTER(i32), ctypes.POINTER(i32),
                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)], ctypes.c_int),
         "mpdet_batch_free": ([P], ctypes.c_int),
+        "mpdet_batch": ([i64, P, i32, P, P, P, ctypes.c_int, P], ctypes.c_int),
         "mpdet_logabsdet_grad": ([P, P, i64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), P,
                                   ctypes.c_double, ctypes.c_int], ctypes.c_int),
         "mpdet_get_inverse": ([P, NumV, ctypes.c_int], ctypes.c_int),
@@ -398,6 +399,40 @@ class Mpdet:
         self._check(self.lib.mpdet_profile_read(self.h, ctypes.byref(ms), ctypes.byref(nl), ctypes.byref(macs),
                                                 ctypes.byref(total)), "profile_read")
         return dict(update_ms=ms.value, update_launches=nl.value, update_limb_macs=macs.value, launches=total.value)
+
+
+def batch_once(mats, p: int, stream=None):
+    """One-shot batch (mpdet_batch): ``mats`` is a list of host triples of
+    N_m * N_m numbers (row-major); returns (zero_k[count], [minors triple of
+    each matrix]).  Allocates and frees the batch's device memory inside the
+    call."""
+    lib = load()
+    n = int(p) // 32
+    Ns = np.array([int(round(len(t[0]) ** 0.5)) for t in mats], dtype=np.int64)
+    ins = [tuple(np.ascontiguousarray(a) for a in _norm_host(t, n)) for t in mats]
+    outs = [empty(int(N), p) for N in Ns]
+    zk = np.zeros(len(mats), np.int64)
+    in_arr = (NumV * len(mats))(*[_numv(t) for t in ins])
+    out_arr = (NumV * len(mats))(*[_numv(t) for t in outs])
+    if stream is None:
+        try:
+            import torch
+
+            stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else None
+        except Exception:
+            stream = None
+    rc = lib.mpdet_batch(len(mats), Ns.ctypes.data_as(ctypes.c_void_p), int(p), ctypes.cast(in_arr, ctypes.c_void_p),
+                         ctypes.cast(out_arr, ctypes.c_void_p), zk.ctypes.data_as(ctypes.c_void_p), 0,
+                         ctypes.c_void_p(stream or 0))
+    if rc:
+        raise MpdetError(rc, f"batch(count={len(mats)}, p={p})")
+    return zk, outs
+
+
+def _norm_host(t, n):
+    s, e, m = t
+    return (np.asarray(s, np.int8).reshape(-1), np.asarray(e, np.int64).reshape(-1),
+            np.asarray(m, np.uint32).reshape(-1, n))
 
 
 def tune_cache_key(device: str, p: int, Ns) -> str:

@@ -398,4 +398,37 @@ extern "C" int mpdet_batch_autotune(mpdet_batch_t b, int reps, int32_t* variant,
   return MPDET_OK;
 }
 
+extern "C" int mpdet_batch(int64_t count, const int64_t* Ns, int32_t p_bits, const mpdet_numv* in,
+                           mpdet_numv* minors_out, int64_t* status_out, int device_ptr, void* cuda_stream) {
+  if (count < 1 || !Ns || !in || !minors_out) return MPDET_EINVAL;
+  for (int64_t m = 0; m < count; ++m)
+    if (!in[m].sign || !in[m].exp || !in[m].limbs || !minors_out[m].sign || !minors_out[m].exp ||
+        !minors_out[m].limbs)
+      return MPDET_EINVAL;
+  mpdet_batch_t b = nullptr;
+  int rc = mpdet_batch_create(count, Ns, p_bits, cuda_stream, &b);
+  if (rc) return rc;
+  for (int64_t m = 0; m < count && !rc; ++m) rc = mpdet_batch_set_mp(b, m, in[m], device_ptr);
+  const mpdet_numv none{nullptr, nullptr, nullptr};
+  if (!rc) rc = enqueue_factor(b, b->stream, none, nullptr, cudaMemcpyDeviceToDevice);
+  if (!rc) b->launches += 1;
+  // matrix m's minors D_1..D_{N_m} sit at offset doff[m] of the batch's minors
+  const cudaMemcpyKind k = device_ptr ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  const int n = b->n;
+  for (int64_t m = 0; m < count && !rc; ++m) {
+    const MpArr d = view(b->D, b->doff[m], n);
+    const int64_t N = b->Ns[m];
+    if (cudaMemcpyAsync(minors_out[m].limbs, d.m, (size_t)N * n * 4, k, b->stream) != cudaSuccess ||
+        cudaMemcpyAsync(minors_out[m].exp, d.e, (size_t)N * 8, k, b->stream) != cudaSuccess ||
+        cudaMemcpyAsync(minors_out[m].sign, d.s, (size_t)N, k, b->stream) != cudaSuccess)
+      rc = MPDET_ECUDA;
+  }
+  if (!rc && status_out && cudaMemcpyAsync(status_out, b->dzero, count * 8, k, b->stream) != cudaSuccess)
+    rc = MPDET_ECUDA;
+  if (!rc && (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(b->stream) != cudaSuccess)) rc = MPDET_ECUDA;
+  if (rc) cudaStreamSynchronize(b->stream);
+  mpdet_batch_free(b);
+  return rc;
+}
+
 extern "C" int64_t mpdet_batch_launches(mpdet_batch_t b) { return b ? b->launches : -1; }

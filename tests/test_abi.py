@@ -72,6 +72,8 @@ def test_more_entry_points_reject_bad_arguments_without_a_device(lib):
     assert lib.mpdet_batch_tune(None, 1, 0) == m.EINVAL
     assert lib.mpdet_batch_autotune(None, 1, None, None, None, None) == m.EINVAL
     assert lib.mpdet_batch_launches(None) == -1
+    assert lib.mpdet_batch(0, ns, 512, None, None, None, 0, None) == m.EINVAL  # empty batch
+    assert lib.mpdet_batch(2, ns, 512, None, None, None, 0, None) == m.EINVAL  # no buffers
     assert lib.mpdet_selftest_timeout(0, 0, None) == m.EINVAL  # limit < 1
     z = m.NumV(None, None, None)
     assert lib.mpdet_factor_noalloc(0, 512, 0, z, z, z, None, None) == m.EINVAL
