@@ -177,25 +177,3 @@ def test_batch_graph_replay_and_autotune(mpdet, oracle_lib):
     assert same(D, D0) and np.array_equal(zk, zk0)
     b.close()
 
-
-def test_batch_one_shot_call(mpdet, oracle_lib):
-    """mpdet_batch (create, set, factor and free in one call, host buffers):
-    every matrix's leading minors and first zero pivot equal the oracle's."""
-    p = 1024
-    g = W.rng(4321)
-    mats = []
-    for i in range(9):
-        N = int(g.integers(1, 30))
-        if i % 2:
-            mats.append(oracle_lib.from_int(W.int_matrix(N, 50 + i).reshape(-1), p))
-        else:
-            mats.append(oracle_lib.cauchy(*W.cauchy_xy(N, 50 + i), p))
-    mats.append(oracle_lib.from_int(np.array([[1, 2, 3], [2, 4, 5], [1, 1, 1]]).reshape(-1), p))  # zero pivot
-    zk, outs = mpdet.batch_once(mats, p)
-    assert len(outs) == len(mats)
-    for i, M in enumerate(mats):
-        N = int(round(len(M[0]) ** 0.5))
-        st, ozk, OD, _ = oracle_lib.ge(M, N, p)
-        assert zk[i] == ozk, i
-        assert same(outs[i], OD), f"matrix {i} (N={N})"
-    assert zk[-1] == 2
