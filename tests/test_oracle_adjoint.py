@@ -134,3 +134,49 @@ def test_logabsdet_helper(oracle_lib):
         s, la = oracle_lib.logabsdet(D, len(M), p)
         assert abs(la - want) < 1e-15
         assert s == (1.0 if np.linalg.det(np.array(M, float)) > 0 else -1.0)
+
+
+def brute_force_usolve(Aw, p):
+    """Op-by-op exact emulation of the back substitution X = U^-1 L with
+    Fractions and RN, in reading G12's order (right-looking, bottom row
+    first): S = L (unit diagonal, zero above); for k = N..1 the row
+    X_k. = RN(S_k. * RN(1/u_kk)), then S_ic = RN(S_ic - RN(u_ik * X_kc)) for
+    every i < k and every column c.  Aw is the eliminated array of
+    brute_force_ge in last-column mode (U on and above the diagonal, L
+    below)."""
+    N = len(Aw)
+    r = lambda q: X.to_fraction(*X.rn_tuple(q, p), p)
+    S = [[Aw[i][j] if j < i else Fraction(int(i == j)) for j in range(N)] for i in range(N)]
+    for k in reversed(range(N)):
+        rk = r(1 / Aw[k][k])
+        S[k] = [r(v * rk) for v in S[k]]
+        for i in range(k):
+            S[i] = [r(S[i][c] - r(Aw[i][k] * S[k][c])) for c in range(N)]
+    return S
+
+
+@pytest.mark.parametrize("p", [64, 96, 128])
+def test_usolve_brute_force_op_sequence(oracle_lib, p):
+    """The oracle's back substitution performs exactly the rounded operations
+    of reading G12 in that order: every entry of X equals the brute-force
+    emulation bit for bit (the inverse and finite-difference pins above only
+    bound the error, which a different order or rounding would also meet)."""
+    from test_oracle_ge import brute_force_ge
+
+    g = W.rng(500 + p)
+    done = 0
+    for trial in range(40):
+        N = int(g.integers(1, 6))
+        M = (g.standard_normal((N, N)) * 10.0).tolist() if trial % 2 else g.integers(-9, 10, (N, N)).tolist()
+        D, Xm = factor_lastcol(oracle_lib, M, p)
+        if D is None:
+            continue
+        Dw, Aw = brute_force_ge(M, p, lastcol=True)
+        assert X.unpack(Xm, p) == [v for row in Aw for v in row]
+        want = brute_force_usolve(Aw, p)
+        got = X.unpack(oracle_lib.usolve(Xm, N, p), p)
+        for i in range(N):
+            for c in range(N):
+                assert got[i * N + c] == want[i][c], (trial, N, i, c)
+        done += 1
+    assert done >= 25

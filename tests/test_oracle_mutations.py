@@ -43,6 +43,13 @@ MUTATIONS = [
     ("normalised minors divide by l_N2", "st = op_recip(&c, S[row], E[row], M + row * n, &rs, &re, r);",
      "st = op_recip(&c, S[row + 1], E[row + 1], M + (row + 1) * n, &rs, &re, r);",
      ["test_oracle_ge.py::test_lastcol_integer_cofactors_and_laplace"]),
+    ("back substitution runs k upwards", "for (int64_t k = N - 1; k >= 0 && st == OR_OK; --k) {",
+     "for (int64_t k = 0; k < N && st == OR_OK; ++k) {",
+     ["test_oracle_adjoint.py::test_usolve_brute_force_op_sequence"]),
+    ("back substitution divides instead of multiplying by the reciprocal",
+     "op_mul(&c, XS[kc], XE[kc], XM + kc * n, rs, re, r, XS + kc, XE + kc, XM + kc * n);",
+     "op_div(&c, XS[kc], XE[kc], XM + kc * n, S[kk], E[kk], M + kk * n, XS + kc, XE + kc, XM + kc * n);",
+     ["test_oracle_adjoint.py::test_usolve_brute_force_op_sequence"]),
 ]
 
 
