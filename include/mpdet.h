@@ -75,8 +75,12 @@ enum {
 enum { MPDET_LASTCOL = 1, MPDET_HOSTMEM = 2 };
 
 /* Create a handle for N x N matrices at p bits on the current CUDA device.
- * p must be a power of two with 128 <= p <= 32768 (n = p/32 limbs; the kernel
- * families cover these sizes).  flags: 0 or MPDET_LASTCOL (keep L for the
+ * p must be a multiple of 32 with 64 <= p <= 32768 (n = p/32 limbs).  The
+ * kernel families hold 4, 8, ..., 1024 limbs; any other n runs in the next
+ * family's frame (mantissa in its top n limbs, the low limbs zero) with every
+ * operation rounded at p bits, so the results are those of the p-bit format,
+ * at the cost of the frame (p = 3072 costs as much as p = 4096).  Buffers
+ * crossing the ABI always hold n = p/32 limbs per number.  flags: 0 or MPDET_LASTCOL (keep L for the
  * last-column minors, 1.5x the work: Sec. 3 counts it as twice the row
  * operations).  cuda_stream: a cudaStream_t (NULL = legacy default stream).
  * Allocates (4n + 9) * N^2 bytes of device memory plus O(N n).
@@ -197,7 +201,8 @@ int64_t mpdet_steps_done(mpdet_t h);
  * digit convolution where that engine exists (p = 512, 1024, 2048),
  * warp-specialised so that the tensor core, the rounding and the subtraction
  * overlap; 2 the same one phase at a time (p = 2048 only); 0 with IMAD limb
- * products everywhere.  MPDET_TUNE_TC_MIN_ROWS (value >= 0): an update launch
+ * products everywhere (always for a p that runs in a larger frame).
+ * MPDET_TUNE_TC_MIN_ROWS (value >= 0): an update launch
  * of fewer rows than this takes the IMAD kernel even when the tensor engine is
  * selected (its tiles are 128 rows high).  By default the threshold follows the
  * precision: 64 rows at p = 2048, and the IMAD kernel always at p = 512 and
@@ -237,9 +242,9 @@ int mpdet_profile_read(mpdet_t h, double* update_ms, int64_t* update_launches, d
 
 /* Factorisation that allocates no memory.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory, such as
- * code running while a stream is captured into a CUDA graph, host frameworks
- * that give a plugin its buffers and forbid it its own allocations, and
- * latency-bound loops that cannot take an allocation mid-step.
+ * host frameworks that give a plugin its buffers and forbid it allocations of
+ * its own (the framework owns the memory budget), and latency-bound loops
+ * that cannot take an allocation mid-step.
  *
  * It runs the same kernels and the same rounded operations as mpdet_factor
  * (results are bit-identical), with all working memory (the in-place matrix,
@@ -250,14 +255,17 @@ int mpdet_profile_read(mpdet_t h, double* update_ms, int64_t* update_launches, d
  * with n = p/32 (about N <= 478 at p = 512, N <= 251 at p = 2048); larger
  * problems return MPDET_ENOSCRATCH and should use mpdet_create.
  *
+ * p must be one of the kernel families' sizes (a power of two, 128 <= p <=
+ * 32768); other precisions return MPDET_EINVAL.
+ *
  * Arguments (all device memory of the current device, 16-byte aligned):
  *   A       N*N numbers, row-major, read only (copied into the scratch);
  *   minors  N numbers, receives D_1..D_N (D_N = det);
  *   lastcol N numbers, receives C_1N..C_NN when flags has MPDET_LASTCOL
  *           (may be NULL pointers otherwise).
  * zero_pivot_k (host, may be NULL) and the return value are as for
- * mpdet_factor.  The call is enqueued on cuda_stream and synchronises that
- * stream before it returns.
+ * mpdet_factor.  The call is enqueued on cuda_stream; it copies the status
+ * words to the host and synchronises that stream before it returns.
  *
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) and caches it; make that first call before any
@@ -390,8 +398,10 @@ int mpdet_free(mpdet_t h);
 /* Message for the last failing call on h (static string when h == NULL). */
 const char* mpdet_last_error(mpdet_t h);
 
-/* Limb count and slice geometry chosen for p: n = p/32, W limbs per lane,
- * G lanes per number; returns MPDET_EINVAL for an unsupported p. */
+/* Limb count and slice geometry chosen for p: n = p/32, and the frame the
+ * kernels hold a number in: W limbs per lane, G lanes per number (W * G >= n,
+ * equal when n is a kernel family's size); returns MPDET_EINVAL for an
+ * unsupported p. */
 int mpdet_geometry(int32_t p_bits, int32_t* n, int32_t* W, int32_t* G);
 
 #ifdef __cplusplus

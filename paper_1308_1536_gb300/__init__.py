@@ -402,16 +402,27 @@ class Mpdet:
 
 
 def batch_once(mats, p: int, stream=None):
-    """One-shot batch (mpdet_batch): ``mats`` is a list of host triples of
-    N_m * N_m numbers (row-major); returns (zero_k[count], [minors triple of
-    each matrix]).  Allocates and frees the batch's device memory inside the
-    call."""
+    """One-shot batch (mpdet_batch): ``mats`` is a list of triples of
+    N_m * N_m numbers (row-major), all host arrays or all CUDA tensors;
+    returns (zero_k[count], [minors triple of each matrix]) in the same kind
+    of memory.  Allocates and frees the batch's device memory inside the
+    call, which synchronises the stream."""
     lib = load()
     n = int(p) // 32
     Ns = np.array([int(round(len(t[0]) ** 0.5)) for t in mats], dtype=np.int64)
-    ins = [tuple(np.ascontiguousarray(a) for a in _norm_host(t, n)) for t in mats]
-    outs = [empty(int(N), p) for N in Ns]
-    zk = np.zeros(len(mats), np.int64)
+    dev = _is_dev(mats[0][0])
+    if dev:
+        import torch
+
+        ins = [tuple(a.contiguous() for a in t) for t in mats]
+        outs = [(torch.zeros(int(N), dtype=torch.int8, device=t[0].device),
+                 torch.zeros(int(N), dtype=torch.int64, device=t[0].device),
+                 torch.zeros((int(N), n), dtype=torch.int32, device=t[0].device)) for N, t in zip(Ns, ins)]
+        zk = torch.zeros(len(mats), dtype=torch.int64, device=ins[0][0].device)
+    else:
+        ins = [tuple(np.ascontiguousarray(a) for a in _norm_host(t, n)) for t in mats]
+        outs = [empty(int(N), p) for N in Ns]
+        zk = np.zeros(len(mats), np.int64)
     in_arr = (NumV * len(mats))(*[_numv(t) for t in ins])
     out_arr = (NumV * len(mats))(*[_numv(t) for t in outs])
     if stream is None:
@@ -422,8 +433,7 @@ def batch_once(mats, p: int, stream=None):
         except Exception:
             stream = None
     rc = lib.mpdet_batch(len(mats), Ns.ctypes.data_as(ctypes.c_void_p), int(p), ctypes.cast(in_arr, ctypes.c_void_p),
-                         ctypes.cast(out_arr, ctypes.c_void_p), zk.ctypes.data_as(ctypes.c_void_p), 0,
-                         ctypes.c_void_p(stream or 0))
+                         ctypes.cast(out_arr, ctypes.c_void_p), _ptr(zk), int(dev), ctypes.c_void_p(stream or 0))
     if rc:
         raise MpdetError(rc, f"batch(count={len(mats)}, p={p})")
     return zk, outs
@@ -533,6 +543,14 @@ class Batch:
             A = np.ascontiguousarray(A, np.float64)
         self._check(self.lib.mpdet_batch_set_f64(self.h, int(m), _ptr(A), int(self.Ns[m]), int(dev)),
                     "batch_set_f64")
+
+    def set_mp(self, m, A):
+        """Matrix m from N_m * N_m numbers already at p bits (a triple of host
+        arrays, or of CUDA tensors for device memory), row-major, canonical."""
+        dev = _is_dev(A[0])
+        if not dev:
+            A = tuple(np.ascontiguousarray(a) for a in _norm_host(A, self.n))
+        self._check(self.lib.mpdet_batch_set_mp(self.h, int(m), _numv(A), int(dev)), "batch_set_mp")
 
     def factor(self, out=None, zero_k=None):
         """Host mode: returns (zero_k[count], minors triple of sum(N) numbers);

@@ -52,7 +52,8 @@ int batch_variants(int n, const BatchVariant** out) {
 
 struct mpdet_batch_ctx {
   int64_t count = 0, total = 0, total_d = 0, max_n = 0;
-  int p = 0, n = 0, nsm = 0;
+  // p, n: the kernels' frame; nu: the limbs of the precision asked for (pad = n - nu)
+  int p = 0, n = 0, nu = 0, pad = 0, nsm = 0;
   int max_blocks = 0;  // blocks the per-block multiplier scratch Z is sized for
   cudaStream_t stream = nullptr;
   const mpd::KernelSet* ks = nullptr;
@@ -83,8 +84,9 @@ static void free_arr(MpArr* a) {
   *a = MpArr{};
 }
 
-static bool alloc_arr(MpArr* a, int64_t count, int n) {
+static bool alloc_arr(MpArr* a, int64_t count, int n, int pad) {
   if (count < 1) count = 1;
+  a->pad = pad;
   return cudaMalloc(&a->m, (size_t)count * n * 4) == cudaSuccess && cudaMalloc(&a->e, (size_t)count * 8) == cudaSuccess &&
          cudaMalloc(&a->s, (size_t)count) == cudaSuccess;
 }
@@ -118,8 +120,11 @@ extern "C" int mpdet_batch_create(int64_t count, const int64_t* Ns, int32_t p_bi
   mpdet_batch_t b = new (std::nothrow) mpdet_batch_ctx();
   if (!b) return MPDET_ENOMEM;
   b->count = count;
-  b->p = p_bits;
-  b->n = n;
+  b->nu = n;
+  b->n = mpd::frame_limbs(n);
+  b->p = 32 * b->n;
+  b->pad = b->n - b->nu;
+  n = b->n;
   b->stream = (cudaStream_t)cuda_stream;
   b->ks = mpd::kernel_set_for(n);
   b->Ns.assign(Ns, Ns + count);
@@ -150,8 +155,8 @@ extern "C" int mpdet_batch_create(int64_t count, const int64_t* Ns, int32_t p_bi
     b->bpsm = b->bpsm_max[0];
     b->max_blocks = b->nsm * mx;
   }
-  ok = ok && alloc_arr(&b->X0, b->total, n) && alloc_arr(&b->X, b->total, n) && alloc_arr(&b->D, b->total_d, n) &&
-       alloc_arr(&b->Z, (int64_t)b->max_blocks * b->max_n, n);
+  ok = ok && alloc_arr(&b->X0, b->total, n, b->pad) && alloc_arr(&b->X, b->total, n, b->pad) &&
+       alloc_arr(&b->D, b->total_d, n, b->pad) && alloc_arr(&b->Z, (int64_t)b->max_blocks * b->max_n, n, b->pad);
   ok = ok && cudaMalloc(&b->dN, count * 8) == cudaSuccess && cudaMalloc(&b->dxoff, count * 8) == cudaSuccess &&
        cudaMalloc(&b->ddoff, count * 8) == cudaSuccess && cudaMalloc(&b->dzero, count * 8) == cudaSuccess &&
        cudaMalloc(&b->dorder, count * 4) == cudaSuccess && cudaMalloc(&b->dqueue, 16) == cudaSuccess;
@@ -168,7 +173,9 @@ extern "C" int mpdet_batch_create(int64_t count, const int64_t* Ns, int32_t p_bi
   return MPDET_OK;
 }
 
-static MpArr view(const MpArr& a, int64_t off, int n) { return MpArr{a.s + off, a.e + off, a.m + (size_t)off * n}; }
+static MpArr view(const MpArr& a, int64_t off, int n) {
+  return MpArr{a.s + off, a.e + off, a.m + (size_t)off * n, a.pad};
+}
 
 static int stage_in(mpdet_batch_t b, const void* src, size_t bytes, const void** dev) {
   if (b->stage_bytes < bytes) {
@@ -236,16 +243,21 @@ extern "C" int mpdet_batch_set_cauchy(mpdet_batch_t b, int64_t m, const double* 
   return finish(b, device_ptr);
 }
 
-extern "C" int mpdet_batch_set_mp(mpdet_batch_t b, int64_t m, mpdet_numv A, int device_ptr) {
-  if (!b || m < 0 || m >= b->count || !A.sign || !A.exp || !A.limbs) return MPDET_EINVAL;
+// Copy matrix m's N_m * N_m numbers into the stored inputs (no synchronisation;
+// a copy from pageable host memory returns once the source has been read).
+static int copy_mp_in(mpdet_batch_t b, int64_t m, const mpdet_numv& A, int device_ptr) {
   const int64_t NN = b->Ns[m] * b->Ns[m];
   const MpArr v = view(b->X0, b->xoff[m], b->n);
   const cudaMemcpyKind k = device_ptr ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  if (cudaMemcpyAsync(v.m, A.limbs, (size_t)NN * b->n * 4, k, b->stream) != cudaSuccess ||
-      cudaMemcpyAsync(v.e, A.exp, (size_t)NN * 8, k, b->stream) != cudaSuccess ||
-      cudaMemcpyAsync(v.s, A.sign, (size_t)NN, k, b->stream) != cudaSuccess)
+  if (mpd::copy_numbers(v, b->n, A.sign, A.exp, A.limbs, b->nu, NN, true, k, b->stream) != cudaSuccess)
     return MPDET_ECUDA;
-  return finish(b, device_ptr);
+  return MPDET_OK;
+}
+
+extern "C" int mpdet_batch_set_mp(mpdet_batch_t b, int64_t m, mpdet_numv A, int device_ptr) {
+  if (!b || m < 0 || m >= b->count || !A.sign || !A.exp || !A.limbs) return MPDET_EINVAL;
+  const int rc = copy_mp_in(b, m, A, device_ptr);
+  return rc ? rc : finish(b, device_ptr);
 }
 
 // One factorisation of the stored inputs: working copy, cleared queue and
@@ -261,9 +273,8 @@ static int enqueue_factor(mpdet_batch_t b, cudaStream_t st, mpdet_numv minors, i
   mpd::BatchDescHost bd{b->dN, b->dxoff, b->ddoff, b->dorder, b->dzero, b->dqueue, b->count, b->max_n};
   const int blocks = (int)std::min<int64_t>((int64_t)b->nsm * b->bpsm, b->count);
   if (b->variants[b->variant].launch(b->X, b->D, b->Z, bd, b->p, blocks, st) != cudaSuccess) return MPDET_ECUDA;
-  if ((minors.limbs && cudaMemcpyAsync(minors.limbs, b->D.m, (size_t)b->total_d * n * 4, k, st) != cudaSuccess) ||
-      (minors.exp && cudaMemcpyAsync(minors.exp, b->D.e, (size_t)b->total_d * 8, k, st) != cudaSuccess) ||
-      (minors.sign && cudaMemcpyAsync(minors.sign, b->D.s, (size_t)b->total_d, k, st) != cudaSuccess) ||
+  if (mpd::copy_numbers(b->D, n, minors.sign, minors.exp, minors.limbs, b->nu, b->total_d, false, k, st) !=
+          cudaSuccess ||
       (zero_k && cudaMemcpyAsync(zero_k, b->dzero, b->count * 8, k, st) != cudaSuccess))
     return MPDET_ECUDA;
   return MPDET_OK;
@@ -400,7 +411,10 @@ extern "C" int mpdet_batch_autotune(mpdet_batch_t b, int reps, int32_t* variant,
 
 extern "C" int mpdet_batch(int64_t count, const int64_t* Ns, int32_t p_bits, const mpdet_numv* in,
                            mpdet_numv* minors_out, int64_t* status_out, int device_ptr, void* cuda_stream) {
-  if (count < 1 || !Ns || !in || !minors_out) return MPDET_EINVAL;
+  // sizes first: count bounds how far the pointer arrays may be read
+  if (count < 1 || count > (int64_t)1 << 30 || !Ns || !in || !minors_out) return MPDET_EINVAL;
+  for (int64_t m = 0; m < count; ++m)
+    if (Ns[m] < 1 || Ns[m] > 65536) return MPDET_EINVAL;
   for (int64_t m = 0; m < count; ++m)
     if (!in[m].sign || !in[m].exp || !in[m].limbs || !minors_out[m].sign || !minors_out[m].exp ||
         !minors_out[m].limbs)
@@ -408,7 +422,8 @@ extern "C" int mpdet_batch(int64_t count, const int64_t* Ns, int32_t p_bits, con
   mpdet_batch_t b = nullptr;
   int rc = mpdet_batch_create(count, Ns, p_bits, cuda_stream, &b);
   if (rc) return rc;
-  for (int64_t m = 0; m < count && !rc; ++m) rc = mpdet_batch_set_mp(b, m, in[m], device_ptr);
+  // all inputs are enqueued without a wait in between; one synchronisation at the end
+  for (int64_t m = 0; m < count && !rc; ++m) rc = copy_mp_in(b, m, in[m], device_ptr);
   const mpdet_numv none{nullptr, nullptr, nullptr};
   if (!rc) rc = enqueue_factor(b, b->stream, none, nullptr, cudaMemcpyDeviceToDevice);
   if (!rc) b->launches += 1;
@@ -418,9 +433,8 @@ extern "C" int mpdet_batch(int64_t count, const int64_t* Ns, int32_t p_bits, con
   for (int64_t m = 0; m < count && !rc; ++m) {
     const MpArr d = view(b->D, b->doff[m], n);
     const int64_t N = b->Ns[m];
-    if (cudaMemcpyAsync(minors_out[m].limbs, d.m, (size_t)N * n * 4, k, b->stream) != cudaSuccess ||
-        cudaMemcpyAsync(minors_out[m].exp, d.e, (size_t)N * 8, k, b->stream) != cudaSuccess ||
-        cudaMemcpyAsync(minors_out[m].sign, d.s, (size_t)N, k, b->stream) != cudaSuccess)
+    if (mpd::copy_numbers(d, n, minors_out[m].sign, minors_out[m].exp, minors_out[m].limbs, b->nu, N, false, k,
+                          b->stream) != cudaSuccess)
       rc = MPDET_ECUDA;
   }
   if (!rc && status_out && cudaMemcpyAsync(status_out, b->dzero, count * 8, k, b->stream) != cudaSuccess)

@@ -147,14 +147,14 @@ __global__ void k_cauchy(const double* __restrict__ x, const double* __restrict_
     lift_f64_slice<W, G>(gp, x[i], xs, xe, XL);
     lift_f64_slice<W, G>(gp, y[j], ys, ye, YL);
     // s = RN(x + y) = RN(x - (-y))
-    sub_round<W, G>(gp, p, xs, xe, XL, (int8_t)(ys ^ (ye != ZEXP ? 1 : 0)), ye, YL, buf);
+    sub_round<W, G>(gp, p, xs, xe, XL, (int8_t)(ys ^ (ye != ZEXP ? 1 : 0)), ye, YL, buf, X.pad);
     uint32_t Mr[W];
     if (xe == ZEXP) {  // x_i + y_j == 0 has no reciprocal: divide a dummy, store +0
 #pragma unroll
       for (int q = 0; q < W; ++q) XL[q] = 0u;
       if (gp.g == G - 1) XL[W - 1] = 0x80000000u;
     }
-    const int adj = recip_round<W, G>(gp, XL, buf, Mr);
+    const int adj = recip_round<W, G>(gp, XL, buf, Mr, X.pad);
     if (active && xe != ZEXP) {
       store_slice<W>(X.m + idx * n + gp.g * W, Mr);
       if (gp.g == 0) {
@@ -209,7 +209,7 @@ __global__ void k_pivot(MpArr X, int64_t N, int64_t k, MpArr D, MpArr R, int* st
     __syncwarp();
     const int8_t ps = D.s[k - 1];
     const int64_t pe = D.e[k - 1];
-    int adj = mul_round<W, G>(gp, A, dprev, Dm);
+    int adj = mul_round<W, G>(gp, A, dprev, Dm, X.pad);
     if (pe == ZEXP || ae == ZEXP) {
       ds = 0;
       de = ZEXP;
@@ -238,7 +238,7 @@ __global__ void k_pivot(MpArr X, int64_t N, int64_t k, MpArr D, MpArr R, int* st
   }
   if (already || k == N - 1) return;
   uint32_t Mr[W];
-  int adj = recip_round<W, G>(gp, A, buf, Mr);
+  int adj = recip_round<W, G>(gp, A, buf, Mr, X.pad);
   if (mine) {
     store_slice<W>(R.m + gp.g * W, Mr);
     if (gp.g == 0) {
@@ -271,7 +271,7 @@ __global__ void k_mult(MpArr X, int64_t N, int64_t k, MpArr R, MpArr Z, const in
   load_slice<W>(X.m + ik * n + gp.g * W, A);
   const int8_t as = X.s[ik];
   const int64_t ae = X.e[ik];
-  int adj = mul_round<W, G>(gp, A, rm, M);
+  int adj = mul_round<W, G>(gp, A, rm, M, X.pad);
   const bool zero = (ae == ZEXP);
   if (zero) {
 #pragma unroll
@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(128, MINB) k_update(MpArr X, UpdArgs a, MpArr 
     int8_t xs = X.s[ij];
     int64_t xe = X.e[ij];
     const int64_t zer = ze_s[r];
-    int adj = mul_round<W, G>(gp, Bk, zbuf + r * n, T);
+    int adj = mul_round<W, G>(gp, Bk, zbuf + r * n, T, X.pad);
     load_slice<W>(X.m + ij * n + gp.g * W, Xv);
     const bool tz = (zer == ZEXP) || (be == ZEXP);
     const int8_t ts = tz ? 0 : (int8_t)(zs_s[r] ^ bs);
@@ -372,7 +372,7 @@ __global__ void __launch_bounds__(128, MINB) k_update(MpArr X, UpdArgs a, MpArr 
 #pragma unroll
       for (int q = 0; q < W; ++q) T[q] = 0u;
     }
-    sub_round<W, G>(gp, p, xs, xe, Xv, ts, te, T, buf);
+    sub_round<W, G>(gp, p, xs, xe, Xv, ts, te, T, buf, X.pad);
     if (active) {
       store_slice<W>(X.m + ij * n + gp.g * W, Xv);
       if (gp.g == 0) {
@@ -410,7 +410,7 @@ __global__ void k_update_col(MpArr X, UpdArgs a, MpArr Z, const int* status, int
   int64_t xe = X.e[ij];
   const int64_t zer = Z.e[i];
   const int8_t zs = Z.s[i];
-  const int adj = mul_round<W, G>(gp, Bk, Z.m + i * n, T);
+  const int adj = mul_round<W, G>(gp, Bk, Z.m + i * n, T, X.pad);
   load_slice<W>(X.m + ij * n + gp.g * W, Xv);
   const bool tz = (zer == ZEXP) || (be == ZEXP);
   const int8_t ts = tz ? 0 : (int8_t)(zs ^ bs);
@@ -419,7 +419,7 @@ __global__ void k_update_col(MpArr X, UpdArgs a, MpArr Z, const int* status, int
 #pragma unroll
     for (int q = 0; q < W; ++q) T[q] = 0u;
   }
-  sub_round<W, G>(gp, p, xs, xe, Xv, ts, te, T, sbuf + (threadIdx.x / G) * SW);
+  sub_round<W, G>(gp, p, xs, xe, Xv, ts, te, T, sbuf + (threadIdx.x / G) * SW, X.pad);
   if (active) {
     store_slice<W>(X.m + ij * n + gp.g * W, Xv);
     if (gp.g == 0) {
@@ -483,7 +483,7 @@ __global__ void k_rowscale(MpArr S, int64_t N, int64_t k, MpArr R) {
   load_slice<W>(S.m + kc * n + gp.g * W, A);
   const int8_t as = S.s[kc];
   const int64_t ae = S.e[kc];
-  const int adj = mul_round<W, G>(gp, A, rm, M);
+  const int adj = mul_round<W, G>(gp, A, rm, M, S.pad);
   if (active) {
     const bool zero = (ae == ZEXP) || (re == ZEXP);
     if (zero) {
@@ -568,7 +568,7 @@ __global__ void k_lastcol(MpArr X, int64_t N, MpArr F, MpArr out, int normalised
   load_slice<W>(X.m + Nj * n + gp.g * W, L);
   const int8_t ls = X.s[Nj];
   const int64_t le = X.e[Nj];
-  int adj = mul_round<W, G>(gp, L, fm, M);
+  int adj = mul_round<W, G>(gp, L, fm, M, X.pad);
   int8_t os;
   int64_t oe;
   if (le == ZEXP || fe == ZEXP) {
@@ -637,7 +637,7 @@ __global__ void k_series(MpArr X, int64_t N, MpArr F, int normalised, MpArr out)
     const int64_t le = X.e[xj];
     const int8_t fs = F.s[fi];
     const int64_t fe = F.e[fi];
-    const int adj = mul_round<W, G>(gp, L, F.m + fi * n, M);
+    const int adj = mul_round<W, G>(gp, L, F.m + fi * n, M, X.pad);
     int8_t os;
     int64_t oe;
     if (le == ZEXP || fe == ZEXP) {
@@ -687,7 +687,7 @@ __global__ void k_recip1(MpArr src, int64_t idx, MpArr dst, int* status, int cod
     if (threadIdx.x == 0) *status = code;
     return;
   }
-  int adj = recip_round<W, G>(gp, A, sbuf + (threadIdx.x / G) * SW, M);
+  int adj = recip_round<W, G>(gp, A, sbuf + (threadIdx.x / G) * SW, M, src.pad);
   if (threadIdx.x < G) {
     store_slice<W>(dst.m + gp.g * W, M);
     if (gp.g == 0) {
@@ -734,6 +734,7 @@ __global__ void __launch_bounds__(128, 4) k_batch(MpArr Xall, MpArr Dall, MpArr 
   __shared__ int8_t r_s;
   __shared__ int s_job, s_zero;
   Grp<G> gp;
+  const int pad = Xall.pad;
   const int gid = threadIdx.x / G;
   uint32_t* buf = sbuf + gid * SW;
   MpArr Z{Zall.s + blockIdx.x * bd.max_n, Zall.e + blockIdx.x * bd.max_n, Zall.m + (size_t)blockIdx.x * bd.max_n * n};
@@ -761,7 +762,7 @@ __global__ void __launch_bounds__(128, 4) k_batch(MpArr Xall, MpArr Dall, MpArr 
 #pragma unroll
           for (int q = 0; q < PW; ++q) Dm[q] = A[q];
         } else {
-          const int adj = mul_round<PW, PG>(pg, A, D.m + (k - 1) * n, Dm);
+          const int adj = mul_round<PW, PG>(pg, A, D.m + (k - 1) * n, Dm, pad);
           const int8_t ps = D.s[k - 1];
           const int64_t pe = D.e[k - 1];
           if (pe == ZEXP || ae == ZEXP) {
@@ -784,7 +785,7 @@ __global__ void __launch_bounds__(128, 4) k_batch(MpArr Xall, MpArr Dall, MpArr 
         if (threadIdx.x == 0) s_zero = (ae == ZEXP);
         if (ae != ZEXP && k < N - 1) {  // warp-uniform: every lane read the same pivot
           uint32_t Mr[PW];
-          const int adj = recip_round<PW, PG>(pg, A, sbuf + (threadIdx.x / PG) * SW, Mr);
+          const int adj = recip_round<PW, PG>(pg, A, sbuf + (threadIdx.x / PG) * SW, Mr, pad);
           if (threadIdx.x < PG) {
             store_slice<PW>(r_m + pg.g * PW, Mr);
             if (pg.g == 0) {
@@ -817,7 +818,7 @@ __global__ void __launch_bounds__(128, 4) k_batch(MpArr Xall, MpArr Dall, MpArr 
         const int64_t i = k + 1 + t, ik = i * N + k;
         uint32_t A[W], M[W];
         load_slice<W>(X.m + ik * n + gp.g * W, A);
-        const int adj = mul_round<W, G>(gp, A, r_m, M);
+        const int adj = mul_round<W, G>(gp, A, r_m, M, pad);
         const int64_t ae = X.e[ik];
         if (active) {
           const bool zero = (ae == ZEXP);
@@ -852,7 +853,7 @@ __global__ void __launch_bounds__(128, 4) k_batch(MpArr Xall, MpArr Dall, MpArr 
         const int8_t bs = X.s[kj];
         const int64_t be = X.e[kj];
         const int64_t zer = Z.e[i];
-        const int adj = mul_round<W, G>(gp, Bk, Z.m + i * n, T);
+        const int adj = mul_round<W, G>(gp, Bk, Z.m + i * n, T, pad);
         const bool tz = (zer == ZEXP) || (be == ZEXP);
         const int8_t ts = tz ? 0 : (int8_t)(Z.s[i] ^ bs);
         const int64_t te = tz ? ZEXP : zer + be + adj;
@@ -863,7 +864,7 @@ __global__ void __launch_bounds__(128, 4) k_batch(MpArr Xall, MpArr Dall, MpArr 
         load_slice<W>(X.m + ij * n + gp.g * W, Xv);
         int8_t xs = X.s[ij];
         int64_t xe = X.e[ij];
-        sub_round<W, G>(gp, p, xs, xe, Xv, ts, te, T, buf);
+        sub_round<W, G>(gp, p, xs, xe, Xv, ts, te, T, buf, pad);
         if (active) {
           store_slice<W>(X.m + ij * n + gp.g * W, Xv);
           if (gp.g == 0) {
@@ -905,7 +906,7 @@ __global__ void k_ops(int op, int64_t count, MpArr A, MpArr B, MpArr O, int p) {
     if (op == 0) {
       store_slice<W>(zb + gp.g * W, b);
       __syncwarp();
-      const int adj = mul_round<W, G>(gp, a, zb, o);
+      const int adj = mul_round<W, G>(gp, a, zb, o, A.pad);
       __syncwarp();
       if (ae == ZEXP || be == ZEXP) {
 #pragma unroll
@@ -916,7 +917,7 @@ __global__ void k_ops(int op, int64_t count, MpArr A, MpArr B, MpArr O, int p) {
       }
     } else if (op == 1 || op == 2) {
       const int8_t bsx = (op == 2 && be != ZEXP) ? (int8_t)(bs ^ 1) : bs;  // a + b = a - (-b)
-      sub_round<W, G>(gp, p, as, ae, a, bsx, be, b, buf);
+      sub_round<W, G>(gp, p, as, ae, a, bsx, be, b, buf, A.pad);
 #pragma unroll
       for (int q = 0; q < W; ++q) o[q] = a[q];
       os = as;
@@ -928,7 +929,7 @@ __global__ void k_ops(int op, int64_t count, MpArr A, MpArr B, MpArr O, int p) {
         for (int q = 0; q < W; ++q) a[q] = 0u;
         if (gp.g == G - 1) a[W - 1] = 0x80000000u;
       }
-      const int adj = recip_round<W, G>(gp, a, buf, o);
+      const int adj = recip_round<W, G>(gp, a, buf, o, A.pad);
       if (z) {
 #pragma unroll
         for (int q = 0; q < W; ++q) o[q] = 0u;

@@ -6,11 +6,16 @@
 
 namespace mpd {
 
-// Structure-of-arrays view of numbers in device memory (n limbs each).
+// Structure-of-arrays view of numbers in device memory (n limbs each).  pad:
+// the precision is p = 32 (n - pad) bits; a precision whose limb count is not
+// one of the kernel families' sizes is held in the next family's frame of n
+// limbs, mantissa in the top n - pad limbs and the low pad limbs zero, and
+// every operation rounds at that position (0: the whole frame).
 struct MpArr {
   int8_t* s;
   int64_t* e;
   uint32_t* m;
+  int pad = 0;
 };
 
 // Device pointers describing a batch of independent matrices.
@@ -116,6 +121,43 @@ cudaError_t update_tc(MpArr X, const UpdArgs& a, MpArr Z, int* status, int p, in
 
 // Kernel set for n = p/32 limbs, or nullptr if this n is not instantiated.
 const KernelSet* kernel_set_for(int n);
+
+// Limbs of the frame that holds numbers of nu limbs (2 <= nu <= 1024): the
+// smallest kernel family size >= nu (powers of two from 4).
+inline int frame_limbs(int nu) {
+  int nf = 4;
+  while (nf < nu) nf *= 2;
+  return nf;
+}
+
+// Copy count numbers between a caller's arrays (nu limbs per number) and a
+// frame array of nf >= nu limbs per number, whose mantissas sit in the top nu
+// limbs with the low nf - nu limbs zero.  to_frame: caller -> frame (the low
+// limbs are cleared), else frame -> caller.  A null caller pointer skips that
+// field.  Asynchronous on st.
+inline cudaError_t copy_numbers(MpArr f, int nf, int8_t* s, int64_t* e, uint32_t* m, int nu, int64_t count,
+                                bool to_frame, cudaMemcpyKind kind, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  cudaError_t r = cudaSuccess;
+  const int pad = nf - nu;
+  if (m) {
+    if (pad == 0) {
+      r = to_frame ? cudaMemcpyAsync(f.m, m, (size_t)count * nf * 4, kind, st)
+                   : cudaMemcpyAsync(m, f.m, (size_t)count * nf * 4, kind, st);
+    } else if (to_frame) {
+      r = cudaMemset2DAsync(f.m, (size_t)nf * 4, 0, (size_t)pad * 4, (size_t)count, st);
+      if (r == cudaSuccess)
+        r = cudaMemcpy2DAsync(f.m + pad, (size_t)nf * 4, m, (size_t)nu * 4, (size_t)nu * 4, (size_t)count, kind, st);
+    } else {
+      r = cudaMemcpy2DAsync(m, (size_t)nu * 4, f.m + pad, (size_t)nf * 4, (size_t)nu * 4, (size_t)count, kind, st);
+    }
+  }
+  if (r == cudaSuccess && e)
+    r = to_frame ? cudaMemcpyAsync(f.e, e, (size_t)count * 8, kind, st) : cudaMemcpyAsync(e, f.e, (size_t)count * 8, kind, st);
+  if (r == cudaSuccess && s)
+    r = to_frame ? cudaMemcpyAsync(f.s, s, (size_t)count, kind, st) : cudaMemcpyAsync(s, f.s, (size_t)count, kind, st);
+  return r;
+}
 
 // one translation unit per (W, G): inst_w<W>_g<G>.cu
 #define MPD_DECLARE_SET(W, G) const KernelSet* kernel_set_w##W##_g##G();

@@ -41,7 +41,9 @@ int default_update_variant(int n) {
 
 struct mpdet_ctx {
   int64_t N = 0;
-  int p = 0, n = 0;
+  // p, n: the frame the kernels work in (a kernel family's limb count);
+  // pu, nu: the precision asked for (pu = 32 nu <= p), pad = n - nu
+  int p = 0, n = 0, pu = 0, nu = 0, pad = 0;
   uint32_t flags = 0;
   cudaStream_t stream = nullptr;
   int device = 0, nsm = 0;
@@ -101,6 +103,7 @@ static int fail(mpdet_t h, int code, const char* fmt, ...) {
 
 static int alloc_arr(mpdet_t h, MpArr* a, int64_t count) {
   int n = h->n;
+  a->pad = h->pad;
   if (cudaMalloc(&a->m, (size_t)count * n * 4) != cudaSuccess) return fail(h, MPDET_ENOMEM, "cudaMalloc limbs");
   if (cudaMalloc(&a->e, (size_t)count * 8) != cudaSuccess) return fail(h, MPDET_ENOMEM, "cudaMalloc exp");
   if (cudaMalloc(&a->s, (size_t)count) != cudaSuccess) return fail(h, MPDET_ENOMEM, "cudaMalloc sign");
@@ -132,7 +135,7 @@ static int alloc_arr_host(mpdet_t h, MpArr* a, int64_t count) {
   h->xhost[0] = hp[0];
   h->xhost[1] = hp[1];
   h->xhost[2] = hp[2];
-  *a = MpArr{(int8_t*)dp[2], (int64_t*)dp[1], (uint32_t*)dp[0]};
+  *a = MpArr{(int8_t*)dp[2], (int64_t*)dp[1], (uint32_t*)dp[0], h->pad};
   return MPDET_OK;
 }
 
@@ -149,8 +152,8 @@ static cudaError_t zero_arr(MpArr a, int64_t count, int n, cudaStream_t st) {
 }
 
 extern "C" int mpdet_geometry(int32_t p_bits, int32_t* n, int32_t* W, int32_t* G) {
-  if (p_bits < 128 || p_bits > 32768 || (p_bits & (p_bits - 1))) return MPDET_EINVAL;
-  const KernelSet* ks = mpd::kernel_set_for(p_bits / 32);
+  if (p_bits < 64 || p_bits > 32768 || (p_bits % 32) != 0) return MPDET_EINVAL;
+  const KernelSet* ks = mpd::kernel_set_for(mpd::frame_limbs(p_bits / 32));
   if (!ks) return MPDET_EINVAL;
   if (n) *n = p_bits / 32;
   if (W) *W = ks->W;
@@ -167,8 +170,11 @@ extern "C" int mpdet_create(int64_t N, int32_t p_bits, uint32_t flags, void* cud
   mpdet_t h = new (std::nothrow) mpdet_ctx();
   if (!h) return MPDET_ENOMEM;
   h->N = N;
-  h->p = p_bits;
-  h->n = p_bits / 32;
+  h->pu = p_bits;
+  h->nu = p_bits / 32;
+  h->n = mpd::frame_limbs(h->nu);
+  h->p = 32 * h->n;
+  h->pad = h->n - h->nu;
   h->flags = flags;
   h->stream = (cudaStream_t)cuda_stream;
   h->ks = mpd::kernel_set_for(h->n);
@@ -296,18 +302,11 @@ extern "C" int mpdet_set_i32(mpdet_t h, const int32_t* A, int64_t ld, int device
   return set_dense(h, A, ld, device_ptr, 1);
 }
 
+// Numbers between a caller's buffer (pu bits: nu limbs each) and a device
+// array of the handle (frame of n limbs each).
 static int copy_arr(mpdet_t h, MpArr dst_dev, const mpdet_numv& src, int64_t count, int device_ptr, bool to_dev) {
   cudaMemcpyKind kind = device_ptr ? cudaMemcpyDeviceToDevice : (to_dev ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost);
-  size_t nb = (size_t)count * h->n * 4;
-  if (to_dev) {
-    if (src.limbs) CU(h, cudaMemcpyAsync(dst_dev.m, src.limbs, nb, kind, h->stream));
-    if (src.exp) CU(h, cudaMemcpyAsync(dst_dev.e, src.exp, (size_t)count * 8, kind, h->stream));
-    if (src.sign) CU(h, cudaMemcpyAsync(dst_dev.s, src.sign, (size_t)count, kind, h->stream));
-  } else {
-    if (src.limbs) CU(h, cudaMemcpyAsync(src.limbs, dst_dev.m, nb, kind, h->stream));
-    if (src.exp) CU(h, cudaMemcpyAsync(src.exp, dst_dev.e, (size_t)count * 8, kind, h->stream));
-    if (src.sign) CU(h, cudaMemcpyAsync(src.sign, dst_dev.s, (size_t)count, kind, h->stream));
-  }
+  CU(h, mpd::copy_numbers(dst_dev, h->n, src.sign, src.exp, src.limbs, h->nu, count, to_dev, kind, h->stream));
   return MPDET_OK;
 }
 
@@ -367,6 +366,7 @@ static int64_t tc_default_min_rows(int p) { return p == 2048 ? 64 : INT64_MAX; }
 // Tensor engine for an update launch of `rows` rows?
 static bool use_tc(mpdet_t h, int64_t rows) {
   if (h->flags & MPDET_HOSTMEM) return false;  // its TMA copies address device memory only
+  if (h->pad) return false;                    // it rounds at the frame's own precision only
   const int64_t thr = h->tc_min_rows >= 0 ? h->tc_min_rows : tc_default_min_rows(h->p);
   return h->engine >= 1 && mpd::tc_supports(h->p, h->engine == 1) && rows >= thr;
 }
@@ -559,7 +559,7 @@ extern "C" int mpdet_profile_read(mpdet_t h, double* update_ms, int64_t* update_
   h->ev_used = 0;
   if (update_ms) *update_ms = h->upd_ms;
   if (update_launches) *update_launches = h->upd_launches;
-  if (update_limb_macs) *update_limb_macs = h->upd_products * (double)h->n * (double)h->n;
+  if (update_limb_macs) *update_limb_macs = h->upd_products * (double)h->nu * (double)h->nu;
   if (launches) *launches = h->launches;
   return MPDET_OK;
 }
@@ -601,7 +601,7 @@ extern "C" int mpdet_factor(mpdet_t h, mpdet_numv det, mpdet_numv minors, int64_
   if (!h->have_matrix) return fail(h, MPDET_ESTATE, "factor: no matrix set");
   int rc = run_steps(h, h->k_done, h->N);
   if (rc) return rc;
-  MpArr last{h->D.s + (h->N - 1), h->D.e + (h->N - 1), h->D.m + (size_t)(h->N - 1) * h->n};
+  MpArr last{h->D.s + (h->N - 1), h->D.e + (h->N - 1), h->D.m + (size_t)(h->N - 1) * h->n, h->pad};
   rc = copy_arr(h, last, det, 1, device_ptr, false);
   if (rc) return rc;
   rc = copy_arr(h, h->D, minors, h->N, device_ptr, false);
@@ -627,12 +627,12 @@ extern "C" int mpdet_lastcol_minors(mpdet_t h, mpdet_numv out, int normalised, i
   }
   const int64_t N = h->N;
   if (N == 1) {  // C_11 = D_0 = 1, delta_{1,1} = 1
-    uint32_t* one = new uint32_t[h->n]();
-    one[h->n - 1] = 0x80000000u;
+    uint32_t* one = new uint32_t[h->nu]();
+    one[h->nu - 1] = 0x80000000u;
     int8_t s = 0;
     int64_t e = 1;
     cudaMemcpyKind k = device_ptr ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
-    cudaError_t ce = cudaMemcpy(out.limbs, one, h->n * 4, k);
+    cudaError_t ce = cudaMemcpy(out.limbs, one, h->nu * 4, k);
     if (ce == cudaSuccess) ce = cudaMemcpy(out.exp, &e, 8, k);
     if (ce == cudaSuccess) ce = cudaMemcpy(out.sign, &s, 1, k);
     delete[] one;
@@ -646,7 +646,7 @@ extern "C" int mpdet_lastcol_minors(mpdet_t h, mpdet_numv out, int normalised, i
     h->launches += 1;
     F = h->R;
   } else {
-    F = MpArr{h->D.s + (N - 2), h->D.e + (N - 2), h->D.m + (size_t)(N - 2) * h->n};
+    F = MpArr{h->D.s + (N - 2), h->D.e + (N - 2), h->D.m + (size_t)(N - 2) * h->n, h->pad};
   }
   CU(h, h->ks->lastcol(h->X, N, F, h->T, normalised, h->status, h->stream));
   h->launches += 1;
@@ -669,9 +669,9 @@ extern "C" int mpdet_minor_series(mpdet_t h, mpdet_numv out, int normalised, int
   if (!(h->flags & MPDET_LASTCOL)) return fail(h, MPDET_ESTATE, "minor_series: handle created without MPDET_LASTCOL");
   if (!h->have_matrix || h->k_done != h->N) return fail(h, MPDET_ESTATE, "minor_series: factorisation not complete");
   const int64_t N = h->N, total = N * (N + 1) / 2;
-  MpArr dst{out.sign, out.exp, out.limbs};
+  MpArr dst{out.sign, out.exp, out.limbs, h->pad};
   MpArr tmp{};
-  if (!device_ptr) {  // host output: a device buffer of the packed triangle for this call
+  if (!device_ptr || h->pad) {  // host output or another limb count: a device frame buffer of the triangle
     int rc = alloc_arr(h, &tmp, total);
     if (rc) {
       free_arr(&tmp);
@@ -701,9 +701,9 @@ extern "C" int mpdet_minor_series(mpdet_t h, mpdet_numv out, int normalised, int
     h->launches += 1;
   }
   int rc = ce == cudaSuccess ? MPDET_OK : fail(h, MPDET_ECUDA, "k_series: %s", cudaGetErrorString(ce));
-  if (!rc && !device_ptr) {
-    rc = copy_arr(h, tmp, out, total, 0, false);
-    if (!rc) rc = finish_call(h, 0);
+  if (!rc && tmp.m) {
+    rc = copy_arr(h, tmp, out, total, device_ptr, false);
+    if (!rc) rc = finish_call(h, device_ptr);
   } else if (!rc) {
     rc = finish_call(h, 1);
   }
@@ -721,10 +721,10 @@ extern "C" int mpdet_get_entries(mpdet_t h, int64_t count, const int64_t* idx, m
   for (int64_t q = 0; q < count; ++q)
     if (idx[q] < 0 || idx[q] >= NN) return fail(h, MPDET_EINVAL, "get_entries: index %lld out of range", (long long)idx[q]);
   const cudaMemcpyKind k = device_ptr ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-  const size_t nb = (size_t)h->n * 4;
+  const size_t nb = (size_t)h->nu * 4;
   for (int64_t q = 0; q < count; ++q) {
     const int64_t i = idx[q];
-    CU(h, cudaMemcpyAsync(out.limbs + (size_t)q * h->n, h->X.m + (size_t)i * h->n, nb, k, h->stream));
+    CU(h, cudaMemcpyAsync(out.limbs + (size_t)q * h->nu, h->X.m + (size_t)i * h->n + h->pad, nb, k, h->stream));
     CU(h, cudaMemcpyAsync(out.exp + q, h->X.e + i, 8, k, h->stream));
     CU(h, cudaMemcpyAsync(out.sign + q, h->X.s + i, 1, k, h->stream));
   }
@@ -836,14 +836,41 @@ extern "C" int mpdet_ops(int op, int64_t count, int32_t p_bits, mpdet_numv a, mp
   if (op < 0 || op > 3 || count < 0 || mpdet_geometry(p_bits, &n, nullptr, nullptr) != MPDET_OK) return MPDET_EINVAL;
   if (!a.sign || !a.exp || !a.limbs || !b.sign || !b.exp || !b.limbs || !out.sign || !out.exp || !out.limbs)
     return MPDET_EINVAL;
-  const KernelSet* ks = mpd::kernel_set_for(n);
+  const int nf = mpd::frame_limbs(n), pad = nf - n;
+  const KernelSet* ks = mpd::kernel_set_for(nf);
   int dev = 0, nsm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return MPDET_ECUDA;
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  if (ks->ops(op, count, MpArr{a.sign, a.exp, a.limbs}, MpArr{b.sign, b.exp, b.limbs},
-              MpArr{out.sign, out.exp, out.limbs}, p_bits, nsm, st) != cudaSuccess ||
-      cudaStreamSynchronize(st) != cudaSuccess) {
+  MpArr A{a.sign, a.exp, a.limbs}, B{b.sign, b.exp, b.limbs}, O{out.sign, out.exp, out.limbs};
+  MpArr F[3] = {};
+  cudaError_t e = cudaSuccess;
+  if (pad) {  // operands of another limb count go through frame copies
+    for (int q = 0; q < 3 && e == cudaSuccess; ++q) {
+      F[q].pad = pad;
+      const int64_t c = count > 0 ? count : 1;
+      e = cudaMalloc(&F[q].m, (size_t)c * nf * 4);
+      if (e == cudaSuccess) e = cudaMalloc(&F[q].e, (size_t)c * 8);
+      if (e == cudaSuccess) e = cudaMalloc(&F[q].s, (size_t)c);
+    }
+    if (e == cudaSuccess)
+      e = mpd::copy_numbers(F[0], nf, a.sign, a.exp, a.limbs, n, count, true, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess)
+      e = mpd::copy_numbers(F[1], nf, b.sign, b.exp, b.limbs, n, count, true, cudaMemcpyDeviceToDevice, st);
+    A = F[0];
+    B = F[1];
+    O = F[2];
+  }
+  if (e == cudaSuccess) e = ks->ops(op, count, A, B, O, 32 * nf, nsm, st);
+  if (e == cudaSuccess && pad)
+    e = mpd::copy_numbers(O, nf, out.sign, out.exp, out.limbs, n, count, false, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  for (MpArr& f : F) {
+    if (f.m) cudaFree(f.m);
+    if (f.e) cudaFree(f.e);
+    if (f.s) cudaFree(f.s);
+  }
+  if (e != cudaSuccess) {
     cudaGetLastError();
     return MPDET_ECUDA;
   }

@@ -4,7 +4,10 @@
 // n = p/32 little-endian uint32 limbs, e an int64; zero is s = 0, m = 0,
 // e = INT64_MIN.  Every operation is the exact result rounded to nearest,
 // ties to even, at p bits (the method works at one fixed precision
-// throughout, Sec. 4.3).
+// throughout, Sec. 4.3).  A precision of fewer limbs than the frame the
+// routines work in (n = W*G) keeps its mantissa in the top limbs of the frame
+// with the low `pad` limbs zero (the same value with the same exponent); the
+// routines then round at limb pad instead of limb 0 (round_frame).
 //
 // Work split: one number is owned by a GROUP of G consecutive lanes of a warp
 // (G in {1,2,4,8,16,32}); lane g of the group holds the W-limb SLICE
@@ -208,6 +211,60 @@ __device__ __forceinline__ void mac_row(uint32_t (&T)[L], const uint32_t (&b)[W]
 }
 
 // ---------------------------------------------------------------------------
+// Final rounding of a normalised frame mantissa.  M is this lane's slice of
+// the n frame limbs holding the top bits of an exact result, rbit the next
+// bit below them and st whether any bit below that is set.  The result keeps
+// p = 32 (n - pad) bits: with pad = 0 the whole frame, with pad > 0 the top
+// n - pad limbs (the numbers of a precision that is not a power of two of
+// limbs live in the next power-of-two frame with their low pad limbs zero).
+// Round to nearest, ties to even, at that position; the dropped limbs come
+// out zero.  Returns 1 when the rounding carried out of the top (M is then
+// 2^(32n - 1) and the exponent grows by one), else 0.  pad is uniform over
+// the warp.
+// ---------------------------------------------------------------------------
+template <int W, int G>
+__device__ __forceinline__ uint32_t round_frame(const Grp<G>& gp, uint32_t (&M)[W], uint32_t rbit, bool st,
+                                                int pad) {
+  uint32_t inc;
+  if (pad == 0) {
+    const uint32_t lsb = gp.from(M[0], 0) & 1u;
+    inc = rbit & ((st ? 1u : 0u) | lsb);
+  } else {
+    // round limb pad - 1 (its top bit is the round bit), kept limbs from pad
+    const int g = gp.g;
+    uint32_t rl = 0u, kl = 0u;
+    bool below = false;
+#pragma unroll
+    for (int q = 0; q < W; ++q) {
+      const int l = g * W + q;
+      if (l < pad - 1) below |= (M[q] != 0u);
+      if (l == pad - 1) rl = M[q];
+      if (l == pad) kl = M[q];
+    }
+    rl = gp.from(rl, (pad - 1) / W);
+    kl = gp.from(kl, pad / W);
+    const bool stk = st || rbit != 0u || (rl & 0x7fffffffu) != 0u || gp.ballot(below) != 0u;
+    inc = (rl >> 31) & ((stk ? 1u : 0u) | (kl & 1u));
+    // the increment enters at limb 0 and runs through the dropped limbs
+    // (set to all ones) into limb pad
+#pragma unroll
+    for (int q = 0; q < W; ++q)
+      if (g * W + q < pad) M[q] = 0xffffffffu;
+  }
+  const uint32_t ones = gp.ballot(all_ones<W>(M));
+  const uint64_t cm = carry_mask(0u, ones, inc);
+  slice_inc<W>(M, (uint32_t)(cm >> gp.g) & 1u);
+  const uint32_t ovf = (uint32_t)(cm >> G) & 1u;
+  if (pad) {
+#pragma unroll
+    for (int q = 0; q < W; ++q)
+      if (gp.g * W + q < pad) M[q] = 0u;
+  }
+  if (ovf && gp.g == G - 1) M[W - 1] = 0x80000000u;  // all limbs wrapped to 0
+  return ovf;
+}
+
+// ---------------------------------------------------------------------------
 // Rounded product of two mantissas.
 //   b: this lane's slice of the first mantissa (registers)
 //   z: the second mantissa, n limbs in memory (shared or global; every lane
@@ -281,7 +338,7 @@ __device__ __forceinline__ void mul_blocks_windowed(const Grp<G>& gp, const uint
 
 template <int W, int G>
 __device__ __forceinline__ int mul_round(const Grp<G>& gp, const uint32_t (&b)[W], const uint32_t* z,
-                                         uint32_t (&M)[W]) {
+                                         uint32_t (&M)[W], int pad = 0) {
   uint32_t H[W], R[W];
 #pragma unroll
   for (int i = 0; i < W; ++i) {
@@ -353,13 +410,7 @@ __device__ __forceinline__ int mul_round(const Grp<G>& gp, const uint32_t (&b)[W
     rbit = (ltop >> 30) & 1u;
     st = (ltop & 0x3fffffffu) | sticky;
   }
-  uint32_t lsb = gp.from(M[0], 0) & 1u;
-  uint32_t inc = rbit & ((st != 0u) | lsb);
-  uint32_t ones = gp.ballot(all_ones<W>(M));
-  uint64_t cm = carry_mask(0u, ones, inc);
-  slice_inc<W>(M, (uint32_t)(cm >> gp.g) & 1u);
-  uint32_t ovf = (uint32_t)(cm >> G) & 1u;
-  if (ovf && gp.g == G - 1) M[W - 1] = 0x80000000u;  // all limbs wrapped to 0
+  const uint32_t ovf = round_frame<W, G>(gp, M, rbit, st != 0u, pad);
   return (top ? 0 : -1) + (int)ovf;
 }
 
@@ -377,7 +428,8 @@ __device__ __forceinline__ int mul_round(const Grp<G>& gp, const uint32_t (&b)[W
 // ---------------------------------------------------------------------------
 template <int W, int G>
 __device__ __forceinline__ void sub_round(const Grp<G>& gp, int p, int8_t& xs, int64_t& xe, uint32_t (&X)[W],
-                                          int8_t ts, int64_t te, const uint32_t (&T)[W], uint32_t* buf) {
+                                          int8_t ts, int64_t te, const uint32_t (&T)[W], uint32_t* buf,
+                                          int pad = 0) {
   constexpr int n = W * G;
   const int g = gp.g;
   const int8_t tsn = (te == ZEXP) ? 0 : (int8_t)(ts ^ 1);  // -t
@@ -544,13 +596,7 @@ __device__ __forceinline__ void sub_round(const Grp<G>& gp, int p, int8_t& xs, i
     st = gp.ballot(stl && sh >= 2) != 0u;
     __syncwarp();
   }
-  uint32_t lsb = gp.from(Mo[0], 0) & 1u;
-  uint32_t inc = rbit & ((st ? 1u : 0u) | lsb);
-  uint32_t ones = gp.ballot(all_ones<W>(Mo));
-  uint64_t im = carry_mask(0u, ones, inc);
-  slice_inc<W>(Mo, (uint32_t)(im >> g) & 1u);
-  uint32_t ovf = (uint32_t)(im >> G) & 1u;
-  if (ovf && g == G - 1) Mo[W - 1] = 0x80000000u;
+  const uint32_t ovf = round_frame<W, G>(gp, Mo, rbit, st, pad);
   if (zero) {
     xs = 0;
     xe = ZEXP;
@@ -616,7 +662,8 @@ __host__ __device__ __forceinline__ uint32_t div21_inverse(uint32_t d) {
 // passes on more than one bit.
 // ---------------------------------------------------------------------------
 template <int W, int G>
-__device__ __forceinline__ int recip_round(const Grp<G>& gp, const uint32_t (&V)[W], uint32_t* qbuf, uint32_t (&M)[W]) {
+__device__ __forceinline__ int recip_round(const Grp<G>& gp, const uint32_t (&V)[W], uint32_t* qbuf, uint32_t (&M)[W],
+                                           int pad = 0) {
   constexpr int n = W * G;
   static_assert(W >= 4, "the quotient test reads three limbs of the top slice");
   const int g = gp.g;
@@ -709,13 +756,7 @@ __device__ __forceinline__ int recip_round(const Grp<G>& gp, const uint32_t (&V)
     M[i] = (qn >= 2u) ? M[i] : v;
   }
   const uint32_t rbit = (qn >= 2u) ? 0u : (qbuf[0] & 1u);
-  const uint32_t lsb = gp.from(M[0], 0) & 1u;
-  const uint32_t inc = rbit & ((rnz ? 1u : 0u) | lsb);
-  const uint32_t ones = gp.ballot(all_ones<W>(M));
-  const uint64_t im = carry_mask(0u, ones, inc);
-  slice_inc<W>(M, (uint32_t)(im >> g) & 1u);
-  const uint32_t ovf = (uint32_t)(im >> G) & 1u;
-  if (ovf && g == G - 1) M[W - 1] = 0x80000000u;
+  const uint32_t ovf = round_frame<W, G>(gp, M, rbit, rnz, pad);
   __syncwarp();
   return (qn >= 2u) ? 2 : 1 + (int)ovf;
 }

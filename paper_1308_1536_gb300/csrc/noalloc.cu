@@ -1,15 +1,16 @@
 // Factorisation entry point that allocates no memory.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA stream is
-// being captured into a graph (an allocation there breaks the capture), a
-// host framework that hands a plugin its buffers and forbids it to allocate
-// device memory of its own, and latency-bound loops that cannot afford an
-// allocation or a pool growth in the middle of a step.  For them
-// mpdet_factor_noalloc runs the same elimination kernels as mpdet_factor but
-// keeps every piece of working memory (the in-place matrix, the multipliers,
-// the pivot reciprocal and the status words) in one statically sized device
-// array that is part of the library image.  The caller provides only the
-// input matrix and the output buffers.
+// Some callers cannot call cudaMalloc: a host framework that hands a plugin
+// its buffers and forbids it to allocate device memory of its own (the
+// framework owns the memory budget and its pools), and latency-bound loops
+// that cannot afford an allocation or a pool growth in the middle of a step.
+// For them mpdet_factor_noalloc runs the same elimination kernels as
+// mpdet_factor but keeps every piece of working memory (the in-place matrix,
+// the multipliers, the pivot reciprocal and the status words) in one
+// statically sized device array that is part of the library image.  The
+// caller provides only the input matrix and the output buffers.  The call
+// reads the status words back to the host and synchronises its stream before
+// it returns.
 #include <cstring>
 #include <mutex>
 
@@ -87,6 +88,7 @@ extern "C" int mpdet_factor_noalloc(int64_t N, int32_t p_bits, uint32_t flags, m
   if (zero_pivot_k) *zero_pivot_k = 0;
   int32_t n = 0;
   if (N < 1 || mpdet_geometry(p_bits, &n, nullptr, nullptr) != MPDET_OK) return MPDET_EINVAL;
+  if (mpd::frame_limbs(n) != n) return MPDET_EINVAL;  // a kernel family's own limb count only
   if (flags & ~(uint32_t)MPDET_LASTCOL) return MPDET_EINVAL;
   if (!A.sign || !A.exp || !A.limbs || !minors.sign || !minors.exp || !minors.limbs) return MPDET_EINVAL;
   const bool want_lastcol = (flags & MPDET_LASTCOL) != 0;

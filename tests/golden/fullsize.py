@@ -13,7 +13,7 @@ Files (one per workload; the method is elimination without pivoting, Sec. 3
 and Alg. 1, with the augmented matrix [A I] for the last-column minors):
 
 * c2_cauchy_N1024_p2048.txt, c2_int_N1024_p2048.txt: workload C2, last-column
-  mode.  Status and first zero pivot; D_1..D_1024; C_1N..C_NN (eq.
+  mode (the integer matrix is the benchmark's: seed + 100).  Status and first zero pivot; D_1..D_1024; C_1N..C_NN (eq.
   minorsdef); one digest per row of the in-place array (U and L).
 * c3_batch_4096_p1024.txt: workload C3, 4096 matrices of sizes N uniform in
   [8, 256], even index Cauchy, odd index integer.  Per matrix: N, first zero
@@ -29,8 +29,8 @@ and Alg. 1, with the augmented matrix [A I] for the last-column minors):
   of the full N = 4096 factorisation).  D_1..D_256 and one digest per row of
   the block's upper triangle (j >= i) after elimination.
 
-Usage: python tests/golden/fullsize.py [c2 c3 c4 c5]   (all by default;
-about 1.5 hours on 8 cores).
+Usage: python tests/golden/fullsize.py [c2_cauchy c2_int c3 c4 c5]   (all by
+default; about 1.5 hours on 8 cores).
 """
 from __future__ import annotations
 
@@ -156,9 +156,9 @@ def c2(kind: str):
     N, p = cfg["N"], cfg["p"]
     if kind == "cauchy":
         x, y = W.cauchy_xy(N, cfg["seed"])
-        A = oracle.cauchy(x, y, p)
-    else:
-        A = oracle.from_int(W.int_matrix(N, cfg["seed"]).reshape(-1), p)
+        A = cauchy_parallel(x, y, p)
+    else:  # the benchmark's integer matrix (its own seed, apart from the Cauchy draw)
+        A = oracle.from_int(W.int_matrix(N, cfg["seed"] + 100).reshape(-1), p)
     st, zk, D, X = oracle.ge(A, N, p, lastcol=True, nthreads=_threads())
     recs = [("S", 0, st, zk)]
     recs += [("D", k + 1, d) for k, d in enumerate(num_digests(D))]
@@ -237,16 +237,16 @@ def _c5_rows(args):
     return i0, out
 
 
-def c5_block(x, y, p):
-    """The leading Cauchy block A_ij = RN(1/RN(x_i + y_j)) from the oracle's
-    element operations, rows computed in parallel processes (the same two
-    operations as oracle.cauchy, which is single-threaded)."""
+def cauchy_parallel(x, y, p):
+    """The Cauchy matrix A_ij = RN(1/RN(x_i + y_j)) from the oracle's element
+    operations, rows computed in parallel processes (the same two operations
+    as oracle.cauchy, which is single-threaded)."""
     import multiprocessing as mp
 
     import oracle
 
     K = len(x)
-    step = 4
+    step = max(1, K // (8 * _threads()))
     with mp.get_context("spawn").Pool(_threads()) as pool:
         parts = pool.map(_c5_rows, [(i, min(K, i + step), x, y, p) for i in range(0, K, step)], chunksize=1)
     A = oracle.empty(K * K, p)
@@ -266,7 +266,7 @@ def c5():
     p, K = cfg["p"], C5_LEAD
     x, y = W.cauchy_xy(cfg["N"], cfg["seed"])
     x, y = x[:K], y[:K]
-    A = c5_block(x, y, p)
+    A = cauchy_parallel(x, y, p)
     st, zk, D, X = oracle.ge(A, K, p, nthreads=_threads())
     recs = [("S", 0, st, zk)]
     recs += [("D", k + 1, d) for k, d in enumerate(num_digests(D))]
@@ -276,12 +276,11 @@ def c5():
 
 
 if __name__ == "__main__":
-    which = sys.argv[1:] or ["c2", "c4", "c3", "c5"]
+    which = sys.argv[1:] or ["c2_cauchy", "c2_int", "c4", "c3", "c5"]
     for w in which:
         t = time.time()
-        if w == "c2":
-            c2("cauchy")
-            c2("int")
+        if w.startswith("c2_"):
+            c2(w[3:])
         else:
             globals()[w]()
         print(f"{w}: {time.time() - t:.0f} s", flush=True)

@@ -45,7 +45,13 @@ def test_geometry_and_invalid_precisions(lib):
     assert m.geometry(512) == (16, 16, 1)
     assert m.geometry(2048) == (64, 16, 4)
     assert m.geometry(32768) == (1024, 32, 32)
-    for p in (0, 64, 96, 1000, 3072, 65536):
+    # any multiple of 32 in [64, 32768]: n = p/32 limbs in the next family's frame (W x G limbs)
+    assert m.geometry(64) == (2, 4, 1)
+    assert m.geometry(96) == (3, 4, 1)
+    assert m.geometry(160) == (5, 8, 1)
+    assert m.geometry(3072) == (96, 16, 8)
+    assert m.geometry(32736) == (1023, 32, 32)
+    for p in (0, 32, 100, 1000, 32800, 65536):
         with pytest.raises(m.MpdetError):
             m.geometry(p)
 
@@ -93,3 +99,18 @@ def test_noalloc_size_limit_without_a_device(lib):
                ctypes.cast(ctypes.byref(l32), ctypes.c_void_p))
     assert lib.mpdet_factor_noalloc(1024, 2048, 0, v, v, v, None, None) == m.ENOSCRATCH
     assert lib.mpdet_factor_noalloc(479, 512, 0, v, v, v, None, None) == m.ENOSCRATCH
+    assert lib.mpdet_factor_noalloc(8, 96, 0, v, v, v, None, None) == m.EINVAL  # power-of-two limb counts only
+
+
+def test_one_shot_batch_checks_sizes_before_pointers(lib):
+    """mpdet_batch validates count and every N before it reads the pointer
+    arrays: a bad size is refused even though in[] holds one entry only."""
+    import paper_1308_1536_gb300 as m
+
+    s8, e64, l32 = ctypes.c_int8(), ctypes.c_int64(), ctypes.c_uint32()  # never dereferenced
+    v = m.NumV(ctypes.cast(ctypes.byref(s8), ctypes.c_void_p), ctypes.cast(ctypes.byref(e64), ctypes.c_void_p),
+               ctypes.cast(ctypes.byref(l32), ctypes.c_void_p))
+    one = (m.NumV * 1)(v)
+    ns = (ctypes.c_int64 * 2)(4, 0)
+    assert lib.mpdet_batch(2, ns, 512, one, one, None, 0, None) == m.EINVAL  # N = 0 before in[1] is read
+    assert lib.mpdet_batch((1 << 30) + 1, ns, 512, one, one, None, 0, None) == m.EINVAL

@@ -41,7 +41,7 @@ def oracle_minors(oracle, kind, d, p):
     return zk, D
 
 
-@pytest.mark.parametrize("p", [512, 1024, 4096])
+@pytest.mark.parametrize("p", [96, 512, 1024, 3072, 4096])
 def test_batch_mixed_vs_oracle(mpdet, oracle_lib, p):
     g = W.rng(77 + p)
     items = []
@@ -177,3 +177,71 @@ def test_batch_graph_replay_and_autotune(mpdet, oracle_lib):
     assert same(D, D0) and np.array_equal(zk, zk0)
     b.close()
 
+
+
+def _one_shot_mats(oracle_lib, p):
+    g = W.rng(4321)
+    mats = []
+    for i in range(11):
+        N = int(g.integers(1, 40))
+        if i % 2:
+            mats.append(oracle_lib.from_int(W.int_matrix(N, 50 + i).reshape(-1), p))
+        else:
+            mats.append(oracle_lib.cauchy(*W.cauchy_xy(N, 50 + i), p))
+    mats.append(oracle_lib.from_int(np.array([[1, 2, 3], [2, 4, 5], [1, 1, 1]]).reshape(-1), p))  # zero pivot, k = 2
+    mats.append(oracle_lib.from_int(np.array([[0, 1], [1, 0]]).reshape(-1), p))  # zero pivot, k = 1
+    return mats
+
+
+@pytest.mark.parametrize("device", [False, True])
+def test_batch_one_shot_call(mpdet, oracle_lib, device):
+    """mpdet_batch (create, set, factor and free in one call) with host and
+    with device buffers: every matrix's leading minors and first zero pivot
+    equal the oracle's and the batch handle's (mpdet_batch_set_mp +
+    mpdet_batch_factor) bit for bit."""
+    import torch
+
+    p = 1024
+    mats = _one_shot_mats(oracle_lib, p)
+    Ns = [int(round(len(M[0]) ** 0.5)) for M in mats]
+    if device:
+        dm = [(torch.from_numpy(M[0]).cuda(), torch.from_numpy(M[1]).cuda(),
+               torch.from_numpy(np.ascontiguousarray(M[2]).view(np.int32)).cuda()) for M in mats]
+        zk_d, outs_d = mpdet.batch_once(dm, p)
+        zk = zk_d.cpu().numpy()
+        outs = [(o[0].cpu().numpy(), o[1].cpu().numpy(), o[2].cpu().numpy().view(np.uint32)) for o in outs_d]
+    else:
+        zk, outs = mpdet.batch_once(mats, p)
+    assert len(outs) == len(mats)
+    b = mpdet.Batch(Ns, p)
+    for m, M in enumerate(mats):
+        b.set_mp(m, M)
+    hzk, hD = b.factor()
+    b.close()
+    for i, M in enumerate(mats):
+        N = Ns[i]
+        st, ozk, OD, _ = oracle_lib.ge(M, N, p)
+        assert zk[i] == ozk == hzk[i], i
+        assert same(outs[i], OD), f"matrix {i} (N={N})"
+        assert same(b.minors_of(hD, i), OD), f"handle path, matrix {i} (N={N})"
+    assert zk[-2] == 2 and zk[-1] == 1
+
+
+def test_batch_set_mp_device_inputs(mpdet, oracle_lib):
+    """mpdet_batch_set_mp from device memory equals the lift of the same
+    matrices by mpdet_batch_set_i32 / _cauchy."""
+    import torch
+
+    p = 512
+    items = _mixed_items(W.rng(17), 9, 33)
+    b1 = make_batch(mpdet, items, p)
+    zk1, D1 = b1.factor()
+    b2 = mpdet.Batch(b1.Ns, p)
+    for m, (k, d) in enumerate(items):
+        M = oracle_lib.cauchy(*d, p) if k == "cauchy" else oracle_lib.from_int(np.asarray(d).reshape(-1), p)
+        b2.set_mp(m, (torch.from_numpy(M[0]).cuda(), torch.from_numpy(M[1]).cuda(),
+                      torch.from_numpy(np.ascontiguousarray(M[2]).view(np.int32)).cuda()))
+    zk2, D2 = b2.factor()
+    assert np.array_equal(zk1, zk2) and same(D1, D2)
+    b1.close()
+    b2.close()

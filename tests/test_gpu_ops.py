@@ -49,7 +49,7 @@ def first_bad(got, want):
     return None
 
 
-@pytest.mark.parametrize("p", [128, 256, 512, 1024, 2048, 4096, 32768])
+@pytest.mark.parametrize("p", [64, 96, 128, 160, 256, 512, 1024, 2048, 3072, 4096, 32768])
 def test_ops_vs_oracle(mpdet, oracle_lib, p):
     A, B = cases(p, 5000 + p)
     for op in ("mul", "sub", "add"):

@@ -1,7 +1,7 @@
 """GPU parity: the CUDA path through the C ABI must equal the CPU oracle bit
 for bit (integer limbs, exponents and signs), on seeded inputs that span
-several tiles, ragged tails, every kernel family (p = 128 .. 32768) and the
-degenerate cases of the method (zero pivots, N = 1, exact cancellations)."""
+several tiles, ragged tails, every kernel family (p = 128 .. 32768), precisions
+between the families (p = 64, 96, 160, 3072) and the degenerate cases of the method (zero pivots, N = 1, exact cancellations)."""
 import numpy as np
 import pytest
 
@@ -98,6 +98,58 @@ def test_parity_small(mpdet, oracle_lib, p, kind, lastcol):
         else:
             data = g.standard_normal((N, N))
         check_case(mpdet, oracle_lib, N, p, lastcol, kind, data)
+
+
+@pytest.mark.parametrize("p", [64, 96, 160, 3072])
+def test_parity_any_multiple_of_32(mpdet, oracle_lib, p):
+    """Precisions whose limb count is not a kernel family's (p = 64, 96, 160
+    and 3072 live in frames of 4, 4, 8 and 128 limbs with the low limbs zero)
+    round at p bits: every output equals the oracle's at p bits, in both
+    modes, on all three kinds of input (Cauchy entries RN(1/RN(x+y)) round
+    at p = 64 and 96 already)."""
+    g = W.rng(2000 + p)
+    for N, kind, lastcol in ((1, "f64", True), (2, "int", True), (3, "cauchy", False), (17, "cauchy", True),
+                             (40, "int", False), (33, "f64", True), (29, "cauchy", False), (24, "int", True)):
+        if kind == "cauchy":
+            data = W.cauchy_xy(N, int(g.integers(1 << 30)))
+        elif kind == "int":
+            data = W.int_matrix(N, int(g.integers(1 << 30)))
+        else:
+            data = g.standard_normal((N, N))
+        check_case(mpdet, oracle_lib, N, p, lastcol, kind, data)
+
+
+@pytest.mark.parametrize("p", [96, 3072])
+def test_any_multiple_of_32_series_adjoint_and_host_io(mpdet, oracle_lib, p):
+    """The same precisions through the series of minor arrays, the adjoint
+    and the device-buffer outputs (the frame's limbs are converted at the
+    boundary in every direction)."""
+    import torch
+
+    N = 12
+    A = W.rng(3000 + p).standard_normal((N, N))
+    h = mpdet.Mpdet(N, p, lastcol=True)
+    s, la, G = h.logabsdet_grad(A)
+    Xi = h.get_inverse()
+    ser = h.minor_series()
+    n = p // 32
+    dev = (torch.empty(N * (N + 1) // 2, dtype=torch.int8, device="cuda"),
+           torch.empty(N * (N + 1) // 2, dtype=torch.int64, device="cuda"),
+           torch.empty((N * (N + 1) // 2, n), dtype=torch.int32, device="cuda"))
+    h.minor_series(out=dev)
+    torch.cuda.synchronize()
+    ser_dev = (dev[0].cpu().numpy(), dev[1].cpu().numpy(), dev[2].cpu().numpy().view(np.uint32))
+    ent = h.get_entries(np.array([0, 5, N * N - 1]))
+    h.close()
+    st, zk, D, Xm = oracle_lib.ge(oracle_lib.from_f64(A.reshape(-1), p), N, p, lastcol=True)
+    assert st == 0
+    OX = oracle_lib.usolve(Xm, N, p)
+    assert_same(Xi, OX, "A^-1")
+    assert np.array_equal(G, oracle_lib.to_f64(OX, p).reshape(N, N).T)
+    OS = oracle_lib.minor_series(Xm, D, N, p)
+    assert_same(ser, OS, "series (host)")
+    assert_same(ser_dev, OS, "series (device)")
+    assert_same(ent, tuple(a[[0, 5, N * N - 1]] for a in Xm), "sampled entries")
 
 
 @pytest.mark.parametrize("p", [8192, 16384, 32768])

@@ -1,10 +1,10 @@
 """The allocation-free entry point (mpdet_factor_noalloc) against the regular
 one (mpdet_factor + mpdet_lastcol_minors).
 
-mpdet_factor_noalloc serves callers that cannot allocate device memory (code
-running under stream capture, frameworks that forbid a plugin its own
-allocations, latency-bound loops): it keeps its working memory in a static
-device array.  Its results must equal the regular path's bit for bit, also
+mpdet_factor_noalloc serves callers that cannot allocate device memory (host
+frameworks that own every buffer and forbid a plugin its own allocations,
+latency-bound loops that cannot take an allocation mid-step): it keeps its
+working memory in a static device array.  Its results must equal the regular path's bit for bit, also
 on a second call in a row, which finds the array holding the first call's
 contents.  This file is named to be collected last."""
 import numpy as np
