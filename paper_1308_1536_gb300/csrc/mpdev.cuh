@@ -243,7 +243,8 @@ __device__ __forceinline__ uint32_t round_frame(const Grp<G>& gp, uint32_t (&M)[
     }
     rl = gp.from(rl, (pad - 1) / W);
     kl = gp.from(kl, pad / W);
-    const bool stk = st || rbit != 0u || (rl & 0x7fffffffu) != 0u || gp.ballot(below) != 0u;
+    const bool low = gp.ballot(below) != 0u;  // every lane votes: not inside a short-circuit
+    const bool stk = st || rbit != 0u || (rl & 0x7fffffffu) != 0u || low;
     inc = (rl >> 31) & ((stk ? 1u : 0u) | (kl & 1u));
     // the increment enters at limb 0 and runs through the dropped limbs
     // (set to all ones) into limb pad
