@@ -33,6 +33,11 @@ Functions and the passages they follow:
   log|det| (d log|det| / dA = A^-T; all minors are partial derivatives of
   the determinant, Sec. 3), by right-looking back substitution.
 * ``to_f64``: round numbers to binary64 (nearest even, subnormals).
+* ``cauchy_ball, ge_ball, lastcol_ball``: the same values, each with a
+  rigorous radius (|exact - value| <= radius; midpoint-radius intervals, the
+  rigorous bounds the paper leaves to future work, Sec. 4.4).  Radii are
+  pairs (m uint32, e int64) meaning m * 2^(e - 32), rounded up; e = RAD_INF
+  marks an unbounded radius.  ``rad_op`` exposes their arithmetic.
 """
 from __future__ import annotations
 
@@ -87,8 +92,14 @@ def _load():
             lib.or_lastcol.argtypes = [i64, i32, i32, P, P, P, ctypes.c_int8, i64, P, P, P, P]
             lib.or_usolve.argtypes = [i64, i32, i32, P, P, P, P, P, P]
             lib.or_to_f64_v.argtypes = [i64, i32, P, P, P, P]
+            lib.or_rad_op.argtypes = [i32, ctypes.c_uint32, i64, ctypes.c_uint32, i64, P, P, P]
+            lib.or_cauchy_ball.argtypes = [i64, i32, P, P, P, P, P, P, P]
+            lib.or_ge_ball.argtypes = [i64, i32, i32, P, P, P, P, P, P, P, P, P, P, P]
+            lib.or_lastcol_ball.argtypes = [i64, i32, i32, P, P, P, P, P, ctypes.c_int8, i64, P, ctypes.c_uint32, i64,
+                                            P, P, P, P, P]
             for f in ("or_mul_v", "or_add_v", "or_recip_v", "or_from_f64_v", "or_from_i64_v", "or_cauchy",
-                      "or_ge_range", "or_ge_range_div", "or_div_v", "or_lastcol", "or_usolve", "or_to_f64_v"):
+                      "or_ge_range", "or_ge_range_div", "or_div_v", "or_lastcol", "or_usolve", "or_to_f64_v",
+                      "or_rad_op", "or_cauchy_ball", "or_ge_ball", "or_lastcol_ball"):
                 getattr(lib, f).restype = i32
             _lib = lib
     return _lib
@@ -278,3 +289,71 @@ def logabsdet(D, N: int, p: int):
         return 0.0, float("-inf")
     top = int(m[-1]) * 2.0 ** -32 + int(m[-2]) * 2.0 ** -64  # m / 2^p in [1/2, 1)
     return (-1.0 if int(s) else 1.0), math.log(top) + float(int(e)) * math.log(2.0)
+
+
+# ---------------------------------------------------------------------------
+# ball mode (values with rigorous radii)
+# ---------------------------------------------------------------------------
+RAD_INF = np.iinfo(np.int64).max
+
+
+def rad_zeros(count: int):
+    return np.zeros(count, np.uint32), np.full(count, ZEXP, np.int64)
+
+
+def rad_op(op: int, a, b):
+    """Radius arithmetic: op 0 a+b up, 1 a*b up, 2 a*b down, 3 a/b up,
+    4 a-b down.  a, b: (m, e) pairs.  Returns ((m, e), positive)."""
+    om, oe, pos = ctypes.c_uint32(), ctypes.c_int64(), ctypes.c_int()
+    _check(_load().or_rad_op(int(op), int(a[0]), int(a[1]), int(b[0]), int(b[1]), ctypes.byref(om),
+                             ctypes.byref(oe), ctypes.byref(pos)), "rad_op")
+    return (int(om.value), int(oe.value)), bool(pos.value)
+
+
+def cauchy_ball(x, y, p: int):
+    """cauchy() with the radius of every entry (x, y exact)."""
+    x = np.ascontiguousarray(x, np.float64)
+    y = np.ascontiguousarray(y, np.float64)
+    N = x.shape[0]
+    o = empty(N * N, p)
+    r = rad_zeros(N * N)
+    _check(_load().or_cauchy_ball(N, p, _ptr(x), _ptr(y), *map(_ptr, o), *map(_ptr, r)), "cauchy_ball")
+    return o, r
+
+
+def ge_ball(A, RA, N: int, p: int, lastcol: bool = False):
+    """ge() over all steps with radii: RA are the input's radii (None:
+    exact input).  Returns (status, zero_k, D, X, RD, RX); the values D, X
+    are bit-identical to ge()'s."""
+    S, E, M = (np.array(t, copy=True) for t in _norm(A, p))
+    RXm, RXe = (rad_zeros(N * N) if RA is None else (np.array(RA[0], np.uint32, copy=True),
+                                                        np.array(RA[1], np.int64, copy=True)))
+    D = empty(N, p)
+    RD = rad_zeros(N)
+    zk = np.zeros(1, np.int64)
+    st = _load().or_ge_ball(N, p, int(lastcol), _ptr(S), _ptr(E), _ptr(M), _ptr(RXm), _ptr(RXe), *map(_ptr, D),
+                            *map(_ptr, RD), _ptr(zk))
+    if st not in (OK, EZEROPIVOT):
+        raise RuntimeError(f"oracle ge_ball failed with status {st}")
+    return st, int(zk[0]), D, (S, E, M), RD, (RXm, RXe)
+
+
+def lastcol_ball(X, RX, D, RD, N: int, p: int, normalised: bool = False):
+    """lastcol_minors() with radii (from a lastcol-mode ge_ball)."""
+    S, E, M = _norm(X, p)
+    Ds, De, Dm = _norm(D, p)
+    if N >= 2:
+        ds, de, dm = Ds[N - 2], De[N - 2], np.ascontiguousarray(Dm[N - 2])
+        rdm, rde = int(RD[0][N - 2]), int(RD[1][N - 2])
+    else:
+        ds, de = 0, 1
+        dm = np.zeros(p // 32, np.uint32)
+        dm[-1] = 0x80000000
+        rdm, rde = 0, ZEXP
+    o = empty(N, p)
+    r = rad_zeros(N)
+    RXm = np.ascontiguousarray(RX[0], np.uint32)
+    RXe = np.ascontiguousarray(RX[1], np.int64)
+    _check(_load().or_lastcol_ball(N, p, int(normalised), _ptr(S), _ptr(E), _ptr(M), _ptr(RXm), _ptr(RXe), int(ds),
+                                   int(de), _ptr(dm), rdm, rde, *map(_ptr, o), *map(_ptr, r)), "lastcol_ball")
+    return o, r

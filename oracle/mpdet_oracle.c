@@ -792,3 +792,321 @@ int or_to_f64_v(int64_t cnt, int p, const int8_t *S, const int64_t *E, const uin
   for (int64_t i = 0; i < cnt; ++i) out[i] = to_f64_one(p, n, S[i], E[i], M + i * n);
   return OR_OK;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Ball mode: rigorous error bounds beside the method's values.              */
+/*                                                                           */
+/* The paper leaves rigorous bounds as future work (Sec. 4.4): interval      */
+/* arithmetic gives upper and lower bounds at every operation.  Here every   */
+/* number x~ of the elimination (computed exactly as above, round to nearest) */
+/* carries a radius rho with |x* - x~| <= rho, where x* is the value exact    */
+/* arithmetic would give at the same place of the elimination of the exact   */
+/* input (midpoint-radius intervals).  Radii are small numbers              */
+/*   rho = m * 2^(e - 32),  m in [2^31, 2^32) (or m = 0: rho = 0),           */
+/* every radius operation rounds up (down where a lower bound is needed), in  */
+/* integer arithmetic only.  e = RAD_INF marks an unbounded radius.          */
+/* Rules (u~ = RN(result); hu = half an ulp of u~ at p bits, 2^(e_u - p - 1), */
+/* 0 when u~ = 0; |x~|^ and |x~|_ are upper and lower bounds of |x~| from its */
+/* top limb):                                                                 */
+/*   u~ = RN(x~ y~):  rho_u = ((hu + |x~|^ rho_y) + |y~|^ rho_x) + rho_x rho_y  */
+/*   u~ = RN(x~ - t~): rho_u = (hu + rho_x) + rho_t                           */
+/*   u~ = RN(1/a~):  rho_u = hu + rho_a / (|a~|_ (|a~|_ - rho_a)),            */
+/*                   unbounded unless |a~|_ > rho_a                          */
+/*   negation and copies keep the radius.                                    */
+/* Exact inputs (lifted doubles and integers) have radius 0.                 */
+/* ------------------------------------------------------------------------- */
+#define RAD_INF INT64_MAX
+
+typedef struct {
+  uint32_t m;
+  int64_t e;
+} rad_t;
+
+static const rad_t RAD_ZERO = {0, ZEXP};
+static const rad_t RAD_UNB = {0xffffffffu, RAD_INF};
+
+static int rad_is_zero(rad_t a) { return a.m == 0; }
+static int rad_is_inf(rad_t a) { return a.e == RAD_INF; }
+
+/* the smallest radius >= V * 2^E (up != 0) or the largest <= V * 2^E */
+static rad_t rad_from64(uint64_t V, int64_t E, int up) {
+  if (!V) return RAD_ZERO;
+  int t = 64 - __builtin_clzll(V);
+  uint64_t m;
+  if (t <= 32) m = V << (32 - t);
+  else {
+    m = V >> (t - 32);
+    if (up && (V & ((1ull << (t - 32)) - 1))) m += 1;
+    if (m >> 32) { /* rounded up to 2^32 */
+      m >>= 1;
+      t += 1;
+    }
+  }
+  rad_t r = {(uint32_t)m, E + t};
+  return r;
+}
+
+/* b at the scale 2^(ea - 63) (a's), rounded up; d = ea - eb >= 0 */
+static uint64_t rad_align_up(rad_t b, int64_t d) {
+  if (d <= 31) return (uint64_t)b.m << (31 - d);
+  int64_t sh = d - 31;
+  if (sh >= 32) return 1; /* 0 < b < one unit of that scale */
+  uint64_t v = (uint64_t)b.m >> sh;
+  if ((uint64_t)b.m & ((1ull << sh) - 1)) v += 1;
+  return v;
+}
+
+static rad_t rad_add(rad_t a, rad_t b) {
+  if (rad_is_inf(a) || rad_is_inf(b)) return RAD_UNB;
+  if (rad_is_zero(a)) return b;
+  if (rad_is_zero(b)) return a;
+  if (b.e > a.e) {
+    rad_t t = a;
+    a = b;
+    b = t;
+  }
+  uint64_t A = (uint64_t)a.m << 31;
+  return rad_from64(A + rad_align_up(b, a.e - b.e), a.e - 63, 1);
+}
+
+static rad_t rad_mul(rad_t a, rad_t b, int up) {
+  if (rad_is_zero(a) || rad_is_zero(b)) return RAD_ZERO;
+  if (rad_is_inf(a) || rad_is_inf(b)) return RAD_UNB;
+  return rad_from64((uint64_t)a.m * b.m, a.e + b.e - 64, up);
+}
+
+/* a / b rounded up (b > 0 finite) */
+static rad_t rad_div_up(rad_t a, rad_t b) {
+  if (rad_is_zero(a)) return RAD_ZERO;
+  if (rad_is_inf(a)) return RAD_UNB;
+  uint64_t num = (uint64_t)a.m << 32;
+  uint64_t q = num / b.m;
+  if (q * b.m != num) q += 1;
+  return rad_from64(q, a.e - b.e - 32, 1);
+}
+
+/* a - b rounded down; *pos = 0 when a - b <= 0 */
+static rad_t rad_sub_down(rad_t a, rad_t b, int *pos) {
+  *pos = 0;
+  if (rad_is_inf(b) || rad_is_zero(a)) return RAD_ZERO;
+  if (rad_is_zero(b)) {
+    *pos = 1;
+    return a;
+  }
+  if (b.e > a.e) return RAD_ZERO;
+  uint64_t A = (uint64_t)a.m << 31, B = rad_align_up(b, a.e - b.e);
+  if (B >= A) return RAD_ZERO;
+  *pos = 1;
+  return rad_from64(A - B, a.e - 63, 0);
+}
+
+/* bounds of |x| for a p-bit number from its top limb */
+static rad_t rad_mag(int64_t e, const uint32_t *m, int n, int up) {
+  if (iszero(e)) return RAD_ZERO;
+  uint64_t top = m[n - 1];
+  if (up) {
+    int rest = 0;
+    for (int i = 0; i < n - 1; ++i) rest |= m[i] != 0;
+    top += (uint64_t)rest;
+  }
+  return rad_from64(top, e - 32, up);
+}
+
+/* half an ulp of a p-bit result with exponent e (0 for a zero result) */
+static rad_t rad_hu(int64_t e, int p) {
+  if (iszero(e)) return RAD_ZERO;
+  rad_t r = {0x80000000u, e - p};
+  return r;
+}
+
+static rad_t ball_mul(int p, int n, int64_t eu, int64_t ex, const uint32_t *mx, rad_t rx, int64_t ey,
+                      const uint32_t *my, rad_t ry) {
+  rad_t r = rad_add(rad_hu(eu, p), rad_mul(rad_mag(ex, mx, n, 1), ry, 1));
+  r = rad_add(r, rad_mul(rad_mag(ey, my, n, 1), rx, 1));
+  return rad_add(r, rad_mul(rx, ry, 1));
+}
+
+static rad_t ball_sub(int p, int64_t eu, rad_t rx, rad_t rt) { return rad_add(rad_add(rad_hu(eu, p), rx), rt); }
+
+static rad_t ball_recip(int p, int n, int64_t eu, int64_t ea, const uint32_t *ma, rad_t ra) {
+  rad_t lo = rad_mag(ea, ma, n, 0);
+  int pos = 0;
+  rad_t gap = rad_sub_down(lo, ra, &pos);
+  if (!pos) return RAD_UNB;
+  return rad_add(rad_hu(eu, p), rad_div_up(ra, rad_mul(lo, gap, 0)));
+}
+
+/* Radius arithmetic on its own (tests of the rounding directions):
+ * op 0: a + b up, 1: a * b up, 2: a * b down, 3: a / b up, 4: a - b down
+ * (*pos receives 0 when a - b <= 0). */
+int or_rad_op(int op, uint32_t am, int64_t ae, uint32_t bm, int64_t be, uint32_t *om, int64_t *oe, int *pos) {
+  rad_t a = {am, ae}, b = {bm, be}, r = RAD_ZERO;
+  int ps = 1;
+  switch (op) {
+    case 0: r = rad_add(a, b); break;
+    case 1: r = rad_mul(a, b, 1); break;
+    case 2: r = rad_mul(a, b, 0); break;
+    case 3: r = rad_div_up(a, b); break;
+    case 4: r = rad_sub_down(a, b, &ps); break;
+    default: return OR_EINVAL;
+  }
+  *om = r.m;
+  *oe = r.e;
+  if (pos) *pos = ps;
+  return OR_OK;
+}
+
+/* Cauchy entries with radii: s = RN(x_i + y_j) (x, y exact), a = RN(1/s). */
+int or_cauchy_ball(int64_t N, int p, const double *x, const double *y, int8_t *so, int64_t *eo, uint32_t *mo,
+                   uint32_t *rm, int64_t *re) {
+  ctx_t c;
+  int st = ctx_init(&c, p);
+  if (st) return st;
+  int n = c.n;
+  uint32_t *tm = (uint32_t *)calloc((size_t)3 * n, sizeof(uint32_t));
+  uint32_t *xm = tm + n, *ym = tm + 2 * n;
+  for (int64_t i = 0; i < N && st == OR_OK; ++i)
+    for (int64_t j = 0; j < N; ++j) {
+      int8_t xs, ys, ts;
+      int64_t xe, ye, te, idx = i * N + j;
+      op_from_f64(&c, x[i], &xs, &xe, xm);
+      op_from_f64(&c, y[j], &ys, &ye, ym);
+      op_add(&c, xs, xe, xm, ys, ye, ym, 0, &ts, &te, tm);
+      rad_t rs = ball_sub(p, te, RAD_ZERO, RAD_ZERO);
+      st = op_recip(&c, ts, te, tm, so + idx, eo + idx, mo + idx * n);
+      if (st) break;
+      rad_t ra = ball_recip(p, n, eo[idx], te, tm, rs);
+      rm[idx] = ra.m;
+      re[idx] = ra.e;
+    }
+  free(tm);
+  free(c.buf);
+  return st;
+}
+
+/* The elimination of ge_range (one thread, all N steps) with radii: the
+ * values are the same operations in the same order; RX (N*N radii, in/out)
+ * holds the input's radii on entry, RD (N) receives those of D_1..D_N. */
+int or_ge_ball(int64_t N, int p, int lastcol, int8_t *S, int64_t *E, uint32_t *M, uint32_t *RXm, int64_t *RXe,
+               int8_t *Ds, int64_t *De, uint32_t *Dm, uint32_t *RDm, int64_t *RDe, int64_t *zero_k) {
+  ctx_t c;
+  int st = ctx_init(&c, p);
+  if (st) return st;
+  if (N < 1) {
+    free(c.buf);
+    return OR_EINVAL;
+  }
+  int n = c.n;
+  uint32_t *r = (uint32_t *)calloc(n, sizeof(uint32_t));
+  uint32_t *one = (uint32_t *)calloc(n, sizeof(uint32_t));
+  uint32_t *t = (uint32_t *)calloc(n, sizeof(uint32_t));
+  uint32_t *zm = (uint32_t *)calloc((size_t)N * n, sizeof(uint32_t));
+  int8_t *zs = (int8_t *)calloc(N, 1);
+  int64_t *ze = (int64_t *)calloc(N, sizeof(int64_t));
+  rad_t *zr = (rad_t *)calloc(N, sizeof(rad_t));
+  one[n - 1] = 0x80000000u;
+  if (zero_k) *zero_k = 0;
+#define RX(ij) ((rad_t){RXm[ij], RXe[ij]})
+  rad_t rprev = RAD_ZERO; /* radius of D_{k-1}; D_0 = 1 exactly */
+  for (int64_t k = 0; k < N; ++k) {
+    int64_t kk = k * N + k;
+    if (k == 0) op_mul(&c, 0, 1, one, S[kk], E[kk], M + kk * n, Ds, De, Dm);
+    else op_mul(&c, Ds[k - 1], De[k - 1], Dm + (k - 1) * n, S[kk], E[kk], M + kk * n, Ds + k, De + k, Dm + k * n);
+    rad_t rd = (k == 0) ? ball_mul(p, n, De[k], 1, one, RAD_ZERO, E[kk], M + kk * n, RX(kk))
+                        : ball_mul(p, n, De[k], De[k - 1], Dm + (k - 1) * n, rprev, E[kk], M + kk * n, RX(kk));
+    RDm[k] = rd.m;
+    RDe[k] = rd.e;
+    rprev = rd;
+    if (iszero(E[kk])) {
+      if (zero_k) *zero_k = k + 1;
+      for (int64_t q = k; q < N; ++q) {
+        setzero(Ds + q, De + q, Dm + q * n, n);
+        RDm[q] = 0;
+        RDe[q] = ZEXP;
+      }
+      if (k < N - 1) st = OR_EZEROPIVOT;
+      break;
+    }
+    if (k == N - 1) break;
+    int8_t rs;
+    int64_t re;
+    op_recip(&c, S[kk], E[kk], M + kk * n, &rs, &re, r);
+    rad_t rr = ball_recip(p, n, re, E[kk], M + kk * n, RX(kk));
+    for (int64_t i = k + 1; i < N; ++i) {
+      int64_t ik = i * N + k;
+      op_mul(&c, S[ik], E[ik], M + ik * n, rs, re, r, zs + i, ze + i, zm + i * n);
+      zr[i] = ball_mul(p, n, ze[i], E[ik], M + ik * n, RX(ik), re, r, rr);
+    }
+    for (int64_t i = k + 1; i < N; ++i) {
+      for (int64_t j = lastcol ? 0 : k + 1; j < N; ++j) {
+        if (j == k) continue;
+        int64_t ij = i * N + j, kj = k * N + j;
+        int8_t ts;
+        int64_t te;
+        op_mul(&c, zs[i], ze[i], zm + i * n, S[kj], E[kj], M + kj * n, &ts, &te, t);
+        rad_t rt = ball_mul(p, n, te, ze[i], zm + i * n, zr[i], E[kj], M + kj * n, RX(kj));
+        rad_t rx = RX(ij);
+        op_add(&c, S[ij], E[ij], M + ij * n, ts, te, t, 1, S + ij, E + ij, M + ij * n);
+        rad_t ru = ball_sub(p, E[ij], rx, rt);
+        RXm[ij] = ru.m;
+        RXe[ij] = ru.e;
+      }
+      if (lastcol) {
+        int64_t ik = i * N + k;
+        copynum(iszero(ze[i]) ? 0 : (int8_t)(zs[i] ^ 1), ze[i], zm + i * n, n, S + ik, E + ik, M + ik * n);
+        RXm[ik] = zr[i].m;
+        RXe[ik] = zr[i].e;
+      }
+    }
+  }
+#undef RX
+  free(zr);
+  free(ze);
+  free(zs);
+  free(zm);
+  free(t);
+  free(one);
+  free(r);
+  free(c.buf);
+  return st;
+}
+
+/* Last-column minors (as or_lastcol) with radii: C_jN = RN(D_{N-1} l_Nj),
+ * C_NN = D_{N-1}; normalised: delta_j = RN(l_Nj * RN(1/l_N1)), delta_1 = 1
+ * (radius 0), delta_N = RN(1/l_N1).  rdm/rde: radius of D_{N-1}; RXm/RXe:
+ * the radii of the eliminated array. */
+int or_lastcol_ball(int64_t N, int p, int normalised, const int8_t *S, const int64_t *E, const uint32_t *M,
+                    const uint32_t *RXm, const int64_t *RXe, int8_t dsg, int64_t dex, const uint32_t *dm, uint32_t rdm,
+                    int64_t rde, int8_t *os, int64_t *oe, uint32_t *om, uint32_t *rm, int64_t *re) {
+  int st = or_lastcol(N, p, normalised, S, E, M, dsg, dex, dm, os, oe, om);
+  if (st) return st;
+  int n = p / 32;
+  const int64_t row = (N - 1) * N;
+  rad_t rD = {rdm, rde};
+  if (!normalised) {
+    for (int64_t j = 0; j + 1 < N; ++j) {
+      rad_t rl = {RXm[row + j], RXe[row + j]};
+      rad_t r = ball_mul(p, n, oe[j], dex, dm, rD, E[row + j], M + (row + j) * n, rl);
+      rm[j] = r.m;
+      re[j] = r.e;
+    }
+    rm[N - 1] = rdm;
+    re[N - 1] = rde;
+  } else {
+    rm[0] = 0;
+    re[0] = ZEXP;
+    if (N > 1) {
+      rad_t rl1 = {RXm[row], RXe[row]};
+      rad_t rr = ball_recip(p, n, oe[N - 1], E[row], M + row * n, rl1);
+      for (int64_t j = 1; j + 1 < N; ++j) {
+        rad_t rl = {RXm[row + j], RXe[row + j]};
+        rad_t r = ball_mul(p, n, oe[j], E[row + j], M + (row + j) * n, rl, oe[N - 1], om + (N - 1) * n, rr);
+        rm[j] = r.m;
+        re[j] = r.e;
+      }
+      rm[N - 1] = rr.m;
+      re[N - 1] = rr.e;
+    }
+  }
+  return OR_OK;
+}

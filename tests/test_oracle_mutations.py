@@ -50,6 +50,18 @@ MUTATIONS = [
      "op_mul(&c, XS[kc], XE[kc], XM + kc * n, rs, re, r, XS + kc, XE + kc, XM + kc * n);",
      "op_div(&c, XS[kc], XE[kc], XM + kc * n, S[kk], E[kk], M + kk * n, XS + kc, XE + kc, XM + kc * n);",
      ["test_oracle_adjoint.py::test_usolve_brute_force_op_sequence"]),
+    ("ball subtraction forgets its own rounding error",
+     "static rad_t ball_sub(int p, int64_t eu, rad_t rx, rad_t rt) { return rad_add(rad_add(rad_hu(eu, p), rx), rt); }",
+     "static rad_t ball_sub(int p, int64_t eu, rad_t rx, rad_t rt) { return rad_add(rx, rt); }",
+     ["test_oracle_ball.py::test_ball_brute_force_radius_sequence"]),
+    ("ball product drops the radius-times-radius term", "  return rad_add(r, rad_mul(rx, ry, 1));\n}",
+     "  return r;\n}", ["test_oracle_ball.py::test_ball_brute_force_radius_sequence"]),
+    ("ball product bounds |x| from below", "rad_t r = rad_add(rad_hu(eu, p), rad_mul(rad_mag(ex, mx, n, 1), ry, 1));",
+     "rad_t r = rad_add(rad_hu(eu, p), rad_mul(rad_mag(ex, mx, n, 0), ry, 1));",
+     ["test_oracle_ball.py::test_ball_brute_force_radius_sequence"]),
+    ("radius sum rounds down", "  return rad_from64(A + rad_align_up(b, a.e - b.e), a.e - 63, 1);",
+     "  return rad_from64(A + rad_align_up(b, a.e - b.e), a.e - 63, 0);",
+     ["test_oracle_ball.py::test_radius_arithmetic_rounds_as_defined"]),
 ]
 
 
