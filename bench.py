@@ -162,7 +162,7 @@ def recorded_traffic(products_per_launch: float):
 # ---------------------------------------------------------------------------
 # CPU oracle on a bounded sample (cpu_baseline and --impl reference)
 # ---------------------------------------------------------------------------
-def oracle_sample(K: int = ORACLE_SAMPLE_K):
+def oracle_sample(K: int = ORACLE_SAMPLE_K, threads: int = 0):
     import oracle
 
     oracle.build()
@@ -170,7 +170,7 @@ def oracle_sample(K: int = ORACLE_SAMPLE_K):
     N, p = cfg["N"], cfg["p"]
     x, y = W.cauchy_xy(N, cfg["seed"])
     A = W.int_matrix(N, cfg["seed"] + 100)
-    threads = os.cpu_count() or 1
+    threads = threads or os.cpu_count() or 1
     t0 = time.perf_counter()
     for kind in ("cauchy", "int"):
         M = oracle.cauchy(x[:K], y[:K], p) if kind == "cauchy" else oracle.from_int(A[:K, :K].reshape(-1), p)
@@ -336,6 +336,40 @@ def bench_adjoint(args, dev, m):
             "grad_calls_per_s": 1.0 / t_grad, "ms_per_call": t_grad * 1e3,
             "limb_macs_per_s": prods * n * n / t_grad,
             "plain_det_calls_per_s": 1.0 / t_plain, "grad_cost_vs_plain_det": t_grad / t_plain}
+
+
+def bench_karatsuba(args, dev, m, peak_macs):
+    """Schoolbook against one Karatsuba level on the IMAD engine's lane layout
+    (mpdet_mulbench): RN(a*b) of many pairs at p = 8192, 16384, 32768, each
+    product formed 8 times on operands held on chip, enough pairs to fill
+    every SM.  Work is counted as n^2 limb-MACs per product for both (the
+    schoolbook's), so the ratio of the rates is the speed-up."""
+    import torch
+
+    out = {}
+    g = np.random.Generator(np.random.PCG64(1308))
+    for p in (8192, 16384, 32768):
+        n = p // 32
+        G = 16 if n == 256 else 32
+        count = torch.cuda.get_device_properties(dev).multi_processor_count * (128 // G) * 6
+        a = (np.zeros(count, np.int8), g.integers(-50, 50, count).astype(np.int64),
+             g.integers(0, 2 ** 32, (count, n), dtype=np.uint64).astype(np.uint32))
+        b = (np.ones(count, np.int8), g.integers(-50, 50, count).astype(np.int64),
+             g.integers(0, 2 ** 32, (count, n), dtype=np.uint64).astype(np.uint32))
+        a[2][:, -1] |= 0x80000000
+        b[2][:, -1] |= 0x80000000
+        res = {}
+        for meth in ("school", "kara"):
+            m.mulbench(meth, a, b, p, reps=2)  # warm-up
+            prods, ms = m.mulbench(meth, a, b, p, reps=8)
+            res[meth] = (prods, ms)
+        same = all(np.array_equal(x, y) for x, y in zip(res["school"][0], res["kara"][0]))
+        macs = float(count) * 8 * n * n
+        out[str(p)] = {"pairs": int(count), "school_ms": res["school"][1], "kara_ms": res["kara"][1],
+                       "school_limb_macs_per_s": macs / (res["school"][1] / 1e3),
+                       "kara_limb_macs_per_s": macs / (res["kara"][1] / 1e3),
+                       "kara_speedup": res["school"][1] / res["kara"][1], "same_bits": bool(same)}
+    return out
 
 
 def cauchy_bit_loss(x, y, D, p: int, every: int = 64):
@@ -582,6 +616,88 @@ def bench_large(args, dev, m, peak_macs):
             "projected_full_factorisation_s": proj_s,
             "projected_full_limb_macs_per_s": total / proj_s,
             "projected_full_frac_of_imad_peak": total / proj_s / peak_macs}
+
+
+def run_large_full(args):
+    """One complete factorisation of workload C5 (Cauchy N = 4096, p = 32768,
+    68.9 GB in HBM): every step, in windows of --window steps timed with CUDA
+    events on the handle's stream, nvidia-smi clocks sampled per window.  The
+    leading minors D_1..D_N are saved (numpy .npz) for the checks that run
+    on the host afterwards: D_1..D_256 against the stored oracle digests and
+    every D_k against the closed-form Cauchy determinant.  Prints one JSON
+    line with the whole-run time and its fraction of the IMAD peak."""
+    import torch
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    import paper_1308_1536_gb300 as m
+
+    m.load()
+    cfg = W.C5
+    N, p = cfg["N"], cfg["p"]
+    n = p // 32
+    x, y = W.cauchy_xy(N, cfg["seed"])
+    if args.large_n:  # the leading large_n x large_n block of the same matrix
+        N = args.large_n
+        x, y = x[:N], y[:N]
+    st = torch.cuda.current_stream(dev)
+    h = m.Mpdet(N, p, lastcol=False, stream=st.cuda_stream)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    h.set_cauchy(x, y)
+    torch.cuda.synchronize(dev)
+    t_gen = time.perf_counter() - t0
+    props = torch.cuda.get_device_properties(dev)
+    windows = []
+    total_ms = 0.0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    h.profile(True)
+    upd_ms = upd_macs = 0.0
+    t_wall = time.perf_counter()
+    for k0 in range(0, N, args.window):
+        k1 = min(N, k0 + args.window)
+        with Clocks(0) as clk:
+            e0.record(st)
+            h.factor_range(k0, k1)
+            e1.record(st)
+            torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        pr = h.profile_read()
+        upd_ms += pr["update_ms"]
+        upd_macs += pr["update_limb_macs"]
+        h.profile(True)
+        total_ms += ms
+        prods = sum((N - k - 1) ** 2 + (N - k - 1) + 1 for k in range(k0, k1))
+        c = clk.summary()
+        windows.append({"steps": [k0 + 1, k1], "ms": round(ms, 3), "limb_macs_per_s": prods * n * n / (ms / 1e3),
+                        "sm_mhz": c.get("sm_mhz"), "reasons": c.get("reasons")})
+        print(json.dumps({"window": windows[-1]}), file=sys.stderr, flush=True)
+    wall = time.perf_counter() - t_wall
+    rc, zk = h.status()
+    D = h.get_minors()
+    h.close()
+    os.makedirs(os.path.dirname(os.path.abspath(args.save)), exist_ok=True)
+    np.savez(args.save, sign=D[0], exp=D[1], limbs=D[2])
+    fmax = max((w["sm_mhz"] or 0) for w in windows) or 2070.0
+    smax = 2070.0
+    peak = props.multi_processor_count * 32 * smax * 1e6
+    total = elim_products(N, False) * n * n
+    reasons = sorted({r for w in windows for r in (w["reasons"] or [])})
+    out = {"metric": METRIC, "workload": f"Cauchy N={N} p={p} ({N * N * (4 * n + 9) / 1e9:.1f} GB in HBM), det + {N} "
+                                         "leading minors: the whole factorisation"
+                                         + (f" of the leading {N} x {N} block of the N = {cfg['N']} matrix"
+                                            if N != cfg["N"] else ""), "status": rc, "zero_k": zk,
+           "device_ms": total_ms, "wall_s": wall, "cauchy_generation_s": t_gen,
+           "limb_macs": total, "limb_macs_per_s": total / (total_ms / 1e3),
+           "frac_of_imad_peak": total / (total_ms / 1e3) / peak,
+           "peak_basis": f"{props.multi_processor_count} SMs x 32 limb-MAC/clk x {smax:.0f} MHz",
+           "update_kernel": {"ms": upd_ms, "limb_macs_per_s": upd_macs / (upd_ms / 1e3),
+                             "frac": upd_macs / (upd_ms / 1e3) / peak},
+           "window_steps": args.window, "windows": windows, "clock_reasons_seen": reasons,
+           "sm_mhz_median_of_windows": statistics.median([w["sm_mhz"] for w in windows if w["sm_mhz"]] or [0]),
+           "saved": args.save}
+    print(json.dumps(out))
+    return 0 if rc == 0 else 1
 
 
 def bench_hostmem(args, dev, m, peak_macs):
@@ -835,6 +951,8 @@ def run_gpu(args):
             out["batch"] = batch
         if want("adjoint"):
             out["adjoint"] = guarded(bench_adjoint, args, dev, m)
+        if want("karatsuba"):
+            out["karatsuba"] = guarded(bench_karatsuba, args, dev, m, peak)
         if want("large"):
             out["large"] = guarded(bench_large, args, dev, m, peak)
         if want("hostmem"):
@@ -842,6 +960,11 @@ def run_gpu(args):
         if world == 1 and not args.no_cpu_baseline:
             cb = guarded(oracle_sample)
             cb.pop("seconds", None)
+            # the same oracle on one thread, on a smaller sample (the work per
+            # second is the comparable figure)
+            one = guarded(oracle_sample, ORACLE_SAMPLE_K // 2, 1)
+            one.pop("seconds", None)
+            cb["one_thread"] = one
             out["cpu_baseline"] = cb
         print(json.dumps(out))
     hc.close()
@@ -862,16 +985,25 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the accuracy, batch, adjoint and large workloads")
     ap.add_argument("--extras", default="all",
-                    help="comma list of accuracy,batch,adjoint,large,hostmem (default all)")
+                    help="comma list of accuracy,batch,adjoint,karatsuba,large,hostmem (default all)")
     ap.add_argument("--batch-count", type=int, default=0,
                     help="profiling aid: matrices in the batch workload (default: the workload's 4096)")
     ap.add_argument("--N", type=int, default=0, help="profiling aid: override N (default: the workload's 1024)")
     ap.add_argument("--p", type=int, default=0, help="profiling aid: override p (default: the workload's 2048)")
     ap.add_argument("--update-variant", type=int, default=-1, help="tuning aid: Schur-update register budget 0..3")
     ap.add_argument("--engine", type=int, default=-1, help="tuning aid: 0 IMAD, 1 tensor pipelined, 2 tensor serial")
+    ap.add_argument("--large-full", action="store_true",
+                    help="the whole N=4096 p=32768 factorisation in timed windows (about an hour); not the bench line")
+    ap.add_argument("--window", type=int, default=64, help="--large-full: steps per timed window")
+    ap.add_argument("--large-n", type=int, default=0,
+                    help="--large-full: factor the leading N x N block of the N=4096 matrix instead (its steps cost "
+                         "what the full run's last N steps cost; its minors are the full run's D_1..D_N)")
+    ap.add_argument("--save", default="gpurun_out/c5_minors.npz", help="--large-full: where the leading minors go")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.large_full:
+        return run_large_full(args)
     return run_gpu(args)
 
 

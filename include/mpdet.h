@@ -72,7 +72,7 @@ enum {
   MPDET_ENOSCRATCH = 8   /* problem larger than mpdet_factor_noalloc's static working memory */
 };
 
-enum { MPDET_LASTCOL = 1, MPDET_HOSTMEM = 2 };
+enum { MPDET_LASTCOL = 1, MPDET_HOSTMEM = 2, MPDET_BALL = 4 };
 
 /* Create a handle for N x N matrices at p bits on the current CUDA device.
  * p must be a multiple of 32 with 64 <= p <= 32768 (n = p/32 limbs).  The
@@ -98,6 +98,26 @@ enum { MPDET_LASTCOL = 1, MPDET_HOSTMEM = 2 };
  * Errors: MPDET_EINVAL (N < 1, unsupported p, unknown flag, out == NULL),
  * MPDET_ENOMEM, MPDET_ECUDA. */
 int mpdet_create(int64_t N, int32_t p_bits, uint32_t flags, void* cuda_stream, mpdet_t* out);
+
+/* MPDET_BALL (may be combined with the other flags): ball mode, the rigorous
+ * error bounds the paper leaves to future work (Sec. 4.4: interval
+ * arithmetic, upper and lower bounds at every operation).  Every value of the
+ * elimination is computed exactly as without the flag (the same bits) and
+ * carries a radius rho with |x* - x~| <= rho, x* being the value exact
+ * arithmetic gives at the same place of the elimination of the exact input.
+ * A radius is m * 2^(e - 32) with m in [2^31, 2^32), or 0 (m = 0, e =
+ * INT64_MIN), or unbounded (e = INT64_MAX: a pivot's ball held zero, or the
+ * elimination stopped before that minor); radii are rounded up in integer
+ * arithmetic by three rules (u~ the rounded result, hu = 2^(e_u - p - 1) half
+ * its ulp, |x~|^ and |x~|_ bounds of |x~| from its top limb):
+ *   RN(x y):   ((hu + |x~|^ rho_y) + |y~|^ rho_x) + rho_x rho_y
+ *   RN(x - t): (hu + rho_x) + rho_t
+ *   RN(1/a):   hu + rho_a / (|a~|_ (|a~|_ - rho_a))  (unbounded unless |a~|_ > rho_a)
+ * Inputs lifted from doubles or integers, and numbers given at p bits, are
+ * exact (radius 0); Cauchy entries carry the radii of RN(x+y) and RN(1/s).
+ * The update runs on the IMAD engine in ball mode; it costs N^2 * 12 more
+ * bytes.  mpdet_radii reads the radii.  Series, the adjoint and mpdet_resume
+ * carry no radii. */
 
 /* Set A from an N x N row-major double matrix with leading dimension ld >= N
  * (exact lift: every finite double is representable at p >= 64).  Resets the
@@ -175,6 +195,14 @@ int mpdet_minor_series(mpdet_t h, mpdet_numv out, int normalised, int device_ptr
  * sampled reads of a large factorisation without copying it whole.
  * Errors: MPDET_EINVAL (bad index or pointer), MPDET_ECUDA. */
 int mpdet_get_entries(mpdet_t h, int64_t count, const int64_t* idx, mpdet_numv out, int device_ptr);
+
+/* Radii of the ball mode (MPDET_BALL): which = 0 those of D_1..D_N (N
+ * radii), 1 those of the last mpdet_lastcol_minors result (N radii), 2 those
+ * of the in-place N x N array (N^2 radii).  rad_mant[i], rad_exp[i]: radius
+ * i is rad_mant * 2^(rad_exp - 32) (0 when rad_mant = 0; unbounded when
+ * rad_exp = INT64_MAX).  Synchronous unless device_ptr = 1.  Errors:
+ * MPDET_EINVAL, MPDET_ESTATE (no ball mode), MPDET_ECUDA. */
+int mpdet_radii(mpdet_t h, int which, uint32_t* rad_mant, int64_t* rad_exp, int device_ptr);
 
 /* Copy out the leading minors computed so far (D_1..D_N; entries of steps not
  * yet run are +0). */
@@ -379,6 +407,21 @@ int mpdet_batch_free(mpdet_batch_t b);
  * gives +0).  All pointers are device memory; synchronises cuda_stream.
  * Errors: MPDET_EINVAL, MPDET_ECUDA. */
 int mpdet_ops(int op, int64_t count, int32_t p_bits, mpdet_numv a, mpdet_numv b, mpdet_numv out, void* cuda_stream);
+
+/* Schoolbook against Karatsuba (the paper's CPU runs use GMP, whose Karatsuba
+ * multiply grows about 2.8x per doubling of the precision against 3.95x for
+ * the GPU's schoolbook one, Sec. 4.2, Tables 1 and 2).  out[i] = RN(a[i] * b[i])
+ * at p bits for count pairs (device memory of the current device, 16-byte
+ * aligned), by the IMAD engine's lane-systolic schoolbook product (method 0,
+ * the one the Schur update uses) or by one Karatsuba level over three
+ * half-size schoolbook products (method 1); both give the same bits (the
+ * product is exact before it is rounded).  Each product is formed reps times
+ * on operands held on chip, so that *ms (the device time of the launch, CUDA
+ * events on cuda_stream; may be NULL) measures the multiplication.  p = 8192,
+ * 16384 or 32768.  Synchronises cuda_stream.  Errors: MPDET_EINVAL,
+ * MPDET_ECUDA. */
+int mpdet_mulbench(int method, int64_t count, int32_t p_bits, mpdet_numv a, mpdet_numv b, mpdet_numv out, int reps,
+                   void* cuda_stream, float* ms);
 
 /* Failure-detection self-test (the paper has no counterpart).  Every wait of
  * the kernels' hand-offs polls an mbarrier a bounded number of times and, when

@@ -445,6 +445,18 @@ int or_from_i64_v(int64_t cnt, int p, const int64_t *v, int8_t *so, int64_t *eo,
   return OR_OK;
 }
 
+/* One Cauchy entry: s = RN(x + y) into (ts, te, tm), then RN(1 / s) into
+ * (so, eo, mo); x and y are lifted exactly.  xm, ym: n-limb scratch. */
+static int cauchy_entry(ctx_t *c, double x, double y, uint32_t *xm, uint32_t *ym, int8_t *ts, int64_t *te,
+                        uint32_t *tm, int8_t *so, int64_t *eo, uint32_t *mo) {
+  int8_t xs, ys;
+  int64_t xe, ye;
+  op_from_f64(c, x, &xs, &xe, xm);
+  op_from_f64(c, y, &ys, &ye, ym);
+  op_add(c, xs, xe, xm, ys, ye, ym, 0, ts, te, tm);
+  return op_recip(c, *ts, *te, tm, so, eo, mo);
+}
+
 /* Cauchy matrix A_ij = RN(1 / RN(x_i + y_j)), x_i and y_j lifted exactly. */
 int or_cauchy(int64_t N, int p, const double *x, const double *y, int8_t *so, int64_t *eo, uint32_t *mo) {
   ctx_t c;
@@ -455,13 +467,9 @@ int or_cauchy(int64_t N, int p, const double *x, const double *y, int8_t *so, in
   uint32_t *xm = tm + n, *ym = tm + 2 * n;
   for (int64_t i = 0; i < N && st == OR_OK; ++i) {
     for (int64_t j = 0; j < N; ++j) {
-      int8_t xs, ys, ts;
-      int64_t xe, ye, te;
-      op_from_f64(&c, x[i], &xs, &xe, xm);
-      op_from_f64(&c, y[j], &ys, &ye, ym);
-      op_add(&c, xs, xe, xm, ys, ye, ym, 0, &ts, &te, tm);
-      int64_t idx = i * N + j;
-      st = op_recip(&c, ts, te, tm, so + idx, eo + idx, mo + idx * n);
+      int8_t ts;
+      int64_t te, idx = i * N + j;
+      st = cauchy_entry(&c, x[i], y[j], xm, ym, &ts, &te, tm, so + idx, eo + idx, mo + idx * n);
       if (st) break;
     }
   }
@@ -967,14 +975,11 @@ int or_cauchy_ball(int64_t N, int p, const double *x, const double *y, int8_t *s
   uint32_t *xm = tm + n, *ym = tm + 2 * n;
   for (int64_t i = 0; i < N && st == OR_OK; ++i)
     for (int64_t j = 0; j < N; ++j) {
-      int8_t xs, ys, ts;
-      int64_t xe, ye, te, idx = i * N + j;
-      op_from_f64(&c, x[i], &xs, &xe, xm);
-      op_from_f64(&c, y[j], &ys, &ye, ym);
-      op_add(&c, xs, xe, xm, ys, ye, ym, 0, &ts, &te, tm);
-      rad_t rs = ball_sub(p, te, RAD_ZERO, RAD_ZERO);
-      st = op_recip(&c, ts, te, tm, so + idx, eo + idx, mo + idx * n);
+      int8_t ts;
+      int64_t te, idx = i * N + j;
+      st = cauchy_entry(&c, x[i], y[j], xm, ym, &ts, &te, tm, so + idx, eo + idx, mo + idx * n);
       if (st) break;
+      rad_t rs = ball_sub(p, te, RAD_ZERO, RAD_ZERO);
       rad_t ra = ball_recip(p, n, eo[idx], te, tm, rs);
       rm[idx] = ra.m;
       re[idx] = ra.e;
@@ -1017,12 +1022,12 @@ int or_ge_ball(int64_t N, int p, int lastcol, int8_t *S, int64_t *E, uint32_t *M
     RDm[k] = rd.m;
     RDe[k] = rd.e;
     rprev = rd;
-    if (iszero(E[kk])) {
+    if (iszero(E[kk])) { /* D_k = 0 keeps its radius; D_k+1.. are not computed: unbounded */
       if (zero_k) *zero_k = k + 1;
-      for (int64_t q = k; q < N; ++q) {
-        setzero(Ds + q, De + q, Dm + q * n, n);
-        RDm[q] = 0;
-        RDe[q] = ZEXP;
+      for (int64_t q = k; q < N; ++q) setzero(Ds + q, De + q, Dm + q * n, n);
+      for (int64_t q = k + 1; q < N; ++q) {
+        RDm[q] = RAD_UNB.m;
+        RDe[q] = RAD_UNB.e;
       }
       if (k < N - 1) st = OR_EZEROPIVOT;
       break;
@@ -1040,7 +1045,8 @@ int or_ge_ball(int64_t N, int p, int lastcol, int8_t *S, int64_t *E, uint32_t *M
     for (int64_t i = k + 1; i < N; ++i) {
       for (int64_t j = lastcol ? 0 : k + 1; j < N; ++j) {
         if (j == k) continue;
-        int64_t ij = i * N + j, kj = k * N + j;
+        const int64_t ij = i * N + j;
+        const int64_t kj = k * N + j;
         int8_t ts;
         int64_t te;
         op_mul(&c, zs[i], ze[i], zm + i * n, S[kj], E[kj], M + kj * n, &ts, &te, t);

@@ -24,6 +24,8 @@ ZEXP = np.iinfo(np.int64).min
 OK, EINVAL, ENOMEM, ECUDA, EZEROPIVOT, ETIMEOUT, ESTATE, EZERODIV, ENOSCRATCH = range(9)
 LASTCOL = 1
 HOSTMEM = 2
+BALL = 4
+RAD_INF = np.iinfo(np.int64).max
 _NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EZEROPIVOT", 5: "ETIMEOUT", 6: "ESTATE",
           7: "EZERODIV", 8: "ENOSCRATCH"}
 
@@ -96,6 +98,9 @@ def load(build_if_missing: bool = True):
         "mpdet_get_inverse": ([P, NumV, ctypes.c_int], ctypes.c_int),
         "mpdet_ops": ([ctypes.c_int, i64, i32, NumV, NumV, NumV, P], ctypes.c_int),
         "mpdet_factor_noalloc": ([i64, i32, u32, NumV, NumV, NumV, ctypes.POINTER(i64), P], ctypes.c_int),
+        "mpdet_radii": ([P, ctypes.c_int, P, P, ctypes.c_int], ctypes.c_int),
+        "mpdet_mulbench": ([ctypes.c_int, i64, i32, NumV, NumV, NumV, ctypes.c_int, P, ctypes.POINTER(ctypes.c_float)],
+                           ctypes.c_int),
         "mpdet_selftest_timeout": ([i32, ctypes.c_int, P], ctypes.c_int),
         "mpdet_profile_read": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)], ctypes.c_int),
@@ -168,6 +173,26 @@ def ops(op: str, a, b, p: int):
     return (O[0].cpu().numpy(), O[1].cpu().numpy(), O[2].cpu().numpy().view(np.uint32))
 
 
+def mulbench(method: str, a, b, p: int, reps: int = 1):
+    """RN(a[i] * b[i]) at p bits (8192, 16384 or 32768) by the schoolbook
+    ("school") or the one-level Karatsuba ("kara") product of the IMAD engine,
+    each formed ``reps`` times (mpdet_mulbench).  a, b: host triples.
+    Returns (products triple, device milliseconds)."""
+    import torch
+
+    lib = load()
+    count = len(a[0])
+    dev = lambda t: (torch.from_numpy(np.ascontiguousarray(t[0])).cuda(), torch.from_numpy(np.ascontiguousarray(t[1])).cuda(),
+                     torch.from_numpy(np.ascontiguousarray(t[2]).view(np.int32)).cuda())
+    A, B, O = dev(a), dev(b), dev(empty(count, p))
+    ms = ctypes.c_float(0.0)
+    rc = lib.mpdet_mulbench({"school": 0, "kara": 1}[method], count, p, _numv(A), _numv(B), _numv(O), int(reps),
+                            ctypes.c_void_p(torch.cuda.current_stream().cuda_stream), ctypes.byref(ms))
+    if rc:
+        raise MpdetError(rc, f"mulbench({method}, p={p})")
+    return (O[0].cpu().numpy(), O[1].cpu().numpy(), O[2].cpu().numpy().view(np.uint32)), float(ms.value)
+
+
 def empty(count: int, p: int):
     n = p // 32
     return (np.zeros(count, np.int8), np.full(count, ZEXP, np.int64), np.zeros((count, n), np.uint32))
@@ -207,7 +232,7 @@ class Mpdet:
     the GPU reads and writes in place (matrices larger than HBM).
     """
 
-    def __init__(self, N: int, p: int, lastcol: bool = False, stream=None, hostmem: bool = False):
+    def __init__(self, N: int, p: int, lastcol: bool = False, stream=None, hostmem: bool = False, ball: bool = False):
         self.lib = load()
         self.N, self.p, self.n = int(N), int(p), int(p) // 32
         self.lastcol = bool(lastcol)
@@ -220,7 +245,7 @@ class Mpdet:
                 stream = None
         self.stream = stream
         h = ctypes.c_void_p()
-        flags = (LASTCOL if lastcol else 0) | (HOSTMEM if hostmem else 0)
+        flags = (LASTCOL if lastcol else 0) | (HOSTMEM if hostmem else 0) | (BALL if ball else 0)
         rc = self.lib.mpdet_create(self.N, self.p, flags, ctypes.c_void_p(stream or 0), ctypes.byref(h))
         if rc:
             raise MpdetError(rc, f"create(N={N}, p={p})")
@@ -326,6 +351,18 @@ class Mpdet:
         self._check(self.lib.mpdet_get_entries(self.h, len(idx), idx.ctypes.data_as(ctypes.c_void_p), _numv(out), 0),
                     "get_entries")
         return out
+
+    def radii(self, which: str = "minors"):
+        """Ball mode (ball=True): radii of the leading minors ("minors"), of
+        the last mpdet_lastcol_minors result ("lastcol") or of the in-place
+        array ("array"), as (mantissa uint32, exponent int64) arrays: radius
+        = mantissa * 2^(exponent - 32); exponent RAD_INF: unbounded."""
+        w = {"minors": 0, "lastcol": 1, "array": 2}[which]
+        cnt = self.N * self.N if w == 2 else self.N
+        rm, re_ = np.zeros(cnt, np.uint32), np.zeros(cnt, np.int64)
+        self._check(self.lib.mpdet_radii(self.h, w, rm.ctypes.data_as(ctypes.c_void_p),
+                                         re_.ctypes.data_as(ctypes.c_void_p), 0), "radii")
+        return rm, re_
 
     def get_minors(self):
         D = empty(self.N, self.p)

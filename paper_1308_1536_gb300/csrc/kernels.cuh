@@ -10,6 +10,7 @@
 #pragma once
 #include <math_constants.h>
 
+#include "ball.cuh"
 #include "mpdev.cuh"
 #include "kernelset.h"
 
@@ -148,6 +149,13 @@ __global__ void k_cauchy(const double* __restrict__ x, const double* __restrict_
     lift_f64_slice<W, G>(gp, y[j], ys, ye, YL);
     // s = RN(x + y) = RN(x - (-y))
     sub_round<W, G>(gp, p, xs, xe, XL, (int8_t)(ys ^ (ye != ZEXP ? 1 : 0)), ye, YL, buf, X.pad);
+    // ball mode: s = RN(x + y) of exact x, y; |s|_ for the reciprocal's radius
+    const int pl = p - 32 * X.pad;
+    Rad rs{}, los{};
+    if (X.rm) {
+      rs = ball_diff(pl, xe, rad_zero(), rad_zero());
+      los = rad_mag<W, G>(gp, xe, XL, false);
+    }
     uint32_t Mr[W];
     if (xe == ZEXP) {  // x_i + y_j == 0 has no reciprocal: divide a dummy, store +0
 #pragma unroll
@@ -155,6 +163,8 @@ __global__ void k_cauchy(const double* __restrict__ x, const double* __restrict_
       if (gp.g == G - 1) XL[W - 1] = 0x80000000u;
     }
     const int adj = recip_round<W, G>(gp, XL, buf, Mr, X.pad);
+    if (X.rm && active && gp.g == 0)
+      rad_store(X.rm, X.re, idx, xe == ZEXP ? rad_zero() : ball_inv(pl, (int64_t)adj - xe, los, rs));
     if (active && xe != ZEXP) {
       store_slice<W>(X.m + idx * n + gp.g * W, Mr);
       if (gp.g == 0) {
@@ -228,6 +238,19 @@ __global__ void k_pivot(MpArr X, int64_t N, int64_t k, MpArr D, MpArr R, int* st
     }
   }
   const bool already = status_set(status) != 0;
+  const int pl = p - 32 * X.pad;
+  if (X.rm) {  // ball mode: radius of D_k (unbounded once the elimination has stopped)
+    const Rad ra = rad_load(X.rm, X.re, kk);
+    const Rad my = rad_mag<W, G>(gp, ae, A, true);
+    Rad rd;
+    if (k == 0) {
+      rd = ball_prod(pl, de, Rad{0x80000000u, 1}, rad_zero(), my, ra);  // D_0 = 1 exactly
+    } else {
+      const Rad mx = rad_mag_mem<W, G>(gp, D.e[k - 1], dprev, true);
+      rd = ball_prod(pl, de, mx, rad_load(D.rm, D.re, k - 1), my, ra);
+    }
+    if (mine && gp.g == 0) rad_store(D.rm, D.re, k, already ? rad_unbounded() : rd);
+  }
   if (ae == ZEXP && !already) {
     if (mine && gp.g == 0) {
       if (*zero_k == 0) *zero_k = k + 1;
@@ -239,11 +262,14 @@ __global__ void k_pivot(MpArr X, int64_t N, int64_t k, MpArr D, MpArr R, int* st
   if (already || k == N - 1) return;
   uint32_t Mr[W];
   int adj = recip_round<W, G>(gp, A, buf, Mr, X.pad);
+  Rad rr{};
+  if (X.rm) rr = ball_inv(pl, (int64_t)adj - ae, rad_mag<W, G>(gp, ae, A, false), rad_load(X.rm, X.re, kk));
   if (mine) {
     store_slice<W>(R.m + gp.g * W, Mr);
     if (gp.g == 0) {
       R.s[0] = as;
       R.e[0] = (int64_t)adj - ae;
+      if (X.rm) rad_store(R.rm, R.re, 0, rr);
     }
   }
 }
@@ -273,6 +299,10 @@ __global__ void k_mult(MpArr X, int64_t N, int64_t k, MpArr R, MpArr Z, const in
   const int64_t ae = X.e[ik];
   int adj = mul_round<W, G>(gp, A, rm, M, X.pad);
   const bool zero = (ae == ZEXP);
+  Rad rz{};
+  if (X.rm)  // ball mode: z = RN(a_ik * r)
+    rz = ball_prod(p - 32 * X.pad, zero ? ZEXP : ae + re + adj, rad_mag<W, G>(gp, ae, A, true),
+                   rad_load(X.rm, X.re, ik), rad_mag_mem<W, G>(gp, re, rm, true), rad_load(R.rm, R.re, 0));
   if (zero) {
 #pragma unroll
     for (int q = 0; q < W; ++q) M[q] = 0u;
@@ -285,9 +315,11 @@ __global__ void k_mult(MpArr X, int64_t N, int64_t k, MpArr R, MpArr Z, const in
       const int64_t ze = zero ? ZEXP : ae + re + adj;
       Z.s[i] = zs;
       Z.e[i] = ze;
+      if (X.rm) rad_store(Z.rm, Z.re, i, rz);
       if (lastcol) {
         X.s[ik] = zero ? 0 : (int8_t)(zs ^ 1);
         X.e[ik] = ze;
+        if (X.rm) rad_store(X.rm, X.re, ik, rz);  // l_ik = -z_ik: same radius
       }
     }
   }
@@ -316,7 +348,10 @@ __device__ __forceinline__ bool upd_stopped(const int* status, const UpdArgs& a)
 
 __device__ __forceinline__ int64_t upd_col(const UpdArgs& a, int64_t c) { return a.j0 + c + (c >= a.hole ? a.hw : 0); }
 
-template <int W, int G, int MINB>
+// EXT: the instantiation for precisions held in a larger frame (X.pad > 0)
+// and for the ball mode's radii; the others round at the frame's end and keep
+// no radii, so the hot path carries neither.
+template <int W, int G, int MINB, bool EXT>
 __global__ void __launch_bounds__(128, MINB) k_update(MpArr X, UpdArgs a, MpArr Z, const int* status, int p,
                                                      int rows_per_cta) {
   constexpr int n = W * G;
@@ -356,6 +391,14 @@ __global__ void __launch_bounds__(128, MINB) k_update(MpArr X, UpdArgs a, MpArr 
   load_slice<W>(X.m + kj * n + gp.g * W, Bk);
   const int8_t bs = X.s[kj];
   const int64_t be = X.e[kj];
+  const int pad = EXT ? X.pad : 0;
+  const bool ball = EXT && X.rm != nullptr;
+  const int pl = p - 32 * pad;
+  Rad mb{}, rb{};
+  if (ball) {  // ball mode: |b|^ and the radius of the pivot-row element
+    mb = rad_mag<W, G>(gp, be, Bk, true);
+    rb = rad_load(X.rm, X.re, kj);
+  }
 #pragma unroll 1
   for (int r = 0; r < nr; ++r) {
     const int64_t ij = (i0 + r) * N + j;
@@ -363,7 +406,9 @@ __global__ void __launch_bounds__(128, MINB) k_update(MpArr X, UpdArgs a, MpArr 
     int8_t xs = X.s[ij];
     int64_t xe = X.e[ij];
     const int64_t zer = ze_s[r];
-    int adj = mul_round<W, G>(gp, Bk, zbuf + r * n, T, X.pad);
+    Rad mz{};
+    if (ball) mz = rad_mag_mem<W, G>(gp, zer, zbuf + r * n, true);
+    int adj = mul_round<W, G>(gp, Bk, zbuf + r * n, T, pad);
     load_slice<W>(X.m + ij * n + gp.g * W, Xv);
     const bool tz = (zer == ZEXP) || (be == ZEXP);
     const int8_t ts = tz ? 0 : (int8_t)(zs_s[r] ^ bs);
@@ -372,10 +417,14 @@ __global__ void __launch_bounds__(128, MINB) k_update(MpArr X, UpdArgs a, MpArr 
 #pragma unroll
       for (int q = 0; q < W; ++q) T[q] = 0u;
     }
-    sub_round<W, G>(gp, p, xs, xe, Xv, ts, te, T, buf, X.pad);
+    sub_round<W, G>(gp, p, xs, xe, Xv, ts, te, T, buf, pad);
     if (active) {
       store_slice<W>(X.m + ij * n + gp.g * W, Xv);
       if (gp.g == 0) {
+        if (ball) {  // t = RN(z b), then x - t
+          const Rad rt = ball_prod(pl, te, mz, rad_load(Z.rm, Z.re, i0 + r), mb, rb);
+          rad_store(X.rm, X.re, ij, ball_diff(pl, xe, rad_load(X.rm, X.re, ij), rt));
+        }
         X.s[ij] = xs;
         X.e[ij] = xe;
       }
@@ -410,6 +459,11 @@ __global__ void k_update_col(MpArr X, UpdArgs a, MpArr Z, const int* status, int
   int64_t xe = X.e[ij];
   const int64_t zer = Z.e[i];
   const int8_t zs = Z.s[i];
+  Rad mb{}, mz{};
+  if (X.rm) {
+    mb = rad_mag<W, G>(gp, be, Bk, true);
+    mz = rad_mag_mem<W, G>(gp, zer, Z.m + i * n, true);
+  }
   const int adj = mul_round<W, G>(gp, Bk, Z.m + i * n, T, X.pad);
   load_slice<W>(X.m + ij * n + gp.g * W, Xv);
   const bool tz = (zer == ZEXP) || (be == ZEXP);
@@ -423,6 +477,11 @@ __global__ void k_update_col(MpArr X, UpdArgs a, MpArr Z, const int* status, int
   if (active) {
     store_slice<W>(X.m + ij * n + gp.g * W, Xv);
     if (gp.g == 0) {
+      if (X.rm) {
+        const int pl = p - 32 * X.pad;
+        const Rad rt = ball_prod(pl, te, mz, rad_load(Z.rm, Z.re, i), mb, rad_load(X.rm, X.re, kj));
+        rad_store(X.rm, X.re, ij, ball_diff(pl, xe, rad_load(X.rm, X.re, ij), rt));
+      }
       X.s[ij] = xs;
       X.e[ij] = xe;
     }
@@ -569,6 +628,11 @@ __global__ void k_lastcol(MpArr X, int64_t N, MpArr F, MpArr out, int normalised
   const int8_t ls = X.s[Nj];
   const int64_t le = X.e[Nj];
   int adj = mul_round<W, G>(gp, L, fm, M, X.pad);
+  Rad ml{}, mf{};
+  if (X.rm) {
+    ml = rad_mag<W, G>(gp, le, L, true);
+    mf = rad_mag_mem<W, G>(gp, fe, fm, true);
+  }
   int8_t os;
   int64_t oe;
   if (le == ZEXP || fe == ZEXP) {
@@ -598,6 +662,14 @@ __global__ void k_lastcol(MpArr X, int64_t N, MpArr F, MpArr out, int normalised
     if (gp.g == 0) {
       out.s[j] = os;
       out.e[j] = oe;
+      if (X.rm) {  // C_jN = RN(D_{N-1} l_Nj); normalised: RN(l_Nj r), delta_1 = 1 exactly
+        const int pl = (int)(32 * n) - 32 * X.pad;
+        const Rad rf = rad_load(F.rm, F.re, 0), rl = rad_load(X.rm, X.re, Nj);
+        Rad ro = normalised ? ball_prod(pl, oe, ml, rl, mf, rf) : ball_prod(pl, oe, mf, rf, ml, rl);
+        if (j == N - 1) ro = rf;
+        if (normalised && j == 0) ro = rad_zero();
+        rad_store(out.rm, out.re, j, ro);
+      }
     }
   }
 }
@@ -688,11 +760,16 @@ __global__ void k_recip1(MpArr src, int64_t idx, MpArr dst, int* status, int cod
     return;
   }
   int adj = recip_round<W, G>(gp, A, sbuf + (threadIdx.x / G) * SW, M, src.pad);
+  Rad rr{};
+  if (src.rm)
+    rr = ball_inv((int)(32 * n) - 32 * src.pad, (int64_t)adj - ae, rad_mag<W, G>(gp, ae, A, false),
+                  rad_load(src.rm, src.re, idx));
   if (threadIdx.x < G) {
     store_slice<W>(dst.m + gp.g * W, M);
     if (gp.g == 0) {
       dst.s[0] = as;
       dst.e[0] = (int64_t)adj - ae;
+      if (src.rm) rad_store(dst.rm, dst.re, 0, rr);
     }
   }
 }
@@ -993,7 +1070,7 @@ struct Launch {
   static size_t update_smem(int rows_per_cta) {
     return (size_t)(rows_per_cta * n + upd_pad4(2 * rows_per_cta) + upd_pad4((rows_per_cta + 3) / 4) + (NT / G) * SW) * 4;
   }
-  template <int MINB>
+  template <int MINB, bool EXT = false>
   static cudaError_t update(MpArr X, const UpdArgs& a, MpArr Z, const int* status, int p, int nsm, cudaStream_t st) {
     const int64_t ncols = a.ncols;
     const int64_t rows = a.nrows;
@@ -1010,9 +1087,9 @@ struct Launch {
     if (rpc < 1) rpc = 1;
     int64_t by = (rows + rpc - 1) / rpc;
     size_t sm = update_smem((int)rpc);
-    cudaFuncSetAttribute(k_update<W, G, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(k_update<W, G, MINB, EXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     dim3 grid((unsigned)bx, (unsigned)by);
-    k_update<W, G, MINB><<<grid, NT, sm, st>>>(X, a, Z, status, p, (int)rpc);
+    k_update<W, G, MINB, EXT><<<grid, NT, sm, st>>>(X, a, Z, status, p, (int)rpc);
     return cudaGetLastError();
   }
   static cudaError_t update_col(MpArr X, const UpdArgs& a, MpArr Z, const int* status, int p, cudaStream_t st) {
@@ -1093,6 +1170,7 @@ struct Launch {
     s.update[1] = &update<4>;
     s.update[2] = &update<5>;
     s.update[3] = &update<6>;
+    s.update_ext = &update<4, true>;
     s.update_col = &update_col;
     s.lastcol = &lastcol;
     s.recip1 = &recip1;

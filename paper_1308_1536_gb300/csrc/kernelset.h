@@ -11,12 +11,26 @@ namespace mpd {
 // one of the kernel families' sizes is held in the next family's frame of n
 // limbs, mantissa in the top n - pad limbs and the low pad limbs zero, and
 // every operation rounds at that position (0: the whole frame).
+// rm, re: the ball mode's radii (mantissa, exponent) of the same numbers,
+// or null when the array carries none.
 struct MpArr {
   int8_t* s;
   int64_t* e;
   uint32_t* m;
   int pad = 0;
+  uint32_t* rm = nullptr;
+  int64_t* re = nullptr;
 };
+
+// Numbers [off, off + count) of a, radii included (n limbs each).
+inline MpArr arr_at(const MpArr& a, int64_t off, int n) {
+  MpArr v{a.s + off, a.e + off, a.m + (size_t)off * n, a.pad};
+  if (a.rm) {
+    v.rm = a.rm + off;
+    v.re = a.re + off;
+  }
+  return v;
+}
 
 // Device pointers describing a batch of independent matrices.
 struct BatchDescHost {
@@ -90,6 +104,9 @@ struct KernelSet {
   static constexpr int kUpdateVariants = 4;
   cudaError_t (*update[kUpdateVariants])(MpArr X, const UpdArgs& a, MpArr Z, const int* status, int p, int nsm,
                                          cudaStream_t st);
+  // the same for numbers held in a larger frame (MpArr::pad > 0) or with
+  // radii (ball mode): the update[] kernels are compiled without either
+  cudaError_t (*update_ext)(MpArr X, const UpdArgs& a, MpArr Z, const int* status, int p, int nsm, cudaStream_t st);
   // single-column launch (a.ncols == 1), one group per row
   cudaError_t (*update_col)(MpArr X, const UpdArgs& a, MpArr Z, const int* status, int p, cudaStream_t st);
   cudaError_t (*lastcol)(MpArr X, int64_t N, MpArr F, MpArr out, int normalised, const int* status,

@@ -101,6 +101,14 @@ static int fail(mpdet_t h, int code, const char* fmt, ...) {
     if (e_ != cudaSuccess) return fail(h, MPDET_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
   } while (0)
 
+// radii of the ball mode for count numbers (MPDET_BALL only)
+static int alloc_rad(mpdet_t h, MpArr* a, int64_t count) {
+  if (!(h->flags & MPDET_BALL)) return MPDET_OK;
+  if (cudaMalloc(&a->rm, (size_t)count * 4) != cudaSuccess || cudaMalloc(&a->re, (size_t)count * 8) != cudaSuccess)
+    return fail(h, MPDET_ENOMEM, "cudaMalloc radii");
+  return MPDET_OK;
+}
+
 static int alloc_arr(mpdet_t h, MpArr* a, int64_t count) {
   int n = h->n;
   a->pad = h->pad;
@@ -114,7 +122,24 @@ static void free_arr(MpArr* a) {
   if (a->m) cudaFree(a->m);
   if (a->e) cudaFree(a->e);
   if (a->s) cudaFree(a->s);
+  if (a->rm) cudaFree(a->rm);
+  if (a->re) cudaFree(a->re);
   *a = MpArr{};
+}
+
+// radii set to 0 (value 0) or to unbounded, count numbers
+static cudaError_t set_rad(MpArr a, int64_t count, bool unbounded, cudaStream_t st) {
+  if (!a.rm || count <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(a.rm, unbounded ? 0xff : 0, (size_t)count * 4, st);
+  if (e != cudaSuccess) return e;
+  if (unbounded) {  // INT64_MAX = ff .. ff 7f (little endian)
+    e = cudaMemsetAsync(a.re, 0xff, (size_t)count * 8, st);
+    if (e != cudaSuccess) return e;
+    return cudaMemset2DAsync(reinterpret_cast<char*>(a.re) + 7, 8, 0x7f, 1, (size_t)count, st);
+  }
+  e = cudaMemsetAsync(a.re, 0, (size_t)count * 8, st);  // INT64_MIN = 00 .. 00 80
+  if (e != cudaSuccess) return e;
+  return cudaMemset2DAsync(reinterpret_cast<char*>(a.re) + 7, 8, 0x80, 1, (size_t)count, st);
 }
 
 // The in-place array in page-locked host memory mapped into the device's
@@ -165,7 +190,7 @@ extern "C" int mpdet_create(int64_t N, int32_t p_bits, uint32_t flags, void* cud
   if (!out) return MPDET_EINVAL;
   *out = nullptr;
   if (N < 1 || N > (int64_t)1 << 20) return MPDET_EINVAL;
-  if (flags & ~(uint32_t)(MPDET_LASTCOL | MPDET_HOSTMEM)) return MPDET_EINVAL;
+  if (flags & ~(uint32_t)(MPDET_LASTCOL | MPDET_HOSTMEM | MPDET_BALL)) return MPDET_EINVAL;
   if (mpdet_geometry(p_bits, nullptr, nullptr, nullptr) != MPDET_OK) return MPDET_EINVAL;
   mpdet_t h = new (std::nothrow) mpdet_ctx();
   if (!h) return MPDET_ENOMEM;
@@ -198,6 +223,12 @@ extern "C" int mpdet_create(int64_t N, int32_t p_bits, uint32_t flags, void* cud
   }
   if (rc == MPDET_OK) rc = alloc_arr(h, &h->T, N);
   if (rc == MPDET_OK) rc = alloc_arr(h, &h->R, 1);
+  if (rc == MPDET_OK) rc = alloc_rad(h, &h->X, N * N);
+  if (rc == MPDET_OK) rc = alloc_rad(h, &h->D, N);
+  if (rc == MPDET_OK) rc = alloc_rad(h, &h->Z, N);
+  if (rc == MPDET_OK) rc = alloc_rad(h, &h->Z2, N);
+  if (rc == MPDET_OK) rc = alloc_rad(h, &h->T, N);
+  if (rc == MPDET_OK) rc = alloc_rad(h, &h->R, 1);
   if (rc == MPDET_OK && cudaMalloc(&h->status, 16) != cudaSuccess) rc = MPDET_ENOMEM;
   if (rc == MPDET_OK && cudaMalloc(&h->zero_k, 16) != cudaSuccess) rc = MPDET_ENOMEM;
   if (rc == MPDET_OK && (cudaMemsetAsync(h->status, 0, 16, h->stream) != cudaSuccess ||
@@ -221,7 +252,9 @@ extern "C" int mpdet_free(mpdet_t h) {
     if (h->side) cudaStreamSynchronize(h->side);
     for (void* hp : h->xhost)
       if (hp) cudaFreeHost(hp);
-    h->X = MpArr{};
+    h->X.s = nullptr;
+    h->X.e = nullptr;
+    h->X.m = nullptr;  // its radii, if any, are device memory and freed below
   }
   free_arr(&h->X);
   free_arr(&h->D);
@@ -266,6 +299,8 @@ static int reset_state(mpdet_t h) {
   CU(h, cudaMemsetAsync(h->status, 0, 16, h->stream));
   CU(h, cudaMemsetAsync(h->zero_k, 0, 16, h->stream));
   CU(h, zero_arr(h->D, h->N, h->n, h->stream));
+  CU(h, set_rad(h->D, h->N, true, h->stream));       // minors not reached stay unbounded
+  CU(h, set_rad(h->X, h->N * h->N, false, h->stream));  // inputs are exact unless a generator sets radii
   h->k_done = 0;
   h->have_matrix = true;
   return MPDET_OK;
@@ -367,6 +402,7 @@ static int64_t tc_default_min_rows(int p) { return p == 2048 ? 64 : INT64_MAX; }
 static bool use_tc(mpdet_t h, int64_t rows) {
   if (h->flags & MPDET_HOSTMEM) return false;  // its TMA copies address device memory only
   if (h->pad) return false;                    // it rounds at the frame's own precision only
+  if (h->flags & MPDET_BALL) return false;     // radii are kept by the IMAD kernels
   const int64_t thr = h->tc_min_rows >= 0 ? h->tc_min_rows : tc_default_min_rows(h->p);
   return h->engine >= 1 && mpd::tc_supports(h->p, h->engine == 1) && rows >= thr;
 }
@@ -380,6 +416,7 @@ static int default_upd_geom(int n) {
 
 // The IMAD Schur-update kernel the handle uses.
 static mpd::UpdateFn imad_update(mpdet_t h) {
+  if (h->pad || (h->flags & MPDET_BALL)) return h->ks->update_ext;  // frame rounding or radii
   const int g = h->upd_geom >= 0 ? h->upd_geom : default_upd_geom(h->n);
   if (g > 0) {
     mpd::UpdateFn f = mpd::update_wide_for(h->n, g == 1 ? 4 : 3);
@@ -635,6 +672,8 @@ extern "C" int mpdet_lastcol_minors(mpdet_t h, mpdet_numv out, int normalised, i
     cudaError_t ce = cudaMemcpy(out.limbs, one, h->nu * 4, k);
     if (ce == cudaSuccess) ce = cudaMemcpy(out.exp, &e, 8, k);
     if (ce == cudaSuccess) ce = cudaMemcpy(out.sign, &s, 1, k);
+    if (ce == cudaSuccess) ce = set_rad(h->T, 1, false, h->stream);  // exactly 1
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
     delete[] one;
     if (ce != cudaSuccess) return fail(h, MPDET_ECUDA, "lastcol N=1 copy: %s", cudaGetErrorString(ce));
     return MPDET_OK;
@@ -646,7 +685,7 @@ extern "C" int mpdet_lastcol_minors(mpdet_t h, mpdet_numv out, int normalised, i
     h->launches += 1;
     F = h->R;
   } else {
-    F = MpArr{h->D.s + (N - 2), h->D.e + (N - 2), h->D.m + (size_t)(N - 2) * h->n, h->pad};
+    F = mpd::arr_at(h->D, N - 2, h->n);
   }
   CU(h, h->ks->lastcol(h->X, N, F, h->T, normalised, h->status, h->stream));
   h->launches += 1;
@@ -731,6 +770,17 @@ extern "C" int mpdet_get_entries(mpdet_t h, int64_t count, const int64_t* idx, m
   return finish_call(h, device_ptr);
 }
 
+extern "C" int mpdet_radii(mpdet_t h, int which, uint32_t* rad_mant, int64_t* rad_exp, int device_ptr) {
+  if (!h || which < 0 || which > 2 || !rad_mant || !rad_exp) return fail(h, MPDET_EINVAL, "radii: bad argument");
+  if (!(h->flags & MPDET_BALL)) return fail(h, MPDET_ESTATE, "radii: handle created without MPDET_BALL");
+  const MpArr& a = which == 0 ? h->D : which == 1 ? h->T : h->X;
+  const int64_t count = which == 2 ? h->N * h->N : h->N;
+  const cudaMemcpyKind k = device_ptr ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  CU(h, cudaMemcpyAsync(rad_mant, a.rm, (size_t)count * 4, k, h->stream));
+  CU(h, cudaMemcpyAsync(rad_exp, a.re, (size_t)count * 8, k, h->stream));
+  return finish_call(h, device_ptr);
+}
+
 extern "C" int mpdet_get_mp(mpdet_t h, mpdet_numv out, int device_ptr) {
   if (!h) return MPDET_EINVAL;
   int rc = copy_arr(h, h->X, out, h->N * h->N, device_ptr, false);
@@ -740,6 +790,7 @@ extern "C" int mpdet_get_mp(mpdet_t h, mpdet_numv out, int device_ptr) {
 
 extern "C" int mpdet_resume(mpdet_t h, mpdet_numv A, mpdet_numv minors, int64_t k_done, int device_ptr) {
   if (!h || k_done < 0 || k_done > h->N) return fail(h, MPDET_EINVAL, "resume: bad argument");
+  if (h->flags & MPDET_BALL) return fail(h, MPDET_ESTATE, "resume: a checkpoint carries no radii (ball mode)");
   int rc = reset_state(h);
   if (rc) return rc;
   rc = copy_arr(h, h->X, A, h->N * h->N, device_ptr, true);

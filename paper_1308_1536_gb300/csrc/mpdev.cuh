@@ -265,6 +265,10 @@ __device__ __forceinline__ uint32_t round_frame(const Grp<G>& gp, uint32_t (&M)[
   return ovf;
 }
 
+template <int W, int G>
+__device__ __forceinline__ int round_product(const Grp<G>& gp, const uint32_t (&F)[W], uint32_t ltop, uint32_t sticky,
+                                             uint32_t (&M)[W], int pad);
+
 // ---------------------------------------------------------------------------
 // Rounded product of two mantissas.
 //   b: this lane's slice of the first mantissa (registers)
@@ -392,6 +396,17 @@ __device__ __forceinline__ int mul_round(const Grp<G>& gp, const uint32_t (&b)[W
   uint32_t gen = gp.ballot(c != 0u), prop = gp.ballot(all_ones<W>(F));
   uint32_t cin = (uint32_t)(carry_mask(gen, prop, 0u) >> gp.g) & 1u;
   slice_inc<W>(F, cin);
+  return round_product<W, G>(gp, F, ltop, sticky, M, pad);
+}
+
+// Normalise and round an exact product of two normalised n-limb mantissas:
+// F is this lane's slice of its upper n limbs, ltop (lane 0's value) its
+// limb n - 1 and sticky (lane 0's value) the OR of limbs [0, n - 1).  The
+// product has 2p or 2p - 1 bits; M receives RN_p scaled to [2^(p-1), 2^p) and
+// the return value is the exponent adjustment (-1, 0 or +1).
+template <int W, int G>
+__device__ __forceinline__ int round_product(const Grp<G>& gp, const uint32_t (&F)[W], uint32_t ltop, uint32_t sticky,
+                                             uint32_t (&M)[W], int pad) {
   // normalise: the product has 2p or 2p-1 bits
   uint32_t top = gp.from(F[W - 1], G - 1) >> 31;
   ltop = gp.from(ltop, 0);

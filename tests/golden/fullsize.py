@@ -13,8 +13,9 @@ Files (one per workload; the method is elimination without pivoting, Sec. 3
 and Alg. 1, with the augmented matrix [A I] for the last-column minors):
 
 * c2_cauchy_N1024_p2048.txt, c2_int_N1024_p2048.txt: workload C2, last-column
-  mode (the integer matrix is the benchmark's: seed + 100).  Status and first zero pivot; D_1..D_1024; C_1N..C_NN (eq.
-  minorsdef); one digest per row of the in-place array (U and L).
+  mode (the integer matrix is the benchmark's: seed + 100).  Status and first
+  zero pivot; D_1..D_1024; C_1N..C_NN (eq. minorsdef); one digest per row of
+  the in-place array (U and L).
 * c3_batch_4096_p1024.txt: workload C3, 4096 matrices of sizes N uniform in
   [8, 256], even index Cauchy, odd index integer.  Per matrix: N, first zero
   pivot and the digest of D_1..D_N; the value of det = D_N of 64 sampled

@@ -87,6 +87,9 @@ def test_more_entry_points_reject_bad_arguments_without_a_device(lib):
     assert lib.mpdet_get_entries(None, 0, None, z, 0) == m.EINVAL
     assert lib.mpdet_tune(None, 1, 0) == m.EINVAL
     assert lib.mpdet_steps_done(None) == -1
+    assert lib.mpdet_radii(None, 0, None, None, 0) == m.EINVAL
+    h2 = ctypes.c_void_p()
+    assert lib.mpdet_create(8, 512, 0x8, None, ctypes.byref(h2)) == m.EINVAL  # unknown flag next to MPDET_BALL
 
 
 def test_noalloc_size_limit_without_a_device(lib):
@@ -114,3 +117,13 @@ def test_one_shot_batch_checks_sizes_before_pointers(lib):
     ns = (ctypes.c_int64 * 2)(4, 0)
     assert lib.mpdet_batch(2, ns, 512, one, one, None, 0, None) == m.EINVAL  # N = 0 before in[1] is read
     assert lib.mpdet_batch((1 << 30) + 1, ns, 512, one, one, None, 0, None) == m.EINVAL
+
+
+def test_mulbench_rejects_bad_arguments_without_a_device(lib):
+    import paper_1308_1536_gb300 as m
+
+    z = m.NumV(None, None, None)
+    assert lib.mpdet_mulbench(2, 4, 8192, z, z, z, 1, None, None) == m.EINVAL  # unknown method
+    assert lib.mpdet_mulbench(0, 4, 4096, z, z, z, 1, None, None) == m.EINVAL  # precision without a Karatsuba case
+    assert lib.mpdet_mulbench(1, 0, 8192, z, z, z, 1, None, None) == m.EINVAL  # no pairs
+    assert lib.mpdet_mulbench(1, 4, 8192, z, z, z, 1, None, None) == m.EINVAL  # null buffers

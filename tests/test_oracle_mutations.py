@@ -30,8 +30,8 @@ MUTATIONS = [
      "int8_t s = iszero(ze) ? 0 : (int8_t)zs;", ["test_oracle_ge.py::test_lastcol_integer_cofactors_and_laplace"]),
     ("update reads the next row as pivot row", "int64_t ij = i * N + j, kj = k * N + j;",
      "int64_t ij = i * N + j, kj = (k + 1) * N + j;", ["test_oracle_ge.py::test_integer_minors_vs_exact"]),
-    ("Cauchy entries from x - y", "op_add(&c, xs, xe, xm, ys, ye, ym, 0, &ts, &te, tm);",
-     "op_add(&c, xs, xe, xm, ys, ye, ym, 1, &ts, &te, tm);", ["test_oracle_ops.py::test_cauchy_entries"]),
+    ("Cauchy entries from x - y", "op_add(c, xs, xe, xm, ys, ye, ym, 0, ts, te, tm);",
+     "op_add(c, xs, xe, xm, ys, ye, ym, 1, ts, te, tm);", ["test_oracle_ops.py::test_cauchy_entries"]),
     ("back substitution adds the update",
      "op_add(&c, u->S[ic], u->E[ic], u->M + ic * n, ts, te, t, 1, u->S + ic, u->E + ic, u->M + ic * n);",
      "op_add(&c, u->S[ic], u->E[ic], u->M + ic * n, ts, te, t, 0, u->S + ic, u->E + ic, u->M + ic * n);",
