@@ -226,6 +226,8 @@ def bench_batch(args, dev, m, rank=0, world=1):
     Ns, kinds, seeds = Ns_all[mine], kinds_all[mine], seeds_all[mine]
     b = m.Batch(Ns, p, stream=torch.cuda.current_stream(dev).cuda_stream)
     inputs = []
+    torch.cuda.synchronize(dev)
+    t_lift0 = time.perf_counter()
     for i in range(len(Ns)):
         N = int(Ns[i])
         if kinds[i] == "cauchy":
@@ -235,6 +237,8 @@ def bench_batch(args, dev, m, rank=0, world=1):
             d = W.int_matrix(N, int(seeds[i]))
             b.set_i32(i, d)
         inputs.append(d)
+    torch.cuda.synchronize(dev)
+    t_lift = time.perf_counter() - t_lift0  # every matrix's input set from host arrays (lift or generation)
     tot = int(np.sum(Ns))
     out = (torch.empty(tot, dtype=torch.int8, device=dev), torch.empty(tot, dtype=torch.int64, device=dev),
            torch.empty((tot, n), dtype=torch.int32, device=dev))
@@ -258,18 +262,32 @@ def bench_batch(args, dev, m, rank=0, world=1):
     launches = (b.launches() - l0) // args.steps
     b.close()
     macs = batch_products(Ns_all) * n * n
-    # single-matrix path on a sample (every 16th matrix), same p, same GPU
+    # single-matrix path on a sample (every 16th matrix), same p, same GPU:
+    # (a) lift + factor per matrix (as a user with raw inputs would call it),
+    # (b) from the same p-bit inputs the batch starts from (mpdet_set_mp from
+    # device buffers, then factor), like for like with the batch's timed step
     sample = list(range(0, len(Ns), 16))
     handles = {}
-    t_single = 0.0
+    lifted = {}
+    for i in sample:
+        N = int(Ns[i])
+        h = handles.get(N)
+        if h is None:
+            h = handles[N] = m.Mpdet(N, p, stream=torch.cuda.current_stream(dev).cuda_stream)
+        if kinds[i] == "cauchy":
+            h.set_cauchy(*inputs[i])
+        else:
+            h.set_i32(inputs[i])
+        Xl = h.get_mp()
+        lifted[i] = (torch.from_numpy(Xl[0]).to(dev), torch.from_numpy(Xl[1]).to(dev),
+                     torch.from_numpy(np.ascontiguousarray(Xl[2]).view(np.int32)).to(dev))
+    t_single = t_single_mp = 0.0
     for rep in range(2):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         for i in sample:
             N = int(Ns[i])
-            h = handles.get(N)
-            if h is None:
-                h = handles[N] = m.Mpdet(N, p, stream=torch.cuda.current_stream(dev).cuda_stream)
+            h = handles[N]
             if kinds[i] == "cauchy":
                 h.set_cauchy(*inputs[i])
             else:
@@ -277,9 +295,17 @@ def bench_batch(args, dev, m, rank=0, world=1):
             h.factor_range(0, N)
         torch.cuda.synchronize(dev)
         t_single = time.perf_counter() - t0  # second repetition counts (handles warm)
+        t0 = time.perf_counter()
+        for i in sample:
+            h = handles[int(Ns[i])]
+            h.set_mp(lifted[i])
+            h.factor_range(0, int(Ns[i]))
+        torch.cuda.synchronize(dev)
+        t_single_mp = time.perf_counter() - t0
     for h in handles.values():
         h.close()
     single_dets = len(sample) / t_single
+    single_dets_mp = len(sample) / t_single_mp
     return {"workload": f"{len(Ns_all)} matrices N~U[8,256], half Cauchy half integer, p=1024: det + leading minors",
             "ranks": world, "matrices_per_rank": int(len(Ns)),
             "dets_per_s": len(Ns_all) / (ms / 1e3), "ms_per_step": ms, "limb_macs_per_s": macs / (ms / 1e3),
@@ -288,9 +314,13 @@ def bench_batch(args, dev, m, rank=0, world=1):
                           "blocks_per_sm": tuned["blocks_per_sm"], "candidates": tuned["candidates"],
                           "best_ms": tuned["ms"]},
             "cuda_graph": True,
-            "single_path_dets_per_s": single_dets,
-            "vs_single_path": (len(Ns) / (ms / 1e3)) / single_dets,
-            "single_path_sample": f"every 16th matrix ({len(sample)}), set + factor per matrix, includes input lift"}
+            "single_path_dets_per_s": single_dets_mp,
+            "vs_single_path": (len(Ns) / (ms / 1e3)) / single_dets_mp,
+            "single_path_sample": f"every 16th matrix ({len(sample)}), from the same p-bit inputs as the batch "
+                                  "(set_mp from device buffers + factor per matrix)",
+            "with_lift_dets_per_s": len(Ns) / (t_lift + ms / 1e3),
+            "single_path_with_lift_dets_per_s": single_dets,
+            "vs_single_path_with_lift": (len(Ns) / (ms / 1e3)) / single_dets}
 
 
 def bench_adjoint(args, dev, m):
@@ -579,6 +609,19 @@ def bench_large(args, dev, m, peak_macs):
     ms = e0.elapsed_time(e1)
     assert h.status()[0] == 0
     h.close()
+    # the same two steps with the update's products by one Karatsuba level
+    hk = m.Mpdet(N, p, lastcol=False, stream=st.cuda_stream)
+    hk.tune(karatsuba=True)
+    hk.set_cauchy(x, y)
+    hk.factor_range(0, 1)
+    torch.cuda.synchronize(dev)
+    e0.record(st)
+    hk.factor_range(1, 1 + w)
+    e1.record(st)
+    torch.cuda.synchronize(dev)
+    ms_kara = e0.elapsed_time(e1)
+    assert hk.status()[0] == 0
+    hk.close()
     prods = sum((N - k - 1) ** 2 + (N - k - 1) + 1 for k in range(1, 1 + w))
     rate = prods * n * n / (ms / 1e3)
     upd = pr["update_limb_macs"] / (pr["update_ms"] / 1e3)
@@ -609,6 +652,7 @@ def bench_large(args, dev, m, peak_macs):
     return {"workload": f"Cauchy N={N} p={p} (68.9 GB in HBM), det + leading minors: steps 2..{1 + w} "
                         "timed (the heaviest; one full run is about an hour)",
             "window_ms": ms, "limb_macs_per_s": rate, "frac_of_imad_peak": rate / peak_macs,
+            "karatsuba_window_ms": ms_kara, "karatsuba_speedup": ms / ms_kara,
             "update_kernel": {"achieved": upd / 1e12, "peak": peak_macs / 1e12, "unit": "Tlimb-MAC/s",
                               "frac": upd / peak_macs, "launches": int(pr["update_launches"])},
             "cauchy_generation_s": t_gen,
@@ -642,6 +686,8 @@ def run_large_full(args):
         x, y = x[:N], y[:N]
     st = torch.cuda.current_stream(dev)
     h = m.Mpdet(N, p, lastcol=False, stream=st.cuda_stream)
+    if args.karatsuba:
+        h.tune(karatsuba=True)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     h.set_cauchy(x, y)
@@ -694,6 +740,7 @@ def run_large_full(args):
            "update_kernel": {"ms": upd_ms, "limb_macs_per_s": upd_macs / (upd_ms / 1e3),
                              "frac": upd_macs / (upd_ms / 1e3) / peak},
            "window_steps": args.window, "windows": windows, "clock_reasons_seen": reasons,
+           "update_products": "karatsuba (one level)" if args.karatsuba else "schoolbook",
            "sm_mhz_median_of_windows": statistics.median([w["sm_mhz"] for w in windows if w["sm_mhz"]] or [0]),
            "saved": args.save}
     print(json.dumps(out))
@@ -999,6 +1046,8 @@ def main():
                     help="--large-full: factor the leading N x N block of the N=4096 matrix instead (its steps cost "
                          "what the full run's last N steps cost; its minors are the full run's D_1..D_N)")
     ap.add_argument("--save", default="gpurun_out/c5_minors.npz", help="--large-full: where the leading minors go")
+    ap.add_argument("--karatsuba", action="store_true",
+                    help="--large-full: the IMAD update's products by one Karatsuba level")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

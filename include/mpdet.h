@@ -245,6 +245,11 @@ int64_t mpdet_steps_done(mpdet_t h);
  * precision's own (16 limbs per lane below p = 32768), 1 or 2 32 limbs per
  * lane (p = 2048 .. 16384) compiled for 4 or 3 resident blocks per SM, -1
  * (default) the one measured fastest for the precision.
+ * MPDET_TUNE_KARATSUBA: 1 forms the IMAD update's products by one Karatsuba
+ * level over three half-size schoolbook products (p = 8192, 16384, 32768;
+ * the product is exact before it is rounded, so the bits are the same), 0
+ * (default) the schoolbook product.  Ignored in ball mode and for
+ * precisions held in a larger frame.
  * Errors: MPDET_EINVAL. */
 enum {
   MPDET_TUNE_UPDATE_VARIANT = 1,
@@ -252,7 +257,8 @@ enum {
   MPDET_TUNE_TC_MIN_ROWS = 3,
   MPDET_TUNE_LOOKAHEAD = 4,
   MPDET_TUNE_LOOKAHEAD_RESERVE = 5,
-  MPDET_TUNE_UPDATE_GEOMETRY = 6
+  MPDET_TUNE_UPDATE_GEOMETRY = 6,
+  MPDET_TUNE_KARATSUBA = 7
 };
 int mpdet_tune(mpdet_t h, int param, int value);
 

@@ -412,17 +412,19 @@ class Mpdet:
 
     # -- tuning (bit-identical results for every setting) -------------------
     def tune(self, update_variant: int | None = None, engine: int | None = None, tc_min_rows: int | None = None,
-             lookahead: bool | None = None, lookahead_reserve: int | None = None, update_geometry: int | None = None):
+             lookahead: bool | None = None, lookahead_reserve: int | None = None, update_geometry: int | None = None,
+             karatsuba: bool | None = None):
         """update_variant: IMAD update register budget 0..3; engine: 1 tensor
         cores (p = 512, 1024, 2048), 2 the same one phase at a time (p =
         2048), 0 IMAD; tc_min_rows: update launches of fewer rows take the
         IMAD kernel; lookahead: overlap step k+1's pivot and multipliers with
         step k's update on a second stream; lookahead_reserve: SMs left to
         that stream; update_geometry: IMAD update lane geometry (0 own, 1/2
-        32 limbs per lane for 4/3 blocks per SM, -1 per precision).  Results
-        are bit-identical for every setting."""
+        32 limbs per lane for 4/3 blocks per SM, -1 per precision); karatsuba:
+        the IMAD update's products by one Karatsuba level (p >= 8192).
+        Results are bit-identical for every setting."""
         for key, val in ((1, update_variant), (2, engine), (3, tc_min_rows), (4, lookahead), (5, lookahead_reserve),
-                         (6, update_geometry)):
+                         (6, update_geometry), (7, karatsuba)):
             if val is not None:
                 self._check(self.lib.mpdet_tune(self.h, key, int(val)), "tune")
 

@@ -11,6 +11,7 @@
 #include <math_constants.h>
 
 #include "ball.cuh"
+#include "karatsuba.cuh"
 #include "mpdev.cuh"
 #include "kernelset.h"
 
@@ -350,8 +351,10 @@ __device__ __forceinline__ int64_t upd_col(const UpdArgs& a, int64_t c) { return
 
 // EXT: the instantiation for precisions held in a larger frame (X.pad > 0)
 // and for the ball mode's radii; the others round at the frame's end and keep
-// no radii, so the hot path carries neither.
-template <int W, int G, int MINB, bool EXT>
+// no radii, so the hot path carries neither.  KARA: the products by one
+// Karatsuba level (mul_round_kara, 3n words of scratch per group after the
+// per-group scratch) instead of the schoolbook mul_round; the same bits.
+template <int W, int G, int MINB, bool EXT, bool KARA = false>
 __global__ void __launch_bounds__(128, MINB) k_update(MpArr X, UpdArgs a, MpArr Z, const int* status, int p,
                                                      int rows_per_cta) {
   constexpr int n = W * G;
@@ -368,6 +371,8 @@ __global__ void __launch_bounds__(128, MINB) k_update(MpArr X, UpdArgs a, MpArr 
   int64_t* ze_s = reinterpret_cast<int64_t*>(smem + rows_per_cta * n);
   int8_t* zs_s = reinterpret_cast<int8_t*>(smem + rows_per_cta * n + upd_pad4(2 * rows_per_cta));
   uint32_t* buf = smem + rows_per_cta * n + upd_pad4(2 * rows_per_cta) + upd_pad4((rows_per_cta + 3) / 4) + gib * SW;
+  uint32_t* kscr = smem + rows_per_cta * n + upd_pad4(2 * rows_per_cta) + upd_pad4((rows_per_cta + 3) / 4) +
+                   (blockDim.x / G) * SW + gib * (KARA ? 3 * n : 0);
   const int64_t ncols = a.ncols;
   const int64_t i0 = a.row0 + (int64_t)blockIdx.y * rows_per_cta;
   const int64_t rend = a.row0 + a.nrows;
@@ -408,7 +413,11 @@ __global__ void __launch_bounds__(128, MINB) k_update(MpArr X, UpdArgs a, MpArr 
     const int64_t zer = ze_s[r];
     Rad mz{};
     if (ball) mz = rad_mag_mem<W, G>(gp, zer, zbuf + r * n, true);
-    int adj = mul_round<W, G>(gp, Bk, zbuf + r * n, T, pad);
+    int adj;
+    if constexpr (KARA)
+      adj = mul_round_kara<W, G>(gp, Bk, zbuf + r * n, T, kscr, pad);
+    else
+      adj = mul_round<W, G>(gp, Bk, zbuf + r * n, T, pad);
     load_slice<W>(X.m + ij * n + gp.g * W, Xv);
     const bool tz = (zer == ZEXP) || (be == ZEXP);
     const int8_t ts = tz ? 0 : (int8_t)(zs_s[r] ^ bs);
@@ -1067,10 +1076,11 @@ struct Launch {
     k_mult<W, G><<<(unsigned)blocks, NT, 0, st>>>(X, N, k, R, Z, status, p, lastcol);
     return cudaGetLastError();
   }
-  static size_t update_smem(int rows_per_cta) {
-    return (size_t)(rows_per_cta * n + upd_pad4(2 * rows_per_cta) + upd_pad4((rows_per_cta + 3) / 4) + (NT / G) * SW) * 4;
+  static size_t update_smem(int rows_per_cta, bool kara = false) {
+    return (size_t)(rows_per_cta * n + upd_pad4(2 * rows_per_cta) + upd_pad4((rows_per_cta + 3) / 4) + (NT / G) * SW +
+                    (kara ? (NT / G) * 3 * n : 0)) * 4;
   }
-  template <int MINB, bool EXT = false>
+  template <int MINB, bool EXT = false, bool KARA = false>
   static cudaError_t update(MpArr X, const UpdArgs& a, MpArr Z, const int* status, int p, int nsm, cudaStream_t st) {
     const int64_t ncols = a.ncols;
     const int64_t rows = a.nrows;
@@ -1082,14 +1092,15 @@ struct Launch {
     int64_t by_needed = (target + bx - 1) / bx;
     int64_t rpc = (rows + by_needed - 1) / by_needed;
     int64_t rmax = 32;
-    while (rmax > 1 && update_smem((int)rmax) > 96 * 1024) rmax /= 2;
+    const size_t cap = KARA ? 112 * 1024 : 96 * 1024;
+    while (rmax > 1 && update_smem((int)rmax, KARA) > cap) rmax /= 2;
     if (rpc > rmax) rpc = rmax;
     if (rpc < 1) rpc = 1;
     int64_t by = (rows + rpc - 1) / rpc;
-    size_t sm = update_smem((int)rpc);
-    cudaFuncSetAttribute(k_update<W, G, MINB, EXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    size_t sm = update_smem((int)rpc, KARA);
+    cudaFuncSetAttribute(k_update<W, G, MINB, EXT, KARA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     dim3 grid((unsigned)bx, (unsigned)by);
-    k_update<W, G, MINB, EXT><<<grid, NT, sm, st>>>(X, a, Z, status, p, (int)rpc);
+    k_update<W, G, MINB, EXT, KARA><<<grid, NT, sm, st>>>(X, a, Z, status, p, (int)rpc);
     return cudaGetLastError();
   }
   static cudaError_t update_col(MpArr X, const UpdArgs& a, MpArr Z, const int* status, int p, cudaStream_t st) {
@@ -1171,6 +1182,7 @@ struct Launch {
     s.update[2] = &update<5>;
     s.update[3] = &update<6>;
     s.update_ext = &update<4, true>;
+    if constexpr (W >= 16 && n >= 256) s.update_kara = &update<3, false, true>;
     s.update_col = &update_col;
     s.lastcol = &lastcol;
     s.recip1 = &recip1;

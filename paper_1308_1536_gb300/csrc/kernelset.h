@@ -107,6 +107,10 @@ struct KernelSet {
   // the same for numbers held in a larger frame (MpArr::pad > 0) or with
   // radii (ball mode): the update[] kernels are compiled without either
   cudaError_t (*update_ext)(MpArr X, const UpdArgs& a, MpArr Z, const int* status, int p, int nsm, cudaStream_t st);
+  // the update with its products by one Karatsuba level (n >= 256 only, else
+  // null): the same bits, a tuning choice (MPDET_TUNE_KARATSUBA)
+  cudaError_t (*update_kara)(MpArr X, const UpdArgs& a, MpArr Z, const int* status, int p, int nsm, cudaStream_t st) =
+      nullptr;
   // single-column launch (a.ncols == 1), one group per row
   cudaError_t (*update_col)(MpArr X, const UpdArgs& a, MpArr Z, const int* status, int p, cudaStream_t st);
   cudaError_t (*lastcol)(MpArr X, int64_t N, MpArr F, MpArr out, int normalised, const int* status,

@@ -68,6 +68,7 @@ struct mpdet_ctx {
   // IMAD update geometry: 0 the kernel set's own, 1 / 2 32 limbs per lane
   // compiled for 4 / 3 blocks per SM (n = 64 .. 512); -1 per precision
   int upd_geom = -1;
+  int kara = 0;  // 1: IMAD update products by one Karatsuba level (n >= 256)
   cudaStream_t side = nullptr;
   cudaEvent_t ev_mult = nullptr, ev_rest = nullptr;
   bool have_matrix = false;
@@ -417,6 +418,7 @@ static int default_upd_geom(int n) {
 // The IMAD Schur-update kernel the handle uses.
 static mpd::UpdateFn imad_update(mpdet_t h) {
   if (h->pad || (h->flags & MPDET_BALL)) return h->ks->update_ext;  // frame rounding or radii
+  if (h->kara && h->ks->update_kara) return h->ks->update_kara;
   const int g = h->upd_geom >= 0 ? h->upd_geom : default_upd_geom(h->n);
   if (g > 0) {
     mpd::UpdateFn f = mpd::update_wide_for(h->n, g == 1 ? 4 : 3);
@@ -568,6 +570,11 @@ extern "C" int mpdet_tune(mpdet_t h, int param, int value) {
     case MPDET_TUNE_UPDATE_GEOMETRY:
       if (value < -1 || value > 2) return fail(h, MPDET_EINVAL, "tune: update geometry %d", value);
       h->upd_geom = value;
+      return MPDET_OK;
+    case MPDET_TUNE_KARATSUBA:
+      if (value < 0 || value > 1) return fail(h, MPDET_EINVAL, "tune: karatsuba %d", value);
+      if (value && !h->ks->update_kara) return fail(h, MPDET_EINVAL, "tune: no Karatsuba update below p = 8192");
+      h->kara = value;
       return MPDET_OK;
     default:
       return fail(h, MPDET_EINVAL, "tune: unknown parameter %d", param);

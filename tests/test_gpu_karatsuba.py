@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 import exactref as X
+from paper_1308_1536_gb300 import workloads as W
 from test_oracle_ops import rand_num, special_mantissas
 
 pytestmark = pytest.mark.gpu
@@ -46,3 +47,22 @@ def test_karatsuba_equals_schoolbook_and_oracle(mpdet, oracle_lib, p):
         for i in range(len(a)):
             assert got[0][i] == want[0][i] and got[1][i] == want[1][i] and np.array_equal(got[2][i], want[2][i]), \
                 f"{name} p={p}: product {i} differs from the oracle"
+
+
+@pytest.mark.parametrize("p,N", [(8192, 11), (16384, 7), (32768, 5)])
+def test_update_with_karatsuba_products_equals_oracle(mpdet, oracle_lib, p, N):
+    """The elimination with the IMAD update's products formed by one
+    Karatsuba level (MPDET_TUNE_KARATSUBA) equals the oracle bit for bit:
+    leading minors, the whole in-place array and the last-column minors."""
+    x, y = W.cauchy_xy(N, 4000 + N)
+    h = mpdet.Mpdet(N, p, lastcol=True)
+    h.tune(karatsuba=True, engine=0)
+    h.set_cauchy(x, y)
+    rc, zk, D = h.factor()
+    Xm = h.get_mp()
+    C = h.lastcol_minors()
+    h.close()
+    st, ozk, OD, OX = oracle_lib.ge(oracle_lib.cauchy(x, y, p), N, p, lastcol=True, nthreads=8)
+    assert (rc, zk) == (st, ozk)
+    assert X.same(D, OD) and X.same(Xm, OX)
+    assert X.same(C, oracle_lib.lastcol_minors(OX, OD, N, p))
