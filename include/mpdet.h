@@ -92,8 +92,10 @@ enum { MPDET_LASTCOL = 1, MPDET_HOSTMEM = 2, MPDET_BALL = 4 };
  * production size N = 12000 at 32768 bits (590 GB, Sec. 4.2 pages blocks
  * to disk for it).  Every update of a p-bit number reads and writes 8n + 18
  * bytes for n^2 limb multiply-accumulates, so at p >= 8192 the link keeps
- * up with the arithmetic.  The update then runs on the IMAD engine (the
- * tensor-core engine's TMA copies address device memory only).  Results are
+ * up with the arithmetic.  At p = 512 .. 2048 the update then runs on the
+ * IMAD engine (that tensor-core engine's TMA copies address device memory
+ * only); at p = 4096 .. 32768 the tensor-core engine reads and writes the
+ * array with plain loads and stores and serves it.  Results are
  * bit-identical to the device-resident array.
  * Errors: MPDET_EINVAL (N < 1, unsupported p, unknown flag, out == NULL),
  * MPDET_ENOMEM, MPDET_ECUDA. */
@@ -226,15 +228,22 @@ int64_t mpdet_steps_done(mpdet_t h);
  * IMAD Schur-update kernel: value v in 0..3 compiles it for at least 3 + v
  * resident 128-thread blocks per SM.  MPDET_TUNE_ENGINE selects how the
  * update forms its products: 1 (default) on the tensor cores as an exact
- * digit convolution where that engine exists (p = 512, 1024, 2048),
- * warp-specialised so that the tensor core, the rounding and the subtraction
- * overlap; 2 the same one phase at a time (p = 2048 only); 0 with IMAD limb
- * products everywhere (always for a p that runs in a larger frame).
+ * digit convolution where an engine exists for p: at p = 512, 1024, 2048
+ * 8-bit digits of both operands, warp-specialised so that the tensor core,
+ * the rounding and the subtraction overlap; at p = 4096, 8192, 16384, 32768
+ * 8-bit digits of the multiplier against 4-bit digits of the pivot-row
+ * element (every column sum exact in fp32 over the whole mantissa), only the
+ * upper half of each product formed when the lower half cannot change its
+ * rounding, else that product recomputed exactly; 2 the p = 2048 engine one
+ * phase at a time (p = 2048 only); 0 with IMAD limb products everywhere
+ * (always for a p that runs in a larger frame, and in ball mode).  The
+ * large-precision engine allocates, on its first use by a handle, N p / 4
+ * bytes for the multipliers' digits and 32 p bytes per SM for staged products.
  * MPDET_TUNE_TC_MIN_ROWS (value >= 0): an update launch
  * of fewer rows than this takes the IMAD kernel even when the tensor engine is
  * selected (its tiles are 128 rows high).  By default the threshold follows the
- * precision: 64 rows at p = 2048, and the IMAD kernel always at p = 512 and
- * 1024, where it measured faster at every size.  MPDET_TUNE_LOOKAHEAD:
+ * precision: 64 rows at p = 2048 and at p = 4096 .. 32768, and the IMAD
+ * kernel always at p = 512 and 1024, where it measured faster at every size.  MPDET_TUNE_LOOKAHEAD:
  * 1 (default) overlaps the pivot and multipliers of step k+1 with the update
  * of step k: a second stream owned by the handle updates column k+1 first and
  * runs them while the handle's stream updates the other columns; 0 runs each

@@ -140,6 +140,17 @@ bool tc_supports(int p, int pipelined);
 cudaError_t update_tc(MpArr X, const UpdArgs& a, MpArr Z, int* status, int p, int nsm, cudaStream_t st,
                       int pipelined);
 
+// Tensor-core engine of the rank-1 update for p = 4096 .. 32768 (tc_large.cu):
+// 8-bit digits of z against 4-bit digits of b, the multipliers' digits
+// precomputed per launch into zd (tcl_zd_bytes(N, p) bytes), the staged
+// products in slab (tcl_slab_bytes(nsm, p) bytes).  nsm: the SMs the launch
+// may fill (one block each).
+bool tcl_supports(int p);
+size_t tcl_zd_bytes(int64_t N, int p);
+size_t tcl_slab_bytes(int nsm, int p);
+cudaError_t update_tcl(MpArr X, const UpdArgs& a, MpArr Z, int* status, int p, int nsm, cudaStream_t st, void* zd,
+                       uint32_t* slab);
+
 // Kernel set for n = p/32 limbs, or nullptr if this n is not instantiated.
 const KernelSet* kernel_set_for(int n);
 

@@ -58,7 +58,11 @@ struct mpdet_ctx {
   size_t stage_bytes = 0;
   int64_t k_done = 0;
   int upd_variant = 1;
-  int engine = 1;  // 1: tensor cores, pipelined (p = 512..2048); 2: tensor cores, one role at a time; 0: IMAD
+  int engine = 1;  // 1: tensor cores, pipelined (p = 512..2048; 4096..32768); 2: tensor cores, one role at a time; 0: IMAD
+  // large-precision tensor engine: the multipliers' digits and the staged
+  // products (allocated on first use)
+  void* zd = nullptr;
+  uint32_t* slab = nullptr;
   int64_t tc_min_rows = -1;  // shorter update launches take the IMAD kernel; -1: per precision
   // look-ahead: the side stream updates column k+1 and runs the pivot and the
   // multipliers of step k+1 while the handle's stream updates the rest of
@@ -267,6 +271,8 @@ extern "C" int mpdet_free(mpdet_t h) {
   if (h->status) cudaFree(h->status);
   if (h->zero_k) cudaFree(h->zero_k);
   if (h->stage) cudaFree(h->stage);
+  if (h->zd) cudaFree(h->zd);
+  if (h->slab) cudaFree(h->slab);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   if (h->ev_mult) cudaEventDestroy(h->ev_mult);
   if (h->ev_rest) cudaEventDestroy(h->ev_rest);
@@ -397,7 +403,18 @@ static int next_event(mpdet_t h, cudaEvent_t* ev) {
 // p = 2048; at p = 512 and 1024 the IMAD kernel measured faster at every
 // size (whole eliminations, lastcol mode, N = 256 .. 2048), so it takes all
 // launches there unless the threshold is set.
-static int64_t tc_default_min_rows(int p) { return p == 2048 ? 64 : INT64_MAX; }
+static int64_t tc_default_min_rows(int p) { return (p == 2048 || mpd::tcl_supports(p)) ? 64 : INT64_MAX; }
+
+// Large-precision tensor engine (p = 4096 .. 32768) for an update launch of
+// `rows` rows?  It reads and writes the array with plain loads and stores (its
+// TMA copies read only its own digit buffer), so a host-resident array is
+// served too.
+static bool use_tcl(mpdet_t h, int64_t rows) {
+  if (h->pad) return false;                 // it rounds at the frame's own precision only
+  if (h->flags & MPDET_BALL) return false;  // radii are kept by the IMAD kernels
+  const int64_t thr = h->tc_min_rows >= 0 ? h->tc_min_rows : tc_default_min_rows(h->p);
+  return h->engine >= 1 && mpd::tcl_supports(h->p) && rows >= thr;
+}
 
 // Tensor engine for an update launch of `rows` rows?
 static bool use_tc(mpdet_t h, int64_t rows) {
@@ -432,12 +449,23 @@ static mpd::UpdateFn imad_update(mpdet_t h) {
 // exists, the rest on the IMAD kernel.  nsm: SMs the launch may fill.
 static int launch_update(mpdet_t h, MpArr A, const UpdArgs& a, MpArr Z, int nsm, cudaStream_t st) {
   if (a.nrows <= 0 || a.ncols <= 0) return MPDET_OK;
-  if (a.ncols == 1)
+  if (a.ncols == 1) {
     CU(h, h->ks->update_col(A, a, Z, h->status, h->p, st));
-  else if (use_tc(h, a.nrows))
+  } else if (use_tcl(h, a.nrows)) {
+    if (!h->zd) {
+      const size_t zb = mpd::tcl_zd_bytes(h->N, h->p);
+      if (cudaMalloc(&h->zd, zb) != cudaSuccess) return fail(h, MPDET_ENOMEM, "digit buffer of %zu bytes", zb);
+      CU(h, cudaMemsetAsync(h->zd, 0, zb, st));
+    }
+    if (!h->slab && cudaMalloc(&h->slab, mpd::tcl_slab_bytes(h->nsm, h->p)) != cudaSuccess)
+      return fail(h, MPDET_ENOMEM, "product slab of %zu bytes", mpd::tcl_slab_bytes(h->nsm, h->p));
+    CU(h, mpd::update_tcl(A, a, Z, h->status, h->p, nsm, st, h->zd, h->slab));
+    h->launches += 1;  // the digit kernel
+  } else if (use_tc(h, a.nrows)) {
     CU(h, mpd::update_tc(A, a, Z, h->status, h->p, nsm, st, h->engine == 1 ? 1 : 0));
-  else
+  } else {
     CU(h, imad_update(h)(A, a, Z, h->status, h->p, nsm, st));
+  }
   h->launches += 1;
   return MPDET_OK;
 }
