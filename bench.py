@@ -435,6 +435,7 @@ def cauchy_bit_loss(x, y, D, p: int, every: int = 64):
     sgn, ex, limbs = D
     n = p // 32
     out, ks, ls = [], [], []
+    min_bits = (float(p + 1), 0)
     for k in range(1, len(x) + 1):
         i = k - 1
         nm, ne = num
@@ -465,6 +466,8 @@ def cauchy_bit_loss(x, y, D, p: int, every: int = 64):
             else:
                 rel = math.log2(abs(diff[0])) + diff[1] - (math.log2(num[0]) + num[1])
                 bits = max(0.0, -rel)
+        if bits < min_bits[0]:
+            min_bits = (bits, k)
         if k == 1 or k % every == 0 or k == len(x):
             out.append({"k": k, "bits": round(bits, 1), "loss": round(p - bits, 1)})
         if bits > 16:
@@ -479,7 +482,8 @@ def cauchy_bit_loss(x, y, D, p: int, every: int = 64):
         sxx = sum((a - kb) ** 2 for a in ks)
         slope = sum((a - kb) * (b - lb) for a, b in zip(ks, ls)) / sxx if sxx else None
     return {"per_k": out, "bits_per_row": None if slope is None else round(slope, 3),
-            "fit_range": [ks[0], ks[-1]] if ks else None}
+            "fit_range": [ks[0], ks[-1]] if ks else None,
+            "min_bits": round(min_bits[0], 1), "min_bits_k": min_bits[1]}
 
 
 def _primes_below(limit: int, count: int):
@@ -576,72 +580,94 @@ def integer_bit_loss(A, D, p: int, kmax: int = 256, every: int = 32):
     return {"per_k": out, "bits_per_row": None if slope is None else round(slope, 3)}
 
 
+def tcl_mma_macs_per_product(p: int) -> int:
+    """bf16 multiply-accumulates the large-precision tensor engine issues per
+    product at p = 4096 .. 32768 (its tile K ranges; the lower half of the
+    convolution below 32 limbs under the rounding point is not formed).  The
+    schoolbook count of the same 8-bit x 4-bit convolution is 32 n^2."""
+    n = p // 32
+    KD, KB, R0, T = 4 * n, 8 * n, 8 * n - 256, n // 32 + 1
+    tot = 0
+    for tau in range(T):
+        rho = R0 + 256 * tau
+        lo = (KD - 1 - min((rho + 255) // 2, KD - 1)) // 16
+        hi = (KD - 1 - ((rho - KB + 1) // 2 if rho > KB else 0)) // 16 + 1
+        tot += (hi - lo) * 16 * 256
+    return tot
+
+
 def bench_large(args, dev, m, peak_macs):
     """Workload C5 at full size: Cauchy N = 4096, p = 32768 (1024 limbs,
-    68.9 GB in HBM), det and leading minors.  The whole factorisation takes
-    about an hour, so a window of its heaviest steps is timed (the matrix is
-    generated on the device, step 1 runs untimed as warm-up, steps 2..1+w are
-    timed with CUDA events on the handle's stream); the Schur-update launches
-    inside the window are timed one by one against the integer-multiply peak."""
+    68.9 GB in HBM), det and leading minors.  A window of its heaviest steps
+    is timed here (the matrix is generated on the device, step 1 runs untimed
+    as warm-up, steps 2..1+w are timed with CUDA events on the handle's
+    stream) on the tensor-core engine, and two steps on the IMAD engine with
+    schoolbook and with Karatsuba products for comparison; the whole run is
+    bench.py --large-full.  The Schur-update launches inside the window are
+    timed one by one against the tensor and integer-multiply peaks."""
     import torch
 
     cfg = W.C5
-    N, p, w = cfg["N"], cfg["p"], 2
+    N, p, w = cfg["N"], cfg["p"], 8
     n = p // 32
     x, y = W.cauchy_xy(N, cfg["seed"])
     st = torch.cuda.current_stream(dev)
-    h = m.Mpdet(N, p, lastcol=False, stream=st.cuda_stream)
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    h.set_cauchy(x, y)
-    torch.cuda.synchronize(dev)
-    t_gen = time.perf_counter() - t0
-    h.factor_range(0, 1)
-    torch.cuda.synchronize(dev)
-    h.profile(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(st)
-    h.factor_range(1, 1 + w)
-    e1.record(st)
-    torch.cuda.synchronize(dev)
-    pr = h.profile_read()
-    h.profile(False)
-    ms = e0.elapsed_time(e1)
-    assert h.status()[0] == 0
-    h.close()
-    # the same two steps with the update's products by one Karatsuba level
-    hk = m.Mpdet(N, p, lastcol=False, stream=st.cuda_stream)
-    hk.tune(karatsuba=True)
-    hk.set_cauchy(x, y)
-    hk.factor_range(0, 1)
-    torch.cuda.synchronize(dev)
-    e0.record(st)
-    hk.factor_range(1, 1 + w)
-    e1.record(st)
-    torch.cuda.synchronize(dev)
-    ms_kara = e0.elapsed_time(e1)
-    assert hk.status()[0] == 0
-    hk.close()
+
+    def window(engine, steps, karatsuba=False, profile=False):
+        h = m.Mpdet(N, p, lastcol=False, stream=st.cuda_stream)
+        h.tune(engine=engine, karatsuba=karatsuba)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        h.set_cauchy(x, y)
+        torch.cuda.synchronize(dev)
+        tg = time.perf_counter() - t0
+        h.factor_range(0, 1)
+        torch.cuda.synchronize(dev)
+        if profile:
+            h.profile(True)
+        e0.record(st)
+        h.factor_range(1, 1 + steps)
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        pr = h.profile_read() if profile else None
+        assert h.status()[0] == 0
+        h.close()
+        return e0.elapsed_time(e1), tg, pr
+
+    ms, t_gen, pr = window(1, w, profile=True)
+    ms_imad, _, _ = window(0, 2)
+    ms_kara, _, _ = window(0, 2, karatsuba=True)
     prods = sum((N - k - 1) ** 2 + (N - k - 1) + 1 for k in range(1, 1 + w))
+    prods2 = sum((N - k - 1) ** 2 + (N - k - 1) + 1 for k in range(1, 3))
     rate = prods * n * n / (ms / 1e3)
     upd = pr["update_limb_macs"] / (pr["update_ms"] / 1e3)
+    # tensor roofline of the update kernel: the bf16 MMA work it issues per
+    # product against the measured sustained bf16 rate (a kernel inside a
+    # long step)
+    mma_flops = 2.0 * tcl_mma_macs_per_product(p) * (pr["update_limb_macs"] / (n * n))
+    tflops = mma_flops / (pr["update_ms"] / 1e3) / 1e12
+    try:
+        tpeak = float(measured_peaks()["bf16_tflops_sustained"])
+    except Exception:
+        tpeak = 1700.0
     total = elim_products(N, False) * n * n
     # Whole-run projection: a step's cost depends on its trailing size R =
     # N - k - 1 (and p), not on the steps before it, so steps of smaller
     # leading blocks of the same matrix stand in for the late steps of the
     # full run; the step time is interpolated linearly between the sampled R
     # (in R^2, the work) and summed over R = 0..N-1.
-    samples = [(N - 2, ms / w)]
+    samples = [(N - 1 - (1 + w) / 2, ms / w)]
     for Rs in (2048, 1024, 512, 256, 128, 64, 16):
         Ns = Rs + 2
         hs = m.Mpdet(Ns, p, lastcol=False, stream=st.cuda_stream)
         hs.set_cauchy(x[:Ns], y[:Ns])
         hs.factor_range(0, 1)
         e0.record(st)
-        hs.factor_range(1, 1 + w)
+        hs.factor_range(1, 3)
         e1.record(st)
         torch.cuda.synchronize(dev)
-        samples.append((Rs, e0.elapsed_time(e1) / w))
+        samples.append((Rs, e0.elapsed_time(e1) / 2))
         hs.close()
     samples.sort()
     rs = np.array([s_[0] for s_ in samples], dtype=np.float64)
@@ -650,11 +676,20 @@ def bench_large(args, dev, m, peak_macs):
     t_all = np.interp(Rall ** 2, rs ** 2, ts, left=ts[0])  # ms per step at trailing size R
     proj_s = float(t_all.sum()) / 1e3
     return {"workload": f"Cauchy N={N} p={p} (68.9 GB in HBM), det + leading minors: steps 2..{1 + w} "
-                        "timed (the heaviest; one full run is about an hour)",
+                        "timed (the heaviest; bench.py --large-full runs them all)",
+            "engine": "tensor (8-bit x 4-bit digit convolution on tcgen05)",
             "window_ms": ms, "limb_macs_per_s": rate, "frac_of_imad_peak": rate / peak_macs,
-            "karatsuba_window_ms": ms_kara, "karatsuba_speedup": ms / ms_kara,
-            "update_kernel": {"achieved": upd / 1e12, "peak": peak_macs / 1e12, "unit": "Tlimb-MAC/s",
-                              "frac": upd / peak_macs, "launches": int(pr["update_launches"])},
+            "imad_window_ms_2_steps": ms_imad, "imad_limb_macs_per_s": prods2 * n * n / (ms_imad / 1e3),
+            "imad_karatsuba_window_ms_2_steps": ms_kara,
+            "imad_karatsuba_limb_macs_per_s": prods2 * n * n / (ms_kara / 1e3),
+            "tensor_vs_imad": (prods * n * n / (ms / 1e3)) / (prods2 * n * n / (ms_imad / 1e3)),
+            "update_kernel": {"kernel": "k_update_tcl<1024>", "achieved": upd / 1e12, "peak": peak_macs / 1e12,
+                              "unit": "Tlimb-MAC/s", "frac": upd / peak_macs, "launches": int(pr["update_launches"]),
+                              "tensor": {"achieved": tflops, "peak": tpeak, "unit": "TFLOP/s",
+                                         "frac": tflops / tpeak,
+                                         "basis": "bf16 MMA flops issued (tcl_mma_macs_per_product x 2 per "
+                                                  "product) / CUDA-event time, against MEASURED_PEAKS "
+                                                  "bf16_tflops_sustained (of measured)"}},
             "cauchy_generation_s": t_gen,
             "step_ms_by_trailing_size": {str(int(a)): round(b, 3) for a, b in samples},
             "projected_full_factorisation_s": proj_s,
@@ -738,13 +773,51 @@ def run_large_full(args):
            "frac_of_imad_peak": total / (total_ms / 1e3) / peak,
            "peak_basis": f"{props.multi_processor_count} SMs x 32 limb-MAC/clk x {smax:.0f} MHz",
            "update_kernel": {"ms": upd_ms, "limb_macs_per_s": upd_macs / (upd_ms / 1e3),
-                             "frac": upd_macs / (upd_ms / 1e3) / peak},
+                             "frac": upd_macs / (upd_ms / 1e3) / peak,
+                             "tensor_tflops": 2.0 * tcl_mma_macs_per_product(p) * upd_macs / (n * n) / (upd_ms / 1e3)
+                             / 1e12 if p >= 4096 else None,
+                             "tensor_frac_of_sustained_bf16": 2.0 * tcl_mma_macs_per_product(p) * upd_macs / (n * n)
+                             / (upd_ms / 1e3) / 1e12 / float(measured_peaks().get("bf16_tflops_sustained", 1700.0))
+                             if p >= 4096 else None},
            "window_steps": args.window, "windows": windows, "clock_reasons_seen": reasons,
            "update_products": "karatsuba (one level)" if args.karatsuba else "schoolbook",
            "sm_mhz_median_of_windows": statistics.median([w["sm_mhz"] for w in windows if w["sm_mhz"]] or [0]),
            "saved": args.save}
     print(json.dumps(out))
     return 0 if rc == 0 else 1
+
+
+def check_large(path: str, lead: int = 256):
+    """Host checks of the leading minors saved by --large-full (no GPU):
+    D_1..D_lead against the digests the CPU oracle wrote for the leading
+    lead x lead block (tests/golden/c5_cauchy_lead256_p32768.txt; the
+    leading minors of a matrix depend only on its leading block), and every
+    D_k against the closed-form Cauchy determinant (correct bits per k, the
+    fewest over all k, the loss in bits per row)."""
+    sys.path.insert(0, os.path.join(ROOT, "tests", "golden"))
+    import fullsize as F
+
+    z = np.load(path)
+    D = (z["sign"], z["exp"], z["limbs"])
+    cfg = W.C5
+    N, p = len(D[0]), cfg["p"]
+    x, y = W.cauchy_xy(cfg["N"], cfg["seed"])
+    x, y = x[:N], y[:N]
+    out = {"what": f"leading minors of the saved run ({path}), N = {N}, p = {p}"}
+    try:
+        want = [r[1] for r in F.read("c5")["D"]]
+        got = F.num_digests((D[0][:lead], D[1][:lead], D[2][:lead]))
+        bad = F.first_mismatch(got, want[:lead])
+        out["oracle_leading"] = {"k": [1, lead], "bit_exact": bad is None,
+                                 "first_mismatch_k": None if bad is None else bad + 1}
+    except FileNotFoundError:
+        out["oracle_leading"] = {"skipped": "no stored oracle values"}
+    t0 = time.perf_counter()
+    out["closed_form"] = cauchy_bit_loss(x, y, D, p, every=256)
+    out["closed_form_s"] = time.perf_counter() - t0
+    print(json.dumps(out))
+    ok = out["oracle_leading"].get("bit_exact", True) and out["closed_form"]["min_bits"] > 0
+    return 0 if ok else 1
 
 
 def bench_hostmem(args, dev, m, peak_macs):
@@ -1039,6 +1112,8 @@ def main():
     ap.add_argument("--p", type=int, default=0, help="profiling aid: override p (default: the workload's 2048)")
     ap.add_argument("--update-variant", type=int, default=-1, help="tuning aid: Schur-update register budget 0..3")
     ap.add_argument("--engine", type=int, default=-1, help="tuning aid: 0 IMAD, 1 tensor pipelined, 2 tensor serial")
+    ap.add_argument("--check-large", default="", metavar="NPZ",
+                    help="host checks (no GPU) of the leading minors a --large-full run saved")
     ap.add_argument("--large-full", action="store_true",
                     help="the whole N=4096 p=32768 factorisation in timed windows (about an hour); not the bench line")
     ap.add_argument("--window", type=int, default=64, help="--large-full: steps per timed window")
@@ -1051,6 +1126,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.check_large:
+        return check_large(args.check_large)
     if args.large_full:
         return run_large_full(args)
     return run_gpu(args)

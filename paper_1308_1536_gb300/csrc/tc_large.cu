@@ -15,8 +15,12 @@
 // at most KD terms in [-1016, 1024], so c_r lies in [-1016 KD, 1024 KD]: a
 // window narrower than 2^23 at every n <= 1024, exact in fp32, and adding
 // kMagic = 2^23 + 1016 KD puts it in [2^23, 2^24) where the fp32 bits are
-// 0x4B000000 + (c_r + 1016 KD).  The 2^p m_b term is added to the limbs by
-// the epilogue.
+// 0x4B000000 + (c_r + 1016 KD).  The MMA adds kMagic itself: one more K step
+// per tile, issued after the digit steps, multiplies a constant A with ones
+// in two columns by a constant B holding 2^23 and 1016 KD (both exact in
+// bf16); every partial sum before it is an integer below 2^23 in magnitude,
+// the final one lies in [2^23, 2^24), so all of them are exact.  The 2^p m_b
+// term is added to the limbs by the epilogue.
 //
 // GEMM shape, per block of M = 128 rows i and one column j: D[i][r] =
 // sum_k' A[i][k'] B[k'][r], K reversed (k' = KD - 1 - s):
@@ -61,11 +65,21 @@ namespace tcl {
 constexpr int M = 128;       // rows per block (MMA M)
 constexpr int NT = 256;      // positions per tile (MMA N)
 constexpr int STAGES = 4;    // ring depth
-constexpr int NCORE = 80;    // B cores per stage (78 are read)
+constexpr int NCORE = 80;    // B cores in a stage's window (78 are read)
+// The B cores live in a sliding ring of RING cores plus a mirror of its first
+// NCORE: a stage's window is RING-contiguous from its start slot; within a
+// pass each stage's window starts 16 cores after the previous one's (the next
+// 64 are shared), so a stage builds 16 new cores, the first stage of a pass
+// all 80.  The window start advances by 16 per stage and by 80 after a pass's
+// last stage; the builders of stage g wait for stage g - STAGES to complete,
+// so stages g-STAGES+1 .. g-1 are the only ones in flight, and the cores
+// stage g writes lie less than STAGES * 80 = RING cores after the first core
+// of stage g-STAGES+1's window: no core still to be read is overwritten.
+constexpr int RING = STAGES * 80;
 constexpr int NTH = 384;
 constexpr int LIMIT = 1 << 22;
 constexpr uint32_t A_BYTES = M * 64 * 2;   // 128 rows x 64 digits (bf16)
-constexpr uint32_t B_BYTES = NCORE * 128;
+constexpr uint32_t B_BYTES = (RING + NCORE) * 128;
 
 template <int n>
 struct Cfg {
@@ -83,13 +97,16 @@ struct Cfg {
   static constexpr int kOff = 1016 * KD;
   static constexpr int OFF_A = 0;
   static constexpr int OFF_B = OFF_A + STAGES * (int)A_BYTES;
-  static constexpr int OFF_F = OFF_B + STAGES * (int)B_BYTES;          // two bf16 parity arrays
+  static constexpr int OFF_F = OFF_B + (int)B_BYTES;                   // two bf16 parity arrays
   static constexpr int OFF_SCR = OFF_F + (2 * FL * 2 + 15) / 16 * 16;  // subtraction scratch
   static constexpr int OFF_META = OFF_SCR + NGRP * SW * 4;            // 2 x 128 x 32 bytes
-  static constexpr int OFF_BAR = OFF_META + 2 * M * 32;
-  static constexpr int SMEM = OFF_BAR + 256;
+  static constexpr int OFF_ONE = OFF_META + 2 * M * 32;  // A of the bias step: 2 k-cores x 16 m-cores
+  static constexpr int OFF_BIAS = OFF_ONE + 4096;        // B of the bias step: 2 k-cores x 32 n-cores
+  static constexpr int OFF_BAR = OFF_BIAS + 8192;
+  static constexpr int SMEM = OFF_BAR + 8 * (3 * STAGES + 10);
   static_assert(SMEM <= 227 * 1024, "shared memory");
   static_assert((long long)KD * 2040 < (1ll << 23), "column sums exact with the magic bias");
+  static_assert(OFF_ONE % 16 == 0 && OFF_BAR % 16 == 0, "alignment");
   // MMA K steps (16 reversed digits) that meet tile tau's positions
   // [rho, rho + 256): s from max(0, ceil((rho - KB) / 2)) to
   // min(KD - 1, floor((rho + 255) / 2))
@@ -188,6 +205,28 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
                  "+r"(v[30]), "+r"(v[31]));
 }
 
+// 32 columns without waiting: the registers are valid after tmem_wait(v)
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+        "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+}
+// wait for this thread's tensor-memory loads; v is named so that no use of it
+// moves above the wait
+__device__ __forceinline__ void tmem_wait(uint32_t (&v)[32]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]),
+                 "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15]),
+                 "+r"(v[16]), "+r"(v[17]), "+r"(v[18]), "+r"(v[19]), "+r"(v[20]), "+r"(v[21]), "+r"(v[22]),
+                 "+r"(v[23]), "+r"(v[24]), "+r"(v[25]), "+r"(v[26]), "+r"(v[27]), "+r"(v[28]), "+r"(v[29]),
+                 "+r"(v[30]), "+r"(v[31]));
+}
+
 // bf16 bits of a small integer (|e| <= 256: exact)
 __device__ __forceinline__ uint32_t bfi(int e) { return __float_as_uint((float)e) >> 16; }
 
@@ -243,13 +282,15 @@ __global__ void __launch_bounds__(NTH, 1) k_update_tcl(MpArr X, UpdArgs a, MpArr
     return;
   }
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + C::OFF_BAR);
-  // 0-3 afull, 4-7 bfull, 8-11 empty, 12 tfull, 13 tempty, 14-15 sfull, 16-17 sfree, 18 mdone,
-  // 19: tensor-memory address (u32), 20: error flag
-  const uint32_t b_afull = su32(&bars[0]), b_bfull = su32(&bars[4]), b_empty = su32(&bars[8]);
-  const uint32_t b_tfull = su32(&bars[12]), b_tempty = su32(&bars[13]), b_sfull = su32(&bars[14]),
-                 b_sfree = su32(&bars[16]), b_mdone = su32(&bars[18]);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(&bars[19]);
-  volatile int* eflag = reinterpret_cast<volatile int*>(&bars[20]);
+  // [0, S) afull, [S, 2S) bfull, [2S, 3S) empty (S = STAGES); then tfull, tempty (tensor-memory
+  // half 0), tempty1 (half 1), sfull x 2, sfree x 2, mdone, the tensor-memory address (u32) and
+  // the error flag
+  constexpr int S3 = 3 * STAGES;
+  const uint32_t b_afull = su32(&bars[0]), b_bfull = su32(&bars[STAGES]), b_empty = su32(&bars[2 * STAGES]);
+  const uint32_t b_tfull = su32(&bars[S3]), b_tempty = su32(&bars[S3 + 1]), b_tempty1 = su32(&bars[S3 + 2]);
+  const uint32_t b_sfull = su32(&bars[S3 + 3]), b_sfree = su32(&bars[S3 + 5]), b_mdone = su32(&bars[S3 + 7]);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(&bars[S3 + 8]);
+  volatile int* eflag = reinterpret_cast<volatile int*>(&bars[S3 + 9]);
   Meta* meta = reinterpret_cast<Meta*>(sm + C::OFF_META);
   uint16_t* F0 = reinterpret_cast<uint16_t*>(sm + C::OFF_F);  // f~(2u), u = index - OFFU
   uint16_t* F1 = F0 + C::FL;                                  // f~(2u + 1)
@@ -263,6 +304,15 @@ __global__ void __launch_bounds__(NTH, 1) k_update_tcl(MpArr X, UpdArgs a, MpArr
 
   // ---- set-up --------------------------------------------------------------
   for (int q = tid; q < 2 * C::FL; q += NTH) F0[q] = 0;  // zero padding around the digits
+  // the bias step: A rows (1, 1, 0, ...) in k-core 0; B rows 2^23 and 1016 KD
+  // at every position in k-core 0; k-core 1 of both zero
+  for (int q = tid; q < (4096 + 8192) / 16; q += NTH) {
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (q < 128) v.x = 0x3F803F80u;                                              // A: 1.0, 1.0
+    else if (q >= 256 && q < 256 + 256) v.x = 0x4B00u | (bfi(C::kOff) << 16);    // B: 2^23, kOff
+    reinterpret_cast<uint4*>(sm + C::OFF_ONE)[q] = v;
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   if (tid == 0) {
     for (int s = 0; s < STAGES; ++s) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b_afull + 8 * s));
@@ -271,6 +321,7 @@ __global__ void __launch_bounds__(NTH, 1) k_update_tcl(MpArr X, UpdArgs a, MpArr
     }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b_tfull));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(b_tempty));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(b_tempty1));
     for (int b = 0; b < 2; ++b) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(b_sfull + 8 * b));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(b_sfree + 8 * b));
@@ -325,17 +376,22 @@ __global__ void __launch_bounds__(NTH, 1) k_update_tcl(MpArr X, UpdArgs a, MpArr
     if (lane == 0) {
       const uint32_t idesc =
           (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-      int64_t g = 0, pg = 0;
+      int64_t g = 0;
+      int wpos = 0;                  // ring slot of the current stage's window
+      int64_t uses0 = 0, uses1 = 0;  // passes that used tensor-memory half 0 / 1 so far
       bool ok = true;
+      const uint64_t ad_one = desc(su32(sm + C::OFF_ONE), 2048, 128);
+      const uint64_t bd_bias = desc(su32(sm + C::OFF_BIAS), 4096, 128);
       for (int64_t q = q0; q < q1 && ok; ++q)
-        for (int pi = 0; pi < C::NPASS && ok; ++pi, ++pg) {
-          if (pg >= 1 && !wait_bar(b_tempty, (uint32_t)((pg - 1) & 1))) ok = false;
-          if (!ok || *eflag) {
+        for (int pi = 0; pi < C::NPASS && ok; ++pi) {
+          if (*eflag) {
             ok = false;
             break;
           }
-          asm volatile("tcgen05.fence::after_thread_sync;");
           const int nt = C::ntile(pi);
+          // a half is free once the epilogue has read the previous pass's
+          // sums from it; the two halves are waited for separately, so that
+          // the MMAs into half 0 start while half 1 is still being read
           bool started0 = false, started1 = false;
           for (int sg = C::sg_lo(pi); sg < C::sg_hi(pi); ++sg, ++g) {
             const int slot = (int)(g % STAGES);
@@ -346,12 +402,22 @@ __global__ void __launch_bounds__(NTH, 1) k_update_tcl(MpArr X, UpdArgs a, MpArr
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint32_t aS = su32(sm + C::OFF_A + slot * A_BYTES);
-            const uint32_t bS = su32(sm + C::OFF_B + slot * B_BYTES);
+            const uint32_t bS = su32(sm + C::OFF_B + wpos * 128);
+            wpos += sg + 1 < C::sg_hi(pi) ? 16 : NCORE;
+            if (wpos >= RING) wpos -= RING;
             for (int t = 0; t < nt; ++t) {
               const int tau = 2 * pi + t;
               const int lo = C::ks_lo(tau) > 4 * sg ? C::ks_lo(tau) : 4 * sg;
               const int hi = C::ks_hi(tau) < 4 * sg + 4 ? C::ks_hi(tau) : 4 * sg + 4;
               bool& started = t ? started1 : started0;
+              if (lo < hi && !started) {
+                const int64_t u = t ? uses1 : uses0;
+                if (u >= 1 && !wait_bar(t ? b_tempty1 : b_tempty, (uint32_t)((u - 1) & 1))) {
+                  ok = false;
+                  break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+              }
               for (int ks = lo; ks < hi; ++ks) {
                 const uint64_t ad = desc(aS + 4096u * (uint32_t)(ks - 4 * sg), 2048, 128);
                 const uint64_t bd = desc(bS + 128u * (uint32_t)(32 * t + 4 * (ks - 4 * sg)), 256, 128);
@@ -362,11 +428,20 @@ __global__ void __launch_bounds__(NTH, 1) k_update_tcl(MpArr X, UpdArgs a, MpArr
                 started = true;
               }
             }
+            if (!ok) break;
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                 b_empty + 8 * slot));
           }
           if (!ok) break;
+          // the bias step, last into each tile of the pass
+          for (int t = 0; t < nt; ++t)
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, "
+                "p;\n}" ::"r"(tmem + (uint32_t)(NT * t)),
+                "l"(ad_one), "l"(bd_bias), "r"(idesc), "r"(1u));
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(b_tfull));
+          uses0 += 1;
+          if (nt == 2) uses1 += 1;
         }
       if (!ok) *eflag = 1;
       // every MMA issued has completed before the tensor memory is freed
@@ -378,6 +453,7 @@ __global__ void __launch_bounds__(NTH, 1) k_update_tcl(MpArr X, UpdArgs a, MpArr
     // ================= builders: B cores ==================================
     const int bt = tid - 64;
     int64_t g = 0;
+    int wpos = 0;  // ring slot of the current stage's window
     bool stop = false;
     for (int64_t q = q0; q < q1 && !stop; ++q) {
       const int64_t kj = a.brow * N + upd_col(a, q % ncols);
@@ -428,12 +504,15 @@ __global__ void __launch_bounds__(NTH, 1) k_update_tcl(MpArr X, UpdArgs a, MpArr
             stop = true;
             break;
           }
-          // core d = d0 + dl, row rr: f~(8d + rr + 2kk - 2KD + 2), kk = 0..7,
-          // = F_{rr & 1}[u0 + kk] with u0 = 4d + (rr >> 1) - KD + 1
-          unsigned char* B = sm + C::OFF_B + slot * B_BYTES;
+          // core d = d0 + dl of the window, row rr: f~(8d + rr + 2kk - 2KD + 2),
+          // kk = 0..7, = F_{rr & 1}[u0 + kk] with u0 = 4d + (rr >> 1) - KD + 1;
+          // the first stage of a pass builds the whole window, the others its
+          // last 16 cores
+          unsigned char* Bring = sm + C::OFF_B;
           const int d0 = nc0 + 16 * sg;
-          for (int q2 = bt; q2 < NCORE * 8; q2 += 64) {
-            const int dl = q2 >> 3, rr = q2 & 7;
+          const int dl0 = sg == C::sg_lo(pi) ? 0 : NCORE - 16;
+          for (int q2 = bt; q2 < (NCORE - dl0) * 8; q2 += 64) {
+            const int dl = dl0 + (q2 >> 3), rr = q2 & 7;
             const int u0 = 4 * (d0 + dl) + (rr >> 1) - C::KD + 1;
             uint4 v = make_uint4(0u, 0u, 0u, 0u);
             if (u0 + 7 >= 0 && u0 <= C::KB / 2) {
@@ -441,8 +520,13 @@ __global__ void __launch_bounds__(NTH, 1) k_update_tcl(MpArr X, UpdArgs a, MpArr
               v = make_uint4((uint32_t)f[0] | ((uint32_t)f[1] << 16), (uint32_t)f[2] | ((uint32_t)f[3] << 16),
                              (uint32_t)f[4] | ((uint32_t)f[5] << 16), (uint32_t)f[6] | ((uint32_t)f[7] << 16));
             }
-            *reinterpret_cast<uint4*>(B + dl * 128 + rr * 16) = v;
+            int x = wpos + dl;
+            if (x >= RING) x -= RING;
+            *reinterpret_cast<uint4*>(Bring + x * 128 + rr * 16) = v;
+            if (x < NCORE) *reinterpret_cast<uint4*>(Bring + (x + RING) * 128 + rr * 16) = v;  // mirror
           }
+          wpos += sg + 1 < C::sg_hi(pi) ? 16 : NCORE;
+          if (wpos >= RING) wpos -= RING;
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // read by the tensor core
           bbar();
           if (bt == 0) arrive(b_bfull + 8 * slot);
@@ -454,7 +538,6 @@ __global__ void __launch_bounds__(NTH, 1) k_update_tcl(MpArr X, UpdArgs a, MpArr
     // ================= epilogue: one thread per row =======================
     const int r = tid - 128;
     const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-    const float kMagic = (float)(8388608 + C::kOff);
     const int64_t kOffL = (int64_t)C::kOff * 0x11111111ll;
     int64_t pg = 0, it = 0;
     bool ok = true;
@@ -485,28 +568,38 @@ __global__ void __launch_bounds__(NTH, 1) k_update_tcl(MpArr X, UpdArgs a, MpArr
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
         const int nch = 8 * C::ntile(pi);
-        for (int ch = 0; ch < nch; ++ch) {
-          uint32_t v[32];
-          tmem_ld32(tl + (uint32_t)(32 * ch), v);
-          if (ch == nch - 1) {  // the pass's sums are in registers: free the tensor memory
+        // chunk ch: 32 sums (4 limbs) whose fp32 bits are 0x4B000000 + u,
+        // u = c_r + kOff; the next chunk's load is in flight meanwhile
+        // b's limbs L - n of a chunk (zero below limb n), loaded a chunk ahead
+        auto blimbs = [&](const int ch) -> uint4 {
+          const int L0 = n - 32 + 64 * pi + 4 * ch;
+          return L0 >= n ? __ldg(reinterpret_cast<const uint4*>(bm + (L0 - n))) : make_uint4(0u, 0u, 0u, 0u);
+        };
+        uint4 bq = blimbs(0);
+        auto step = [&](const int ch, uint32_t(&cur)[32], uint32_t(&nxt)[32]) {
+          tmem_wait(cur);
+          const uint4 bc = bq;
+          if (ch + 1 < nch) {
+            tmem_ld32_async(tl + (uint32_t)(32 * (ch + 1)), nxt);
+            bq = blimbs(ch + 1);
+          }
+          const uint32_t bl[4] = {bc.x, bc.y, bc.z, bc.w};
+          if ((ch & 7) == 7) {  // a tile's sums are in registers: free its half of the tensor memory
             asm volatile("tcgen05.fence::before_thread_sync;");
             __syncwarp();
-            if (lane == 0) arrive(b_tempty);
+            if (lane == 0) arrive(ch == 7 ? b_tempty : b_tempty1);
           }
           const int L0 = n - 32 + 64 * pi + 4 * ch;  // first limb of the chunk
           uint32_t lim[4];
 #pragma unroll
           for (int l4 = 0; l4 < 4; ++l4) {
-            uint32_t u[8];
-#pragma unroll
-            for (int qq = 0; qq < 8; ++qq)
-              u[qq] = __float_as_uint(__fadd_rn(__uint_as_float(v[8 * l4 + qq]), kMagic)) & 0x7fffffu;
-            const uint32_t a01 = u[0] + (u[1] << 4), a23 = u[2] + (u[3] << 4);
-            const uint32_t a45 = u[4] + (u[5] << 4), a67 = u[6] + (u[7] << 4);
-            const uint64_t s = (uint64_t)a01 + ((uint64_t)a23 << 8) + ((uint64_t)a45 << 16) + ((uint64_t)a67 << 24);
-            acc += (int64_t)s - kOffL;
-            const int L = L0 + l4;
-            if (L >= n) acc += (int64_t)bm[L - n];  // 2^p m_b
+            const uint32_t* w = cur + 8 * l4;
+            // w0 + 16 w1 = u0 + 16 u1 + 17 * 0x4B000000, and 17 * 0x4B000000 =
+            // 0xFB000000 mod 2^32: adding 0x05000000 leaves u0 + 16 u1 < 2^28
+            const uint32_t a01 = w[0] + (w[1] << 4) + 0x05000000u, a23 = w[2] + (w[3] << 4) + 0x05000000u;
+            const uint32_t a45 = w[4] + (w[5] << 4) + 0x05000000u, a67 = w[6] + (w[7] << 4) + 0x05000000u;
+            const uint64_t sv = (uint64_t)a01 + ((uint64_t)a23 << 8) + ((uint64_t)a45 << 16) + ((uint64_t)a67 << 24);
+            acc += (int64_t)sv - kOffL + (int64_t)bl[l4];  // and 2^p m_b from limb n on
             lim[l4] = (uint32_t)acc;
             acc >>= 32;
           }
@@ -526,6 +619,13 @@ __global__ void __launch_bounds__(NTH, 1) k_update_tcl(MpArr X, UpdArgs a, MpArr
               }
             }
           }
+        };
+        uint32_t va[32], vb[32];
+        tmem_ld32_async(tl, va);
+#pragma unroll 1
+        for (int ch = 0; ch < nch; ch += 2) {
+          step(ch, va, vb);
+          step(ch + 1, vb, va);
         }
       }
       if (!ok) break;
@@ -557,13 +657,35 @@ __global__ void __launch_bounds__(NTH, 1) k_update_tcl(MpArr X, UpdArgs a, MpArr
       bool okw = wait_bar(b_sfull + 8 * buf, (uint32_t)((it >> 1) & 1)) && !*eflag;
       ok = __all_sync(FULL, okw);
       if (!ok) break;
+      // a row's staged product and x_ij; with 16 limbs per lane the next row's
+      // are loaded while this one is computed (registers allow it there)
+      constexpr bool PREF = W <= 16;
+      auto load_row = [&](const int rr, uint32_t(&f)[W], uint32_t(&x)[W], int8_t& xs_, int64_t& xe_) {
+        const int64_t i = i0 + rr;
+        const int64_t ij = (i < rend ? i : i0) * N + j;
+        load_slice_cg<W>(slab + ((size_t)(blockIdx.x * 2 + buf) * M + rr) * n + gp.g * W, f);
+        load_slice<W>(X.m + ij * n + gp.g * W, x);
+        xs_ = X.s[ij];
+        xe_ = X.e[ij];
+      };
+      uint32_t F[W], Xv[W];
+      int8_t xs = 0;
+      int64_t xe = 0;
+      if constexpr (PREF) load_row(grp, F, Xv, xs, xe);
       for (int rr = grp; rr < M; rr += C::NGRP) {
+        if constexpr (!PREF) load_row(rr, F, Xv, xs, xe);
         const int64_t i = i0 + rr;
         const bool active = i < rend;
+        const bool more = rr + C::NGRP < M;  // the same for every group of the warp
+        uint32_t Fn[PREF ? W : 1], Xn[PREF ? W : 1];
+        int8_t xsn = 0;
+        int64_t xen = 0;
+        if constexpr (PREF) {
+          if (more) load_row(rr + C::NGRP, Fn, Xn, xsn, xen);
+        }
         const Meta mt = meta[buf * M + rr];
         const bool used = mt.te != ZEXP;
-        uint32_t F[W], Mr[W];
-        load_slice_cg<W>(slab + ((size_t)(blockIdx.x * 2 + buf) * M + rr) * n + gp.g * W, F);
+        uint32_t Mr[W];
         int adj = round_product<W, G>(gp, F, mt.ltop, mt.sticky, Mr, 0);
         const bool unsafe = active && used && mt.unsafe != 0;
         if (__any_sync(FULL, unsafe)) {  // exact product by the IMAD engine
@@ -581,10 +703,6 @@ __global__ void __launch_bounds__(NTH, 1) k_update_tcl(MpArr X, UpdArgs a, MpArr
           for (int w = 0; w < W; ++w) Mr[w] = 0u;
         }
         const int64_t ij = (active ? i : i0) * N + j;
-        uint32_t Xv[W];
-        load_slice<W>(X.m + ij * n + gp.g * W, Xv);
-        int8_t xs = X.s[ij];
-        int64_t xe = X.e[ij];
         const int64_t te = used ? mt.te + adj : ZEXP;
         sub_round<W, G>(gp, p, xs, xe, Xv, used ? (int8_t)mt.ts : (int8_t)0, te, Mr, scr, 0);
         if (active) {
@@ -592,6 +710,17 @@ __global__ void __launch_bounds__(NTH, 1) k_update_tcl(MpArr X, UpdArgs a, MpArr
           if (gp.g == 0) {
             X.s[ij] = xs;
             X.e[ij] = xe;
+          }
+        }
+        if constexpr (PREF) {
+          if (more) {
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+              F[w] = Fn[w];
+              Xv[w] = Xn[w];
+            }
+            xs = xsn;
+            xe = xen;
           }
         }
       }
