@@ -787,6 +787,27 @@ def run_large_full(args):
     return 0 if rc == 0 else 1
 
 
+def factor_window(N: int, p: int, k1: int) -> int:
+    """Profiling aid: steps [0, k1) of the seeded Cauchy matrix of size N at
+    precision p, look-ahead off (each step: pivot, multipliers, one update
+    launch), on cuda:0.  Prints the status."""
+    import torch
+
+    import paper_1308_1536_gb300 as m
+
+    m.load()
+    x, y = W.cauchy_xy(N, 11)
+    h = m.Mpdet(N, p, lastcol=False)
+    h.tune(lookahead=0)
+    h.set_cauchy(x, y)
+    h.factor_range(0, k1)
+    torch.cuda.synchronize()
+    rc = h.status()
+    h.close()
+    print(json.dumps({"factor_window": [N, p, k1], "status": list(rc)}))
+    return 0 if rc[0] == 0 else 1
+
+
 def check_large(path: str, lead: int = 256):
     """Host checks of the leading minors saved by --large-full (no GPU):
     D_1..D_lead against the digests the CPU oracle wrote for the leading
@@ -1112,6 +1133,8 @@ def main():
     ap.add_argument("--p", type=int, default=0, help="profiling aid: override p (default: the workload's 2048)")
     ap.add_argument("--update-variant", type=int, default=-1, help="tuning aid: Schur-update register budget 0..3")
     ap.add_argument("--engine", type=int, default=-1, help="tuning aid: 0 IMAD, 1 tensor pipelined, 2 tensor serial")
+    ap.add_argument("--factor-window", type=int, nargs=3, metavar=("N", "P", "K1"),
+                    help="profiling aid: steps [0, K1) of the seeded N x N Cauchy matrix at p bits, look-ahead off")
     ap.add_argument("--check-large", default="", metavar="NPZ",
                     help="host checks (no GPU) of the leading minors a --large-full run saved")
     ap.add_argument("--large-full", action="store_true",
@@ -1128,6 +1151,8 @@ def main():
         return run_reference(args)
     if args.check_large:
         return check_large(args.check_large)
+    if args.factor_window:
+        return factor_window(*args.factor_window)
     if args.large_full:
         return run_large_full(args)
     return run_gpu(args)
