@@ -30,8 +30,8 @@
 //   B[k'][r] = f_{r + 2k' - 2KD + 2}(b_j): its 8 x 8 core matrices (k-core
 //     kc, n-core nc) depend only on d = nc + 2 kc, so one no-swizzle
 //     descriptor with leading offset 256 and stride offset 128 bytes reads
-//     them from a run of distinct cores, built per stage from b_j's digits
-//     (80 cores, 10 KB).
+//     them from a run of 78 distinct cores, kept in a sliding ring (below)
+//     and built from b_j's digits.
 // Lazy low half: only the positions r >= R0 = 8n - 256 are formed (the upper
 // n limbs of the product and 32 limbs below them), in T = n/32 + 1 tiles of
 // 256 positions, two tiles (all 512 tensor-memory columns) per pass.  The
@@ -44,8 +44,9 @@
 // Roles (384 threads, one block per SM, persistent over a range of (row
 // block, column) items):
 //   warp 0       TMA producer of the A stages (4-stage ring)
-//   warp 1       MMA issuer (one thread)
-//   warps 2-3    builders: b_j's balanced nibbles per column, B cores per stage
+//   warp 1       MMA issuer (one thread); the bias step last in each tile
+//   warps 2-3    builders: b_j's balanced nibbles per column, the new B cores
+//                of each stage
 //   warps 4-7    epilogue: one thread per row drains the column sums of a pass
 //                from tensor memory, forms the limbs (running carry) and
 //                stores the product's upper n limbs in a global slab
