@@ -262,11 +262,13 @@ def test_full_size_C2_sampled(mpdet, oracle_lib):
         assert C[0][N - 1] == D[0][N - 2] and C[1][N - 1] == D[1][N - 2] and np.array_equal(C[2][N - 1], D[2][N - 2])
 
 
-@pytest.mark.parametrize("N,p,lastcol", [(70, 1024, True), (33, 8192, True), (40, 4096, False)])
+@pytest.mark.parametrize("N,p,lastcol", [(70, 1024, True), (33, 8192, True), (40, 4096, False), (100, 4096, True)])
 def test_host_resident_array(mpdet, oracle_lib, N, p, lastcol):
     """The N x N array in page-locked host memory (MPDET_HOSTMEM), read and
     written in place by the kernels: bit-identical to the device-resident
-    array and to the oracle, windows and the last-column minors included."""
+    array and to the oracle, windows and the last-column minors included
+    (N = 100 at p = 4096: the tensor-core engine's launches of >= 64 rows
+    read and write the host-resident array)."""
     x, y = W.cauchy_xy(N, 4040 + N)
     out = []
     for host in (False, True):
