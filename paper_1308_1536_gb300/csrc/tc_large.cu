@@ -25,8 +25,8 @@
 // GEMM shape, per block of M = 128 rows i and one column j: D[i][r] =
 // sum_k' A[i][k'] B[k'][r], K reversed (k' = KD - 1 - s):
 //   A[i][k'] = e_{KD-1-k'}(z_i): precomputed per step (k_zdig) in global
-//     memory in core-matrix order and streamed by TMA, 64 digits (16 KB) per
-//     pipeline stage;
+//     memory, row-major, and streamed by TMA with 128-byte swizzle, 64 digits
+//     x 128 rows (16 KB) per pipeline stage;
 //   B[k'][r] = f_{r + 2k' - 2KD + 2}(b_j): its 8 x 8 core matrices (k-core
 //     kc, n-core nc) depend only on d = nc + 2 kc, so one no-swizzle
 //     descriptor with leading offset 256 and stride offset 128 bytes reads
@@ -155,6 +155,14 @@ __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvt
 
 // UMMA shared-memory descriptor, no swizzle, K-major: lbo steps between core
 // matrices along K, sbo along M / N.
+// UMMA shared-memory descriptor of a K-major operand in the 128-byte swizzle
+// layout: rows of 128 bytes, 8-row groups 1024 bytes apart (stride offset);
+// a K step of 16 bf16 moves the start address by 32 bytes within the row.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
 __device__ __forceinline__ uint64_t desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
   return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)((lbo & 0x3FFFF) >> 4) << 16) |
          ((uint64_t)((sbo & 0x3FFFF) >> 4) << 32) | ((uint64_t)1 << 46);
@@ -233,9 +241,10 @@ __device__ __forceinline__ uint32_t bfi(int e) { return __float_as_uint((float)e
 
 // ---------------------------------------------------------------------------
 // A operand: balanced 8-bit digits of the multipliers z_i, i in [row0, row0 +
-// nrows), as bf16 in core-matrix order: Zd[kc][i][kk] holds digit
-// s = KD - 1 - (8 kc + kk) of z_i (16 bytes per core row; rows i of the whole
-// N-row array).  One thread per row; the carry chain runs over the limbs.
+// nrows), as bf16, row-major: Zd[i][k'] holds digit s = KD - 1 - k' of z_i
+// (rows i of the whole N-row array).  A TMA copy with 128-byte swizzle moves
+// 64 digits of 128 rows into the layout the MMA reads (K-major, 128-byte
+// swizzle).  One thread per row; the carry chain runs over the limbs.
 // ---------------------------------------------------------------------------
 template <int n>
 __global__ void k_zdig(MpArr Z, int64_t N, int64_t row0, int64_t nrows, uint4* __restrict__ zd) {
@@ -262,7 +271,7 @@ __global__ void k_zdig(MpArr Z, int64_t N, int64_t row0, int64_t nrows, uint4* _
       h[q + 4] = __float_as_uint(__uint_as_float(0x4B000000u | ((y1 >> (8 * q)) & 255u)) - 8388736.0f) >> 16;
     }
     // element kk holds digit q = 7 - kk
-    zd[(int64_t)(KD / 8 - 1 - m) * N + i] =
+    zd[i * (KD / 8) + (KD / 8 - 1 - m)] =
         make_uint4(h[7] | (h[6] << 16), h[5] | (h[4] << 16), h[3] | (h[2] << 16), h[1] | (h[0] << 16));
   }
 }
@@ -359,9 +368,9 @@ __global__ void __launch_bounds__(NTH, 1) k_update_tcl(MpArr X, UpdArgs a, MpArr
                          "r"(A_BYTES)
                          : "memory");
             asm volatile(
-                "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
-                "%4}], [%5];" ::"r"(su32(sm + C::OFF_A + slot * A_BYTES)),
-                "l"(reinterpret_cast<uint64_t>(&tmz)), "r"(0), "r"(i0), "r"(8 * sg), "r"(b_afull + 8 * slot)
+                "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+                "[%4];" ::"r"(su32(sm + C::OFF_A + slot * A_BYTES)),
+                "l"(reinterpret_cast<uint64_t>(&tmz)), "r"(64 * sg), "r"(i0), "r"(b_afull + 8 * slot)
                 : "memory");
           }
       }
@@ -420,7 +429,7 @@ __global__ void __launch_bounds__(NTH, 1) k_update_tcl(MpArr X, UpdArgs a, MpArr
                 asm volatile("tcgen05.fence::after_thread_sync;");
               }
               for (int ks = lo; ks < hi; ++ks) {
-                const uint64_t ad = desc(aS + 4096u * (uint32_t)(ks - 4 * sg), 2048, 128);
+                const uint64_t ad = desc_sw128(aS + 32u * (uint32_t)(ks - 4 * sg));
                 const uint64_t bd = desc(bS + 128u * (uint32_t)(32 * t + 4 * (ks - 4 * sg)), 256, 128);
                 asm volatile(
                     "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, "
@@ -773,12 +782,14 @@ static cudaError_t launch_tcl(MpArr X, const UpdArgs& a, MpArr Z, int* status, i
   const EncodeTiledFnL enc = encode_tiled_l();
   if (!enc) return cudaErrorNotSupported;
   CUtensorMap tm;
-  const cuuint64_t dims[3] = {8, (cuuint64_t)a.N, (cuuint64_t)(C::KD / 8)};
-  const cuuint64_t strides[2] = {16, (cuuint64_t)a.N * 16};
-  const cuuint32_t box[3] = {8, (cuuint32_t)tcl::M, 8};
-  const cuuint32_t es[3] = {1, 1, 1};
-  if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, zd, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+  // Zd[i][k']: KD digits per row; a box is 64 digits (128 bytes) x 128 rows,
+  // written with the 128-byte swizzle the A descriptor names
+  const cuuint64_t dims[2] = {(cuuint64_t)C::KD, (cuuint64_t)a.N};
+  const cuuint64_t strides[1] = {(cuuint64_t)C::KD * 2};
+  const cuuint32_t box[2] = {64, (cuuint32_t)tcl::M};
+  const cuuint32_t es[2] = {1, 1};
+  if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, zd, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
       CUDA_SUCCESS)
     return cudaErrorInvalidValue;
   const int64_t items = (a.nrows + tcl::M - 1) / tcl::M * a.ncols;
