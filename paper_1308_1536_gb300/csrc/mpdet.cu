@@ -395,14 +395,13 @@ static int next_event(mpdet_t h, cudaEvent_t* ev) {
   return MPDET_OK;
 }
 
-// Default shortest launch (rows) for the tensor engine, from GB300
-// measurements of whole eliminations: at p = 2048 it is twice as fast as the
-// IMAD kernel from about 64 rows on, at p = 1024 some 12 % faster from about
-// 128 rows on, and at p = 512 slower at every size measured (N <= 2048).
-// Default row threshold of the tensor engine per precision: 64 rows at
-// p = 2048; at p = 512 and 1024 the IMAD kernel measured faster at every
-// size (whole eliminations, lastcol mode, N = 256 .. 2048), so it takes all
-// launches there unless the threshold is set.
+// Default row threshold of the tensor engines per precision, from GB300
+// measurements of whole eliminations: 64 rows at p = 2048 (twice the IMAD
+// kernel's speed from about 64 rows on) and at p = 4096 .. 32768 (a launch of
+// fewer rows fills less than half of a 128-row block, and the IMAD kernel
+// takes the last steps); at p = 512 and 1024 the IMAD kernel measured faster
+// at every size (lastcol mode, N = 256 .. 2048), so it takes all launches
+// there unless the threshold is set.
 static int64_t tc_default_min_rows(int p) { return (p == 2048 || mpd::tcl_supports(p)) ? 64 : INT64_MAX; }
 
 // Large-precision tensor engine (p = 4096 .. 32768) for an update launch of
