@@ -1,0 +1,183 @@
+"""The arithmetic the large-precision tensor engine (p = 4096 .. 32768) relies
+on, checked exactly with Python integers on the CPU: 8-bit balanced digits of
+the multiplier against 4-bit balanced digits of the pivot-row element, the
+radix-16 column sums and their bound (exact in fp32 with the magic bias for
+every n <= 1024), the limb formula of the epilogue on raw fp32 words, the
+lazy low half (when the band of limbs n-32 .. n-2 holds both a one and a zero,
+the upper limbs, limb n-1 and a non-zero sticky bit follow from the formed
+positions alone), the tiles' K ranges (every non-zero term of a tile inside
+its MMA K steps) and the core addressing of the B operand (d = n-core +
+2 k-core), and the MMA work count bench.py reports.  Small n, the same
+formulas."""
+import random
+
+import numpy as np
+import pytest
+
+import bench
+
+
+def balanced(m, nd, bits):
+    """Digits in [-2^(bits-1), 2^(bits-1)) and the carry out of the top."""
+    R, h = 1 << bits, 1 << (bits - 1)
+    d, c = [], 0
+    for s in range(nd):
+        v = ((m >> (bits * s)) & (R - 1)) + c
+        c = 1 if v >= h else 0
+        d.append(v - R * c)
+    return d, c
+
+
+def product_sums(n, z, b):
+    KD, KB = 4 * n, 8 * n
+    e, cz = balanced(z, KD, 8)
+    f, cb = balanced(b, KB, 4)
+    fb = f + [1]
+    c = [0] * (16 * n)
+    for s in range(KD):
+        if e[s]:
+            for t in range(KB + 1):
+                c[2 * s + t] += e[s] * fb[t]
+    return e, cz, f, cb, c
+
+
+def tiles(n):
+    KD, KB, R0, T = 4 * n, 8 * n, 8 * n - 256, n // 32 + 1
+    out = []
+    for tau in range(T):
+        rho = R0 + 256 * tau
+        lo = (KD - 1 - min((rho + 255) // 2, KD - 1)) // 16
+        hi = (KD - 1 - ((rho - KB + 1) // 2 if rho > KB else 0)) // 16 + 1
+        out.append((rho, lo, hi))
+    return out
+
+
+def epilogue(n, c, b):
+    """Limbs from the formed positions (r >= R0) with the raw-fp32-word
+    formula, carry-in zero, 2^p b added from limb n on."""
+    KD, R0 = 4 * n, 8 * n - 256
+    kOff = 1016 * KD
+    magic = np.float32(2 ** 23 + kOff)
+    acc, limbs = 0, {}
+    for r0 in range(R0, 16 * n, 8):
+        w = [int((np.float32(c[r0 + q]) + magic).view(np.uint32)) for q in range(8)]
+        a = [(w[2 * k] + (w[2 * k + 1] << 4) + 0x05000000) & 0xFFFFFFFF for k in range(4)]
+        acc += a[0] + (a[1] << 8) + (a[2] << 16) + (a[3] << 24) - kOff * 0x11111111
+        L = r0 // 8
+        if L >= n:
+            acc += (b >> (32 * (L - n))) & 0xFFFFFFFF
+        limbs[L] = acc & 0xFFFFFFFF
+        acc >>= 32
+    return limbs, acc
+
+
+def band_decides(n, limbs):
+    l0 = limbs[n - 32]
+    mid = [limbs[L] for L in range(n - 31, n - 1)]
+    orv, andv = 0, 0xFFFFFFFF
+    for v in mid:
+        orv |= v
+        andv &= v
+    return ((l0 >> 19) | orv) != 0 and (((~l0 & 0xFFFFFFFF) >> 19) | (andv ^ 0xFFFFFFFF)) != 0
+
+
+@pytest.mark.parametrize("n", [32, 64, 128])
+def test_digits_sums_and_epilogue(n):
+    p, KD = 32 * n, 4 * n
+    g = random.Random(4000 + n)
+    cases = [(g.getrandbits(p) | (1 << (p - 1)), g.getrandbits(p) | (1 << (p - 1))) for _ in range(3)]
+    cases += [((1 << p) - 1, (1 << p) - 1), (1 << (p - 1), (1 << p) - 1),
+              (int("80" * (p // 8), 16), int("8" * (p // 4), 16)), (int("ff80" * (p // 16), 16), int("f8" * (p // 8), 16))]
+    decided = 0
+    for z, b in cases:
+        e, cz, f, cb, c = product_sums(n, z, b)
+        assert cz == 1 and cb == 1  # normalised mantissas carry out of the top digit
+        assert sum(v << (8 * s) for s, v in enumerate(e)) + (1 << p) == z
+        assert sum(v << (4 * t) for t, v in enumerate(f)) + (1 << p) == b
+        # the nibbles are those of b + 0x88..8, less 8
+        t8 = b + int("8" * (8 * n), 16)
+        assert [((t8 >> (4 * i)) & 15) - 8 for i in range(8 * n)] == f
+        assert all(-1016 * KD <= v <= 1024 * KD for v in c)
+        P = sum(v << (4 * r) for r, v in enumerate(c)) + (b << p)
+        assert P == z * b
+        limbs, top = epilogue(n, c, b)
+        if band_decides(n, limbs):
+            decided += 1
+            assert top == 0
+            for L in range(n - 1, 2 * n):
+                assert limbs[L] == (P >> (32 * L)) & 0xFFFFFFFF
+            assert P & ((1 << (32 * (n - 1))) - 1) != 0  # the sticky bit is 1
+    assert decided >= 3  # the random operands take the formed positions alone
+
+
+def test_window_fits_fp32_at_every_precision():
+    for n in (128, 256, 512, 1024):
+        KD = 4 * n
+        lo, hi = -1016 * KD, 1024 * KD
+        assert hi - lo < 2 ** 23  # [2^23, 2^24) holds the biased window
+        magic = 2 ** 23 + 1016 * KD
+        assert float(np.float32(magic)) == magic
+        # both bias constants are exact in bf16 (8 significant bits)
+        for v in (2 ** 23, 1016 * KD):
+            f = np.array([v], np.float32)
+            assert (f.view(np.uint32) & 0xFFFF)[0] == 0
+
+
+@pytest.mark.parametrize("n", [32, 64, 128])
+def test_tile_k_ranges_cover_every_term(n):
+    KD, KB = 4 * n, 8 * n
+    g = random.Random(n)
+    p = 32 * n
+    e, _, f, _, _ = product_sums(n, g.getrandbits(p) | (1 << (p - 1)), g.getrandbits(p) | (1 << (p - 1)))
+    fb = f + [1]
+    for rho, lo, hi in tiles(n):
+        for r in range(rho, rho + 256):
+            for s in range(KD):
+                t = r - 2 * s
+                if 0 <= t <= KB and e[s] and fb[t]:
+                    assert lo * 16 <= KD - 1 - s < hi * 16
+
+
+def test_b_core_addressing():
+    """Element (k', r) of the B operand at the descriptor address (leading
+    offset 256, stride offset 128, start 128 (32 t + 4 (ks - 4 sg)) in the
+    stage window of cores d0 .. d0 + 79, d0 = n-core(R0 + 512 pi) + 16 sg)
+    holds f~(r - 2 s) with s = KD - 1 - k'."""
+    n = 64
+    KD, KB, R0 = 4 * n, 8 * n, 8 * n - 256
+    g = random.Random(5)
+    f, _ = balanced(g.getrandbits(32 * n) | (1 << (32 * n - 1)), KB, 4)
+    fb = f + [1]
+
+    def ft(x):
+        return fb[x] if 0 <= x <= KB else 0
+
+    T = n // 32 + 1
+    for pi in range((T + 1) // 2):
+        nc0 = (R0 + 512 * pi) // 8
+        for sg in range(KD // 64):
+            d0 = nc0 + 16 * sg
+            core = {}
+            for dl in range(80):
+                for rr in range(8):
+                    for kk in range(8):
+                        core[dl * 128 + rr * 16 + kk * 2] = ft(8 * (d0 + dl) + rr + 2 * kk - 2 * KD + 2)
+            for t in range(2 if 2 * pi + 1 < T else 1):
+                for ks in range(4 * sg, 4 * sg + 4):
+                    start = 128 * (32 * t + 4 * (ks - 4 * sg))
+                    for kl in range(16):
+                        for nn in range(0, 256, 13):
+                            addr = start + (nn // 8) * 128 + (kl // 8) * 256 + (nn % 8) * 16 + (kl % 8) * 2
+                            assert addr < 80 * 128
+                            r = R0 + 512 * pi + 256 * t + nn
+                            s = KD - 1 - (16 * ks + kl)
+                            assert core[addr] == ft(r - 2 * s)
+
+
+@pytest.mark.parametrize("n", [128, 1024])
+def test_mma_work_count(n):
+    """bench.tcl_mma_macs_per_product: the K steps the engine issues per tile,
+    times 16 x 256 MACs; at most the schoolbook 8 x 4-bit count 32 n^2."""
+    want = sum((hi - lo) * 16 * 256 for _, lo, hi in tiles(n))
+    assert bench.tcl_mma_macs_per_product(32 * n) == want
+    assert want <= 32 * n * n
