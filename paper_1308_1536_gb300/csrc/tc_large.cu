@@ -25,8 +25,8 @@
 // GEMM shape, per block of M = 128 rows i and one column j: D[i][r] =
 // sum_k' A[i][k'] B[k'][r], K reversed (k' = KD - 1 - s):
 //   A[i][k'] = e_{KD-1-k'}(z_i): precomputed per step (k_zdig) in global
-//     memory, row-major, and streamed by TMA with 128-byte swizzle, 64 digits
-//     x 128 rows (16 KB) per pipeline stage;
+//     memory, row-major, and streamed by TMA with 128-byte swizzle, 128
+//     digits x 128 rows (two 16 KB boxes) per pipeline stage;
 //   B[k'][r] = f_{r + 2k' - 2KD + 2}(b_j): its 8 x 8 core matrices (k-core
 //     kc, n-core nc) depend only on d = nc + 2 kc, so one no-swizzle
 //     descriptor with leading offset 256 and stride offset 128 bytes reads
@@ -43,7 +43,7 @@
 //
 // Roles (384 threads, one block per SM, persistent over a range of (row
 // block, column) items):
-//   warp 0       TMA producer of the A stages (4-stage ring)
+//   warp 0       TMA producer of the A stages (3-stage ring of 8 MMA K steps)
 //   warp 1       MMA issuer (one thread); the bias step last in each tile
 //   warps 2-3    builders: b_j's balanced nibbles per column, the new B cores
 //                of each stage
@@ -65,21 +65,23 @@ namespace tcl {
 
 constexpr int M = 128;       // rows per block (MMA M)
 constexpr int NT = 256;      // positions per tile (MMA N)
-constexpr int STAGES = 4;    // ring depth
-constexpr int NCORE = 80;    // B cores in a stage's window (78 are read)
+constexpr int STAGES = 3;    // ring depth
+constexpr int KSPS = 8;      // MMA K steps (16 digits each) per stage
+constexpr int NCORE = 96;    // B cores in a stage's window (94 are read)
 // The B cores live in a sliding ring of RING cores plus a mirror of its first
 // NCORE: a stage's window is RING-contiguous from its start slot; within a
-// pass each stage's window starts 16 cores after the previous one's (the next
-// 64 are shared), so a stage builds 16 new cores, the first stage of a pass
-// all 80.  The window start advances by 16 per stage and by 80 after a pass's
-// last stage; the builders of stage g wait for stage g - STAGES to complete,
-// so stages g-STAGES+1 .. g-1 are the only ones in flight, and the cores
-// stage g writes lie less than STAGES * 80 = RING cores after the first core
-// of stage g-STAGES+1's window: no core still to be read is overwritten.
-constexpr int RING = STAGES * 80;
+// pass each stage's window starts 4 KSPS = 32 cores after the previous one's
+// (the next 64 are shared), so a stage builds 32 new cores, the first stage of
+// a pass all 96.  The window start advances by 32 per stage and by NCORE after
+// a pass's last stage; the builders of stage g wait for stage g - STAGES to
+// complete, so stages g-STAGES+1 .. g-1 are the only ones in flight, and the
+// cores stage g writes lie less than STAGES * NCORE = RING cores after the
+// first core of stage g-STAGES+1's window: no core still to be read is
+// overwritten.
+constexpr int RING = STAGES * NCORE;
 constexpr int NTH = 384;
 constexpr int LIMIT = 1 << 22;
-constexpr uint32_t A_BYTES = M * 64 * 2;   // 128 rows x 64 digits (bf16)
+constexpr uint32_t A_BYTES = M * 16 * KSPS * 2;  // 128 rows x 128 digits (bf16): two 128-byte swizzle boxes
 constexpr uint32_t B_BYTES = (RING + NCORE) * 128;
 
 template <int n>
@@ -120,10 +122,11 @@ struct Cfg {
   __host__ __device__ static constexpr int ntile(int pi) { return 2 * pi + 1 < T ? 2 : 1; }
   // stages (64 reversed digits) of pass pi: [sg_lo, sg_hi)
   __host__ __device__ static constexpr int sg_lo(int pi) {
-    return (ntile(pi) == 2 && ks_lo(2 * pi + 1) < ks_lo(2 * pi) ? ks_lo(2 * pi + 1) : ks_lo(2 * pi)) / 4;
+    return (ntile(pi) == 2 && ks_lo(2 * pi + 1) < ks_lo(2 * pi) ? ks_lo(2 * pi + 1) : ks_lo(2 * pi)) / KSPS;
   }
   __host__ __device__ static constexpr int sg_hi(int pi) {
-    return ((ntile(pi) == 2 && ks_hi(2 * pi + 1) > ks_hi(2 * pi) ? ks_hi(2 * pi + 1) : ks_hi(2 * pi)) + 3) / 4;
+    return ((ntile(pi) == 2 && ks_hi(2 * pi + 1) > ks_hi(2 * pi) ? ks_hi(2 * pi + 1) : ks_hi(2 * pi)) + KSPS - 1) /
+           KSPS;
   }
 };
 
@@ -367,11 +370,12 @@ __global__ void __launch_bounds__(NTH, 1) k_update_tcl(MpArr X, UpdArgs a, MpArr
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b_afull + 8 * slot),
                          "r"(A_BYTES)
                          : "memory");
-            asm volatile(
-                "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
-                "[%4];" ::"r"(su32(sm + C::OFF_A + slot * A_BYTES)),
-                "l"(reinterpret_cast<uint64_t>(&tmz)), "r"(64 * sg), "r"(i0), "r"(b_afull + 8 * slot)
-                : "memory");
+            for (int bx = 0; bx < KSPS / 4; ++bx)
+              asm volatile(
+                  "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+                  "[%4];" ::"r"(su32(sm + C::OFF_A + slot * A_BYTES + 16384 * bx)),
+                  "l"(reinterpret_cast<uint64_t>(&tmz)), "r"(16 * KSPS * sg + 64 * bx), "r"(i0), "r"(b_afull + 8 * slot)
+                  : "memory");
           }
       }
       if (!ok) *eflag = 1;
@@ -413,12 +417,12 @@ __global__ void __launch_bounds__(NTH, 1) k_update_tcl(MpArr X, UpdArgs a, MpArr
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint32_t aS = su32(sm + C::OFF_A + slot * A_BYTES);
             const uint32_t bS = su32(sm + C::OFF_B + wpos * 128);
-            wpos += sg + 1 < C::sg_hi(pi) ? 16 : NCORE;
+            wpos += sg + 1 < C::sg_hi(pi) ? 4 * KSPS : NCORE;
             if (wpos >= RING) wpos -= RING;
             for (int t = 0; t < nt; ++t) {
               const int tau = 2 * pi + t;
-              const int lo = C::ks_lo(tau) > 4 * sg ? C::ks_lo(tau) : 4 * sg;
-              const int hi = C::ks_hi(tau) < 4 * sg + 4 ? C::ks_hi(tau) : 4 * sg + 4;
+              const int lo = C::ks_lo(tau) > KSPS * sg ? C::ks_lo(tau) : KSPS * sg;
+              const int hi = C::ks_hi(tau) < KSPS * sg + KSPS ? C::ks_hi(tau) : KSPS * sg + KSPS;
               bool& started = t ? started1 : started0;
               if (lo < hi && !started) {
                 const int64_t u = t ? uses1 : uses0;
@@ -429,8 +433,9 @@ __global__ void __launch_bounds__(NTH, 1) k_update_tcl(MpArr X, UpdArgs a, MpArr
                 asm volatile("tcgen05.fence::after_thread_sync;");
               }
               for (int ks = lo; ks < hi; ++ks) {
-                const uint64_t ad = desc_sw128(aS + 32u * (uint32_t)(ks - 4 * sg));
-                const uint64_t bd = desc(bS + 128u * (uint32_t)(32 * t + 4 * (ks - 4 * sg)), 256, 128);
+                const uint32_t kl = (uint32_t)(ks - KSPS * sg);  // K step within the stage
+                const uint64_t ad = desc_sw128(aS + 16384u * (kl >> 2) + 32u * (kl & 3u));
+                const uint64_t bd = desc(bS + 128u * (32u * (uint32_t)t + 4u * kl), 256, 128);
                 asm volatile(
                     "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, "
                     "p;\n}" ::"r"(tmem + (uint32_t)(NT * t)),
@@ -519,8 +524,8 @@ __global__ void __launch_bounds__(NTH, 1) k_update_tcl(MpArr X, UpdArgs a, MpArr
           // the first stage of a pass builds the whole window, the others its
           // last 16 cores
           unsigned char* Bring = sm + C::OFF_B;
-          const int d0 = nc0 + 16 * sg;
-          const int dl0 = sg == C::sg_lo(pi) ? 0 : NCORE - 16;
+          const int d0 = nc0 + 4 * KSPS * sg;
+          const int dl0 = sg == C::sg_lo(pi) ? 0 : NCORE - 4 * KSPS;
           for (int q2 = bt; q2 < (NCORE - dl0) * 8; q2 += 64) {
             const int dl = dl0 + (q2 >> 3), rr = q2 & 7;
             const int u0 = 4 * (d0 + dl) + (rr >> 1) - C::KD + 1;
@@ -535,7 +540,7 @@ __global__ void __launch_bounds__(NTH, 1) k_update_tcl(MpArr X, UpdArgs a, MpArr
             *reinterpret_cast<uint4*>(Bring + x * 128 + rr * 16) = v;
             if (x < NCORE) *reinterpret_cast<uint4*>(Bring + (x + RING) * 128 + rr * 16) = v;  // mirror
           }
-          wpos += sg + 1 < C::sg_hi(pi) ? 16 : NCORE;
+          wpos += sg + 1 < C::sg_hi(pi) ? 4 * KSPS : NCORE;
           if (wpos >= RING) wpos -= RING;
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // read by the tensor core
           bbar();
