@@ -65,24 +65,21 @@ namespace tcl {
 
 constexpr int M = 128;       // rows per block (MMA M)
 constexpr int NT = 256;      // positions per tile (MMA N)
-constexpr int STAGES = 3;    // ring depth
-constexpr int KSPS = 8;      // MMA K steps (16 digits each) per stage
-constexpr int NCORE = 96;    // B cores in a stage's window (94 are read)
+// Stage geometry (per precision, in Cfg): KSPS MMA K steps of 16 digits per
+// stage, STAGES stages in the ring; a stage's B window spans NCORE cores.
 // The B cores live in a sliding ring of RING cores plus a mirror of its first
 // NCORE: a stage's window is RING-contiguous from its start slot; within a
-// pass each stage's window starts 4 KSPS = 32 cores after the previous one's
-// (the next 64 are shared), so a stage builds 32 new cores, the first stage of
-// a pass all 96.  The window start advances by 32 per stage and by NCORE after
-// a pass's last stage; the builders of stage g wait for stage g - STAGES to
-// complete, so stages g-STAGES+1 .. g-1 are the only ones in flight, and the
-// cores stage g writes lie less than STAGES * NCORE = RING cores after the
-// first core of stage g-STAGES+1's window: no core still to be read is
-// overwritten.
-constexpr int RING = STAGES * NCORE;
+// pass each stage's window starts 4 KSPS cores after the previous one's (the
+// next 64 are shared), so a stage builds 4 KSPS new cores, the first stage of
+// a pass all NCORE.  The window start advances by 4 KSPS per stage and by
+// NCORE after a pass's last stage; the builders of stage g wait for stage
+// g - STAGES to complete, so stages g-STAGES+1 .. g-1 are the only ones in
+// flight, and the cores stage g writes lie less than STAGES * NCORE = RING
+// cores after the first core of stage g-STAGES+1's window: no core still to be
+// read is overwritten.
 constexpr int NTH = 384;
 constexpr int LIMIT = 1 << 22;
-constexpr uint32_t A_BYTES = M * 16 * KSPS * 2;  // 128 rows x 128 digits (bf16): two 128-byte swizzle boxes
-constexpr uint32_t B_BYTES = (RING + NCORE) * 128;
+
 
 template <int n>
 struct Cfg {
@@ -98,6 +95,12 @@ struct Cfg {
   static constexpr int OFFU = 8;            // index of u = 0 in the nibble arrays
   static constexpr int FL = KB / 2 + 16;    // entries per parity array
   static constexpr int kOff = 1016 * KD;
+  static constexpr int KSPS = n <= 512 ? 16 : 8;       // MMA K steps per stage
+  static constexpr int STAGES = n <= 512 ? 2 : 3;      // ring depth
+  static constexpr int NCORE = (63 + 4 * KSPS + 15) / 16 * 16;  // B window (63 + 4 KSPS cores read)
+  static constexpr int RING = STAGES * NCORE;
+  static constexpr uint32_t A_BYTES = M * 16 * KSPS * 2;  // 128 rows x 16 KSPS digits: KSPS / 4 swizzle boxes
+  static constexpr uint32_t B_BYTES = (RING + NCORE) * 128;
   static constexpr int OFF_A = 0;
   static constexpr int OFF_B = OFF_A + STAGES * (int)A_BYTES;
   static constexpr int OFF_F = OFF_B + (int)B_BYTES;                   // two bf16 parity arrays
@@ -120,7 +123,7 @@ struct Cfg {
     return (KD - 1 - (R0 + 256 * tau > KB ? (R0 + 256 * tau - KB + 1) / 2 : 0)) / 16 + 1;
   }
   __host__ __device__ static constexpr int ntile(int pi) { return 2 * pi + 1 < T ? 2 : 1; }
-  // stages (64 reversed digits) of pass pi: [sg_lo, sg_hi)
+  // stages (16 KSPS reversed digits each) of pass pi: [sg_lo, sg_hi)
   __host__ __device__ static constexpr int sg_lo(int pi) {
     return (ntile(pi) == 2 && ks_lo(2 * pi + 1) < ks_lo(2 * pi) ? ks_lo(2 * pi + 1) : ks_lo(2 * pi)) / KSPS;
   }
@@ -285,6 +288,8 @@ __global__ void __launch_bounds__(NTH, 1) k_update_tcl(MpArr X, UpdArgs a, MpArr
                                                       const __grid_constant__ CUtensorMap tmz) {
   using C = Cfg<n>;
   constexpr int W = C::W, G = C::G;
+  constexpr int STAGES = C::STAGES, KSPS = C::KSPS, NCORE = C::NCORE, RING = C::RING;
+  constexpr uint32_t A_BYTES = C::A_BYTES;
   extern __shared__ __align__(1024) unsigned char sm[];
   if (upd_stopped(status, a)) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
