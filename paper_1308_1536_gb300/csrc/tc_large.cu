@@ -25,8 +25,8 @@
 // GEMM shape, per block of M = 128 rows i and one column j: D[i][r] =
 // sum_k' A[i][k'] B[k'][r], K reversed (k' = KD - 1 - s):
 //   A[i][k'] = e_{KD-1-k'}(z_i): precomputed per step (k_zdig) in global
-//     memory, row-major, and streamed by TMA with 128-byte swizzle, 128
-//     digits x 128 rows (two 16 KB boxes) per pipeline stage;
+//     memory, row-major, and streamed by TMA with 128-byte swizzle, 256
+//     digits x 128 rows (four 16 KB boxes) per pipeline stage;
 //   B[k'][r] = f_{r + 2k' - 2KD + 2}(b_j): its 8 x 8 core matrices (k-core
 //     kc, n-core nc) depend only on d = nc + 2 kc, so one no-swizzle
 //     descriptor with leading offset 256 and stride offset 128 bytes reads
@@ -43,7 +43,7 @@
 //
 // Roles (384 threads, one block per SM, persistent over a range of (row
 // block, column) items):
-//   warp 0       TMA producer of the A stages (3-stage ring of 8 MMA K steps)
+//   warp 0       TMA producer of the A stages (2-stage ring of 16 MMA K steps)
 //   warp 1       MMA issuer (one thread); the bias step last in each tile
 //   warps 2-3    builders: b_j's balanced nibbles per column, the new B cores
 //                of each stage
@@ -65,18 +65,19 @@ namespace tcl {
 
 constexpr int M = 128;       // rows per block (MMA M)
 constexpr int NT = 256;      // positions per tile (MMA N)
-// Stage geometry (per precision, in Cfg): KSPS MMA K steps of 16 digits per
-// stage, STAGES stages in the ring; a stage's B window spans NCORE cores.
-// The B cores live in a sliding ring of RING cores plus a mirror of its first
-// NCORE: a stage's window is RING-contiguous from its start slot; within a
-// pass each stage's window starts 4 KSPS cores after the previous one's (the
-// next 64 are shared), so a stage builds 4 KSPS new cores, the first stage of
-// a pass all NCORE.  The window start advances by 4 KSPS per stage and by
-// NCORE after a pass's last stage; the builders of stage g wait for stage
-// g - STAGES to complete, so stages g-STAGES+1 .. g-1 are the only ones in
-// flight, and the cores stage g writes lie less than STAGES * NCORE = RING
-// cores after the first core of stage g-STAGES+1's window: no core still to be
-// read is overwritten.
+// Stage geometry (in Cfg): KSPS MMA K steps of 16 digits per stage, STAGES
+// stages in the ring; a stage's B window spans NCORE cores.  The B cores live
+// in a sliding ring of RING = STAGES * NCORE cores plus a mirror of its first
+// MIRROR = NCORE - 4 KSPS, so that every window is contiguous: within a pass
+// each stage's window starts 4 KSPS cores after the previous one's (the next
+// NCORE - 4 KSPS are shared), so a stage builds 4 KSPS new cores, the first
+// stage of a pass all NCORE.  The window start advances by 4 KSPS per stage
+// and by NCORE after a pass's last stage, so it is a multiple of 4 KSPS and a
+// window runs at most MIRROR cores past the ring's end.  The builders of stage
+// g wait for stage g - STAGES to complete, so stages g-STAGES+1 .. g-1 are the
+// only ones in flight, and the cores stage g writes lie less than RING cores
+// after the first core of stage g-STAGES+1's window: no core still to be read
+// is overwritten.
 constexpr int NTH = 384;
 constexpr int LIMIT = 1 << 22;
 
@@ -95,12 +96,14 @@ struct Cfg {
   static constexpr int OFFU = 8;            // index of u = 0 in the nibble arrays
   static constexpr int FL = KB / 2 + 16;    // entries per parity array
   static constexpr int kOff = 1016 * KD;
-  static constexpr int KSPS = n <= 512 ? 16 : 8;       // MMA K steps per stage
-  static constexpr int STAGES = n <= 512 ? 2 : 3;      // ring depth
+  static constexpr int KSPS = 16;                     // MMA K steps per stage
+  static constexpr int STAGES = 2;                    // ring depth
   static constexpr int NCORE = (63 + 4 * KSPS + 15) / 16 * 16;  // B window (63 + 4 KSPS cores read)
   static constexpr int RING = STAGES * NCORE;
   static constexpr uint32_t A_BYTES = M * 16 * KSPS * 2;  // 128 rows x 16 KSPS digits: KSPS / 4 swizzle boxes
-  static constexpr uint32_t B_BYTES = (RING + NCORE) * 128;
+  static constexpr int MIRROR = NCORE - 4 * KSPS;
+  static_assert(NCORE % (4 * KSPS) == 0, "window starts multiples of 4 KSPS");
+  static constexpr uint32_t B_BYTES = (RING + MIRROR) * 128;
   static constexpr int OFF_A = 0;
   static constexpr int OFF_B = OFF_A + STAGES * (int)A_BYTES;
   static constexpr int OFF_F = OFF_B + (int)B_BYTES;                   // two bf16 parity arrays
@@ -543,7 +546,7 @@ __global__ void __launch_bounds__(NTH, 1) k_update_tcl(MpArr X, UpdArgs a, MpArr
             int x = wpos + dl;
             if (x >= RING) x -= RING;
             *reinterpret_cast<uint4*>(Bring + x * 128 + rr * 16) = v;
-            if (x < NCORE) *reinterpret_cast<uint4*>(Bring + (x + RING) * 128 + rr * 16) = v;  // mirror
+            if (x < C::MIRROR) *reinterpret_cast<uint4*>(Bring + (x + RING) * 128 + rr * 16) = v;  // mirror
           }
           wpos += sg + 1 < C::sg_hi(pi) ? 4 * KSPS : NCORE;
           if (wpos >= RING) wpos -= RING;
