@@ -564,6 +564,17 @@ __global__ void __launch_bounds__(NTH, 1) k_update_tcl(MpArr X, UpdArgs a, MpArr
     const int64_t kOffL = (int64_t)C::kOff * 0x11111111ll;
     int64_t pg = 0, it = 0;
     bool ok = true;
+    // b's limbs of a pass, a pass ahead: limbs L - n of the pass's 64 limbs
+    // L = n - 32 + 64 pi .. n + 31 + 64 pi (zero below limb n), lane l
+    // holding offsets l (word 0) and 32 + l (word 1); a chunk takes its four
+    // by shuffles
+    auto bload = [&](const uint32_t* bmp, const int pi, uint32_t& w0, uint32_t& w1) {
+      const int k0 = 64 * pi - 32 + lane, k1 = 64 * pi + lane;
+      w0 = k0 >= 0 && k0 < n ? __ldg(bmp + k0) : 0u;
+      w1 = k1 < n ? __ldg(bmp + k1) : 0u;
+    };
+    uint32_t bw0 = 0, bw1 = 0;
+    if (q0 < q1) bload(X.m + (a.brow * N + upd_col(a, q0 % ncols)) * n, 0, bw0, bw1);
     for (int64_t q = q0; q < q1 && ok; ++q, ++it) {
       const int64_t i0 = a.row0 + (q / ncols) * M;
       const int64_t j = upd_col(a, q % ncols);
@@ -586,6 +597,12 @@ __global__ void __launch_bounds__(NTH, 1) k_update_tcl(MpArr X, UpdArgs a, MpArr
       int64_t acc = 0;
       uint32_t l0 = 0, orv = 0, andv = 0xffffffffu, ltop = 0;
       for (int pi = 0; pi < C::NPASS; ++pi, ++pg) {
+        // the next pass's b limbs (the next item's first pass after the last)
+        uint32_t bn0 = 0, bn1 = 0;
+        if (pi + 1 < C::NPASS)
+          bload(bm, pi + 1, bn0, bn1);
+        else if (q + 1 < q1)
+          bload(X.m + (a.brow * N + upd_col(a, (q + 1) % ncols)) * n, 0, bn0, bn1);
         bool okt = wait_bar(b_tfull, (uint32_t)(pg & 1)) && !*eflag;
         ok = __all_sync(FULL, okt);
         if (!ok) break;
@@ -593,20 +610,13 @@ __global__ void __launch_bounds__(NTH, 1) k_update_tcl(MpArr X, UpdArgs a, MpArr
         const int nch = 8 * C::ntile(pi);
         // chunk ch: 32 sums (4 limbs) whose fp32 bits are 0x4B000000 + u,
         // u = c_r + kOff; the next chunk's load is in flight meanwhile
-        // b's limbs L - n of a chunk (zero below limb n), loaded a chunk ahead
-        auto blimbs = [&](const int ch) -> uint4 {
-          const int L0 = n - 32 + 64 * pi + 4 * ch;
-          return L0 >= n ? __ldg(reinterpret_cast<const uint4*>(bm + (L0 - n))) : make_uint4(0u, 0u, 0u, 0u);
-        };
-        uint4 bq = blimbs(0);
         auto step = [&](const int ch, uint32_t(&cur)[32], uint32_t(&nxt)[32]) {
           tmem_wait(cur);
-          const uint4 bc = bq;
-          if (ch + 1 < nch) {
-            tmem_ld32_async(tl + (uint32_t)(32 * (ch + 1)), nxt);
-            bq = blimbs(ch + 1);
-          }
-          const uint32_t bl[4] = {bc.x, bc.y, bc.z, bc.w};
+          if (ch + 1 < nch) tmem_ld32_async(tl + (uint32_t)(32 * (ch + 1)), nxt);
+          const uint32_t bsrc = ch < 8 ? bw0 : bw1;
+          uint32_t bl[4];
+#pragma unroll
+          for (int l4 = 0; l4 < 4; ++l4) bl[l4] = __shfl_sync(FULL, bsrc, (4 * ch + l4) & 31);
           if ((ch & 7) == 7) {  // a tile's sums are in registers: free its half of the tensor memory
             asm volatile("tcgen05.fence::before_thread_sync;");
             __syncwarp();
@@ -650,6 +660,8 @@ __global__ void __launch_bounds__(NTH, 1) k_update_tcl(MpArr X, UpdArgs a, MpArr
           step(ch, va, vb);
           step(ch + 1, vb, va);
         }
+        bw0 = bn0;
+        bw1 = bn1;
       }
       if (!ok) break;
       const bool any1 = ((l0 >> 19) | orv) != 0u;
