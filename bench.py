@@ -320,7 +320,7 @@ def bench_batch(args, dev, m, rank=0, world=1):
                                   "(set_mp from device buffers + factor per matrix)",
             "with_lift_dets_per_s": len(Ns) / (t_lift + ms / 1e3),
             "single_path_with_lift_dets_per_s": single_dets,
-            "vs_single_path_with_lift": (len(Ns) / (ms / 1e3)) / single_dets}
+            "vs_single_path_with_lift": (len(Ns) / (t_lift + ms / 1e3)) / single_dets}
 
 
 def bench_adjoint(args, dev, m):
