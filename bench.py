@@ -1143,7 +1143,7 @@ def main():
     ap.add_argument("--large-n", type=int, default=0,
                     help="--large-full: factor the leading N x N block of the N=4096 matrix instead (its steps cost "
                          "what the full run's last N steps cost; its minors are the full run's D_1..D_N)")
-    ap.add_argument("--save", default="gpurun_out/c5_minors.npz", help="--large-full: where the leading minors go")
+    ap.add_argument("--save", default="c5_minors.npz", help="--large-full: where the leading minors go")
     ap.add_argument("--karatsuba", action="store_true",
                     help="--large-full: the IMAD update's products by one Karatsuba level")
     args = ap.parse_args()
