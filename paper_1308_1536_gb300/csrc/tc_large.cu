@@ -530,7 +530,7 @@ __global__ void __launch_bounds__(NTH, 1) k_update_tcl(MpArr X, UpdArgs a, MpArr
           // core d = d0 + dl of the window, row rr: f~(8d + rr + 2kk - 2KD + 2),
           // kk = 0..7, = F_{rr & 1}[u0 + kk] with u0 = 4d + (rr >> 1) - KD + 1;
           // the first stage of a pass builds the whole window, the others its
-          // last 16 cores
+          // last 4 KSPS cores
           unsigned char* Bring = sm + C::OFF_B;
           const int d0 = nc0 + 4 * KSPS * sg;
           const int dl0 = sg == C::sg_lo(pi) ? 0 : NCORE - 4 * KSPS;

@@ -181,3 +181,102 @@ def test_mma_work_count(n):
     want = sum((hi - lo) * 16 * 256 for _, lo, hi in tiles(n))
     assert bench.tcl_mma_macs_per_product(32 * n) == want
     assert want <= 32 * n * n
+
+
+def stage_plan(n, KSPS):
+    """The stages of one column: (pass, stage index sg, [(tile t, first K
+    step, end K step)]) in issue order, from the tiles' K ranges."""
+    T = n // 32 + 1
+    tl = tiles(n)
+    plan = []
+    for pi in range((T + 1) // 2):
+        ts = [t for t in range(2) if 2 * pi + t < T]
+        lo = min(tl[2 * pi + t][1] for t in ts) // KSPS
+        hi = (max(tl[2 * pi + t][2] for t in ts) + KSPS - 1) // KSPS
+        for sg in range(lo, hi):
+            work = []
+            for t in ts:
+                a = max(tl[2 * pi + t][1], KSPS * sg)
+                b = min(tl[2 * pi + t][2], KSPS * sg + KSPS)
+                if a < b:
+                    work.append((t, a, b))
+            plan.append((pi, sg, sg == lo, sg + 1 == hi, work))
+    return plan
+
+
+@pytest.mark.parametrize("n,KSPS,STAGES", [(128, 16, 2), (256, 16, 2), (1024, 16, 2), (128, 8, 3), (512, 4, 4)])
+def test_b_core_ring(n, KSPS, STAGES):
+    """The sliding ring of B cores: NCORE = 63 + 4 KSPS rounded up to 16
+    cores per window, RING = STAGES NCORE slots plus a mirror of the first
+    NCORE - 4 KSPS.  The builders of a stage write its new cores (all of the
+    window at a pass's first stage, else the last 4 KSPS) at the window start
+    + dl, mirrored below MIRROR; the window start advances by 4 KSPS per stage
+    and NCORE after a pass's last one.  Every core an MMA of the stage reads
+    (start 32 t + 4 kl, 32 n-cores at stride 1, 2 k-cores at stride 2) holds
+    core d = n-core + 2 k-core, and it still does while the next STAGES - 1
+    stages are built (the builders of stage g wait only for stage g - STAGES).
+    Two columns, so the ring wraps across items."""
+    NCORE = (63 + 4 * KSPS + 15) // 16 * 16
+    assert NCORE % (4 * KSPS) == 0
+    RING, MIRROR = STAGES * NCORE, NCORE - 4 * KSPS
+    R0 = 8 * n - 256
+    ring = [None] * (RING + MIRROR)
+    plan = stage_plan(n, KSPS) * 2
+    wb = wm = 0
+    inflight = []  # (window start, expected cores by slot offset) of stages not yet complete
+    for g, (pi, sg, first, last, work) in enumerate(plan):
+        nc0 = (R0 + 512 * pi) // 8
+        d0 = nc0 + 4 * KSPS * sg
+        for dl in range(0 if first else NCORE - 4 * KSPS, NCORE):
+            x = wb + dl
+            if x >= RING:
+                x -= RING
+            ring[x] = d0 + dl
+            if x < MIRROR:
+                ring[x + RING] = d0 + dl
+        wb += NCORE if last else 4 * KSPS
+        if wb >= RING:
+            wb -= RING
+        reads = {}
+        for t, a, b in work:
+            for ks in range(a, b):
+                kl = ks - KSPS * sg
+                for c in range(32):
+                    for kc in range(2):
+                        dl = 32 * t + 4 * kl + c + 2 * kc
+                        ncore = (R0 + 512 * pi + 256 * t) // 8 + c
+                        kcore = 2 * ks + kc
+                        reads[dl] = ncore + 2 * kcore
+        assert max(reads) < NCORE
+        inflight.append((wm, reads))
+        inflight = inflight[-STAGES:]  # stage g - STAGES has completed
+        for w, rd in inflight:
+            assert w + max(rd) < RING + MIRROR
+            for dl, d in rd.items():
+                assert ring[w + dl] == d, (g, dl)
+        wm += NCORE if last else 4 * KSPS
+        if wm >= RING:
+            wm -= RING
+        assert wm % (4 * KSPS) == 0
+
+
+@pytest.mark.parametrize("n", [128, 1024])
+def test_epilogue_b_limbs_by_pass(n):
+    """The epilogue's b limbs: pass pi's 64 limbs L = n - 32 + 64 pi + o
+    (o = 0..63) need b's limb L - n (zero below limb n).  Lane l loads offsets
+    l and 32 + l (b[64 pi - 32 + l], b[64 pi + l], zero outside [0, n)); chunk
+    ch takes limb l4 from lane (4 ch + l4) mod 32 of word ch >= 8."""
+    g = random.Random(n)
+    b = [g.getrandbits(32) for _ in range(n)]
+    T = n // 32 + 1
+    for pi in range((T + 1) // 2):
+        w0 = [b[64 * pi - 32 + l] if 0 <= 64 * pi - 32 + l < n else 0 for l in range(32)]
+        w1 = [b[64 * pi + l] if 64 * pi + l < n else 0 for l in range(32)]
+        nch = 16 if 2 * pi + 1 < T else 8
+        for ch in range(nch):
+            src = w1 if ch >= 8 else w0
+            for l4 in range(4):
+                L = n - 32 + 64 * pi + 4 * ch + l4
+                assert L < 2 * n
+                want = b[L - n] if L >= n else 0
+                assert src[(4 * ch + l4) % 32] == want
