@@ -140,10 +140,11 @@ def test_tile_k_ranges_cover_every_term(n):
 
 def test_b_core_addressing():
     """Element (k', r) of the B operand at the descriptor address (leading
-    offset 256, stride offset 128, start 128 (32 t + 4 (ks - 4 sg)) in the
-    stage window of cores d0 .. d0 + 79, d0 = n-core(R0 + 512 pi) + 16 sg)
-    holds f~(r - 2 s) with s = KD - 1 - k'."""
-    n = 64
+    offset 256, stride offset 128, start 128 (32 t + 4 (ks - KSPS sg)) in the
+    stage window of cores d0 .. d0 + NCORE - 1, d0 = n-core(R0 + 512 pi) +
+    4 KSPS sg; KSPS = 16 MMA K steps per stage, NCORE = 128) holds
+    f~(r - 2 s) with s = KD - 1 - k'."""
+    n, KSPS, NCORE = 64, 16, 128
     KD, KB, R0 = 4 * n, 8 * n, 8 * n - 256
     g = random.Random(5)
     f, _ = balanced(g.getrandbits(32 * n) | (1 << (32 * n - 1)), KB, 4)
@@ -155,20 +156,20 @@ def test_b_core_addressing():
     T = n // 32 + 1
     for pi in range((T + 1) // 2):
         nc0 = (R0 + 512 * pi) // 8
-        for sg in range(KD // 64):
-            d0 = nc0 + 16 * sg
+        for sg in range(KD // (16 * KSPS)):
+            d0 = nc0 + 4 * KSPS * sg
             core = {}
-            for dl in range(80):
+            for dl in range(NCORE):
                 for rr in range(8):
                     for kk in range(8):
                         core[dl * 128 + rr * 16 + kk * 2] = ft(8 * (d0 + dl) + rr + 2 * kk - 2 * KD + 2)
             for t in range(2 if 2 * pi + 1 < T else 1):
-                for ks in range(4 * sg, 4 * sg + 4):
-                    start = 128 * (32 * t + 4 * (ks - 4 * sg))
+                for ks in range(KSPS * sg, KSPS * sg + KSPS):
+                    start = 128 * (32 * t + 4 * (ks - KSPS * sg))
                     for kl in range(16):
                         for nn in range(0, 256, 13):
                             addr = start + (nn // 8) * 128 + (kl // 8) * 256 + (nn % 8) * 16 + (kl % 8) * 2
-                            assert addr < 80 * 128
+                            assert addr < NCORE * 128
                             r = R0 + 512 * pi + 256 * t + nn
                             s = KD - 1 - (16 * ks + kl)
                             assert core[addr] == ft(r - 2 * s)
