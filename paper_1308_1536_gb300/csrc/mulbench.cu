@@ -1,9 +1,9 @@
 // Rounded products RN_p(a_i * b_i) by the IMAD engine's schoolbook product
 // (mul_round, the one the Schur update uses) or by one Karatsuba level over
 // half-size schoolbook products (mul_round_kara), for measuring the two on
-// the same operands (the comparison the survey's Karatsuba item asks for; the
-// paper's CPU runs use GMP's Karatsuba, Sec. 4.2 and Table 2).  Both give the
-// same bits: the product is exact before it is rounded.
+// the same operands (the paper's CPU runs use GMP's Karatsuba, Sec. 4.2 and
+// Table 2).  Both give the same bits: the product is exact before it is
+// rounded.
 #include "../../include/mpdet.h"
 #include "karatsuba.cuh"
 #include "kernelset.h"
