@@ -133,8 +133,10 @@ def factor_noalloc(A, N: int, p: int, minors, lastcol=None, stream=None):
 
         stream = torch.cuda.current_stream().cuda_stream
     zk = ctypes.c_int64(0)
-    rc = lib.mpdet_factor_noalloc(int(N), int(p), LASTCOL if lastcol is not None else 0, _numv(A), _numv(minors),
-                                  _numv(lastcol), ctypes.byref(zk), ctypes.c_void_p(stream or 0))
+    N, n = int(N), int(p) // 32
+    rc = lib.mpdet_factor_noalloc(N, int(p), LASTCOL if lastcol is not None else 0, _numv(A, N * N, n, True, "A"),
+                                  _numv(minors, N, n, True, "minors"), _numv(lastcol, N, n, True, "lastcol"),
+                                  ctypes.byref(zk), ctypes.c_void_p(stream or 0))
     if rc not in (OK, EZEROPIVOT):
         raise MpdetError(rc, f"factor_noalloc(N={N}, p={p})")
     return rc, int(zk.value)
@@ -206,21 +208,45 @@ def _is_torch(a) -> bool:
     return hasattr(a, "data_ptr") and hasattr(a, "is_cuda")
 
 
-def _ptr(a):
+def _ptr(a, count=None, itemsize=None, floating=None, dev=None, what="buffer"):
+    """The address of a contiguous numpy array or torch tensor, checked
+    against what the library will read or write there: at least ``count``
+    elements of ``itemsize`` bytes, floating point or integer, and device
+    memory (a CUDA tensor) when ``dev`` is True, host memory when False.
+    The library trusts its pointers, so a short or mistyped buffer would be
+    read or written past its end; these checks raise ValueError first."""
     if a is None:
         return None
     if _is_torch(a):  # CUDA tensor (device pointer) or pinned / CPU tensor (host pointer)
-        assert a.is_contiguous()
+        contig, nel, isz, isf = a.is_contiguous(), a.numel(), a.element_size(), a.is_floating_point()
+    elif isinstance(a, np.ndarray):
+        contig, nel, isz, isf = a.flags.c_contiguous, a.size, a.itemsize, a.dtype.kind == "f"
+    else:
+        raise TypeError(f"{what}: a numpy array or a torch tensor, not {type(a).__name__}")
+    if not contig:
+        raise ValueError(f"{what}: not contiguous")
+    if itemsize is not None and isz != itemsize:
+        raise ValueError(f"{what}: elements of {isz} bytes, {itemsize} expected")
+    if floating is not None and bool(isf) != floating:
+        raise ValueError(f"{what}: {'floating-point' if floating else 'integer'} elements expected")
+    if count is not None and nel < count:
+        raise ValueError(f"{what}: {nel} elements, at least {count} needed")
+    if dev is not None and _is_dev(a) != dev:
+        raise ValueError(f"{what}: {'device (a CUDA tensor)' if dev else 'host'} memory expected")
+    if _is_torch(a):
         return ctypes.c_void_p(a.data_ptr())
-    assert isinstance(a, np.ndarray) and a.flags.c_contiguous
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
-def _numv(t) -> NumV:
+def _numv(t, count=None, n=None, dev=None, what="numbers") -> NumV:
+    """A (sign int8, exp int64, limbs uint32) triple as the ABI's view, each
+    part checked by _ptr for ``count`` numbers of ``n`` limbs."""
     if t is None:
         return NumV(None, None, None)
     s, e, m = t
-    return NumV(_ptr(s), _ptr(e), _ptr(m))
+    lim = None if count is None or n is None else count * n
+    return NumV(_ptr(s, count, 1, False, dev, f"{what} (sign)"), _ptr(e, count, 8, False, dev, f"{what} (exp)"),
+                _ptr(m, lim, 4, False, dev, f"{what} (limbs)"))
 
 
 class Mpdet:
@@ -279,28 +305,37 @@ class Mpdet:
         dev = _is_dev(A)
         if not dev and not _is_torch(A):
             A = np.ascontiguousarray(A, np.float64)
-        ld = self.N if ld is None else ld
-        self._check(self.lib.mpdet_set_f64(self.h, _ptr(A), ld, int(dev)), "set_f64")
+        ld = self.N if ld is None else int(ld)
+        if ld < self.N:
+            raise ValueError(f"set_f64: ld = {ld} < N = {self.N}")
+        A_ = _ptr(A, (self.N - 1) * ld + self.N, 8, True, dev, "set_f64: A")
+        self._check(self.lib.mpdet_set_f64(self.h, A_, ld, int(dev)), "set_f64")
 
     def set_i32(self, A, ld=None):
         dev = _is_dev(A)
         if not dev and not _is_torch(A):
             A = np.ascontiguousarray(A, np.int32)
-        ld = self.N if ld is None else ld
-        self._check(self.lib.mpdet_set_i32(self.h, _ptr(A), ld, int(dev)), "set_i32")
+        ld = self.N if ld is None else int(ld)
+        if ld < self.N:
+            raise ValueError(f"set_i32: ld = {ld} < N = {self.N}")
+        A_ = _ptr(A, (self.N - 1) * ld + self.N, 4, False, dev, "set_i32: A")
+        self._check(self.lib.mpdet_set_i32(self.h, A_, ld, int(dev)), "set_i32")
 
     def set_cauchy(self, x, y):
         dev = _is_dev(x)
         if not dev and not _is_torch(x):
             x = np.ascontiguousarray(x, np.float64)
             y = np.ascontiguousarray(y, np.float64)
-        self._check(self.lib.mpdet_set_cauchy(self.h, _ptr(x), _ptr(y), int(dev)), "set_cauchy")
+        x_ = _ptr(x, self.N, 8, True, dev, "set_cauchy: x")
+        y_ = _ptr(y, self.N, 8, True, dev, "set_cauchy: y")
+        self._check(self.lib.mpdet_set_cauchy(self.h, x_, y_, int(dev)), "set_cauchy")
 
     def set_mp(self, A):
         dev = _is_dev(A[0])
         if not dev:
             A = tuple(np.ascontiguousarray(t) for t in A)
-        self._check(self.lib.mpdet_set_mp(self.h, _numv(A), int(dev)), "set_mp")
+        self._check(self.lib.mpdet_set_mp(self.h, _numv(A, self.N * self.N, self.n, dev, "set_mp: A"), int(dev)),
+                    "set_mp")
 
     # -- elimination --------------------------------------------------------
     def factor_range(self, k0: int, k1: int):
@@ -313,8 +348,8 @@ class Mpdet:
         call is asynchronous and returns None."""
         zk = ctypes.c_int64(0)
         if out is not None:
-            self._check(self.lib.mpdet_factor(self.h, NumV(None, None, None), _numv(out), ctypes.byref(zk), 1),
-                        "factor")
+            self._check(self.lib.mpdet_factor(self.h, NumV(None, None, None), _numv(out, self.N, self.n, True, "factor: out"),
+                                              ctypes.byref(zk), 1), "factor")
             return None
         D = empty(self.N, self.p)
         rc = self._check(self.lib.mpdet_factor(self.h, NumV(None, None, None), _numv(D), ctypes.byref(zk), 0),
@@ -328,7 +363,8 @@ class Mpdet:
 
     def lastcol_minors(self, normalised: bool = False, out=None):
         if out is not None:
-            self._check(self.lib.mpdet_lastcol_minors(self.h, _numv(out), int(normalised), 1), "lastcol_minors")
+            self._check(self.lib.mpdet_lastcol_minors(self.h, _numv(out, self.N, self.n, True, "lastcol_minors: out"),
+                                                      int(normalised), 1), "lastcol_minors")
             return None
         C = empty(self.N, self.p)
         self._check(self.lib.mpdet_lastcol_minors(self.h, _numv(C), int(normalised), 0), "lastcol_minors")
@@ -338,7 +374,9 @@ class Mpdet:
         """Last-column minors of every leading size n = 1..N (packed: series n
         at offset n(n-1)/2)."""
         if out is not None:
-            self._check(self.lib.mpdet_minor_series(self.h, _numv(out), int(normalised), 1), "minor_series")
+            cnt = self.N * (self.N + 1) // 2
+            self._check(self.lib.mpdet_minor_series(self.h, _numv(out, cnt, self.n, True, "minor_series: out"),
+                                                    int(normalised), 1), "minor_series")
             return None
         S = empty(self.N * (self.N + 1) // 2, self.p)
         self._check(self.lib.mpdet_minor_series(self.h, _numv(S), int(normalised), 0), "minor_series")
@@ -377,7 +415,8 @@ class Mpdet:
     def resume(self, X, D, k_done: int):
         X = tuple(np.ascontiguousarray(t) for t in X)
         D = tuple(np.ascontiguousarray(t) for t in D)
-        self._check(self.lib.mpdet_resume(self.h, _numv(X), _numv(D), int(k_done), 0), "resume")
+        self._check(self.lib.mpdet_resume(self.h, _numv(X, self.N * self.N, self.n, False, "resume: X"),
+                                          _numv(D, self.N, self.n, False, "resume: D"), int(k_done), 0), "resume")
 
     def steps_done(self) -> int:
         return int(self.lib.mpdet_steps_done(self.h))
@@ -400,8 +439,11 @@ class Mpdet:
                 G = out if out is not None else torch.empty((self.N, self.N), dtype=torch.float64, device=A.device)
             else:
                 G = np.empty((self.N, self.N), np.float64)
-        rc = self.lib.mpdet_logabsdet_grad(self.h, _ptr(A), self.N, ctypes.byref(la), ctypes.byref(sg), _ptr(G),
-                                           float(scale), int(dev))
+        NN = self.N * self.N
+        A_ = _ptr(A, NN, 8, True, dev, "logabsdet_grad: A")
+        G_ = _ptr(G, NN, 8, True, dev, "logabsdet_grad: out")
+        rc = self.lib.mpdet_logabsdet_grad(self.h, A_, self.N, ctypes.byref(la), ctypes.byref(sg), G_, float(scale),
+                                           int(dev))
         self._check(rc, "logabsdet_grad")
         return sg.value, la.value, G
 
@@ -462,7 +504,8 @@ def batch_once(mats, p: int, stream=None):
         ins = [tuple(np.ascontiguousarray(a) for a in _norm_host(t, n)) for t in mats]
         outs = [empty(int(N), p) for N in Ns]
         zk = np.zeros(len(mats), np.int64)
-    in_arr = (NumV * len(mats))(*[_numv(t) for t in ins])
+    in_arr = (NumV * len(mats))(*[_numv(t, int(N) * int(N), n, dev, f"batch: matrix {i}")
+                                  for i, (N, t) in enumerate(zip(Ns, ins))])
     out_arr = (NumV * len(mats))(*[_numv(t) for t in outs])
     if stream is None:
         try:
@@ -562,26 +605,37 @@ class Batch:
         if rc:
             raise MpdetError(rc, what)
 
+    def _size(self, m) -> int:
+        m = int(m)
+        if not 0 <= m < len(self.Ns):
+            raise IndexError(f"matrix {m} of a batch of {len(self.Ns)}")
+        return int(self.Ns[m])
+
     def set_cauchy(self, m, x, y):
+        N = self._size(m)
         dev = _is_dev(x)
         if not dev and not _is_torch(x):
             x = np.ascontiguousarray(x, np.float64)
             y = np.ascontiguousarray(y, np.float64)
-        self._check(self.lib.mpdet_batch_set_cauchy(self.h, int(m), _ptr(x), _ptr(y), int(dev)), "batch_set_cauchy")
+        x_ = _ptr(x, N, 8, True, dev, "batch set_cauchy: x")
+        y_ = _ptr(y, N, 8, True, dev, "batch set_cauchy: y")
+        self._check(self.lib.mpdet_batch_set_cauchy(self.h, int(m), x_, y_, int(dev)), "batch_set_cauchy")
 
     def set_i32(self, m, A):
         dev = _is_dev(A)
         if not dev and not _is_torch(A):
             A = np.ascontiguousarray(A, np.int32)
-        self._check(self.lib.mpdet_batch_set_i32(self.h, int(m), _ptr(A), int(self.Ns[m]), int(dev)),
-                    "batch_set_i32")
+        N = self._size(m)
+        self._check(self.lib.mpdet_batch_set_i32(self.h, int(m), _ptr(A, N * N, 4, False, dev, "batch set_i32: A"), N,
+                                                 int(dev)), "batch_set_i32")
 
     def set_f64(self, m, A):
         dev = _is_dev(A)
         if not dev and not _is_torch(A):
             A = np.ascontiguousarray(A, np.float64)
-        self._check(self.lib.mpdet_batch_set_f64(self.h, int(m), _ptr(A), int(self.Ns[m]), int(dev)),
-                    "batch_set_f64")
+        N = self._size(m)
+        self._check(self.lib.mpdet_batch_set_f64(self.h, int(m), _ptr(A, N * N, 8, True, dev, "batch set_f64: A"), N,
+                                                 int(dev)), "batch_set_f64")
 
     def set_mp(self, m, A):
         """Matrix m from N_m * N_m numbers already at p bits (a triple of host
@@ -589,14 +643,19 @@ class Batch:
         dev = _is_dev(A[0])
         if not dev:
             A = tuple(np.ascontiguousarray(a) for a in _norm_host(A, self.n))
-        self._check(self.lib.mpdet_batch_set_mp(self.h, int(m), _numv(A), int(dev)), "batch_set_mp")
+        N = self._size(m)
+        self._check(self.lib.mpdet_batch_set_mp(self.h, int(m), _numv(A, N * N, self.n, dev, "batch set_mp: A"),
+                                                int(dev)), "batch_set_mp")
 
     def factor(self, out=None, zero_k=None):
         """Host mode: returns (zero_k[count], minors triple of sum(N) numbers);
         matrix m's minors are rows offsets[m]:offsets[m+1].  Device mode:
         ``out`` (and optionally ``zero_k``) are CUDA tensors; asynchronous."""
         if out is not None:
-            self._check(self.lib.mpdet_batch_factor(self.h, _numv(out), _ptr(zero_k), 1), "batch_factor")
+            tot = int(self.offsets[-1])
+            self._check(self.lib.mpdet_batch_factor(self.h, _numv(out, tot, self.n, True, "batch factor: out"),
+                                                    _ptr(zero_k, len(self.Ns), 8, False, True, "batch factor: zero_k"), 1),
+                        "batch_factor")
             return None
         D = empty(int(self.offsets[-1]), self.p)
         zk = np.zeros(len(self.Ns), np.int64)
