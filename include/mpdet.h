@@ -242,8 +242,8 @@ int64_t mpdet_steps_done(mpdet_t h);
  * MPDET_TUNE_TC_MIN_ROWS (value >= 0): an update launch
  * of fewer rows than this takes the IMAD kernel even when the tensor engine is
  * selected (its tiles are 128 rows high).  By default the threshold follows the
- * precision: 64 rows at p = 2048 and at p = 4096 .. 32768, and the IMAD
- * kernel always at p = 512 and 1024, where it measured faster at every size.  MPDET_TUNE_LOOKAHEAD:
+ * precision: 64 rows at p = 1024, 2048 and 4096 .. 32768, and the IMAD kernel
+ * always at p = 512, where it measured faster at every size.  MPDET_TUNE_LOOKAHEAD:
  * 1 (default) overlaps the pivot and multipliers of step k+1 with the update
  * of step k: a second stream owned by the handle updates column k+1 first and
  * runs them while the handle's stream updates the other columns; 0 runs each

@@ -397,12 +397,15 @@ static int next_event(mpdet_t h, cudaEvent_t* ev) {
 
 // Default row threshold of the tensor engines per precision, from GB300
 // measurements of whole eliminations: 64 rows at p = 2048 (twice the IMAD
-// kernel's speed from about 64 rows on) and at p = 4096 .. 32768 (a launch of
-// fewer rows fills less than half of a 128-row block, and the IMAD kernel
-// takes the last steps); at p = 512 and 1024 the IMAD kernel measured faster
-// at every size (lastcol mode, N = 256 .. 2048), so it takes all launches
-// there unless the threshold is set.
-static int64_t tc_default_min_rows(int p) { return (p == 2048 || mpd::tcl_supports(p)) ? 64 : INT64_MAX; }
+// kernel's speed from about 64 rows on), at p = 1024 (with two tensor-memory
+// buffers: 0.62 of the IMAD kernel's time at N = 2048, 0.92 at N = 512, 1.05
+// at N = 1024, lastcol mode) and at p = 4096 .. 32768 (a launch of fewer rows
+// fills less than half of a 128-row block, and the IMAD kernel takes the last
+// steps); at p = 512 the IMAD kernel measured faster at every size (4.7 times
+// at N = 2048), so it takes all launches there unless the threshold is set.
+static int64_t tc_default_min_rows(int p) {
+  return (p == 1024 || p == 2048 || mpd::tcl_supports(p)) ? 64 : INT64_MAX;
+}
 
 // Large-precision tensor engine (p = 4096 .. 32768) for an update launch of
 // `rows` rows?  It reads and writes the array with plain loads and stores (its

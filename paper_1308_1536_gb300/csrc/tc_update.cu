@@ -699,7 +699,12 @@ struct Cfg {
   static constexpr int KD = KD_;
   static constexpr int NL = KD / 4;                 // limbs
   static constexpr int TILES = 2 * KD / 128;        // 128-column tensor-memory tiles (2 KD positions)
-  static constexpr int TCOLS = TILES * 128;         // allocated columns (a power of two >= 32)
+  // Tensor-memory buffers: two where a column's tiles fill at most half of
+  // the 512 columns (p = 512, 1024), so that the MMAs of column c + 1 run
+  // while the epilogue drains column c; column c uses buffer c % TB, whose
+  // tiles and full/empty barriers are slots (c % TB) TILES + t.
+  static constexpr int TB = TILES <= 2 ? 2 : 1;
+  static constexpr int TCOLS = TB * TILES * 128;    // allocated columns (a power of two >= 32)
   static constexpr int NCORE = 16 * TILES + KD / 8 - 1;  // Hankel cores
   static constexpr int HBYTES = (NCORE * 128 + 1023) / 1024 * 1024;
   static constexpr int TILE = RowT<NL>::TILE;       // bytes per 32-row tile (swizzled rows)
@@ -733,6 +738,7 @@ struct Cfg {
   static constexpr int OFF_BAR = OFF_EB + (KD + 8) * 2;     // barriers
   static constexpr int SMEM = OFF_BAR + 256;
   static_assert(NL % 16 == 0 && NL <= 64, "tensor engine covers p = 512, 1024, 2048");
+  static_assert(TB * TILES <= 4 && TCOLS <= 512, "four full/empty barrier slots, 512 tensor-memory columns");
   static_assert(OFF_X % 1024 == 0 && OFF_T % 1024 == 0 && OFF_BX % 16 == 0 && OFF_BAR % 8 == 0, "alignment");
   static_assert(SMEM <= 227 * 1024, "shared memory");
 };
@@ -865,6 +871,7 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
       if (!aok) *eflag = 1;
       for (int c = 0; c < nc && aok; ++c) {
         const int hb = c & 1;
+        const int tu = (c % C::TB) * TILES;  // this column's tile slots
         const uint64_t hd = hd0 + (uint64_t)(hb * (C::HBYTES >> 4));
         const uint64_t xd = xd0 + (uint64_t)(hb * (C::XBYTES >> 4));
         if (!wait_bar(b_hready + 8 * hb, (c >> 1) & 1) || *eflag) {
@@ -876,9 +883,10 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
         for (int t = 0; t < TILES; ++t) {
           if (t > 0 && C::merge(t - 1)) continue;  // issued with tile t - 1
           const bool two = C::merge(t);
-          if (okm && c >= 1) {
-            okm = wait_bar(b_empty + 8 * t, (c - 1) & 1);
-            if (two) okm = okm && wait_bar(b_empty + 8 * (t + 1), (c - 1) & 1);
+          if (okm && c >= C::TB) {  // the epilogue has drained the buffer's previous column
+            const uint32_t par = (uint32_t)(c / C::TB - 1) & 1u;
+            okm = wait_bar(b_empty + 8 * (tu + t), par);
+            if (two) okm = okm && wait_bar(b_empty + 8 * (tu + t + 1), par);
           }
           if (!okm) continue;
           asm volatile("tcgen05.fence::after_thread_sync;");
@@ -886,7 +894,7 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
           for (int ks = C::ks_lo(t); ks < C::ks_hi(t); ++ks)
             asm volatile(
                 "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
-                    tmem + (uint32_t)(t * NT)),
+                    tmem + (uint32_t)((tu + t) * NT)),
                 "l"(ad0 + (uint64_t)(ks * 16)), "l"(hd + (uint64_t)((16 * t + 2 * ks) * 8)), "r"(two ? idesc2 : idesc),
                 "r"(ks > C::ks_lo(t) ? 1u : 0u));
           // 2^p * b: the extra K step for the tiles at or above position KD
@@ -895,11 +903,12 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
             if (u >= C::XT0)
               asm volatile(
                   "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
-                      tmem + (uint32_t)(u * NT)),
+                      tmem + (uint32_t)((tu + u) * NT)),
                   "l"(adx), "l"(xd + (uint64_t)((u - C::XT0) * 256)), "r"(idesc), "r"(1u));
-          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(b_full + 8 * t));
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(b_full + 8 * (tu + t)));
           if (two)
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(b_full + 8 * (t + 1)));
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                b_full + 8 * (tu + t + 1)));
         }
         if (!okm) *eflag = 1;
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(b_hfree + 8 * hb));
@@ -1062,6 +1071,9 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
     }
     for (int c = 0; c < nc; ++c) {
       const int tb = c & 1;
+      const int tu = (c % C::TB) * TILES;                          // this column's tile slots
+      const uint32_t tc = tl + (uint32_t)(tu * NT);                // and its tensor memory
+      const uint32_t fpar = (uint32_t)(c / C::TB) & 1u;            // parity of its full barriers
       const int64_t be = be_n;
       const int8_t bs = bs_n;
       if (c + 1 < nc) {
@@ -1075,11 +1087,11 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
       bool okc = true;
       uint32_t va[32], vb[32];
       // tiles complete in issue order: tile T0 done means the ones below are too
-      if (!wait_bar(b_full + 8 * T0, c & 1)) okc = false;
+      if (!wait_bar(b_full + 8 * (tu + T0), fpar)) okc = false;
       okc = __all_sync(0xffffffffu, okc) && !*eflag;
       okc = __all_sync(0xffffffffu, okc);
       asm volatile("tcgen05.fence::after_thread_sync;");
-      if (okc) tmem_ld32_async(tl + 32 * K0, va);
+      if (okc) tmem_ld32_async(tc + 32 * K0, va);
       // biased: the sums already carry kMagic (tiles from XT0 up)
       auto limbs8 = [&](const uint32_t* v, const int64_t* kv, uint32_t(&lim)[8], int64_t& ac, const bool biased) {
 #pragma unroll
@@ -1098,8 +1110,8 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
       auto release_low = [&]() {  // tiles below T0, and T0 when K0 is its last chunk
         asm volatile("tcgen05.fence::before_thread_sync;");
 #pragma unroll
-        for (int t = 0; t < T0; ++t) arrive(b_empty + 8 * t);
-        if ((K0 & 3) == 3) arrive(b_empty + 8 * T0);
+        for (int t = 0; t < T0; ++t) arrive(b_empty + 8 * (tu + t));
+        if ((K0 & 3) == 3) arrive(b_empty + 8 * (tu + T0));
       };
       auto chunk = [&](const int k, uint32_t(&cur)[32], uint32_t(&nxt)[32]) {
         const bool upper = 8 * k >= NL;
@@ -1112,16 +1124,16 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
         if (okc) tmem_wait(cur);
         if (okc && (k & 3) == 3 && k != K0) {  // the tile's last chunk is in registers: release it
           asm volatile("tcgen05.fence::before_thread_sync;");
-          arrive(b_empty + 8 * (k >> 2));
+          arrive(b_empty + 8 * (tu + (k >> 2)));
         }
         if (k + 1 < NCH && okc) {
           if (((k + 1) & 3) == 0) {
-            bool okt = wait_bar(b_full + 8 * ((k + 1) >> 2), c & 1);
+            bool okt = wait_bar(b_full + 8 * (tu + ((k + 1) >> 2)), fpar);
             okt = __all_sync(0xffffffffu, okt) && !*eflag;
             okc = __all_sync(0xffffffffu, okt);
             asm volatile("tcgen05.fence::after_thread_sync;");
           }
-          if (okc) tmem_ld32_async(tl + (uint32_t)(32 * (k + 1)), nxt);
+          if (okc) tmem_ld32_async(tc + (uint32_t)(32 * (k + 1)), nxt);
         }
         if (!okc) return;
         uint32_t lim[8];
@@ -1154,7 +1166,7 @@ __global__ void __launch_bounds__(pipe::NTH, 1) k_update_tcp(MpArr X, UpdArgs a,
 #pragma unroll
             for (int part = 0; part < 4; ++part) {
               uint32_t w8[8];
-              tmem_ld8(tl + (uint32_t)(32 * kk + 8 * part), w8);
+              tmem_ld8(tc + (uint32_t)(32 * kk + 8 * part), w8);
 #pragma unroll
               for (int e = 0; e < 8; ++e) w[8 * part + e] = w8[e];
             }

@@ -500,3 +500,104 @@ def test_constants():
     assert -4161536 + K_MAGIC >= 2 ** 23 and 4194559 + K_MAGIC < 2 ** 24
     for v in range(-128, 257):  # every digit value is exact in bf16
         bf16_exact(v)
+
+
+def simulate_tmem_handoff(KD, TB, nc, seed):
+    """The MMA issuer and the epilogue of one block over nc columns with
+    mbarrier parity waits, in a random interleaving: column c writes buffer
+    c % TB (tile slots (c % TB) TILES + t); the issuer waits, from column TB
+    on, for the empty barriers of its slots with parity (c / TB - 1) & 1 and
+    commits a full barrier per tile group; the epilogue waits for the full
+    barrier of tile T0 and then of each later tile with parity (c / TB) & 1,
+    reads chunks K0 .. NCH - 1 (and, on the exact path, the chunks below K0),
+    and releases each tile after its last chunk (the tiles up to T0 once the
+    K0 chunk is done).  Checks that every read sees its own column's sums,
+    that no tile is written while the previous column in it is unread, and
+    that no barrier is ever two phases ahead of its waiter (a parity wait
+    could not tell)."""
+    g = Geo(KD)
+    rnd = random.Random(seed)
+    TILES, K0, NCH = g.TILES, g.K0, g.NCH
+    T0 = K0 >> 2
+    full = [0] * 4  # completions per slot
+    empty = [0] * 4
+    owner = [None] * 4  # column whose sums a slot holds
+    released = [set() for _ in range(4)]  # columns whose sums a slot no longer needs
+
+    def wait(bar, slot, j):
+        """The j-th completion (parity j & 1) of a barrier: a wait point."""
+        while True:
+            done = bar[slot]
+            assert done <= j + 1, "barrier two phases ahead of its waiter"
+            if done == j + 1:
+                return
+            yield
+
+    def issuer():
+        for c in range(nc):
+            tu = (c % TB) * TILES
+            for t, cnt in g.groups():
+                if c >= TB:
+                    for q in range(cnt):
+                        yield from wait(empty, tu + t + q, c // TB - 1)
+                for q in range(cnt):
+                    slot = tu + t + q
+                    assert owner[slot] is None or owner[slot] in released[slot], "tile overwritten while unread"
+                    owner[slot] = c
+                yield
+                for q in range(cnt):
+                    full[tu + t + q] += 1
+
+    def epilogue(exact_cols):
+        for c in range(nc):
+            tu = (c % TB) * TILES
+            yield from wait(full, tu + T0, c // TB)
+            for t in range(T0 + 1):
+                assert owner[tu + t] == c  # committed in issue order: tiles up to T0 hold column c
+            for k in range(K0, NCH):
+                if k > K0 and (k & 3) == 0:
+                    yield from wait(full, tu + (k >> 2), c // TB)
+                assert owner[tu + (k >> 2)] == c
+                if k == K0 and c in exact_cols:
+                    for kk in range(K0):
+                        assert owner[tu + (kk >> 2)] == c
+                yield
+                if k == K0:
+                    for t in range(T0):
+                        released[tu + t].add(c)
+                        empty[tu + t] += 1
+                    if (K0 & 3) == 3:
+                        released[tu + T0].add(c)
+                        empty[tu + T0] += 1
+                elif (k & 3) == 3:
+                    released[tu + (k >> 2)].add(c)
+                    empty[tu + (k >> 2)] += 1
+
+    agents = [issuer(), epilogue({c for c in range(nc) if rnd.random() < 0.3})]
+    alive = [True, True]
+    for _ in range(100000):  # a wait that never ends shows up as running out of steps
+        if not any(alive):
+            break
+        i = rnd.choice([a for a in range(2) if alive[a]])
+        try:
+            next(agents[i])
+        except StopIteration:
+            alive[i] = False
+    assert not any(alive), "the roles wait for each other"
+    for s in range(TB * TILES):
+        assert full[s] == empty[s] == len(range(s // TILES, nc, TB))  # every use completed and released
+
+
+@pytest.mark.parametrize("KD", KDS)
+def test_tensor_memory_buffers_and_barrier_parities(KD):
+    """The kernel's buffering: two tensor-memory buffers at p = 512 and 1024
+    (a column's tiles fill at most half of the 512 columns), one at p = 2048;
+    the slot and parity arithmetic of both roles under random interleavings,
+    and with one buffer forced at every precision."""
+    g = Geo(KD)
+    TB = 2 if g.TILES <= 2 else 1
+    assert TB * g.TILES <= 4 and TB * g.TILES * 128 <= 512
+    assert {64: 2, 128: 2, 256: 1}[KD] == TB
+    for seed in range(40):
+        simulate_tmem_handoff(KD, TB, 7, seed)
+        simulate_tmem_handoff(KD, 1, 5, 100 + seed)
