@@ -808,6 +808,47 @@ def factor_window(N: int, p: int, k1: int) -> int:
     return 0 if rc[0] == 0 else 1
 
 
+def engine_table(p: int, Ns, reps: int = 2, thresholds=(64, 256, 512)) -> int:
+    """Tuning aid: whole eliminations of the seeded Cauchy matrix (lastcol
+    mode, look-ahead on) at precision p for each N, on the IMAD engine and on
+    the tensor engine with update launches of at least each row threshold;
+    best of ``reps`` wall times around the factorisation (which synchronises),
+    and whether both engines give the same bits.  One JSON line per N."""
+    import torch
+
+    import paper_1308_1536_gb300 as m
+
+    m.load()
+
+    def run(N, engine, thr):
+        x, y = W.cauchy_xy(N, 1310)
+        h = m.Mpdet(N, p, lastcol=True)
+        h.tune(engine=engine)
+        if thr is not None:
+            h.tune(tc_min_rows=thr)
+        best, D = float("inf"), None
+        for _ in range(reps):
+            h.set_cauchy(x, y)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, _, D = h.factor()
+            best = min(best, time.perf_counter() - t0)
+        h.close()
+        return best * 1e3, D
+
+    for N in Ns:
+        ref_ms, Dref = run(N, 0, None)
+        rec = {"engine_table": {"p": p, "N": N}, "imad_ms": round(ref_ms, 2)}
+        for thr in thresholds:
+            if thr >= N:
+                continue
+            ms, D = run(N, 1, thr)
+            rec[f"tensor_min_rows_{thr}_ms"] = round(ms, 2)
+            rec[f"tensor_min_rows_{thr}_same_bits"] = all(np.array_equal(a, b) for a, b in zip(D, Dref))
+        print(json.dumps(rec), flush=True)
+    return 0
+
+
 def check_large(path: str, lead: int = 256):
     """Host checks of the leading minors saved by --large-full (no GPU):
     D_1..D_lead against the digests the CPU oracle wrote for the leading
@@ -1135,6 +1176,8 @@ def main():
     ap.add_argument("--engine", type=int, default=-1, help="tuning aid: 0 IMAD, 1 tensor pipelined, 2 tensor serial")
     ap.add_argument("--factor-window", type=int, nargs=3, metavar=("N", "P", "K1"),
                     help="profiling aid: steps [0, K1) of the seeded N x N Cauchy matrix at p bits, look-ahead off")
+    ap.add_argument("--engine-table", type=int, nargs="+", metavar=("P", "N"),
+                    help="tuning aid: whole eliminations at precision P for each N, IMAD against tensor engine")
     ap.add_argument("--check-large", default="", metavar="NPZ",
                     help="host checks (no GPU) of the leading minors a --large-full run saved")
     ap.add_argument("--large-full", action="store_true",
@@ -1153,6 +1196,10 @@ def main():
         return check_large(args.check_large)
     if args.factor_window:
         return factor_window(*args.factor_window)
+    if args.engine_table:
+        if len(args.engine_table) < 2:
+            ap.error("--engine-table P N [N ...]")
+        return engine_table(args.engine_table[0], args.engine_table[1:])
     if args.large_full:
         return run_large_full(args)
     return run_gpu(args)
