@@ -144,17 +144,17 @@ def measured_peaks():
         return {}
 
 
-def recorded_traffic(products_per_launch: float):
+def recorded_traffic(products_per_launch: float, any_sources: bool = False):
     """DRAM bytes per Schur-update launch: the bytes per product of one ncu
     capture (profiles/k_update_traffic.json, dram__bytes_read.sum +
     dram__bytes_write.sum of a launch of known size) times this run's average
     products per timed launch.  None unless the capture was taken on the
-    current kernel sources."""
+    current kernel sources (any_sources: whatever sources it was taken on)."""
     try:
         t = json.load(open(os.path.join(ROOT, "profiles", "k_update_traffic.json")))
     except Exception:
         return None
-    if t.get("source_sha") != kernel_source_sha():
+    if t.get("source_sha") != kernel_source_sha() and not any_sources:
         return None
     return t["bytes_per_product"] * products_per_launch
 
@@ -1081,7 +1081,11 @@ def run_gpu(args):
         achieved = upd_macs / (upd_ms / 1e3)
         tensor = (p == 2048 and args.engine != 0)  # the default engine per precision
         # the recorded bytes per product belong to the tensor-core kernel at p = 2048
-        tr = recorded_traffic(upd_macs / (n * n) / max(upd_launches, 1)) if tensor and p == 2048 else None
+        per_launch = upd_macs / (n * n) / max(upd_launches, 1)
+        tr = recorded_traffic(per_launch) if tensor and p == 2048 else None
+        # the last capture's figure when the sources have changed since (the
+        # "traffic" key stays null then)
+        tr_old = recorded_traffic(per_launch, any_sources=True) if tensor and p == 2048 and tr is None else None
         if tensor:
             # exact digit convolution on the tensor cores: one limb-MAC is 16 products of 8-bit digits,
             # 32 flops; peak = measured bf16 dense throughput (sustained: the kernel runs inside a long step)
@@ -1097,6 +1101,12 @@ def run_gpu(args):
             roof = {"bound": "alu", "kernel": "k_update (Schur update, IMAD)", "achieved": achieved / 1e12,
                     "peak": peak / 1e12, "unit": "Tlimb-MAC/s", "frac": achieved / peak, "traffic": tr,
                     "peak_basis": f"{nsm} SMs x 32 limb-MAC/clk x {fmax:.0f} MHz"}
+        if tr_old is not None:
+            roof["traffic_last_capture"] = {
+                "bytes": tr_old, "source": "profiles/k_update_traffic.json",
+                "recorded_source_sha": json.load(open(os.path.join(ROOT, "profiles", "k_update_traffic.json")))
+                .get("source_sha"), "current_source_sha": kernel_source_sha(),
+                "note": "captured on earlier sources of the kernel files, not recaptured since"}
         roof["update_share"] = upd_ms / serial_ms
         roof["launches"] = int(upd_launches)
         out = {

@@ -113,3 +113,23 @@ def test_guarded_optional_parts():
     assert bench.guarded(lambda a, b: a + b, 2, 3) == 5
     r = bench.guarded(lambda: {}["missing"])
     assert set(r) == {"error"} and r["error"].startswith("KeyError")
+
+
+def test_recorded_traffic_is_keyed_by_the_kernel_sources():
+    """The bench line's DRAM traffic comes from the ncu record only while the
+    record's source hash is the current one; the last capture's figure is
+    still available, marked as such, when the sources have changed."""
+    import json
+    import os
+
+    import bench
+
+    rec = json.load(open(os.path.join(bench.ROOT, "profiles", "k_update_traffic.json")))
+    same = rec["source_sha"] == bench.kernel_source_sha()
+    assert bench.recorded_traffic(1000.0, any_sources=True) == rec["bytes_per_product"] * 1000.0
+    assert bench.recorded_traffic(1000.0) == (rec["bytes_per_product"] * 1000.0 if same else None)
+    # the record the bench line carries beside a null traffic (the same expressions)
+    last = {"bytes": bench.recorded_traffic(1000.0, any_sources=True), "source": "profiles/k_update_traffic.json",
+            "recorded_source_sha": json.load(open(os.path.join(bench.ROOT, "profiles", "k_update_traffic.json")))
+            .get("source_sha"), "current_source_sha": bench.kernel_source_sha()}
+    assert json.loads(json.dumps(last)) == last
