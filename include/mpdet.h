@@ -123,18 +123,25 @@ int mpdet_create(int64_t N, int32_t p_bits, uint32_t flags, void* cuda_stream, m
 
 /* Set A from an N x N row-major double matrix with leading dimension ld >= N
  * (exact lift: every finite double is representable at p >= 64).  Resets the
- * factorisation.  Step a1 of the method (input lift). */
+ * factorisation.  A is the input of Algorithm 1.  Host input is staged
+ * through a device buffer the handle keeps.  Errors: MPDET_EINVAL (NULL
+ * handle or A, ld < N), MPDET_ENOMEM (staging buffer), MPDET_ECUDA. */
 int mpdet_set_f64(mpdet_t h, const double* A, int64_t ld, int device_ptr);
 
-/* Same for int32 entries (exact). */
+/* Same for int32 entries (exact).  Errors as for mpdet_set_f64. */
 int mpdet_set_i32(mpdet_t h, const int32_t* A, int64_t ld, int device_ptr);
 
-/* Set A from N*N numbers already at p bits (copied; must be canonical). */
+/* Set A (the input of Algorithm 1) from N*N numbers already at p bits,
+ * row-major (copied; must be canonical: normalised mantissa or the zero
+ * encoding).  Resets the factorisation.  Errors: MPDET_EINVAL (NULL handle or
+ * pointer), MPDET_ECUDA. */
 int mpdet_set_mp(mpdet_t h, mpdet_numv A, int device_ptr);
 
 /* Set the Cauchy matrix A_ij = RN(1 / RN(x_i + y_j)) generated on the device
  * (x, y: N doubles each).  The seeded stand-in for the paper's interpolating
- * matrices of eq. (det) and eq. (betaNew), which are nearly singular. */
+ * matrices of eq. (det) and eq. (betaNew), which are nearly singular.
+ * Errors: MPDET_EINVAL (NULL handle or pointer), MPDET_ENOMEM (staging of host
+ * x, y), MPDET_ECUDA. */
 int mpdet_set_cauchy(mpdet_t h, const double* x, const double* y, int device_ptr);
 
 /* Run elimination steps k0+1 .. k1 (1-based; 0 <= k0 <= k1 <= N), asynchronous
@@ -151,12 +158,19 @@ int mpdet_factor_range(mpdet_t h, int64_t k0, int64_t k1);
  * Returns MPDET_EZEROPIVOT when that pivot is at k < N (D_1..D_{k-1} are
  * valid, D_k..D_N are +0); a zero pivot at k = N only makes det = +0 and
  * returns MPDET_OK.  With device_ptr = 1 the outputs are device buffers, the
- * call does not synchronise and zero pivots are read with mpdet_status. */
+ * call does not synchronise and zero pivots are read with mpdet_status
+ * (*zero_pivot_k is then -1).  The leading minors are the running products of
+ * the pivots (Algorithm 1 step 2.1; Sec. 3: elimination without pivoting gives
+ * every top-left minor at no extra cost).  Errors: MPDET_EINVAL (NULL handle),
+ * MPDET_ESTATE (no matrix set), MPDET_EZEROPIVOT, MPDET_ETIMEOUT (a bounded
+ * wait of the tensor engine gave up), MPDET_ECUDA. */
 int mpdet_factor(mpdet_t h, mpdet_numv det, mpdet_numv minors, int64_t* zero_pivot_k, int device_ptr);
 
 /* Synchronise the handle's stream and read the status of the last
- * factorisation: MPDET_OK, MPDET_EZEROPIVOT (zero_pivot_k as above) or
- * MPDET_EZERODIV (normalised minors with l_N1 = 0, device mode). */
+ * factorisation: MPDET_OK, MPDET_EZEROPIVOT (zero_pivot_k as above),
+ * MPDET_EZERODIV (normalised minors with l_N1 = 0, device mode) or
+ * MPDET_ETIMEOUT; MPDET_EINVAL for a NULL handle, MPDET_ECUDA when the
+ * stream's work failed. */
 int mpdet_status(mpdet_t h, int64_t* zero_pivot_k);
 
 /* Signed minors of the last column (eq. minorsdef):
@@ -207,20 +221,24 @@ int mpdet_get_entries(mpdet_t h, int64_t count, const int64_t* idx, mpdet_numv o
 int mpdet_radii(mpdet_t h, int which, uint32_t* rad_mant, int64_t* rad_exp, int device_ptr);
 
 /* Copy out the leading minors computed so far (D_1..D_N; entries of steps not
- * yet run are +0). */
+ * yet run are +0).  Errors: MPDET_EINVAL (NULL handle), MPDET_ECUDA. */
 int mpdet_get_minors(mpdet_t h, mpdet_numv out, int device_ptr);
 
 /* Copy out the in-place N x N array (U in the upper triangle including the
  * diagonal; in MPDET_LASTCOL mode L's strict lower part below it; otherwise
- * the strict lower part is unspecified), e.g. to checkpoint a window. */
+ * the strict lower part is unspecified), e.g. to checkpoint a window.
+ * Errors: MPDET_EINVAL (NULL handle), MPDET_ECUDA. */
 int mpdet_get_mp(mpdet_t h, mpdet_numv out, int device_ptr);
 
 /* Restore a checkpoint: the in-place array after k_done steps and the
  * leading minors D_1..D_{k_done} (N numbers, later entries ignored).  The
- * next mpdet_factor_range must start at k0 = k_done. */
+ * next mpdet_factor_range must start at k0 = k_done; the rest of the
+ * elimination is the same rounded sequence as an uninterrupted one.
+ * Errors: MPDET_EINVAL (NULL handle, k_done outside 0..N), MPDET_ESTATE (ball
+ * mode: a checkpoint carries no radii), MPDET_ECUDA. */
 int mpdet_resume(mpdet_t h, mpdet_numv A, mpdet_numv minors, int64_t k_done, int device_ptr);
 
-/* Steps completed so far (0..N). */
+/* Steps completed so far (0..N); -1 for a NULL handle. */
 int64_t mpdet_steps_done(mpdet_t h);
 
 /* Tuning knobs (results are identical for every setting; only speed
@@ -278,7 +296,8 @@ int mpdet_tune(mpdet_t h, int param, int value);
  * returns the summed device time of those launches (ms), their number, their
  * algorithmic work in limb multiply-accumulates (products * n^2) and the
  * total number of kernels this handle has enqueued since creation.  Any
- * output pointer may be NULL. */
+ * output pointer may be NULL.  Errors: MPDET_EINVAL (NULL handle),
+ * MPDET_ECUDA. */
 int mpdet_profile(mpdet_t h, int enable);
 int mpdet_profile_read(mpdet_t h, double* update_ms, int64_t* update_launches, double* update_limb_macs,
                        int64_t* launches);
@@ -450,7 +469,8 @@ int mpdet_mulbench(int method, int64_t count, int32_t p_bits, mpdet_numv a, mpde
  * MPDET_ECUDA. */
 int mpdet_selftest_timeout(int32_t limit, int arrive, void* cuda_stream);
 
-/* Release the handle and its device memory (NULL is accepted). */
+/* Release the handle and its device or host memory (NULL is accepted);
+ * returns MPDET_OK. */
 int mpdet_free(mpdet_t h);
 
 /* Message for the last failing call on h (static string when h == NULL). */
